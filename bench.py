@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the lattice-kinetic Kohn-Sham solver on GB300.
+
+One step = one complete self-consistent solve of the workload (orbital start,
+relaxation cycles, Hartree, LDA, orthonormalisation, energies) to
+|dE| < 1e-6 Ha, through the C ABI.  The metric is orbital-site updates per
+second (GLUPS): relaxation steps x orbitals x grid sites / wall time of the
+solves.  Default workload: methane, 128^3 grid at h = 0.2 bohr, five doubly
+occupied orbitals, FP32 populations and collide with FP64 reductions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbks|reference]
+
+--impl reference times the FP64 numpy oracle (the method as the paper states
+it, plain CPU code) on the host cores, one relaxation step of the same
+workload per bench step.
+
+Multi-GPU (torchrun): every rank solves its own replica (independent
+systems, no collective on the data path); value = all ranks' updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "GLUPS (orbital-site updates/s)"
+UNIT = "GLUPS"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_relax.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_ch4_128_fp32.json")
+
+WORKLOADS = {
+    "ch4_128": W.ch4_128,
+    "he_24": W.he_24,
+    "h2o_96": W.water_96,
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lbks", "reference"], default="lbks")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ch4_128")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------- oracle leg
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import lattice, lb, scf
+w = W.{wl}()
+n, h, no = w.n, w.h, w.n_orb
+xyz, Z = w.molecule.xyz, w.molecule.Z
+dt = lattice.time_step(w.theta, w.omega, h)
+psi = lb.orthonormalize(scf.initial_orbitals(n, h, xyz, Z, no), h)
+f = lb.equilibrium(psi, w.theta)
+sigma = np.ones(no)
+V = scf.external_potential(n, h, xyz, Z, h)
+times = []
+t_end = time.perf_counter() + {seconds}
+while len(times) < {min_steps} or (time.perf_counter() < t_end and len(times) < {max_steps}):
+    t0 = time.perf_counter()
+    r = lb.step(f, sigma, V, w.omega, w.theta, dt, h)
+    f, sigma = r["fstar"], r["sigma"]
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "updates_per_step": no * n[0] * n[1] * n[2]}}))
+"""
+
+
+def run_oracle_sample(workload: str, seconds: float, min_steps: int, max_steps: int):
+    code = ORACLE_SAMPLE.format(root=ROOT, wl=WORKLOADS[workload].__name__, seconds=seconds,
+                                min_steps=min_steps, max_steps=max_steps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload: str, seconds: float):
+    s = run_oracle_sample(workload, seconds, 2, 1000)
+    t = sum(s["times"])
+    return {"value": len(s["times"]) * s["updates_per_step"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(s['times'])} relaxation steps (Eq. KSLB, all orbitals) of the {workload} workload from "
+                      f"its Gaussian start, FP64 numpy, one thread, {t:.1f} s"}
+
+
+def main_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]()
+    s = run_oracle_sample(args.workload, 0.0, args.warmup + args.steps, args.warmup + args.steps)
+    times = s["times"][args.warmup:]
+    t = sum(times)
+    value = len(times) * s["updates_per_step"] / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name + " single solve", "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
+                   "step": "one oracle relaxation step of all orbitals"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} timed relaxation steps of {w.name}, FP64 numpy, one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if "Active" in f})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic():
+    """dram bytes per launch of the stream-collide kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+        sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        if rec.get("kernel_src_sha256") == sha:
+            return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def time_stream_collide(torch, lbks, w, prec, stream, launches=20):
+    """Average duration of the fused stream-collide kernel in the solver's own
+    launch configuration, CUDA events on the launching stream."""
+    T = torch.float32 if prec == lbks.FP32 else torch.float64
+    nx, ny, nz = w.n
+    N = nx * ny * nz
+    no = w.n_orb
+    with torch.cuda.stream(stream):
+        fa = torch.rand((no, 19, nz, ny, nx), dtype=T, device="cuda")
+        fb = torch.empty_like(fa)
+        u = torch.rand((max(no - 1, 1), nz, ny, nx), dtype=T, device="cuda") * 0.1
+        psi = torch.empty((no, nz, ny, nx), dtype=T, device="cuda")
+        V = -torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda")
+        sig = torch.full((no,), 1e-3, dtype=torch.float64, device="cuda")
+        S = torch.empty((no, no), dtype=torch.float64, device="cuda")
+        lam = torch.empty_like(S)
+        sig2 = torch.empty_like(sig)
+    dt = w.theta * w.h * w.h * (2 - w.omega) / w.omega
+    bufs = [fa, fb]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches)]
+    for i in range(3 + launches):
+        src, dst = bufs[i % 2], bufs[(i + 1) % 2]
+        if i >= 3:
+            evs[2 * (i - 3)].record(stream)
+        lbks.lbks_relax_step(prec, nx, ny, nz, no, w.h, w.omega, w.theta, dt, src, u if no > 1 else None, V, sig,
+                             dst, psi, S, lam, sig2, stream=stream)
+        if i >= 3:
+            evs[2 * (i - 3) + 1].record(stream)
+    stream.synchronize()
+    ms = [evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(launches)]
+    del fa, fb, u, psi, V
+    return statistics.mean(ms), N * no
+
+
+def main_lbks(args):
+    import torch
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1507_07666_gb300 import build as build_mod
+    if rank == 0:
+        build_mod.build()
+    if dist:
+        dist.barrier()
+    from paper_1507_07666_gb300 import lbks
+
+    w = WORKLOADS[args.workload]()
+    prec = lbks.FP32 if args.precision == "fp32" else lbks.FP64
+    sysm = lbks.System(w.n, w.h, w.n_orb, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
+                       omega=w.omega, mix=w.mix, max_cycles=w.max_cycles)
+    xyz, Z = w.molecule.xyz, w.molecule.Z
+    N = w.sites
+    stream = torch.cuda.Stream()
+
+    def solve():
+        sysm.set_geometry(xyz, Z)
+        return sysm.scf(stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    l0 = lbks.lbks_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    results = [solve() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = lbks.lbks_kernel_launches() - l0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    updates = sum(r["steps"] for r in results) * w.n_orb * N
+    value = world * updates / (elapsed_ms / 1e3) / 1e9
+
+    # end to end: host geometry in, energies + density back to the host
+    e2e_updates, t_e2e = 0, 0.0
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        sysm.set_geometry(xyz, Z)
+        r = sysm.scf(stream)
+        rho = sysm.density()
+        t_e2e += time.perf_counter() - t0
+        e2e_updates += r["steps"] * w.n_orb * N
+    e2e = {"value": world * e2e_updates / t_e2e / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(xyz.nbytes + Z.nbytes),
+           "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
+
+    # dominant kernel alone, same launch configuration
+    ms, units = time_stream_collide(torch, lbks, w, prec, stream)
+    elem = 4 if prec == lbks.FP32 else 8
+    bytes_per_launch = 38 * elem * units
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bytes_per_launch / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(), "kernel": "k_stream_collide",
+                "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms,
+                "peak_source": f"hbm_gbs of {peak_kind}"}
+
+    if rank != 0:
+        return 0
+    last = results[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == lbks.FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name + " single solve", "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
+                   "precision": ("FP32 populations and collide, FP64 overlaps/energies/Poisson"
+                                 if prec == lbks.FP32 else "FP64 throughout"),
+                   "n_inner": w.n_inner, "e_tol": w.e_tol,
+                   "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * elem * units / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "solves_per_s": world * args.steps / (elapsed_ms / 1e3),
+        "solve": {"E_total": last["E_total"], "eigenvalues": [float(x) for x in last["eigenvalues"]],
+                  "cycles": last["cycles"], "steps": last["steps"], "converged": last["converged"],
+                  "poisson_iters": last["poisson_iters"]},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    sysm.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return main_reference(args)
+    return main_lbks(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * lbks.h -- C ABI of the GB300 lattice-kinetic Kohn-Sham solver.
+ *
+ * Method: Mendoza, Herrmann, Succi, "Lattice Boltzmann Model for Electronic
+ * Structure Simulations".  Each occupied Kohn-Sham orbital j carries D3Q19
+ * populations f_jp that relax in imaginary time by Eq. KSLB (Sec. 3):
+ *
+ *   f_jp(r + v_p, t+1) = f_jp - omega (f_jp - xi_p psi_j) - dt chi_p V psi_j
+ *                        - omega xi_p sum_{k<j} Lambda_jk psi_k,
+ *   psi_j = sum_p f_jp,  Lambda_jk = <psi_j|psi_k> / <psi_k|psi_k>,
+ *
+ * inside a self-consistent loop that rebuilds the density, the Hartree
+ * potential (lattice Poisson), the LDA exchange-correlation potential, the
+ * Cholesky orthonormalisation of the orbitals and the total energy.
+ *
+ * Conventions (every entry point):
+ *  - Return value: LBKS_OK (0) or a positive LBKS_E* code; lbks_last_error()
+ *    gives a one-line message for the calling thread.  No C++ exception
+ *    crosses this boundary.
+ *  - Units: atomic units (bohr, Hartree).  Grid site (i, j, k) of an
+ *    nx x ny x nz grid at spacing h sits at ((i-(nx-1)/2) h, (j-(ny-1)/2) h,
+ *    (k-(nz-1)/2) h): the box centre is the origin.
+ *  - Grid arrays are x-fastest: index s = x + nx (y + ny z), N = nx ny nz.
+ *  - Population arrays are f[j][p][z][y][x] (orbital, velocity, grid);
+ *    orbital arrays psi[j][z][y][x]; the W field u[j-1][z][y][x] for
+ *    j = 1 .. n_orb-1 (orbital 0 has none).
+ *  - "dev" pointers are CUDA device pointers of the current device, owned by
+ *    the caller; "host" pointers are host memory owned by the caller.
+ *    Handles own their device memory.  A `stream` argument is a borrowed
+ *    cudaStream_t (NULL = legacy default stream); the library never
+ *    destroys it.  Device-pointer entry points are asynchronous on that
+ *    stream unless stated otherwise.
+ *  - Element type of population / orbital / W-field arrays follows
+ *    `precision`: LBKS_FP64 -> double, LBKS_FP32 -> float.  Potentials,
+ *    densities, overlaps and energies are always double.
+ *
+ * D3Q19 velocity order (a data layout shared with callers):
+ *    p:  0 ( 0, 0, 0)
+ *        1 (+1, 0, 0)   2 (-1, 0, 0)   3 ( 0,+1, 0)   4 ( 0,-1, 0)
+ *        5 ( 0, 0,+1)   6 ( 0, 0,-1)
+ *        7 (+1,+1, 0)   8 (-1,-1, 0)   9 (+1,-1, 0)  10 (-1,+1, 0)
+ *       11 (+1, 0,+1)  12 (-1, 0,-1)  13 (+1, 0,-1)  14 (-1, 0,+1)
+ *       15 ( 0,+1,+1)  16 ( 0,-1,-1)  17 ( 0,+1,-1)  18 ( 0,-1,+1)
+ *    lattice weights w = 1/3 (rest), 1/18 (axis), 1/36 (diagonal), c_s^2 = 1/3.
+ */
+#ifndef LBKS_H
+#define LBKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBKS_MAX_ORB 8 /* orbitals per system handled by this build */
+
+enum lbks_status {
+    LBKS_OK = 0,
+    LBKS_EINVAL = 1,    /* bad argument: sizes <= 0, h <= 0, n_orb out of range, null pointer */
+    LBKS_ENOMEM = 2,    /* device allocation failed or byte budget exceeded */
+    LBKS_ENOTCONV = 3,  /* max_cycles reached (results still filled) or overlap not positive definite */
+    LBKS_ETIMEDOUT = 4, /* a bounded wait expired */
+    LBKS_EBUSY = 5,     /* resource in use */
+    LBKS_ECUDA = 6,     /* a CUDA runtime call failed; message has the CUDA error string */
+    LBKS_ENOTFOUND = 7  /* unknown request id */
+};
+
+enum lbks_precision {
+    LBKS_FP64 = 0, /* populations, collide and orbitals in double: the plain path */
+    LBKS_FP32 = 1  /* populations, collide and orbitals in float; overlaps, energies, Poisson in double */
+};
+
+/* Solver controls.  lbks_params_default() fills the defaults in brackets. */
+typedef struct lbks_params {
+    double omega;        /* BGK relaxation frequency, 0 < omega < 2 [1.0]; Sec. 3, Eq. LBeq */
+    double theta;        /* second moment of the equilibrium xi_p psi [0.5]; sets
+                            dt = theta h^2 (2 - omega) / omega (Sec. 3, D relation) */
+    int n_inner;         /* relaxation steps per self-consistent cycle, >= 2 [50] */
+    double mix;          /* linear potential mixing V <- mix V_out + (1-mix) V [0.5] */
+    double e_tol;        /* stop when |E_c - E_{c-1}| < e_tol Hartree [1e-6] */
+    int max_cycles;      /* [200] */
+    int precision;       /* enum lbks_precision [LBKS_FP64] */
+    double softening;    /* nuclear softening a (bohr); <= 0 means a = h [0] */
+    double poisson_rtol; /* CG relative residual target [1e-11] */
+    int poisson_max_iter;/* [20000] */
+} lbks_params;
+
+void lbks_params_default(lbks_params* p);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to cap).  Returns the full message length. */
+int lbks_last_error(char* buf, size_t cap);
+
+/* Library version string, static storage. */
+const char* lbks_version(void);
+
+/* Number of kernels this library has enqueued in this process (a CUDA-graph
+ * replay counts each of its kernel nodes).  Bookkeeping only. */
+uint64_t lbks_kernel_launches(void);
+
+/* ------------------------------------------------------------------ systems */
+typedef struct lbks_system lbks_system;
+
+/* Allocates all device state of one system on the current device: two
+ * population buffers of n_orb*19*N elements, orbitals, W field, potentials,
+ * CG vectors and reduction scratch.  EINVAL: nx, ny, nz < 2, h <= 0,
+ * n_orb < 1 or > LBKS_MAX_ORB, bad params.  ENOMEM: cudaMalloc failed. */
+int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb,
+                       lbks_system** out);
+int lbks_destroy_system(lbks_system* sys);
+
+/* Bytes of device memory lbks_create_system would allocate. */
+size_t lbks_system_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb);
+
+/* Sets the nuclei (xyz: 3*n_atoms bohr relative to the box centre; Z: charges)
+ * and resets the orbitals to the Gaussian start (orbital j on nucleus
+ * order[j mod n_atoms] by decreasing Z, width 1.2 (1 + 0.35 (j div n_atoms))
+ * bohr, offset 0.25 (sin(1+2.1j), sin(2+3.3j), sin(3+4.7j)) bohr,
+ * Cholesky-orthonormalised; f* = xi psi).  Evaluates the starting density,
+ * potentials and energy.  Synchronous.  EINVAL: atom outside the box,
+ * n_atoms < 1, sum Z != 2 n_orb (closed-shell neutral only). */
+int lbks_set_geometry(lbks_system* sys, int n_atoms, const double* xyz, const double* Z);
+
+typedef struct lbks_result {
+    double E_total;                   /* Hartree */
+    double dE;                        /* |E_c - E_{c-1}| of the last cycle */
+    double eigenvalues[LBKS_MAX_ORB]; /* Ritz values of the occupied subspace, ascending */
+    double n_electrons;               /* h^3 sum rho */
+    int cycles;
+    int steps;                        /* relaxation steps (orbital-site updates = steps*n_orb*N) */
+    int converged;
+    int poisson_iters;                /* CG iterations, all cycles */
+    double wall_s;
+} lbks_result;
+
+/* Runs the self-consistent loop from the current state until |dE| < e_tol
+ * or max_cycles (ENOTCONV, result filled).  Blocking; all GPU work is queued
+ * on `stream`. */
+int lbks_scf(lbks_system* sys, void* stream, lbks_result* out);
+
+/* Runs exactly n cycles (no convergence test); result as lbks_scf. */
+int lbks_scf_cycles(lbks_system* sys, int n, void* stream, lbks_result* out);
+
+typedef struct lbks_energy_terms {
+    double T_s, E_ext, E_H, E_xc, E_nn, E_total;
+    double eigenvalues[LBKS_MAX_ORB];      /* Ritz values, ascending */
+    double orbital_energies[LBKS_MAX_ORB]; /* <psi_j|H|psi_j> per orbital */
+    double n_electrons;
+} lbks_energy_terms;
+
+/* Energy terms of the last evaluation (after lbks_set_geometry or a cycle). */
+int lbks_energy(const lbks_system* sys, lbks_energy_terms* out);
+
+/* Host copies (synchronous) of the last evaluation's density rho (N doubles),
+ * orthonormal orbitals (n_orb*N doubles) and potentials (N doubles each).
+ * EINVAL if cap (elements) is too small. */
+int lbks_get_density(const lbks_system* sys, double* host, size_t cap);
+int lbks_get_orbitals(const lbks_system* sys, double* host, size_t cap);
+int lbks_get_potential(const lbks_system* sys, int which /*0 V_in,1 V_out,2 V_H,3 V_ext*/,
+                       double* host, size_t cap);
+
+/* ------------------------------------------------- step-level device kernels
+ * These expose the kernels the solver is built from, on caller-owned device
+ * buffers, so that each step can be checked on its own.                    */
+
+/* One relaxation step (Eq. KSLB with the normalisation of Sec. 3) for
+ * n_orb orbitals on an nx x ny x nz grid:
+ *   f_jp(r)   = f_in_jp(r - v_p) + xi_p u_(j-1)(r - v_p)  (zero outside)
+ *   f_jp     *= sigma_in[j];  psi_j = sum_p f_jp
+ *   f_out_jp  = f_jp - omega (f_jp - xi_p psi_j) - dt chi_p V psi_j
+ *   S         = h^3 psi psi^T;  lambda_jk = S_jk/S_kk (k<j);  sigma_out_j = 1/sqrt(S_jj)
+ * f_out holds the collision WITHOUT the orthogonalisation source; that
+ * source, -omega xi_p sum_k lambda_jk psi_k, is carried by the W field that
+ * lbks_w_field writes from psi_out and lambda_out and the next step pulls
+ * in.  f_in + xi u is the paper's post-collision state.
+ * u_in: (n_orb-1)*N elements or NULL for u = 0.  V: N doubles.
+ * sigma_in / sigma_out: n_orb doubles (may alias).  S_out, lambda_out:
+ * n_orb^2 doubles (row-major, lambda strictly lower).  psi_out: n_orb*N.
+ * f_in and f_out must not alias.  Scratch is library-managed device memory
+ * (allocated once per device and size, reused).  Asynchronous on stream. */
+int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h,
+                    double omega, double theta, double dt,
+                    const void* f_in_dev, const void* u_in_dev, const double* V_dev,
+                    const double* sigma_in_dev, void* f_out_dev, void* psi_out_dev,
+                    double* S_out_dev, double* lambda_out_dev, double* sigma_out_dev,
+                    void* stream);
+
+/* W field of the orthogonalisation source (Sec. 3, W_jp):
+ * u_(j-1)(r) = -omega sum_{k<j} lambda_jk psi_k(r), j = 1..n_orb-1. */
+int lbks_w_field(int precision, size_t n_sites, int n_orb, double omega,
+                 const void* psi_dev, const double* lambda_dev, void* u_out_dev, void* stream);
+
+/* Cholesky S = L L^T of an n x n SPD matrix on the device (FP64, one CTA),
+ * writes L^{-1} (lower, row-major).  Sets *status_dev = 0, or j+1 if the
+ * j-th pivot is not positive. */
+int lbks_cholesky_inverse(int n, const double* S_dev, double* Linv_dev, int* status_dev, void* stream);
+
+/* In-place orthonormalisation at every site: f_jp <- sum_k Linv_jk f_kp and
+ * psi_j <- sum_k Linv_jk psi_k (either pointer may be NULL). */
+int lbks_orth_apply(int precision, size_t n_sites, int n_orb, const double* Linv_dev,
+                    void* f_dev, void* psi_dev, void* stream);
+
+/* Hartree potential: solves (6 V - sum of face neighbours) = 4 pi h^2 rho
+ * with ghost values from the monopole+dipole+quadrupole of rho about the box
+ * centre (Sec. 2, Hartree integral).  v_dev holds the warm start on entry
+ * and the solution on exit.  Conjugate gradients in FP64 until relative
+ * residual <= rtol or max_iter.  Synchronous (reads back the iteration count
+ * and residual).  ENOTCONV if max_iter is reached. */
+int lbks_hartree(int nx, int ny, int nz, double h, const double* rho_dev, double* v_dev,
+                 double rtol, int max_iter, int* iters_out, double* relres_out, void* stream);
+
+/* Spin-unpolarised LDA per site: Slater exchange + Perdew-Zunger-81
+ * correlation; eps and v zero where rho < 1e-14 (Sec. 2, V_xc). */
+int lbks_lda(size_t n_sites, const double* rho_dev, double* eps_dev, double* v_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBKS_H */

@@ -1,0 +1,380 @@
+// Grid fields of the self-consistent loop, all in FP64: external potential,
+// Cholesky of the overlap, LDA exchange-correlation, potential assembly with
+// mixing and energy integrals, and the lattice Poisson solve for the Hartree
+// potential (conjugate gradients with device-resident scalars).
+#include "lbks_internal.cuh"
+#include "lbks_reduce.cuh"
+
+#include <algorithm>
+
+namespace lbks {
+
+namespace {
+
+__device__ __forceinline__ void coords(const Grid& g, double h, uint32_t s, int& x, int& y, int& z, double& rx,
+                                       double& ry, double& rz) {
+    const uint32_t q = g.divx.div(s);
+    x = (int)(s - q * (uint32_t)g.nx);
+    const uint32_t zz = g.divy.div(q);
+    y = (int)(q - zz * (uint32_t)g.ny);
+    z = (int)zz;
+    rx = (x - 0.5 * (g.nx - 1)) * h;
+    ry = (y - 0.5 * (g.ny - 1)) * h;
+    rz = (z - 0.5 * (g.nz - 1)) * h;
+}
+
+int grid_for(size_t n, int cap_blocks) {
+    const size_t need = (n + kThreads - 1) / kThreads;
+    return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap_blocks));
+}
+
+int red_cap(const Scratch& sc, int vals) { return sc.max_vals >= vals ? std::min(sc.max_blocks, num_sms() * 4) : 0; }
+
+// ------------------------------------------------------------ external potential
+// V_ext(r) = -sum_I Z_I / sqrt(|r - R_I|^2 + a^2)   (softened nuclei)
+__global__ void __launch_bounds__(kThreads) k_vext(Grid g, double h, int n_atoms, const double* __restrict__ atoms,
+                                                   double a2, double* __restrict__ v) {
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int x, y, z;
+        double rx, ry, rz;
+        coords(g, h, s, x, y, z, rx, ry, rz);
+        double acc = 0.0;
+        for (int I = 0; I < n_atoms; ++I) {
+            const double dx = rx - atoms[4 * I], dy = ry - atoms[4 * I + 1], dz = rz - atoms[4 * I + 2];
+            acc -= atoms[4 * I + 3] / sqrt(dx * dx + dy * dy + dz * dz + a2);
+        }
+        v[s] = acc;
+    }
+}
+
+// --------------------------------------------------------------------- Cholesky
+// S = L L^T (one CTA), then L^{-1} by forward substitution, one column per thread.
+__global__ void k_cholesky(int n, const double* __restrict__ S, double* __restrict__ Linv, int* status) {
+    __shared__ double L[kMaxOrb * kMaxOrb];
+    __shared__ int bad;
+    if (threadIdx.x == 0) {
+        bad = 0;
+        for (int i = 0; i < n * n; ++i) L[i] = 0.0;
+        for (int j = 0; j < n && !bad; ++j) {
+            double d = S[j * n + j];
+            for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+            if (!(d > 0.0)) {
+                bad = j + 1;
+                break;
+            }
+            const double ljj = sqrt(d);
+            L[j * n + j] = ljj;
+            for (int i = j + 1; i < n; ++i) {
+                double t = S[i * n + j];
+                for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+                L[i * n + j] = t / ljj;
+            }
+        }
+        *status = bad;
+    }
+    __syncthreads();
+    const int k = threadIdx.x;
+    if (k < n) {
+        for (int i = 0; i < n; ++i) {
+            double t;
+            if (bad) {
+                t = (i == k) ? 1.0 : 0.0;  // identity when S is not positive definite
+            } else if (i < k) {
+                t = 0.0;
+            } else {
+                t = (i == k) ? 1.0 : 0.0;
+                for (int m = k; m < i; ++m) t -= L[i * n + m] * Linv[m * n + k];
+                t /= L[i * n + i];
+            }
+            Linv[i * n + k] = t;
+        }
+    }
+}
+
+__global__ void k_fill(double* p, size_t n, double value) {
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) p[s] = value;
+}
+
+// --------------------------------------------------------------------------- LDA
+// Spin-unpolarised Slater exchange + Perdew-Zunger 1981 correlation
+// (Phys. Rev. B 23, 5048, Appendix C).  v = d(rho eps)/d rho.
+__device__ __forceinline__ void lda_point(double rho, double& eps, double& v) {
+    if (!(rho >= 1e-14)) {
+        eps = 0.0;
+        v = 0.0;
+        return;
+    }
+    const double kPi = 3.141592653589793238462643383279502884;
+    const double cx = -0.75 * cbrt(3.0 / kPi);
+    const double ex = cx * cbrt(rho);
+    const double vx = (4.0 / 3.0) * ex;
+    const double rs = cbrt(3.0 / (4.0 * kPi * rho));
+    double ec, vc;
+    if (rs >= 1.0) {
+        const double gam = -0.1423, b1 = 1.0529, b2 = 0.3334;
+        const double sr = sqrt(rs);
+        const double den = 1.0 + b1 * sr + b2 * rs;
+        ec = gam / den;
+        vc = ec * (1.0 + (7.0 / 6.0) * b1 * sr + (4.0 / 3.0) * b2 * rs) / den;
+    } else {
+        const double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+        const double lr = log(rs);
+        ec = A * lr + B + C * rs * lr + D * rs;
+        vc = A * lr + (B - A / 3.0) + (2.0 / 3.0) * C * rs * lr + (2.0 * D - C) / 3.0 * rs;
+    }
+    eps = ex + ec;
+    v = vx + vc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_lda(size_t n, const double* __restrict__ rho, double* __restrict__ eps,
+                                                  double* __restrict__ v) {
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) {
+        double e, w;
+        lda_point(rho[s], e, w);
+        eps[s] = e;
+        v[s] = w;
+    }
+}
+
+// V_out = V_ext + V_H + v_xc; mixing; energy integrals.
+__global__ void __launch_bounds__(kThreads) k_potential(Grid g, double h, const double* __restrict__ rho,
+                                                        const double* __restrict__ vext,
+                                                        const double* __restrict__ vh, double* __restrict__ vout,
+                                                        double* __restrict__ vin, int first, double mix, double* e4,
+                                                        Scratch sc) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        const double r = rho[s];
+        double e, w;
+        lda_point(r, e, w);
+        const double vo = vext[s] + vh[s] + w;
+        vout[s] = vo;
+        vin[s] = first ? vo : mix * vo + (1.0 - mix) * vin[s];
+        acc[0] += vext[s] * r;
+        acc[1] += vh[s] * r;
+        acc[2] += r * e;
+        acc[3] += r;
+    }
+    block_sum_store<4>(acc, sc.partial + (size_t)blockIdx.x * 4);
+    __shared__ double tot[4];
+    if (grid_total<4>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        const double h3 = h * h * h;
+        for (int k = 0; k < 4; ++k) e4[k] = h3 * tot[k];
+    }
+}
+
+// ----------------------------------------------------------------------- Poisson
+__device__ __forceinline__ double multipole_value(const double* mp, double X, double Y, double Z) {
+    const double r2 = X * X + Y * Y + Z * Z;
+    const double r = sqrt(r2);
+    double v = mp[0] / r;
+    v += (mp[1] * X + mp[2] * Y + mp[3] * Z) / (r2 * r);
+    const double quad = mp[4] * X * X + mp[5] * Y * Y + mp[6] * Z * Z +
+                        2.0 * (mp[7] * X * Y + mp[8] * X * Z + mp[9] * Y * Z);
+    return v + 0.5 * quad / (r2 * r2 * r);
+}
+
+// Multipoles {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz} of rho.
+__global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const double* __restrict__ rho, double* mp,
+                                                         Scratch sc) {
+    double acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int x, y, z;
+        double rx, ry, rz;
+        coords(g, h, s, x, y, z, rx, ry, rz);
+        const double r = rho[s];
+        acc[0] += r;
+        acc[1] += r * rx; acc[2] += r * ry; acc[3] += r * rz;
+        acc[4] += r * rx * rx; acc[5] += r * ry * ry; acc[6] += r * rz * rz;
+        acc[7] += r * rx * ry; acc[8] += r * rx * rz; acc[9] += r * ry * rz;
+    }
+    block_sum_store<10>(acc, sc.partial + (size_t)blockIdx.x * 10);
+    __shared__ double tot[10];
+    if (grid_total<10>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        const double h3 = h * h * h;
+        const double tr = tot[4] + tot[5] + tot[6];
+        mp[0] = h3 * tot[0];
+        mp[1] = h3 * tot[1]; mp[2] = h3 * tot[2]; mp[3] = h3 * tot[3];
+        mp[4] = h3 * (3.0 * tot[4] - tr); mp[5] = h3 * (3.0 * tot[5] - tr); mp[6] = h3 * (3.0 * tot[6] - tr);
+        mp[7] = h3 * 3.0 * tot[7]; mp[8] = h3 * 3.0 * tot[8]; mp[9] = h3 * 3.0 * tot[9];
+    }
+}
+
+// (A v)(r) = 6 v(r) - sum of the six face neighbours (zero outside the grid)
+__device__ __forceinline__ double apply_a(const Grid& g, const double* __restrict__ v, uint32_t s, int x, int y, int z) {
+    const int sy = g.nx, sz = g.nx * g.ny;
+    double t = 6.0 * v[s];
+    if (x > 0) t -= v[s - 1];
+    if (x < g.nx - 1) t -= v[s + 1];
+    if (y > 0) t -= v[s - sy];
+    if (y < g.ny - 1) t -= v[s + sy];
+    if (z > 0) t -= v[s - sz];
+    if (z < g.nz - 1) t -= v[s + sz];
+    return t;
+}
+
+// b = 4 pi h^2 rho + ghost values; r = b - A x; p = r; scalars.
+__global__ void __launch_bounds__(kThreads) k_cg_start(Grid g, double h, const double* __restrict__ rho,
+                                                       const double* __restrict__ x, double rtol, PoissonBufs pb,
+                                                       Scratch sc) {
+    const double kPi = 3.141592653589793238462643383279502884;
+    double acc[2] = {0.0, 0.0};
+    const double* mp = pb.mp;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int ix, iy, iz;
+        double rx, ry, rz;
+        coords(g, h, s, ix, iy, iz, rx, ry, rz);
+        double b = 4.0 * kPi * h * h * rho[s];
+        if (ix == 0) b += multipole_value(mp, rx - h, ry, rz);
+        if (ix == g.nx - 1) b += multipole_value(mp, rx + h, ry, rz);
+        if (iy == 0) b += multipole_value(mp, rx, ry - h, rz);
+        if (iy == g.ny - 1) b += multipole_value(mp, rx, ry + h, rz);
+        if (iz == 0) b += multipole_value(mp, rx, ry, rz - h);
+        if (iz == g.nz - 1) b += multipole_value(mp, rx, ry, rz + h);
+        pb.b[s] = b;
+        const double r = b - apply_a(g, x, s, ix, iy, iz);
+        pb.r[s] = r;
+        pb.p[s] = r;
+        acc[0] += b * b;
+        acc[1] += r * r;
+    }
+    block_sum_store<2>(acc, sc.partial + (size_t)blockIdx.x * 2);
+    __shared__ double tot[2];
+    if (grid_total<2>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        CGState* cg = pb.cg;
+        cg->bb = tot[0];
+        cg->rr = tot[1];
+        cg->iters = 0;
+        cg->relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        cg->done = (tot[0] == 0.0 || sqrt(tot[1]) <= rtol * sqrt(tot[0])) ? 1 : 0;
+    }
+}
+
+// ap = A p; alpha = rr / (p . ap)
+__global__ void __launch_bounds__(kThreads) k_cg_ap(Grid g, PoissonBufs pb, Scratch sc) {
+    if (pb.cg->done) return;
+    double acc[1] = {0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        const uint32_t q = g.divx.div(s);
+        const int x = (int)(s - q * (uint32_t)g.nx);
+        const uint32_t zz = g.divy.div(q);
+        const int y = (int)(q - zz * (uint32_t)g.ny);
+        const double a = apply_a(g, pb.p, s, x, y, (int)zz);
+        pb.ap[s] = a;
+        acc[0] += pb.p[s] * a;
+    }
+    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    __shared__ double tot[1];
+    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        pb.cg->pap = tot[0];
+        pb.cg->alpha = pb.cg->rr / tot[0];
+    }
+}
+
+// x += alpha p; r -= alpha ap; beta = rr_new / rr; convergence test
+__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
+                                                        Scratch sc) {
+    if (pb.cg->done) return;
+    const double alpha = pb.cg->alpha;
+    double acc[1] = {0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        x[s] += alpha * pb.p[s];
+        const double r = pb.r[s] - alpha * pb.ap[s];
+        pb.r[s] = r;
+        acc[0] += r * r;
+    }
+    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    __shared__ double tot[1];
+    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        CGState* cg = pb.cg;
+        cg->beta = tot[0] / cg->rr;
+        cg->rr = tot[0];
+        cg->iters += 1;
+        cg->relres = sqrt(tot[0] / cg->bb);
+        cg->done = (sqrt(tot[0]) <= rtol * sqrt(cg->bb)) ? 1 : 0;
+    }
+}
+
+// p = r + beta p
+__global__ void __launch_bounds__(kThreads) k_cg_dir(Grid g, PoissonBufs pb) {
+    if (pb.cg->done) return;
+    const double beta = pb.cg->beta;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
+        pb.p[s] = pb.r[s] + beta * pb.p[s];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------- launchers
+cudaError_t launch_vext(const Grid& g, double h, int n_atoms, const double* atoms, double a, double* v,
+                        cudaStream_t st) {
+    k_vext<<<grid_for(g.N, num_sms() * 8), kThreads, 0, st>>>(g, h, n_atoms, atoms, a * a, v);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, cudaStream_t st) {
+    if (n < 1 || n > kMaxOrb) return cudaErrorInvalidValue;
+    k_cholesky<<<1, 32, 0, st>>>(n, S, Linv, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t st) {
+    k_fill<<<grid_for(n, num_sms() * 8), kThreads, 0, st>>>(p, n, value);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lda(size_t n, const double* rho, double* eps, double* v, cudaStream_t st) {
+    k_lda<<<grid_for(n, num_sms() * 8), kThreads, 0, st>>>(n, rho, eps, v);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_potential(const Grid& g, double h, const double* rho, const double* vext, const double* vh,
+                             double* vout, double* vin, int first, double mix, double* e4, const Scratch& sc,
+                             cudaStream_t st) {
+    const int cap = red_cap(sc, 4);
+    if (cap < 1) return cudaErrorInvalidValue;
+    k_potential<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, vext, vh, vout, vin, first, mix, e4, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multipoles_from_rho(const Grid& g, double h, const double* rho, double* mp, const Scratch& sc,
+                                       cudaStream_t st) {
+    const int cap = red_cap(sc, 10);
+    if (cap < 1) return cudaErrorInvalidValue;
+    k_multipoles<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, mp, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_start(const Grid& g, double h, const double* rho, double* x, double rtol,
+                                 const PoissonBufs& pb, const Scratch& sc, cudaStream_t st) {
+    const int cap = red_cap(sc, 2);
+    if (cap < 1) return cudaErrorInvalidValue;
+    k_cg_start<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, x, rtol, pb, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int iters, const PoissonBufs& pb,
+                                   const Scratch& sc, cudaStream_t st) {
+    const int cap = red_cap(sc, 1);
+    if (cap < 1) return cudaErrorInvalidValue;
+    const int gr = grid_for(g.N, cap);
+    const int ge = grid_for(g.N, num_sms() * 8);
+    for (int i = 0; i < iters; ++i) {
+        k_cg_ap<<<gr, kThreads, 0, st>>>(g, pb, sc);
+        k_cg_update<<<gr, kThreads, 0, st>>>(g, x, rtol, pb, sc);
+        k_cg_dir<<<ge, kThreads, 0, st>>>(g, pb);
+    }
+    count_launches(3ull * iters);
+    return cudaGetLastError();
+}
+
+}  // namespace lbks

@@ -1,0 +1,6 @@
+// FP64 instantiation of the relaxation kernels (the plain path).
+#include "lbks_relax.cuh"
+
+namespace lbks {
+const PrecisionOps& ops_f64() { return Ops<double>::table(); }
+}  // namespace lbks

@@ -1,0 +1,302 @@
+"""ctypes binding of liblbks (include/lbks.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions carry the C names; device arrays are passed as torch CUDA tensors
+(their data pointers), streams as torch.cuda.Stream or raw handles.  If the
+shared library is missing the import fails: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbks.so")
+
+MAX_ORB = 8
+OK, EINVAL, ENOMEM, ENOTCONV, ETIMEDOUT, EBUSY, ECUDA, ENOTFOUND = range(8)
+FP64, FP32 = 0, 1
+_ELEM = {FP64: 8, FP32: 4}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1507_07666_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class LbksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbks error {code}: {msg}")
+        self.code = code
+
+
+class lbks_params(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("theta", ctypes.c_double), ("n_inner", ctypes.c_int),
+                ("mix", ctypes.c_double), ("e_tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
+                ("precision", ctypes.c_int), ("softening", ctypes.c_double),
+                ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int)]
+
+
+class lbks_result(ctypes.Structure):
+    _fields_ = [("E_total", ctypes.c_double), ("dE", ctypes.c_double),
+                ("eigenvalues", ctypes.c_double * MAX_ORB), ("n_electrons", ctypes.c_double),
+                ("cycles", ctypes.c_int), ("steps", ctypes.c_int), ("converged", ctypes.c_int),
+                ("poisson_iters", ctypes.c_int), ("wall_s", ctypes.c_double)]
+
+
+class lbks_energy_terms(ctypes.Structure):
+    _fields_ = [("T_s", ctypes.c_double), ("E_ext", ctypes.c_double), ("E_H", ctypes.c_double),
+                ("E_xc", ctypes.c_double), ("E_nn", ctypes.c_double), ("E_total", ctypes.c_double),
+                ("eigenvalues", ctypes.c_double * MAX_ORB), ("orbital_energies", ctypes.c_double * MAX_ORB),
+                ("n_electrons", ctypes.c_double)]
+
+
+_vp, _d, _i, _sz = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "lbks_params_default": (None, [ctypes.POINTER(lbks_params)]),
+    "lbks_last_error": (_i, [ctypes.c_char_p, _sz]),
+    "lbks_version": (ctypes.c_char_p, []),
+    "lbks_kernel_launches": (ctypes.c_uint64, []),
+    "lbks_create_system": (_i, [ctypes.POINTER(lbks_params), _i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
+    "lbks_destroy_system": (_i, [_vp]),
+    "lbks_system_bytes": (_sz, [ctypes.POINTER(lbks_params), _i, _i, _i, _i]),
+    "lbks_set_geometry": (_i, [_vp, _i, _dp, _dp]),
+    "lbks_scf": (_i, [_vp, _vp, ctypes.POINTER(lbks_result)]),
+    "lbks_scf_cycles": (_i, [_vp, _i, _vp, ctypes.POINTER(lbks_result)]),
+    "lbks_energy": (_i, [_vp, ctypes.POINTER(lbks_energy_terms)]),
+    "lbks_get_density": (_i, [_vp, _dp, _sz]),
+    "lbks_get_orbitals": (_i, [_vp, _dp, _sz]),
+    "lbks_get_potential": (_i, [_vp, _i, _dp, _sz]),
+    "lbks_relax_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                             _vp]),
+    "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
+    "lbks_cholesky_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
+    "lbks_orth_apply": (_i, [_i, _sz, _i, _vp, _vp, _vp, _vp]),
+    "lbks_hartree": (_i, [_i, _i, _i, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _dp, _vp]),
+    "lbks_lda": (_i, [_sz, _vp, _vp, _vp, _vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _lib.lbks_last_error(buf, len(buf))
+    return buf.value.decode(errors="replace")
+
+
+def _check(code):
+    if code != OK:
+        raise LbksError(code, last_error())
+    return code
+
+
+def _ptr(t, dtype=None, optional=False):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError("tensor required")
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _tdtype(precision):
+    import torch
+    return torch.float64 if precision == FP64 else torch.float32
+
+
+# ------------------------------------------------------------------ functions
+def lbks_params_default(**overrides) -> lbks_params:
+    p = lbks_params()
+    _lib.lbks_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def lbks_version() -> str:
+    return _lib.lbks_version().decode()
+
+
+def lbks_kernel_launches() -> int:
+    return int(_lib.lbks_kernel_launches())
+
+
+def lbks_system_bytes(params, nx, ny, nz, n_orb) -> int:
+    return int(_lib.lbks_system_bytes(ctypes.byref(params), nx, ny, nz, n_orb))
+
+
+def lbks_create_system(params, nx, ny, nz, h, n_orb):
+    handle = ctypes.c_void_p()
+    _check(_lib.lbks_create_system(ctypes.byref(params), nx, ny, nz, h, n_orb, ctypes.byref(handle)))
+    return handle
+
+
+def lbks_destroy_system(handle):
+    _check(_lib.lbks_destroy_system(handle))
+
+
+def lbks_set_geometry(handle, xyz, Z):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    Z = np.ascontiguousarray(Z, dtype=np.float64).ravel()
+    _check(_lib.lbks_set_geometry(handle, len(Z), xyz.ctypes.data_as(_dp), Z.ctypes.data_as(_dp)))
+
+
+def _result_dict(r: lbks_result, n_orb: int) -> dict:
+    return {"E_total": r.E_total, "dE": r.dE, "eigenvalues": np.array(r.eigenvalues[:n_orb]),
+            "n_electrons": r.n_electrons, "cycles": r.cycles, "steps": r.steps,
+            "converged": bool(r.converged), "poisson_iters": r.poisson_iters, "wall_s": r.wall_s}
+
+
+def lbks_scf(handle, stream=None, n_orb=MAX_ORB, allow_notconv=False) -> dict:
+    r = lbks_result()
+    code = _lib.lbks_scf(handle, _stream(stream), ctypes.byref(r))
+    if code != OK and not (allow_notconv and code == ENOTCONV):
+        _check(code)
+    return _result_dict(r, n_orb)
+
+
+def lbks_scf_cycles(handle, n, stream=None, n_orb=MAX_ORB) -> dict:
+    r = lbks_result()
+    _check(_lib.lbks_scf_cycles(handle, n, _stream(stream), ctypes.byref(r)))
+    return _result_dict(r, n_orb)
+
+
+def lbks_energy(handle, n_orb=MAX_ORB) -> dict:
+    t = lbks_energy_terms()
+    _check(_lib.lbks_energy(handle, ctypes.byref(t)))
+    return {"T_s": t.T_s, "E_ext": t.E_ext, "E_H": t.E_H, "E_xc": t.E_xc, "E_nn": t.E_nn,
+            "E_total": t.E_total, "eigenvalues": np.array(t.eigenvalues[:n_orb]),
+            "orbital_energies": np.array(t.orbital_energies[:n_orb]), "n_electrons": t.n_electrons}
+
+
+def lbks_get_density(handle, shape):
+    out = np.empty(shape, dtype=np.float64)
+    _check(_lib.lbks_get_density(handle, out.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def lbks_get_orbitals(handle, shape):
+    out = np.empty(shape, dtype=np.float64)
+    _check(_lib.lbks_get_orbitals(handle, out.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def lbks_get_potential(handle, which, shape):
+    out = np.empty(shape, dtype=np.float64)
+    _check(_lib.lbks_get_potential(handle, which, out.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, V, sigma_in, f_out,
+                    psi_out, S_out, lambda_out, sigma_out, stream=None):
+    import torch
+    T = _tdtype(precision)
+    _check(_lib.lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, _ptr(f_in, T),
+                                _ptr(u_in, T, optional=True), _ptr(V, torch.float64),
+                                _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, T),
+                                _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
+                                _ptr(sigma_out, torch.float64), _stream(stream)))
+
+
+def lbks_w_field(precision, n_sites, n_orb, omega, psi, lam, u_out, stream=None):
+    import torch
+    T = _tdtype(precision)
+    _check(_lib.lbks_w_field(precision, n_sites, n_orb, omega, _ptr(psi, T), _ptr(lam, torch.float64),
+                             _ptr(u_out, T, optional=True), _stream(stream)))
+
+
+def lbks_cholesky_inverse(n, S, Linv, status, stream=None):
+    import torch
+    _check(_lib.lbks_cholesky_inverse(n, _ptr(S, torch.float64), _ptr(Linv, torch.float64),
+                                      _ptr(status, torch.int32), _stream(stream)))
+
+
+def lbks_orth_apply(precision, n_sites, n_orb, Linv, f, psi, stream=None):
+    import torch
+    T = _tdtype(precision)
+    _check(_lib.lbks_orth_apply(precision, n_sites, n_orb, _ptr(Linv, torch.float64), _ptr(f, T, optional=True),
+                                _ptr(psi, T, optional=True), _stream(stream)))
+
+
+def lbks_hartree(nx, ny, nz, h, rho, v, rtol=1e-11, max_iter=20000, stream=None):
+    import torch
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    _check(_lib.lbks_hartree(nx, ny, nz, h, _ptr(rho, torch.float64), _ptr(v, torch.float64), rtol, max_iter,
+                             ctypes.byref(it), ctypes.byref(rr), _stream(stream)))
+    return it.value, rr.value
+
+
+def lbks_lda(n_sites, rho, eps, v, stream=None):
+    import torch
+    _check(_lib.lbks_lda(n_sites, _ptr(rho, torch.float64), _ptr(eps, torch.float64), _ptr(v, torch.float64),
+                         _stream(stream)))
+
+
+# ------------------------------------------------------------- convenience
+class System:
+    """Owning wrapper of one lbks_system handle."""
+
+    def __init__(self, n, h, n_orb, **params):
+        self.n = tuple(int(x) for x in n)
+        self.h = float(h)
+        self.n_orb = int(n_orb)
+        self.params = lbks_params_default(**params)
+        self.handle = lbks_create_system(self.params, *self.n, self.h, self.n_orb)
+
+    @property
+    def grid_shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    def set_geometry(self, xyz, Z):
+        lbks_set_geometry(self.handle, xyz, Z)
+
+    def scf(self, stream=None, allow_notconv=False):
+        return lbks_scf(self.handle, stream, self.n_orb, allow_notconv)
+
+    def scf_cycles(self, n, stream=None):
+        return lbks_scf_cycles(self.handle, n, stream, self.n_orb)
+
+    def energy(self):
+        return lbks_energy(self.handle, self.n_orb)
+
+    def density(self):
+        return lbks_get_density(self.handle, self.grid_shape)
+
+    def orbitals(self):
+        return lbks_get_orbitals(self.handle, (self.n_orb,) + self.grid_shape)
+
+    def potential(self, which=1):
+        return lbks_get_potential(self.handle, which, self.grid_shape)
+
+    def close(self):
+        if self.handle is not None:
+            lbks_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

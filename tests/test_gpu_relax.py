@@ -1,0 +1,152 @@
+"""GPU parity of one relaxation step (Eq. KSLB with normalisation) against the
+oracle, element by element, through the C ABI.
+
+The GPU writes the collision without the orthogonalisation source plus the
+W field u; f_split + xi_p u is compared with the oracle's post-collision
+populations.  Grids are ragged (no extent a multiple of the block) and span
+several blocks; n_orb covers 1 (no W), the common 5 and the maximum 8."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lattice, lb
+
+from gpu_util import paper_state, rel_err, require_gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (n, n_orb, omega, seed)
+    ((7, 9, 11), 1, 1.0, 0),
+    ((7, 9, 11), 3, 0.8, 1),
+    ((33, 20, 17), 5, 1.0, 2),
+    ((33, 20, 17), 5, 1.3, 3),
+    ((2, 3, 2), 2, 1.0, 4),
+    ((16, 5, 40), 8, 0.9, 5),
+]
+TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
+
+
+def _run_gpu(torch, lbks, prec, n, n_orb, omega, theta, dt, h, f, u, V, sigma):
+    T = torch.float64 if prec == lbks.FP64 else torch.float32
+    nx, ny, nz = n
+    N = nx * ny * nz
+    f_in = to_dev(torch, f, T)
+    u_in = to_dev(torch, u[1:], T) if n_orb > 1 else None
+    Vd = to_dev(torch, V, torch.float64)
+    sig = to_dev(torch, sigma, torch.float64)
+    f_out = torch.empty_like(f_in)
+    psi = torch.empty((n_orb, nz, ny, nx), dtype=T, device="cuda")
+    S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
+    lam = torch.empty_like(S)
+    sig_out = torch.empty_like(sig)
+    lbks.lbks_relax_step(prec, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, Vd, sig, f_out, psi, S, lam,
+                         sig_out)
+    u_out = torch.zeros((max(n_orb - 1, 1), nz, ny, nx), dtype=T, device="cuda")
+    lbks.lbks_w_field(prec, N, n_orb, omega, psi, lam, u_out if n_orb > 1 else None)
+    torch.cuda.synchronize()
+    return {"f_split": to_np(f_out), "u": to_np(u_out), "psi": to_np(psi), "S": to_np(S), "lam": to_np(lam),
+            "sigma": to_np(sig_out)}
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("n,n_orb,omega,seed", CASES)
+def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed):
+    torch, lbks = require_gpu()
+    theta, h = 0.5, 0.3
+    dt = lattice.time_step(theta, omega, h)
+    f, V, sigma, _, u = W.random_state(n, n_orb, seed)
+    if prec == lbks.FP32:  # the oracle sees exactly the values the GPU stores
+        f, u = f.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    g = _run_gpu(torch, lbks, prec, n, n_orb, omega, theta, dt, h, f, u, V, sigma)
+    ref = lb.step(paper_state(f, u[1:], theta), sigma, V, omega, theta, dt, h)
+    tol = TOL[prec]
+    assert rel_err(g["psi"], ref["psi"]) < tol
+    assert rel_err(g["S"], ref["S"]) < tol
+    np.testing.assert_allclose(g["sigma"], ref["sigma"], rtol=tol)
+    np.testing.assert_allclose(g["lam"], ref["lam"], atol=tol * max(1.0, np.abs(ref["lam"]).max()))
+    fg = paper_state(g["f_split"], g["u"], theta) if n_orb > 1 else g["f_split"]
+    assert rel_err(fg, ref["fstar"]) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_orthonormalising_step_matches_oracle(prec):
+    """Relax step, Cholesky of its overlap and L^{-1} applied to populations
+    and orbitals reproduce the oracle's cycle-ending step."""
+    torch, lbks = require_gpu()
+    n, n_orb, omega, theta, h = (19, 13, 10), 4, 1.0, 0.5, 0.25
+    dt = lattice.time_step(theta, omega, h)
+    f, V, sigma, _, u = W.random_state(n, n_orb, 11)
+    if prec == lbks.FP32:
+        f, u = f.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    T = torch.float64 if prec == lbks.FP64 else torch.float32
+    nx, ny, nz = n
+    N = nx * ny * nz
+    f_in, u_in = to_dev(torch, f, T), to_dev(torch, u[1:], T)
+    Vd, sig = to_dev(torch, V, torch.float64), to_dev(torch, sigma, torch.float64)
+    f_out = torch.empty_like(f_in)
+    psi = torch.empty((n_orb, nz, ny, nx), dtype=T, device="cuda")
+    S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
+    lam, Linv = torch.empty_like(S), torch.empty_like(S)
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    lbks.lbks_relax_step(prec, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, Vd, sig, f_out, psi, S, lam,
+                         torch.empty_like(sig))
+    lbks.lbks_cholesky_inverse(n_orb, S, Linv, status)
+    lbks.lbks_orth_apply(prec, N, n_orb, Linv, f_out, psi)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = lb.step(paper_state(f, u[1:], theta), sigma, V, omega, theta, dt, h, orthonormalize=True)
+    tol = 10 * TOL[prec]
+    tl = 1e-10 if prec == lbks.FP64 else 1e-4
+    np.testing.assert_allclose(to_np(Linv), np.linalg.inv(ref["L"]), rtol=tl, atol=tl)
+    assert rel_err(to_np(psi), ref["psi"]) < tol
+    assert rel_err(to_np(f_out), ref["fstar"]) < tol
+    G = lb.gram(to_np(psi), h)
+    assert np.abs(G - np.eye(n_orb)).max() < (1e-12 if prec == lbks.FP64 else 1e-5)
+
+
+def test_cholesky_reports_non_positive_pivot():
+    torch, lbks = require_gpu()
+    S = torch.tensor([[1.0, 2.0], [2.0, 1.0]], dtype=torch.float64, device="cuda")
+    Linv = torch.empty_like(S)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lbks.lbks_cholesky_inverse(2, S, Linv, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 2  # second pivot 1 - 4 < 0
+
+
+def test_full_size_step_in_bench_configuration():
+    """CH4 128^3, five orbitals, FP32 populations: one step from a random state
+    at full size, all outputs against the oracle."""
+    torch, lbks = require_gpu()
+    n, n_orb, omega, theta, h = (128, 128, 128), 5, 1.0, 0.5, 0.2
+    dt = lattice.time_step(theta, omega, h)
+    f, V, sigma, _, u = W.random_state(n, n_orb, 7)
+    f, u = f.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    g = _run_gpu(torch, lbks, lbks.FP32, n, n_orb, omega, theta, dt, h, f, u, V, sigma)
+    ref = lb.step(paper_state(f, u[1:], theta), sigma, V, omega, theta, dt, h)
+    assert rel_err(g["psi"], ref["psi"]) < 2e-5
+    assert rel_err(g["S"], ref["S"]) < 2e-5
+    assert rel_err(paper_state(g["f_split"], g["u"], theta), ref["fstar"]) < 2e-5
+
+
+def test_relax_step_is_deterministic():
+    torch, lbks = require_gpu()
+    n, n_orb, omega, theta, h = (33, 20, 17), 5, 1.0, 0.5, 0.3
+    dt = lattice.time_step(theta, omega, h)
+    f, V, sigma, _, u = W.random_state(n, n_orb, 9)
+    a = _run_gpu(torch, lbks, lbks.FP32, n, n_orb, omega, theta, dt, h, f, u, V, sigma)
+    b = _run_gpu(torch, lbks, lbks.FP32, n, n_orb, omega, theta, dt, h, f, u, V, sigma)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_step_rejects_bad_arguments():
+    torch, lbks = require_gpu()
+    x = torch.zeros(2 * 19 * 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(lbks.LbksError):  # f_in aliases f_out
+        lbks.lbks_relax_step(0, 2, 2, 2, 2, 0.2, 1.0, 0.5, 0.02, x, None, x[:8], x[:2], x, x[:16], x[:4], x[:4],
+                             x[:2])
+    with pytest.raises(lbks.LbksError):  # too many orbitals
+        lbks.lbks_relax_step(0, 2, 2, 2, 9, 0.2, 1.0, 0.5, 0.02, x, None, x[:8], x[:2], x.clone(), x[:16], x[:4],
+                             x[:4], x[:2])

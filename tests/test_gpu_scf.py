@@ -1,0 +1,131 @@
+"""GPU parity of the full self-consistent solve against the oracle, through
+the C ABI (lbks_create_system / lbks_set_geometry / lbks_scf / lbks_energy).
+
+Tolerances (the benchmark spec's): |Delta E_total| <= 1e-5 Ha, Ritz eigenvalues
+<= 1e-5 Ha, relative density L2 <= 1e-5.  The FP64 path reproduces the
+oracle's trajectory to round-off; FP32 populations stay within the same
+tolerances."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import scf
+
+from gpu_util import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+E_TOL, EIG_TOL, RHO_TOL = 1e-5, 1e-5, 1e-5
+
+
+def _gpu_system(lbks, w, prec, **kw):
+    params = dict(precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta, omega=w.omega, mix=w.mix,
+                  max_cycles=w.max_cycles, poisson_rtol=1e-12)
+    params.update(kw)
+    s = lbks.System(w.n, w.h, w.n_orb, **params)
+    s.set_geometry(w.molecule.xyz, w.molecule.Z)
+    return s
+
+
+def _rho_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _compare(g, ref, gpu_rho, ref_rho, e_tol=E_TOL):
+    assert abs(g["E_total"] - ref["E_total"]) <= e_tol, (g["E_total"], ref["E_total"])
+    np.testing.assert_allclose(np.sort(g["eigenvalues"]), np.sort(ref["eigenvalues"]), atol=EIG_TOL)
+    assert _rho_l2(gpu_rho, ref_rho) <= RHO_TOL
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_initial_state_matches_oracle(prec):
+    torch, lbks = require_gpu()
+    w = W.ch4_small(32, 0.35)
+    s = _gpu_system(lbks, w, prec)
+    st = scf.State(w.n, w.h, w.molecule.xyz, w.molecule.Z, w.n_orb, w.theta, w.omega, poisson_rtol=1e-12)
+    e = s.energy()
+    for k in ("T_s", "E_ext", "E_H", "E_xc", "E_nn", "E_total", "n_electrons"):
+        assert e[k] == pytest.approx(st.terms[k], abs=1e-9 if prec == 0 else 1e-5), k
+    _compare(e, st.terms, s.density(), st.rho)
+    np.testing.assert_allclose(s.potential(3), st.v_ext, rtol=1e-13)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_helium_scf_matches_oracle(prec):
+    torch, lbks = require_gpu()
+    w = W.he_24()
+    st, ref = scf.scf(w.n, w.h, w.molecule.xyz, w.molecule.Z, 1, n_inner=w.n_inner, e_tol=w.e_tol,
+                      poisson_rtol=1e-12)
+    s = _gpu_system(lbks, w, prec)
+    g = s.scf()
+    assert g["converged"]
+    if prec == 0:
+        assert g["cycles"] == ref["cycles"]
+    _compare(g, ref, s.density(), st.rho)
+    assert g["n_electrons"] == pytest.approx(2.0, abs=1e-10)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_methane_trajectory_matches_oracle(prec):
+    """Five orbitals (W source active, degenerate t2 level), three fixed cycles."""
+    torch, lbks = require_gpu()
+    w = W.ch4_small(32, 0.35)
+    w.n_inner = 20
+    st, ref = scf.scf(w.n, w.h, w.molecule.xyz, w.molecule.Z, 5, n_inner=20, poisson_rtol=1e-12, fixed_cycles=3)
+    s = _gpu_system(lbks, w, prec)
+    g = s.scf_cycles(3)
+    assert g["steps"] == ref["steps"]
+    _compare(g, ref, s.density(), st.rho, e_tol=1e-8 if prec == 0 else E_TOL)
+    np.testing.assert_allclose(s.potential(1), st.v_out, atol=1e-8 if prec == 0 else 1e-5)
+    s.close()
+
+
+def test_population_memory_omega_below_one():
+    """omega = 0.8: the populations keep a memory term (1 - omega) f."""
+    torch, lbks = require_gpu()
+    w = W.he_24()
+    w.omega = 0.8
+    st, ref = scf.scf(w.n, w.h, w.molecule.xyz, w.molecule.Z, 1, n_inner=w.n_inner, omega=0.8, poisson_rtol=1e-12,
+                      fixed_cycles=4)
+    s = _gpu_system(lbks, w, 0)
+    g = s.scf_cycles(4)
+    _compare(g, ref, s.density(), st.rho, e_tol=1e-9)
+    s.close()
+
+
+def test_two_orbital_molecule_odd_cycle_length():
+    """LiH with an odd cycle length exercises both graph start buffers."""
+    torch, lbks = require_gpu()
+    w = W.Workload("LiH", W.lih(3.0), (30, 28, 36), 0.3, n_inner=11)
+    st, ref = scf.scf(w.n, w.h, w.molecule.xyz, w.molecule.Z, 2, n_inner=11, poisson_rtol=1e-12, fixed_cycles=5)
+    s = _gpu_system(lbks, w, 0)
+    g = s.scf_cycles(5)
+    _compare(g, ref, s.density(), st.rho, e_tol=1e-8)
+    s.close()
+
+
+def test_scf_is_deterministic():
+    torch, lbks = require_gpu()
+    w = W.he_24()
+    out = []
+    for _ in range(2):
+        s = _gpu_system(lbks, w, 1)
+        out.append((s.scf()["E_total"], s.density()))
+        s.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_geometry_errors():
+    torch, lbks = require_gpu()
+    s = lbks.System((16, 16, 16), 0.3, 1)
+    with pytest.raises(lbks.LbksError) as e:
+        s.set_geometry([[10.0, 0.0, 0.0]], [2.0])  # outside the 4.5 bohr half-box
+    assert e.value.code == lbks.EINVAL
+    with pytest.raises(lbks.LbksError):
+        s.set_geometry([[0.0, 0.0, 0.0]], [1.0])  # one electron for one doubly occupied orbital
+    with pytest.raises(lbks.LbksError):
+        s.scf()  # no geometry yet
+    s.close()
