@@ -63,7 +63,8 @@ def test_helium_scf_matches_oracle(prec):
     if prec == 0:
         assert g["cycles"] == ref["cycles"]
     _compare(g, ref, s.density(), st.rho)
-    assert g["n_electrons"] == pytest.approx(2.0, abs=1e-10)
+    # FP32 orbitals carry ~1e-7 relative rounding into the density's norm
+    assert g["n_electrons"] == pytest.approx(2.0, abs=1e-10 if prec == 0 else 1e-6)
     s.close()
 
 
