@@ -186,6 +186,37 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h,
                     double* S_out_dev, double* lambda_out_dev, double* sigma_out_dev,
                     void* stream);
 
+/* The step of lbks_relax_step for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is an interface convenience.
+ *
+ * Who needs it: code that already owns every byte it may touch on the GPU --
+ * a host application whose memory is fully carved up by another framework's
+ * pool allocator, a plug-in that is not allowed to call cudaMalloc, or a
+ * latency-critical server that cannot afford the implicit device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  Such a caller still
+ * provides every input and output buffer; only the reduction scratch that
+ * lbks_relax_step would allocate moves into a fixed array of this library.
+ *
+ * The scratch is a file-scope __device__ array of 2048 blocks x 36 doubles
+ * plus a counter (about 590 KB); every GPU that loads the library holds it
+ * until the process exits.  On the first call on a device (with that device
+ * current) the library looks up the array's device address; make that
+ * first call before starting any stream capture.  Nothing is allocated or
+ * freed: no cudaMalloc, cudaFree or allocating library routine is called.
+ * Each call clears the arrival counter and overwrites the partials before
+ * reading them; the array otherwise keeps the last call's contents.  All
+ * calls share the one array, so calls that overlap on the GPU (different
+ * streams, or different host threads without ordering) race and give wrong
+ * overlaps: order them on one stream.  EINVAL for n_orb > 8 (the array's
+ * limit) and for every argument lbks_relax_step rejects.  Arguments and
+ * results are exactly those of lbks_relax_step. */
+int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, double h,
+                            double omega, double theta, double dt,
+                            const void* f_in_dev, const void* u_in_dev, const double* V_dev,
+                            const double* sigma_in_dev, void* f_out_dev, void* psi_out_dev,
+                            double* S_out_dev, double* lambda_out_dev, double* sigma_out_dev,
+                            void* stream);
+
 /* W field of the orthogonalisation source (Sec. 3, W_jp):
  * u_(j-1)(r) = -omega sum_{k<j} lambda_jk psi_k(r), j = 1..n_orb-1. */
 int lbks_w_field(int precision, size_t n_sites, int n_orb, double omega,

@@ -39,6 +39,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 }  // namespace
 
+int set_last_error(int code, const char* msg) {
+    g_err = msg ? msg : "";
+    return code;
+}
+
 void count_launches(uint64_t n) {
     if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }

@@ -73,6 +73,8 @@ struct Scratch {
 
 // Launch bookkeeping.
 void count_launches(uint64_t n);
+// Records the calling thread's error message (returned by lbks_last_error); returns code.
+int set_last_error(int code, const char* msg);
 int num_sms();
 
 // ------------------------------------------------------------------ relax ops

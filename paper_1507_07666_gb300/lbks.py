@@ -71,6 +71,8 @@ _SIGS = {
     "lbks_get_potential": (_i, [_vp, _i, _dp, _sz]),
     "lbks_relax_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                              _vp]),
+    "lbks_relax_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                     _vp, _vp]),
     "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
     "lbks_cholesky_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
     "lbks_orth_apply": (_i, [_i, _sz, _i, _vp, _vp, _vp, _vp]),
@@ -216,6 +218,19 @@ def lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_i
                                 _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, T),
                                 _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
                                 _ptr(sigma_out, torch.float64), _stream(stream)))
+
+
+def lbks_relax_step_noalloc(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, V, sigma_in, f_out,
+                            psi_out, S_out, lambda_out, sigma_out, stream=None):
+    """As lbks_relax_step, with the reduction scratch in the library's fixed
+    device array (nothing is allocated; overlapping calls race)."""
+    import torch
+    T = _tdtype(precision)
+    _check(_lib.lbks_relax_step_noalloc(precision, nx, ny, nz, n_orb, h, omega, theta, dt, _ptr(f_in, T),
+                                        _ptr(u_in, T, optional=True), _ptr(V, torch.float64),
+                                        _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, T),
+                                        _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
+                                        _ptr(sigma_out, torch.float64), _stream(stream)))
 
 
 def lbks_w_field(precision, n_sites, n_orb, omega, psi, lam, u_out, stream=None):

@@ -1,0 +1,62 @@
+"""lbks_relax_step_noalloc, the variant for callers that may not allocate GPU
+memory (their memory belongs to another allocator, or cudaMalloc's implicit
+synchronisation is off-limits to them), must give what lbks_relax_step
+gives.  Two calls in a row check that the fixed scratch array carries
+nothing from one call into the next.  Collected last on purpose."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lattice
+
+from gpu_util import rel_err, require_gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 2e-5}
+
+
+def _buffers(torch, prec, n, n_orb, seed):
+    T = torch.float64 if prec == 0 else torch.float32
+    nx, ny, nz = n
+    f, V, sigma, _, u = W.random_state(n, n_orb, seed)
+    return {
+        "f_in": to_dev(torch, f, T), "u_in": to_dev(torch, u[1:], T) if n_orb > 1 else None,
+        "V": to_dev(torch, V, torch.float64), "sigma": to_dev(torch, sigma, torch.float64),
+        "f_out": torch.empty((n_orb, 19, nz, ny, nx), dtype=T, device="cuda"),
+        "psi": torch.empty((n_orb, nz, ny, nx), dtype=T, device="cuda"),
+        "S": torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda"),
+        "lam": torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda"),
+        "sig_out": torch.empty((n_orb,), dtype=torch.float64, device="cuda"),
+    }
+
+
+def _call(fn, prec, n, n_orb, b):
+    omega, theta, h = 1.0, 0.5, 0.3
+    dt = lattice.time_step(theta, omega, h)
+    fn(prec, *n, n_orb, h, omega, theta, dt, b["f_in"], b["u_in"], b["V"], b["sigma"], b["f_out"], b["psi"], b["S"],
+       b["lam"], b["sig_out"])
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+def test_noalloc_step_matches_allocating_step_twice(prec):
+    torch, lbks = require_gpu()
+    cases = [((33, 20, 17), 5, 21), ((64, 48, 40), 3, 22)]  # second call: other sizes, other contents
+    for n, n_orb, seed in cases:
+        ref = _buffers(torch, prec, n, n_orb, seed)
+        _call(lbks.lbks_relax_step, prec, n, n_orb, ref)
+        got = _buffers(torch, prec, n, n_orb, seed)
+        _call(lbks.lbks_relax_step_noalloc, prec, n, n_orb, got)
+        torch.cuda.synchronize()
+        for k in ("f_out", "psi", "S", "lam", "sig_out"):
+            a, b = to_np(got[k]), to_np(ref[k])
+            assert rel_err(a, b) <= TOL[prec], (n, k)
+
+
+def test_noalloc_rejects_more_orbitals_than_its_scratch_holds():
+    torch, lbks = require_gpu()
+    b = _buffers(torch, 0, (4, 4, 4), 2, 0)
+    with pytest.raises(lbks.LbksError) as e:
+        _call(lbks.lbks_relax_step_noalloc, 0, (4, 4, 4), 9, b)
+    assert e.value.code == lbks.EINVAL
+    assert "8 orbitals" in str(e.value)
