@@ -59,6 +59,10 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time only the fused stream-collide kernel (for profiling)")
+    ap.add_argument("--kernel-n", type=int, default=0, help="cubic grid edge for --kernel-only (0: workload's)")
+    ap.add_argument("--launches", type=int, default=20)
     return ap.parse_args()
 
 
@@ -235,6 +239,25 @@ def time_stream_collide(torch, lbks, w, prec, stream, launches=20):
     return statistics.mean(ms), N * no
 
 
+def main_kernel_only(args):
+    """Stream-collide launches alone (3 untimed + --launches timed), for ncu."""
+    import torch
+    from paper_1507_07666_gb300 import build as build_mod
+    build_mod.build()
+    from paper_1507_07666_gb300 import lbks
+    w = WORKLOADS[args.workload]()
+    if args.kernel_n:
+        w.n = (args.kernel_n,) * 3
+    prec = lbks.FP32 if args.precision == "fp32" else lbks.FP64
+    stream = torch.cuda.Stream()
+    ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
+    elem = 4 if prec == lbks.FP32 else 8
+    gbs = 38 * elem * units / (ms / 1e3) / 1e9
+    print(json.dumps({"kernel": "k_stream_collide", "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
+                      "ms_per_launch": ms, "algorithmic_GBps": gbs, "launches": args.launches}), flush=True)
+    return 0
+
+
 def main_lbks(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -350,6 +373,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return main_reference(args)
+    if args.kernel_only:
+        return main_kernel_only(args)
     return main_lbks(args)
 
 

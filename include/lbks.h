@@ -160,6 +160,61 @@ int lbks_get_orbitals(const lbks_system* sys, double* host, size_t cap);
 int lbks_get_potential(const lbks_system* sys, int which /*0 V_in,1 V_out,2 V_H,3 V_ext*/,
                        double* host, size_t cap);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop with continuous batching.  Each request is one closed-shell
+ * single-point solve (grid, spacing, nuclei).  Worker slots (host threads,
+ * each with its own CUDA stream on the server's device) take queued requests
+ * in arrival order, skipping ahead to the first one whose device memory
+ * (lbks_system_bytes) fits in the free budget; a request whose shape matches
+ * an idle pooled system reuses it, so populations and potentials stay
+ * resident between requests; idle pooled systems are freed, oldest first,
+ * when a new shape needs the room.  Slots run concurrently, so the kernels
+ * of different requests overlap on the GPU.  A request's result does not
+ * depend on what else runs (fixed-order reductions, private scratch). */
+typedef struct lbks_server lbks_server;
+
+typedef struct lbks_request {
+    int nx, ny, nz;     /* grid */
+    double h;           /* spacing, bohr */
+    int n_orb;          /* doubly occupied orbitals; sum Z must be 2 n_orb */
+    int n_atoms;
+    const double* xyz;  /* 3*n_atoms, bohr, box-centre origin; copied by lbks_submit */
+    const double* Z;    /* n_atoms; copied */
+    int precision;      /* < 0: server default */
+    int n_inner;        /* <= 0: server default */
+    double e_tol;       /* <= 0: server default */
+    int max_cycles;     /* <= 0: server default */
+} lbks_request;
+
+typedef struct lbks_timing {
+    double queue_s;   /* submit -> slot start */
+    double run_s;     /* slot start -> result */
+    double latency_s; /* submit -> result */
+} lbks_timing;
+
+typedef struct lbks_server_stats {
+    int queued, running, pooled;
+    uint64_t completed;
+    size_t bytes_in_use, budget_bytes;
+} lbks_server_stats;
+
+/* budget_bytes = 0: 85 % of the device's free memory at creation.
+ * defaults = NULL: lbks_params_default().  EINVAL: max_slots not in [1, 64]. */
+int lbks_server_create(const lbks_params* defaults, size_t budget_bytes, int max_slots, lbks_server** out);
+/* Stops the slots after their current requests, frees pooled systems. */
+int lbks_server_destroy(lbks_server* srv);
+/* Queues a copy of the request and returns its id at once.  EINVAL for a
+ * malformed request, ENOMEM when it can never fit the budget. */
+int lbks_submit(lbks_server* srv, const lbks_request* req, uint64_t* id);
+/* *done = 1 once the request finished; then `out` (and `timing`, if not
+ * NULL) are filled, the id is released and the return value is the solve's
+ * status (LBKS_OK, LBKS_ENOTCONV, ...).  ENOTFOUND for an unknown id. */
+int lbks_poll(lbks_server* srv, uint64_t id, lbks_result* out, lbks_timing* timing, int* done);
+/* Blocks until the request finished (without releasing it) or timeout_s
+ * passed (ETIMEDOUT). */
+int lbks_server_wait(lbks_server* srv, uint64_t id, double timeout_s);
+int lbks_server_get_stats(lbks_server* srv, lbks_server_stats* out);
+
 /* ------------------------------------------------- step-level device kernels
  * These expose the kernels the solver is built from, on caller-owned device
  * buffers, so that each step can be checked on its own.                    */

@@ -113,7 +113,7 @@ cudaError_t alloc_scratch(Scratch& sc) {
 // (device, stream): reduction scratch and Poisson vectors grown on demand.
 struct Workspace {
     Scratch sc;
-    double* pvec = nullptr;  // 4 * n_pvec doubles: b, r, p, ap
+    double* pvec = nullptr;  // n_pvec doubles: b, r, p, ap, z, tmp and the coarse levels
     size_t n_pvec = 0;
     CGState* cg = nullptr;
     double* mp = nullptr;
@@ -141,7 +141,7 @@ int workspace(void* stream, size_t n_pvec, Workspace** out) {
         if (w->pvec) cudaFree(w->pvec);
         w->pvec = nullptr;
         w->n_pvec = 0;
-        cudaError_t e = cudaMalloc(&w->pvec, sizeof(double) * 4 * n_pvec);
+        cudaError_t e = cudaMalloc(&w->pvec, sizeof(double) * n_pvec);
         if (e != cudaSuccess) return cuda_fail(e, "workspace allocation");
         w->n_pvec = n_pvec;
     }
@@ -204,8 +204,11 @@ struct lbks_system {
     void* u = nullptr;
     void* psi = nullptr;
     double *vin = nullptr, *vout = nullptr, *vext = nullptr, *vh = nullptr, *rho = nullptr;
-    double* pvec = nullptr;  // b, r, p, ap
+    double* pvec = nullptr;  // b, r, p, ap, z, tmp, then the multigrid levels
     CGState* cg = nullptr;
+    MGHierarchy mg;
+    cudaGraphExec_t poisson_graph = nullptr;  // kPoissonChunk preconditioned CG iterations
+    uint64_t poisson_nodes = 0;
     double* small = nullptr;  // S, lam, sigma, Linv, e4, emat, mp, atoms
     int* status = nullptr;
     double *S, *lam, *sigma, *Linv, *e4, *emat, *mp, *atoms;
@@ -226,8 +229,40 @@ namespace {
 constexpr int kSmall = 4 * kMaxOrb * kMaxOrb + 4 + kScratchVals + 16;
 constexpr int kMaxAtoms = 256;
 
+constexpr int kPoissonChunk = 2;  // PCG iterations per graph launch between convergence checks
+
+PoissonBufs poisson_bufs(double* v, size_t N, CGState* cg, double* mp) {
+    return PoissonBufs{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, cg, mp};
+}
+
+int poisson_graph(lbks_system* s) {
+    if (s->poisson_graph) return LBKS_OK;
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N, s->cg, s->mp);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    g_capturing = true;
+    cudaError_t ee = launch_poisson_iterate(s->g, s->vh, s->prm.poisson_rtol, kPoissonChunk, pb, s->mg, s->sc, s->cap);
+    g_capturing = false;
+    e = cudaStreamEndCapture(s->cap, &gr);
+    if (ee != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return cuda_fail(ee, "capture Poisson iterations");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    size_t nodes = 0;
+    cudaGraphGetNodes(gr, nullptr, &nodes);
+    e = cudaGraphInstantiate(&s->poisson_graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate Poisson graph");
+    s->poisson_nodes = nodes;
+    return LBKS_OK;
+}
+
 int hartree_solve(lbks_system* s, cudaStream_t st) {
-    PoissonBufs pb{s->pvec, s->pvec + s->N, s->pvec + 2 * s->N, s->pvec + 3 * s->N, s->cg, s->mp};
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N, s->cg, s->mp);
+    int rc = poisson_graph(s);
+    if (rc != LBKS_OK) return rc;
     cudaError_t e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, st);
     if (e != cudaSuccess) return cuda_fail(e, "poisson start");
     CGState* hcg = reinterpret_cast<CGState*>(s->host + 8 + kScratchVals);
@@ -239,13 +274,13 @@ int hartree_solve(lbks_system* s, cudaStream_t st) {
         if (hcg->done) break;
         if (done_iters >= s->prm.poisson_max_iter) {
             s->poisson_iters += hcg->iters;
-            return fail(LBKS_ENOTCONV, "Hartree CG: relative residual %.3e after %d iterations", hcg->relres,
+            return fail(LBKS_ENOTCONV, "Hartree PCG: relative residual %.3e after %d iterations", hcg->relres,
                         hcg->iters);
         }
-        const int chunk = std::min(32, s->prm.poisson_max_iter - done_iters);
-        e = launch_poisson_iterate(s->g, s->vh, s->prm.poisson_rtol, chunk, pb, s->sc, st);
+        e = cudaGraphLaunch(s->poisson_graph, st);
         if (e != cudaSuccess) return cuda_fail(e, "poisson iterate");
-        done_iters += chunk;
+        count_launches(s->poisson_nodes);
+        done_iters += kPoissonChunk;
     }
     s->poisson_iters += hcg->iters;
     return LBKS_OK;
@@ -325,7 +360,7 @@ cudaError_t enqueue_cycle(lbks_system* s, cudaStream_t st, int start) {
 int cycle_graph(lbks_system* s, int start) {
     if (s->graph[start]) return LBKS_OK;
     cudaGraph_t gr = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
     g_capturing = true;
     cudaError_t ee = enqueue_cycle(s, s->cap, start);
@@ -393,6 +428,7 @@ void free_system(lbks_system* s) {
         if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
         if (s->f[k]) cudaFree(s->f[k]);
     }
+    if (s->poisson_graph) cudaGraphExecDestroy(s->poisson_graph);
     void* ptrs[] = {s->u, s->psi, s->vin, s->vout, s->vext, s->vh, s->rho, s->pvec, s->cg, s->small, s->status,
                     s->sc.partial, s->sc.counter};
     for (void* p : ptrs)
@@ -438,7 +474,8 @@ size_t lbks_system_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb
     if (!valid_params(p) || nx < 2 || ny < 2 || nz < 2 || n_orb < 1 || n_orb > kMaxOrb) return 0;
     const size_t N = (size_t)nx * ny * nz;
     const size_t e = ops_for(p->precision)->elem;
-    return e * N * ((size_t)n_orb * 19 * 2 + (size_t)std::max(1, n_orb - 1) + n_orb) + sizeof(double) * N * 9 +
+    return e * N * ((size_t)n_orb * 19 * 2 + (size_t)std::max(1, n_orb - 1) + n_orb) + sizeof(double) * N * 11 +
+           sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
            sizeof(double) * ((size_t)num_sms() * 8 * kScratchVals + kSmall);
 }
 
@@ -479,7 +516,7 @@ int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, i
     A((void**)&s->vext, 8 * N);
     A((void**)&s->vh, 8 * N);
     A((void**)&s->rho, 8 * N);
-    A((void**)&s->pvec, 8 * N * 4);
+    A((void**)&s->pvec, 8 * (6 * N + mg_coarse_doubles(nx, ny, nz)));
     A((void**)&s->cg, sizeof(CGState));
     A((void**)&s->small, sizeof(double) * (kSmall + 4 * kMaxAtoms));
     A((void**)&s->status, sizeof(int) * 4);
@@ -495,6 +532,7 @@ int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, i
         free_system(s);
         return rc;
     }
+    s->mg = make_hierarchy(s->g, s->pvec + 6 * N);
     const int M = kMaxOrb * kMaxOrb;
     s->S = s->small;
     s->lam = s->S + M;
@@ -510,7 +548,10 @@ int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, i
 
 int lbks_destroy_system(lbks_system* s) {
     if (!s) return fail(LBKS_EINVAL, "system is NULL");
-    cudaDeviceSynchronize();
+    // the system's own streams; work it queued on caller streams has finished
+    // when lbks_scf returned (it synchronises before returning)
+    if (s->st) cudaStreamSynchronize(s->st);
+    if (s->cap) cudaStreamSynchronize(s->cap);
     free_system(s);
     return LBKS_OK;
 }
@@ -674,10 +715,11 @@ int lbks_hartree(int nx, int ny, int nz, double h, const double* rho, double* v,
         return fail(LBKS_EINVAL, "bad argument");
     const Grid g = make_grid(nx, ny, nz);
     Workspace* w = nullptr;
-    int rc = workspace(stream, g.N, &w);
+    int rc = workspace(stream, 6 * (size_t)g.N + mg_coarse_doubles(nx, ny, nz), &w);
     if (rc != LBKS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    PoissonBufs pb{w->pvec, w->pvec + g.N, w->pvec + 2 * (size_t)g.N, w->pvec + 3 * (size_t)g.N, w->cg, w->mp};
+    const PoissonBufs pb = poisson_bufs(w->pvec, g.N, w->cg, w->mp);
+    const MGHierarchy H = make_hierarchy(g, w->pvec + 6 * (size_t)g.N);
     cudaError_t e = launch_multipoles_from_rho(g, h, rho, w->mp, w->sc, st);
     if (e == cudaSuccess) e = launch_poisson_start(g, h, rho, v, rtol, pb, w->sc, st);
     if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree");
@@ -688,14 +730,14 @@ int lbks_hartree(int nx, int ny, int nz, double h, const double* rho, double* v,
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree readback");
         if (hcg.done || done >= max_iter) break;
-        const int chunk = std::min(32, max_iter - done);
-        e = launch_poisson_iterate(g, v, rtol, chunk, pb, w->sc, st);
+        const int chunk = std::min(2, max_iter - done);
+        e = launch_poisson_iterate(g, v, rtol, chunk, pb, H, w->sc, st);
         if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree iterate");
         done += chunk;
     }
     if (iters_out) *iters_out = hcg.iters;
     if (relres_out) *relres_out = hcg.relres;
-    if (!hcg.done) return fail(LBKS_ENOTCONV, "Hartree CG: relative residual %.3e after %d iterations", hcg.relres,
+    if (!hcg.done) return fail(LBKS_ENOTCONV, "Hartree PCG: relative residual %.3e after %d iterations", hcg.relres,
                                hcg.iters);
     return LBKS_OK;
 }

@@ -1,7 +1,7 @@
 // Grid fields of the self-consistent loop, all in FP64: external potential,
 // Cholesky of the overlap, LDA exchange-correlation, potential assembly with
-// mixing and energy integrals, and the lattice Poisson solve for the Hartree
-// potential (conjugate gradients with device-resident scalars).
+// mixing and energy integrals, multipoles of the density (the Hartree solve
+// itself is in lbks_poisson.cu).
 #include "lbks_internal.cuh"
 #include "lbks_reduce.cuh"
 
@@ -163,17 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(Grid g, double h, const 
     }
 }
 
-// ----------------------------------------------------------------------- Poisson
-__device__ __forceinline__ double multipole_value(const double* mp, double X, double Y, double Z) {
-    const double r2 = X * X + Y * Y + Z * Z;
-    const double r = sqrt(r2);
-    double v = mp[0] / r;
-    v += (mp[1] * X + mp[2] * Y + mp[3] * Z) / (r2 * r);
-    const double quad = mp[4] * X * X + mp[5] * Y * Y + mp[6] * Z * Z +
-                        2.0 * (mp[7] * X * Y + mp[8] * X * Z + mp[9] * Y * Z);
-    return v + 0.5 * quad / (r2 * r2 * r);
-}
-
+// ------------------------------------------------------------------- multipoles
 // Multipoles {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz} of rho.
 __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const double* __restrict__ rho, double* mp,
                                                          Scratch sc) {
@@ -200,109 +190,6 @@ __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const
         mp[4] = h3 * (3.0 * tot[4] - tr); mp[5] = h3 * (3.0 * tot[5] - tr); mp[6] = h3 * (3.0 * tot[6] - tr);
         mp[7] = h3 * 3.0 * tot[7]; mp[8] = h3 * 3.0 * tot[8]; mp[9] = h3 * 3.0 * tot[9];
     }
-}
-
-// (A v)(r) = 6 v(r) - sum of the six face neighbours (zero outside the grid)
-__device__ __forceinline__ double apply_a(const Grid& g, const double* __restrict__ v, uint32_t s, int x, int y, int z) {
-    const int sy = g.nx, sz = g.nx * g.ny;
-    double t = 6.0 * v[s];
-    if (x > 0) t -= v[s - 1];
-    if (x < g.nx - 1) t -= v[s + 1];
-    if (y > 0) t -= v[s - sy];
-    if (y < g.ny - 1) t -= v[s + sy];
-    if (z > 0) t -= v[s - sz];
-    if (z < g.nz - 1) t -= v[s + sz];
-    return t;
-}
-
-// b = 4 pi h^2 rho + ghost values; r = b - A x; p = r; scalars.
-__global__ void __launch_bounds__(kThreads) k_cg_start(Grid g, double h, const double* __restrict__ rho,
-                                                       const double* __restrict__ x, double rtol, PoissonBufs pb,
-                                                       Scratch sc) {
-    const double kPi = 3.141592653589793238462643383279502884;
-    double acc[2] = {0.0, 0.0};
-    const double* mp = pb.mp;
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
-        int ix, iy, iz;
-        double rx, ry, rz;
-        coords(g, h, s, ix, iy, iz, rx, ry, rz);
-        double b = 4.0 * kPi * h * h * rho[s];
-        if (ix == 0) b += multipole_value(mp, rx - h, ry, rz);
-        if (ix == g.nx - 1) b += multipole_value(mp, rx + h, ry, rz);
-        if (iy == 0) b += multipole_value(mp, rx, ry - h, rz);
-        if (iy == g.ny - 1) b += multipole_value(mp, rx, ry + h, rz);
-        if (iz == 0) b += multipole_value(mp, rx, ry, rz - h);
-        if (iz == g.nz - 1) b += multipole_value(mp, rx, ry, rz + h);
-        pb.b[s] = b;
-        const double r = b - apply_a(g, x, s, ix, iy, iz);
-        pb.r[s] = r;
-        pb.p[s] = r;
-        acc[0] += b * b;
-        acc[1] += r * r;
-    }
-    block_sum_store<2>(acc, sc.partial + (size_t)blockIdx.x * 2);
-    __shared__ double tot[2];
-    if (grid_total<2>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
-        CGState* cg = pb.cg;
-        cg->bb = tot[0];
-        cg->rr = tot[1];
-        cg->iters = 0;
-        cg->relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
-        cg->done = (tot[0] == 0.0 || sqrt(tot[1]) <= rtol * sqrt(tot[0])) ? 1 : 0;
-    }
-}
-
-// ap = A p; alpha = rr / (p . ap)
-__global__ void __launch_bounds__(kThreads) k_cg_ap(Grid g, PoissonBufs pb, Scratch sc) {
-    if (pb.cg->done) return;
-    double acc[1] = {0.0};
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
-        const uint32_t q = g.divx.div(s);
-        const int x = (int)(s - q * (uint32_t)g.nx);
-        const uint32_t zz = g.divy.div(q);
-        const int y = (int)(q - zz * (uint32_t)g.ny);
-        const double a = apply_a(g, pb.p, s, x, y, (int)zz);
-        pb.ap[s] = a;
-        acc[0] += pb.p[s] * a;
-    }
-    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
-    __shared__ double tot[1];
-    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
-        pb.cg->pap = tot[0];
-        pb.cg->alpha = pb.cg->rr / tot[0];
-    }
-}
-
-// x += alpha p; r -= alpha ap; beta = rr_new / rr; convergence test
-__global__ void __launch_bounds__(kThreads) k_cg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
-                                                        Scratch sc) {
-    if (pb.cg->done) return;
-    const double alpha = pb.cg->alpha;
-    double acc[1] = {0.0};
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
-        x[s] += alpha * pb.p[s];
-        const double r = pb.r[s] - alpha * pb.ap[s];
-        pb.r[s] = r;
-        acc[0] += r * r;
-    }
-    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
-    __shared__ double tot[1];
-    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
-        CGState* cg = pb.cg;
-        cg->beta = tot[0] / cg->rr;
-        cg->rr = tot[0];
-        cg->iters += 1;
-        cg->relres = sqrt(tot[0] / cg->bb);
-        cg->done = (sqrt(tot[0]) <= rtol * sqrt(cg->bb)) ? 1 : 0;
-    }
-}
-
-// p = r + beta p
-__global__ void __launch_bounds__(kThreads) k_cg_dir(Grid g, PoissonBufs pb) {
-    if (pb.cg->done) return;
-    const double beta = pb.cg->beta;
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
-        pb.p[s] = pb.r[s] + beta * pb.p[s];
 }
 
 }  // namespace
@@ -350,30 +237,6 @@ cudaError_t launch_multipoles_from_rho(const Grid& g, double h, const double* rh
     if (cap < 1) return cudaErrorInvalidValue;
     k_multipoles<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, mp, sc);
     count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_poisson_start(const Grid& g, double h, const double* rho, double* x, double rtol,
-                                 const PoissonBufs& pb, const Scratch& sc, cudaStream_t st) {
-    const int cap = red_cap(sc, 2);
-    if (cap < 1) return cudaErrorInvalidValue;
-    k_cg_start<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, x, rtol, pb, sc);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int iters, const PoissonBufs& pb,
-                                   const Scratch& sc, cudaStream_t st) {
-    const int cap = red_cap(sc, 1);
-    if (cap < 1) return cudaErrorInvalidValue;
-    const int gr = grid_for(g.N, cap);
-    const int ge = grid_for(g.N, num_sms() * 8);
-    for (int i = 0; i < iters; ++i) {
-        k_cg_ap<<<gr, kThreads, 0, st>>>(g, pb, sc);
-        k_cg_update<<<gr, kThreads, 0, st>>>(g, x, rtol, pb, sc);
-        k_cg_dir<<<ge, kThreads, 0, st>>>(g, pb);
-    }
-    count_launches(3ull * iters);
     return cudaGetLastError();
 }
 

@@ -131,21 +131,34 @@ cudaError_t launch_potential(const Grid&, double h, const double* rho, const dou
                              const double* vh, double* vout, double* vin, int first, double mix,
                              double* e4, const Scratch&, cudaStream_t);
 
-struct CGState {  // device-resident CG scalars
-    double bb, rr, pap, alpha, beta, relres;
+struct CGState {  // device-resident scalars of the preconditioned CG
+    double bb, rr, rz, pap, alpha, beta, relres;
     int iters, done;
 };
 struct PoissonBufs {
-    double *b, *r, *p, *ap;
+    double *b, *r, *p, *ap, *z, *tmp;  // fine-grid vectors
     CGState* cg;
     double* mp;  // multipoles of rho (10 doubles)
 };
-// Builds the right-hand side (4 pi h^2 rho + ghost values) and starts CG from x.
+constexpr int kMaxLevels = 10;
+struct MGLevel {
+    Grid g;
+    double *x = nullptr, *b = nullptr, *r = nullptr;
+};
+struct MGHierarchy {
+    int nlev = 0;
+    MGLevel lev[kMaxLevels];
+};
+// lbks_poisson.cu
+int mg_levels(int nx, int ny, int nz);
+size_t mg_coarse_doubles(int nx, int ny, int nz);           // x, b, r of every level below the finest
+MGHierarchy make_hierarchy(const Grid& fine, double* coarse);  // carves `coarse` into the levels
+// Builds the right-hand side (4 pi h^2 rho + ghost values) and r = b - A x.
 cudaError_t launch_poisson_start(const Grid&, double h, const double* rho, double* x, double rtol,
                                  const PoissonBufs&, const Scratch&, cudaStream_t);
-// `iters` CG iterations (no-ops once converged).
+// `iters` preconditioned CG iterations (no-ops once converged).
 cudaError_t launch_poisson_iterate(const Grid&, double* x, double rtol, int iters, const PoissonBufs&,
-                                   const Scratch&, cudaStream_t);
+                                   const MGHierarchy&, const Scratch&, cudaStream_t);
 cudaError_t launch_multipoles_from_rho(const Grid&, double h, const double* rho, double* mp,
                                        const Scratch&, cudaStream_t);
 

@@ -1,0 +1,418 @@
+// Hartree potential: the 7-point lattice Poisson problem
+//   (A v)(r) = 6 v(r) - sum of the six face neighbours = 4 pi h^2 rho(r) + ghost values
+// solved by conjugate gradients preconditioned with one geometric multigrid
+// V-cycle (FP64 throughout, scalars resident on the device).
+//
+// Multigrid hierarchy: coarse point I of a level sits on fine index 2I+1 of
+// the level above (m = n/2 points per axis); coarsening stops when an axis
+// would drop below 2 points.  Prolongation P is trilinear interpolation with
+// zero ghosts, restriction is P^T, and the operator of level l is the
+// rediscretised 2^l (6 - sum of neighbours), the Galerkin product's
+// long-wavelength limit.  Smoothing is red-black Gauss-Seidel, red then
+// black before the coarse correction and black then red after it, with the
+// coarsest level solved by a fixed number of such sweeps: the V-cycle is a
+// fixed symmetric positive definite operator, as conjugate gradients needs.
+#include "lbks_internal.cuh"
+#include "lbks_reduce.cuh"
+
+#include <algorithm>
+
+namespace lbks {
+
+namespace {
+
+constexpr int kPre = 2;       // red-black sweeps before the coarse correction (and after)
+constexpr int kCoarse = 24;   // sweeps each way on the coarsest level
+constexpr uint32_t kCoarseSites = 4096;  // coarsest levels up to this size are solved by one CTA
+
+int grid_for(size_t n, int cap_blocks) {
+    const size_t need = (n + kThreads - 1) / kThreads;
+    return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap_blocks));
+}
+
+int red_cap(const Scratch& sc, int vals) { return sc.max_vals >= vals ? std::min(sc.max_blocks, num_sms() * 4) : 0; }
+
+__device__ __forceinline__ void decode3(const Grid& g, uint32_t s, int& x, int& y, int& z) {
+    const uint32_t q = g.divx.div(s);
+    x = (int)(s - q * (uint32_t)g.nx);
+    const uint32_t zz = g.divy.div(q);
+    y = (int)(q - zz * (uint32_t)g.ny);
+    z = (int)zz;
+}
+
+// 6 v(s) - sum of in-grid face neighbours
+__device__ __forceinline__ double stencil(const Grid& g, const double* __restrict__ v, uint32_t s, int x, int y,
+                                          int z, double self) {
+    const int sy = g.nx, sz = g.nx * g.ny;
+    double t = 6.0 * self;
+    if (x > 0) t -= v[s - 1];
+    if (x < g.nx - 1) t -= v[s + 1];
+    if (y > 0) t -= v[s - sy];
+    if (y < g.ny - 1) t -= v[s + sy];
+    if (z > 0) t -= v[s - sz];
+    if (z < g.nz - 1) t -= v[s + sz];
+    return t;
+}
+
+__device__ __forceinline__ double multipole_value(const double* mp, double X, double Y, double Z) {
+    const double r2 = X * X + Y * Y + Z * Z;
+    const double r = sqrt(r2);
+    double v = mp[0] / r;
+    v += (mp[1] * X + mp[2] * Y + mp[3] * Z) / (r2 * r);
+    const double quad = mp[4] * X * X + mp[5] * Y * Y + mp[6] * Z * Z +
+                        2.0 * (mp[7] * X * Y + mp[8] * X * Z + mp[9] * Y * Z);
+    return v + 0.5 * quad / (r2 * r2 * r);
+}
+
+// ------------------------------------------------------------ multigrid kernels
+// One colour of red-black Gauss-Seidel on A_l = scale (6 - sum nb):
+// x = (b + scale * sum nb x) / (6 scale) at sites with (x+y+z) % 2 == colour.
+__global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, double scale, int colour, double* __restrict__ x,
+                                                        const double* __restrict__ b, const CGState* cg) {
+    if (cg->done) return;
+    const double inv = 1.0 / (6.0 * scale);
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int ix, iy, iz;
+        decode3(g, s, ix, iy, iz);
+        if (((ix + iy + iz) & 1) != colour) continue;
+        const double nb = 6.0 * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+        x[s] = (b[s] + scale * nb) * inv;
+    }
+}
+
+// r = b - A_l x
+__global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, double scale, const double* __restrict__ x,
+                                                          const double* __restrict__ b, double* __restrict__ r,
+                                                          const CGState* cg) {
+    if (cg->done) return;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int ix, iy, iz;
+        decode3(g, s, ix, iy, iz);
+        r[s] = b[s] - scale * stencil(g, x, s, ix, iy, iz, x[s]);
+    }
+}
+
+// b_c(I) = sum over the 27 fine neighbours of fine point 2I+1 with weights
+// prod_axis (1 at the centre, 1/2 beside it)  (= P^T r)
+__global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, const double* __restrict__ rf,
+                                                          double* __restrict__ bc, const CGState* cg) {
+    if (cg->done) return;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < gc.N; s += gridDim.x * kThreads) {
+        int I, J, K;
+        decode3(gc, s, I, J, K);
+        const int fx = 2 * I + 1, fy = 2 * J + 1, fz = 2 * K + 1;
+        double acc = 0.0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int z = fz + dz;
+            if (z < 0 || z >= gf.nz) continue;
+            const double wz = dz ? 0.5 : 1.0;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int y = fy + dy;
+                if (y < 0 || y >= gf.ny) continue;
+                const double wy = dy ? 0.5 : 1.0;
+                const size_t row = ((size_t)z * gf.ny + y) * gf.nx;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = fx + dx;
+                    if (x < 0 || x >= gf.nx) continue;
+                    acc += wz * wy * (dx ? 0.5 : 1.0) * rf[row + x];
+                }
+            }
+        }
+        bc[s] = acc;
+    }
+}
+
+// Coarse indices and weights of fine index i along an axis of m coarse points.
+__device__ __forceinline__ int interp_axis(int i, int m, int* c, double* w) {
+    if (i & 1) {
+        c[0] = (i - 1) >> 1;
+        w[0] = 1.0;
+        return c[0] < m ? 1 : 0;
+    }
+    int k = 0;
+    const int lo = (i >> 1) - 1, hi = i >> 1;
+    if (lo >= 0 && lo < m) { c[k] = lo; w[k] = 0.5; ++k; }
+    if (hi >= 0 && hi < m) { c[k] = hi; w[k] = 0.5; ++k; }
+    return k;
+}
+
+// x_f += P x_c (trilinear, zero ghosts)
+__global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const double* __restrict__ xc,
+                                                         double* __restrict__ xf, const CGState* cg) {
+    if (cg->done) return;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < gf.N; s += gridDim.x * kThreads) {
+        int x, y, z;
+        decode3(gf, s, x, y, z);
+        int cx[2], cy[2], cz[2];
+        double wx[2], wy[2], wz[2];
+        const int nxw = interp_axis(x, gc.nx, cx, wx), nyw = interp_axis(y, gc.ny, cy, wy),
+                  nzw = interp_axis(z, gc.nz, cz, wz);
+        double acc = 0.0;
+        for (int a = 0; a < nzw; ++a)
+            for (int b = 0; b < nyw; ++b) {
+                const size_t row = ((size_t)cz[a] * gc.ny + cy[b]) * gc.nx;
+                for (int c = 0; c < nxw; ++c) acc += wz[a] * wy[b] * wx[c] * xc[row + cx[c]];
+            }
+        xf[s] += acc;
+    }
+}
+
+// Coarsest level in one CTA: x = 0, then kCoarse red/black sweeps and
+// kCoarse black/red sweeps, a barrier between colours.
+__global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, double scale, double* __restrict__ x,
+                                                              const double* __restrict__ b, const CGState* cg) {
+    if (cg->done) return;
+    const double inv = 1.0 / (6.0 * scale);
+    for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) x[s] = 0.0;
+    __syncthreads();
+    for (int half = 0; half < 4 * kCoarse; ++half) {
+        const int k = half >> 1;  // sweep number
+        const int first = k < kCoarse ? 0 : 1;
+        const int colour = (half & 1) ? 1 - first : first;
+        for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) {
+            int ix, iy, iz;
+            decode3(g, s, ix, iy, iz);
+            if (((ix + iy + iz) & 1) != colour) continue;
+            const double nb = 6.0 * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+            x[s] = (b[s] + scale * nb) * inv;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mg_zero(size_t n, double* __restrict__ x, const CGState* cg) {
+    if (cg->done) return;
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) x[s] = 0.0;
+}
+
+// --------------------------------------------------------------------- PCG kernels
+// b = 4 pi h^2 rho + ghost values; r = b - A x; |b|^2, |r|^2.
+__global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const double* __restrict__ rho,
+                                                        const double* __restrict__ x, double rtol, PoissonBufs pb,
+                                                        Scratch sc) {
+    const double kPi = 3.141592653589793238462643383279502884;
+    double acc[2] = {0.0, 0.0};
+    const double* mp = pb.mp;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int ix, iy, iz;
+        decode3(g, s, ix, iy, iz);
+        const double rx = (ix - 0.5 * (g.nx - 1)) * h, ry = (iy - 0.5 * (g.ny - 1)) * h,
+                     rz = (iz - 0.5 * (g.nz - 1)) * h;
+        double b = 4.0 * kPi * h * h * rho[s];
+        if (ix == 0) b += multipole_value(mp, rx - h, ry, rz);
+        if (ix == g.nx - 1) b += multipole_value(mp, rx + h, ry, rz);
+        if (iy == 0) b += multipole_value(mp, rx, ry - h, rz);
+        if (iy == g.ny - 1) b += multipole_value(mp, rx, ry + h, rz);
+        if (iz == 0) b += multipole_value(mp, rx, ry, rz - h);
+        if (iz == g.nz - 1) b += multipole_value(mp, rx, ry, rz + h);
+        pb.b[s] = b;
+        const double r = b - stencil(g, x, s, ix, iy, iz, x[s]);
+        pb.r[s] = r;
+        acc[0] += b * b;
+        acc[1] += r * r;
+    }
+    block_sum_store<2>(acc, sc.partial + (size_t)blockIdx.x * 2);
+    __shared__ double tot[2];
+    if (grid_total<2>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        CGState* cg = pb.cg;
+        cg->bb = tot[0];
+        cg->rr = tot[1];
+        cg->rz = 0.0;
+        cg->iters = 0;
+        cg->relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        cg->done = (tot[0] == 0.0 || sqrt(tot[1]) <= rtol * sqrt(tot[0])) ? 1 : 0;
+    }
+}
+
+// rz = r . z; beta = rz / rz_old (0 on the first iteration)
+__global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scratch sc) {
+    if (pb.cg->done) return;
+    double acc[1] = {0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
+        acc[0] += pb.r[s] * pb.z[s];
+    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    __shared__ double tot[1];
+    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        CGState* cg = pb.cg;
+        cg->beta = cg->rz > 0.0 ? tot[0] / cg->rz : 0.0;
+        cg->rz = tot[0];
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(kThreads) k_pcg_dir(Grid g, PoissonBufs pb) {
+    if (pb.cg->done) return;
+    const double beta = pb.cg->beta;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
+        pb.p[s] = pb.z[s] + beta * pb.p[s];
+}
+
+// ap = A p; alpha = rz / (p . ap)
+__global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scratch sc) {
+    if (pb.cg->done) return;
+    double acc[1] = {0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        int ix, iy, iz;
+        decode3(g, s, ix, iy, iz);
+        const double a = stencil(g, pb.p, s, ix, iy, iz, pb.p[s]);
+        pb.ap[s] = a;
+        acc[0] += pb.p[s] * a;
+    }
+    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    __shared__ double tot[1];
+    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        pb.cg->pap = tot[0];
+        pb.cg->alpha = pb.cg->rz / tot[0];
+    }
+}
+
+// x += alpha p; r -= alpha ap; convergence test on |r| / |b|
+__global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
+                                                         Scratch sc) {
+    if (pb.cg->done) return;
+    const double alpha = pb.cg->alpha;
+    double acc[1] = {0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+        x[s] += alpha * pb.p[s];
+        const double r = pb.r[s] - alpha * pb.ap[s];
+        pb.r[s] = r;
+        acc[0] += r * r;
+    }
+    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    __shared__ double tot[1];
+    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+        CGState* cg = pb.cg;
+        cg->rr = tot[0];
+        cg->iters += 1;
+        cg->relres = sqrt(tot[0] / cg->bb);
+        cg->done = (sqrt(tot[0]) <= rtol * sqrt(cg->bb)) ? 1 : 0;
+    }
+}
+
+cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* tmp0, const CGState* cg, int ge,
+                   cudaStream_t st, uint64_t* nl) {
+    // level 0 works on (x = z0, b = r0, r = tmp0); levels >= 1 on their own arrays
+    auto X = [&](int l) { return l == 0 ? z0 : H.lev[l].x; };
+    auto B = [&](int l) -> const double* { return l == 0 ? r0 : H.lev[l].b; };
+    auto R = [&](int l) { return l == 0 ? tmp0 : H.lev[l].r; };
+    const int L = H.nlev;
+    for (int l = 0; l < L; ++l) {
+        const Grid& g = H.lev[l].g;
+        const double sc = (double)(1 << l);
+        const int gl = grid_for(g.N, ge);
+        if (l == L - 1 && g.N <= kCoarseSites) {
+            k_mg_coarse_solve<<<1, kThreads, 0, st>>>(g, sc, X(l), B(l), cg);
+            ++*nl;
+            break;
+        }
+        k_mg_zero<<<gl, kThreads, 0, st>>>(g.N, X(l), cg);
+        ++*nl;
+        if (l == L - 1) {
+            for (int k = 0; k < kCoarse; ++k) {
+                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+            }
+            for (int k = 0; k < kCoarse; ++k) {
+                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+            }
+            *nl += 4 * kCoarse;
+            break;
+        }
+        for (int k = 0; k < kPre; ++k) {
+            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+        }
+        k_mg_residual<<<gl, kThreads, 0, st>>>(g, sc, X(l), B(l), R(l), cg);
+        const Grid& gc = H.lev[l + 1].g;
+        k_mg_restrict<<<grid_for(gc.N, ge), kThreads, 0, st>>>(g, gc, R(l), H.lev[l + 1].b, cg);
+        *nl += 2 * kPre + 3;
+    }
+    for (int l = L - 2; l >= 0; --l) {
+        const Grid& g = H.lev[l].g;
+        const double sc = (double)(1 << l);
+        const int gl = grid_for(g.N, ge);
+        k_mg_prolong<<<gl, kThreads, 0, st>>>(g, H.lev[l + 1].g, X(l + 1), X(l), cg);
+        for (int k = 0; k < kPre; ++k) {
+            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+        }
+        *nl += 1 + 2 * kPre;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int mg_levels(int nx, int ny, int nz) {
+    int l = 1;
+    while (l < kMaxLevels && nx / 2 >= 2 && ny / 2 >= 2 && nz / 2 >= 2) {
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        ++l;
+    }
+    return l;
+}
+
+size_t mg_coarse_doubles(int nx, int ny, int nz) {
+    size_t total = 0;
+    const int L = mg_levels(nx, ny, nz);
+    for (int l = 1; l < L; ++l) {
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        total += 3 * (size_t)nx * ny * nz;
+    }
+    return total;
+}
+
+MGHierarchy make_hierarchy(const Grid& fine, double* coarse) {
+    MGHierarchy H;
+    H.nlev = mg_levels(fine.nx, fine.ny, fine.nz);
+    H.lev[0].g = fine;
+    int nx = fine.nx, ny = fine.ny, nz = fine.nz;
+    for (int l = 1; l < H.nlev; ++l) {
+        nx /= 2;
+        ny /= 2;
+        nz /= 2;
+        H.lev[l].g = make_grid(nx, ny, nz);
+        const size_t n = (size_t)nx * ny * nz;
+        H.lev[l].x = coarse;
+        H.lev[l].b = coarse + n;
+        H.lev[l].r = coarse + 2 * n;
+        coarse += 3 * n;
+    }
+    return H;
+}
+
+cudaError_t launch_poisson_start(const Grid& g, double h, const double* rho, double* x, double rtol,
+                                 const PoissonBufs& pb, const Scratch& sc, cudaStream_t st) {
+    const int cap = red_cap(sc, 2);
+    if (cap < 1) return cudaErrorInvalidValue;
+    k_pcg_start<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, x, rtol, pb, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int iters, const PoissonBufs& pb,
+                                   const MGHierarchy& H, const Scratch& sc, cudaStream_t st) {
+    const int cap = red_cap(sc, 1);
+    if (cap < 1) return cudaErrorInvalidValue;
+    const int gr = grid_for(g.N, cap);
+    const int ge = num_sms() * 8;
+    uint64_t nl = 0;
+    for (int i = 0; i < iters; ++i) {
+        cudaError_t e = vcycle(H, pb.r, pb.z, pb.tmp, pb.cg, ge, st, &nl);
+        if (e != cudaSuccess) return e;
+        k_pcg_rz<<<gr, kThreads, 0, st>>>(g, pb, sc);
+        k_pcg_dir<<<grid_for(g.N, ge), kThreads, 0, st>>>(g, pb);
+        k_pcg_ap<<<gr, kThreads, 0, st>>>(g, pb, sc);
+        k_pcg_update<<<gr, kThreads, 0, st>>>(g, x, rtol, pb, sc);
+        nl += 4;
+    }
+    count_launches(nl);
+    return cudaGetLastError();
+}
+
+}  // namespace lbks

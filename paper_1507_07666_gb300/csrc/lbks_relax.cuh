@@ -18,6 +18,12 @@
 
 #include <algorithm>
 
+// Minimum resident blocks per SM requested from the register allocator for
+// the stream-collide kernel (a tuning knob; 1 lets it use up to 255 registers).
+#ifndef LBKS_RELAX_MIN_BLOCKS
+#define LBKS_RELAX_MIN_BLOCKS 1
+#endif
+
 namespace lbks {
 
 template <typename T>
@@ -67,7 +73,8 @@ __device__ __forceinline__ uint32_t source_index(const Grid& g, uint32_t s, int 
 // all NO orbitals of a site; psi epilogue; overlap partials; the last block
 // turns S into Lambda and the next step's scale sigma.
 template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads) k_stream_collide(Grid g, Coef c, RelaxIO io, Scratch sc) {
+__global__ void __launch_bounds__(kThreads, LBKS_RELAX_MIN_BLOCKS) k_stream_collide(Grid g, Coef c, RelaxIO io,
+                                                                                  Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
     const T* __restrict__ fin = static_cast<const T*>(io.f_in);
     const T* __restrict__ uin = static_cast<const T*>(io.u_in);

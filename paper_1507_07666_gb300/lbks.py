@@ -52,6 +52,22 @@ class lbks_energy_terms(ctypes.Structure):
                 ("n_electrons", ctypes.c_double)]
 
 
+class lbks_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("h", ctypes.c_double),
+                ("n_orb", ctypes.c_int), ("n_atoms", ctypes.c_int), ("xyz", ctypes.POINTER(ctypes.c_double)),
+                ("Z", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int), ("n_inner", ctypes.c_int),
+                ("e_tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+
+
+class lbks_timing(ctypes.Structure):
+    _fields_ = [("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+
+class lbks_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("pooled", ctypes.c_int),
+                ("completed", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+
 _vp, _d, _i, _sz = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
 _dp = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
@@ -69,6 +85,13 @@ _SIGS = {
     "lbks_get_density": (_i, [_vp, _dp, _sz]),
     "lbks_get_orbitals": (_i, [_vp, _dp, _sz]),
     "lbks_get_potential": (_i, [_vp, _i, _dp, _sz]),
+    "lbks_server_create": (_i, [ctypes.POINTER(lbks_params), _sz, _i, ctypes.POINTER(_vp)]),
+    "lbks_server_destroy": (_i, [_vp]),
+    "lbks_submit": (_i, [_vp, ctypes.POINTER(lbks_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "lbks_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(lbks_result), ctypes.POINTER(lbks_timing),
+                       ctypes.POINTER(_i)]),
+    "lbks_server_wait": (_i, [_vp, ctypes.c_uint64, _d]),
+    "lbks_server_get_stats": (_i, [_vp, ctypes.POINTER(lbks_server_stats)]),
     "lbks_relax_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                              _vp]),
     "lbks_relax_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -266,6 +289,54 @@ def lbks_lda(n_sites, rho, eps, v, stream=None):
     import torch
     _check(_lib.lbks_lda(n_sites, _ptr(rho, torch.float64), _ptr(eps, torch.float64), _ptr(v, torch.float64),
                          _stream(stream)))
+
+
+def lbks_server_create(params=None, budget_bytes=0, max_slots=4):
+    handle = ctypes.c_void_p()
+    _check(_lib.lbks_server_create(ctypes.byref(params) if params is not None else None, budget_bytes, max_slots,
+                                   ctypes.byref(handle)))
+    return handle
+
+
+def lbks_server_destroy(handle):
+    _check(_lib.lbks_server_destroy(handle))
+
+
+def lbks_submit(handle, n, h, xyz, Z, n_orb=None, precision=-1, n_inner=0, e_tol=0.0, max_cycles=0) -> int:
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    Z = np.ascontiguousarray(Z, dtype=np.float64).ravel()
+    if n_orb is None:
+        n_orb = int(round(Z.sum())) // 2
+    req = lbks_request(int(n[0]), int(n[1]), int(n[2]), float(h), int(n_orb), len(Z), xyz.ctypes.data_as(_dp),
+                       Z.ctypes.data_as(_dp), int(precision), int(n_inner), float(e_tol), int(max_cycles))
+    rid = ctypes.c_uint64()
+    _check(_lib.lbks_submit(handle, ctypes.byref(req), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def lbks_poll(handle, rid, n_orb=MAX_ORB):
+    """None while running; (result dict, timing dict) once done (raises on a failed solve)."""
+    r, tm, done = lbks_result(), lbks_timing(), ctypes.c_int()
+    code = _lib.lbks_poll(handle, ctypes.c_uint64(rid), ctypes.byref(r), ctypes.byref(tm), ctypes.byref(done))
+    if code != OK and not done.value:
+        _check(code)
+    if not done.value:
+        return None
+    res = _result_dict(r, n_orb)
+    res["status"] = code
+    if code not in (OK, ENOTCONV):
+        _check(code)
+    return res, {"queue_s": tm.queue_s, "run_s": tm.run_s, "latency_s": tm.latency_s}
+
+
+def lbks_server_wait(handle, rid, timeout_s=600.0):
+    _check(_lib.lbks_server_wait(handle, ctypes.c_uint64(rid), float(timeout_s)))
+
+
+def lbks_server_get_stats(handle) -> dict:
+    st = lbks_server_stats()
+    _check(_lib.lbks_server_get_stats(handle, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in lbks_server_stats._fields_}
 
 
 # ------------------------------------------------------------- convenience
