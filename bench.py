@@ -47,6 +47,19 @@ WORKLOADS = {
     "he_24": W.he_24,
     "h2o_96": W.water_96,
 }
+# workloads too large for a full solve per bench step: one step = one SCF cycle
+# (n_inner relaxation steps, density, Hartree, LDA, orthonormalisation, energies)
+# continuing from the previous cycle
+CYCLES = {"h2o8_256": W.cluster_256}
+# the oracle cannot hold the cluster's 256^3 populations in host memory: its
+# CPU baseline is the same molecule on a coarser grid of the same box
+# (batched and served workloads: one water geometry at 96^3)
+ORACLE_SAMPLE_OF = {"h2o8_256": W.cluster_sample, "water_scan_64": W.water_96, "serving_mix": W.water_96}
+SERVING = {"serving_mix": 48}  # requests of the mixed stream (Poisson arrivals, mean 200/s, seed 0)
+BATCHES = {
+    # 64 seeded water geometries (O-H ~ U[1.6, 2.0] bohr, HOH ~ U[95, 115] deg), 96^3 grid, h = 0.2
+    "water_scan_64": (64, 0),
+}
 
 
 def parse_args():
@@ -55,8 +68,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lbks", "reference"], default="lbks")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ch4_128")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CYCLES) + sorted(BATCHES) + sorted(SERVING), default="ch4_128")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent solve slots")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel-only", action="store_true",
@@ -97,7 +111,8 @@ print(json.dumps({{"times": times, "updates_per_step": no * n[0] * n[1] * n[2]}}
 
 
 def run_oracle_sample(workload: str, seconds: float, min_steps: int, max_steps: int):
-    code = ORACLE_SAMPLE.format(root=ROOT, wl=WORKLOADS[workload].__name__, seconds=seconds,
+    fn = WORKLOADS[workload] if workload in WORKLOADS else ORACLE_SAMPLE_OF[workload]
+    code = ORACLE_SAMPLE.format(root=ROOT, wl=fn.__name__, seconds=seconds,
                                 min_steps=min_steps, max_steps=max_steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
@@ -110,7 +125,8 @@ def cpu_baseline(workload: str, seconds: float):
     s = run_oracle_sample(workload, seconds, 2, 1000)
     t = sum(s["times"])
     return {"value": len(s["times"]) * s["updates_per_step"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(s['times'])} relaxation steps (Eq. KSLB, all orbitals) of the {workload} workload from "
+            "sample": f"{len(s['times'])} relaxation steps (Eq. KSLB, all orbitals) of the "
+                      f"{(WORKLOADS.get(workload) or ORACLE_SAMPLE_OF[workload])().name} workload from "
                       f"its Gaussian start, FP64 numpy, one thread, {t:.1f} s"}
 
 
@@ -118,7 +134,7 @@ def main_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w = WORKLOADS[args.workload]()
+    w = (WORKLOADS[args.workload] if args.workload in WORKLOADS else ORACLE_SAMPLE_OF[args.workload])()
     s = run_oracle_sample(args.workload, 0.0, args.warmup + args.steps, args.warmup + args.steps)
     times = s["times"][args.warmup:]
     t = sum(times)
@@ -208,15 +224,16 @@ def recorded_traffic():
 def time_stream_collide(torch, lbks, w, prec, stream, launches=20):
     """Average duration of the fused stream-collide kernel in the solver's own
     launch configuration, CUDA events on the launching stream."""
-    T = torch.float32 if prec == lbks.FP32 else torch.float64
+    T = {lbks.FP32: torch.float32, lbks.FP64: torch.float64, lbks.BF16: torch.bfloat16}[prec]
+    P = torch.float64 if prec == lbks.FP64 else torch.float32
     nx, ny, nz = w.n
     N = nx * ny * nz
     no = w.n_orb
     with torch.cuda.stream(stream):
         fa = torch.rand((no, 19, nz, ny, nx), dtype=T, device="cuda")
         fb = torch.empty_like(fa)
-        u = torch.rand((max(no - 1, 1), nz, ny, nx), dtype=T, device="cuda") * 0.1
-        psi = torch.empty((no, nz, ny, nx), dtype=T, device="cuda")
+        u = torch.rand((max(no - 1, 1), nz, ny, nx), dtype=P, device="cuda") * 0.1
+        psi = torch.empty((no, nz, ny, nx), dtype=P, device="cuda")
         V = -torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda")
         sig = torch.full((no,), 1e-3, dtype=torch.float64, device="cuda")
         S = torch.empty((no, no), dtype=torch.float64, device="cuda")
@@ -248,13 +265,140 @@ def main_kernel_only(args):
     w = WORKLOADS[args.workload]()
     if args.kernel_n:
         w.n = (args.kernel_n,) * 3
-    prec = lbks.FP32 if args.precision == "fp32" else lbks.FP64
+    prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
     stream = torch.cuda.Stream()
     ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
-    elem = 4 if prec == lbks.FP32 else 8
+    elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
     gbs = 38 * elem * units / (ms / 1e3) / 1e9
     print(json.dumps({"kernel": "k_stream_collide", "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
                       "ms_per_launch": ms, "algorithmic_GBps": gbs, "launches": args.launches}), flush=True)
+    return 0
+
+
+def main_batch(args):
+    """Batched water scan: all geometries relax in the same launches; one
+    bench step = one batched solve of every geometry to |dE| < 1e-6 Ha."""
+    import torch
+    from paper_1507_07666_gb300 import build as build_mod
+    build_mod.build()
+    from paper_1507_07666_gb300 import lbks
+    count, seed = BATCHES[args.workload]
+    mols = W.water_scan(count, seed)
+    w = W.water_96(mols[0])
+    prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
+    b = lbks.Batch(w.n, w.h, w.n_orb, count, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
+                   omega=w.omega, mix=w.mix, max_cycles=w.max_cycles)
+    stream = torch.cuda.Stream()
+    geoms = [(m.xyz, m.Z) for m in mols]
+
+    def solve():
+        b.set_geometries(geoms)
+        return b.scf(stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = lbks.lbks_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [solve() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lbks.lbks_kernel_launches() - l0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    updates = sum(r["steps"] for res in results for r in res) * w.n_orb * w.sites
+    last = results[-1]
+    elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
+    line = {
+        "metric": METRIC, "value": updates / (elapsed_ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {lbks.FP32: "f32", lbks.FP64: "f64", lbks.BF16: "bf16-storage/f32"}[prec], "data": "synthetic",
+        "config": {"workload": f"batched water scan: {count} geometries (seed {seed}), 96^3, h=0.2, one launch "
+                               "per relaxation step for all geometries",
+                   "grid": list(w.n), "n_orb": w.n_orb, "systems": count, "n_inner": w.n_inner,
+                   "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 19 * elem * w.n_orb * w.sites * count / 1e9)},
+        "solves_per_s": count * args.steps / (elapsed_ms / 1e3),
+        "batch": {"converged": sum(r["converged"] for r in last), "cycles_max": max(r["cycles"] for r in last),
+                  "cycles_min": min(r["cycles"] for r in last),
+                  "E_total_range": [min(r["E_total"] for r in last), max(r["E_total"] for r in last)]},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def _serve_arm(lbks, reqs, precision, slots, warm):
+    """Replays the arrival stream against a server; returns per-request
+    latencies (s), the makespan and the results."""
+    srv = lbks.lbks_server_create(lbks.lbks_params_default(precision=precision), 0, slots)
+    try:
+        for _, w in warm:  # first use of each shape: allocation and graph capture
+            rid = lbks.lbks_submit(srv, w.n, w.h, w.molecule.xyz, w.molecule.Z, n_inner=w.n_inner)
+            lbks.lbks_server_wait(srv, rid, 600.0)
+            lbks.lbks_poll(srv, rid)
+        t0 = time.perf_counter()
+        ids = []
+        for t_arr, w in reqs:
+            delay = t0 + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(lbks.lbks_submit(srv, w.n, w.h, w.molecule.xyz, w.molecule.Z, n_inner=w.n_inner))
+        out = {}
+        while len(out) < len(ids):
+            for rid in ids:
+                if rid not in out:
+                    r = lbks.lbks_poll(srv, rid)
+                    if r is not None:
+                        out[rid] = r
+            time.sleep(0.001)
+        makespan = time.perf_counter() - t0
+    finally:
+        lbks.lbks_server_destroy(srv)
+    lat = sorted(out[rid][1]["latency_s"] for rid in ids)
+    return lat, makespan, [out[rid][0] for rid in ids]
+
+
+def main_serving(args):
+    """Continuous-batching request loop on a mixed stream of solves against
+    the plain single-solve FP64 path (one slot, FP64) on the same stream."""
+    import torch
+    from paper_1507_07666_gb300 import build as build_mod
+    build_mod.build()
+    from paper_1507_07666_gb300 import lbks
+    reqs = W.serving_stream(SERVING[args.workload], 200.0, 0)
+    kinds = {}
+    for t, w in reqs:
+        kinds.setdefault(w.name, (t, w))
+    warm = list(kinds.values())
+    pct = lambda lat, q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    lat, span, res = _serve_arm(lbks, reqs, lbks.BF16, args.slots, warm)
+    lat64, span64, res64 = _serve_arm(lbks, reqs, lbks.FP64, 1, warm)
+    de = max(abs(a["E_total"] - b["E_total"]) for a, b in zip(res, res64))
+    odd = [{"request": i, "kind": w.name, "h": round(w.h, 4), "converged": a["converged"], "status": a["status"],
+            "cycles": a["cycles"], "E_total": a["E_total"], "E_total_fp64": b["E_total"],
+            "fp64_converged": b["converged"]}
+           for i, ((_, w), a, b) in enumerate(zip(reqs, res, res64))
+           if not a["converged"] or not b["converged"] or abs(a["E_total"] - b["E_total"]) > 1e-4]
+    line = {
+        "metric": "solves/s (served mixed stream)", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-storage/f32", "data": "synthetic",
+        "config": {"workload": f"served stream: {len(reqs)} requests, Poisson arrivals 200/s (seed 0), uniform over "
+                               "H2 48^3, He 48^3, LiH 64^3, H2O 96^3, CH4 128^3, h ~ U[0.2, 0.25], jitter 0.05 bohr",
+                   "slots": args.slots, "precision": "BF16 populations + FP32 polish"},
+        "latency_s": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": lat[-1]},
+        "plain_fp64_single_slot": {"solves_per_s": len(reqs) / span64, "p50": pct(lat64, 0.5), "p99": pct(lat64, 0.99)},
+        "max_abs_dE_vs_fp64_Ha": de,
+        "converged": sum(r["converged"] for r in res),
+        "fp64_converged": sum(r["converged"] for r in res64),
+        "outliers": odd[:12],
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -273,8 +417,9 @@ def main_lbks(args):
         dist.barrier()
     from paper_1507_07666_gb300 import lbks
 
-    w = WORKLOADS[args.workload]()
-    prec = lbks.FP32 if args.precision == "fp32" else lbks.FP64
+    per_cycle = args.workload in CYCLES
+    w = (CYCLES if per_cycle else WORKLOADS)[args.workload]()
+    prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
     sysm = lbks.System(w.n, w.h, w.n_orb, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
                        omega=w.omega, mix=w.mix, max_cycles=w.max_cycles)
     xyz, Z = w.molecule.xyz, w.molecule.Z
@@ -282,9 +427,13 @@ def main_lbks(args):
     stream = torch.cuda.Stream()
 
     def solve():
+        if per_cycle:
+            return sysm.scf_cycles(1, stream)
         sysm.set_geometry(xyz, Z)
         return sysm.scf(stream)
 
+    if per_cycle:
+        sysm.set_geometry(xyz, Z)
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
@@ -316,7 +465,7 @@ def main_lbks(args):
     for _ in range(max(1, args.steps)):
         t0 = time.perf_counter()
         sysm.set_geometry(xyz, Z)
-        r = sysm.scf(stream)
+        r = sysm.scf_cycles(1, stream) if per_cycle else sysm.scf(stream)
         rho = sysm.density()
         t_e2e += time.perf_counter() - t0
         e2e_updates += r["steps"] * w.n_orb * N
@@ -324,14 +473,22 @@ def main_lbks(args):
            "h2d_bytes_per_step": int(xyz.nbytes + Z.nbytes),
            "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
 
+    sysm.close()  # the kernel timing below allocates its own population pair
+
     # dominant kernel alone, same launch configuration
     ms, units = time_stream_collide(torch, lbks, w, prec, stream)
-    elem = 4 if prec == lbks.FP32 else 8
-    bytes_per_launch = 38 * elem * units
+    elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
+    wide = w.n_orb > 8
+    psi_elem = 8 if prec == lbks.FP64 else 4
+    # more than eight orbitals: the timed step is two kernels, stream-collide
+    # and the overlap (Gram) kernel that reads the orbitals it wrote back
+    bytes_per_launch = (38 * elem + (2 * psi_elem if wide else 0)) * units
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_launch / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(), "kernel": "k_stream_collide",
+                "traffic": None if wide else recorded_traffic(),
+                "kernel": ("k_stream_collide_wide + %s (one relaxation step)"
+                           % ("k_gram_wide" if prec == lbks.FP64 else "k_gram_tc")) if wide else "k_stream_collide",
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms,
                 "peak_source": f"hbm_gbs of {peak_kind}"}
 
@@ -341,11 +498,15 @@ def main_lbks(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == lbks.FP32 else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {lbks.FP32: "f32", lbks.FP64: "f64", lbks.BF16: "bf16-storage/f32"}[prec],
         "data": "synthetic",
-        "config": {"workload": w.name + " single solve", "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
-                   "precision": ("FP32 populations and collide, FP64 overlaps/energies/Poisson"
-                                 if prec == lbks.FP32 else "FP64 throughout"),
+        "config": {"workload": w.name + (" SCF cycles (one per step, from the superposition start)" if per_cycle
+                                          else " single solve"), "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
+                   "precision": {lbks.FP32: "FP32 populations and collide, FP64 overlaps/energies/Poisson",
+                                 lbks.FP64: "FP64 throughout",
+                                 lbks.BF16: "BF16 populations, FP32 collide, FP32 polish below |dE| 1e-4, "
+                                            "FP64 overlaps/energies/Poisson"}[prec],
                    "n_inner": w.n_inner, "e_tol": w.e_tol,
                    "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * elem * units / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -361,7 +522,6 @@ def main_lbks(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
     print(json.dumps(line), flush=True)
-    sysm.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -375,6 +535,10 @@ def main():
         return main_reference(args)
     if args.kernel_only:
         return main_kernel_only(args)
+    if args.workload in BATCHES:
+        return main_batch(args)
+    if args.workload in SERVING:
+        return main_serving(args)
     return main_lbks(args)
 
 

@@ -30,9 +30,10 @@
  *    cudaStream_t (NULL = legacy default stream); the library never
  *    destroys it.  Device-pointer entry points are asynchronous on that
  *    stream unless stated otherwise.
- *  - Element type of population / orbital / W-field arrays follows
- *    `precision`: LBKS_FP64 -> double, LBKS_FP32 -> float.  Potentials,
- *    densities, overlaps and energies are always double.
+ *  - Element type of population arrays follows `precision`: LBKS_FP64 ->
+ *    double, LBKS_FP32 -> float, LBKS_BF16 -> bfloat16 (__nv_bfloat16);
+ *    orbital and W-field arrays are double for LBKS_FP64, float otherwise.
+ *    Potentials, densities, overlaps and energies are always double.
  *
  * D3Q19 velocity order (a data layout shared with callers):
  *    p:  0 ( 0, 0, 0)
@@ -53,7 +54,7 @@
 extern "C" {
 #endif
 
-#define LBKS_MAX_ORB 8 /* orbitals per system handled by this build */
+#define LBKS_MAX_ORB 64 /* orbitals per system handled by this build (above 8: separate Gram kernel) */
 
 enum lbks_status {
     LBKS_OK = 0,
@@ -68,7 +69,9 @@ enum lbks_status {
 
 enum lbks_precision {
     LBKS_FP64 = 0, /* populations, collide and orbitals in double: the plain path */
-    LBKS_FP32 = 1  /* populations, collide and orbitals in float; overlaps, energies, Poisson in double */
+    LBKS_FP32 = 1, /* populations, collide and orbitals in float; overlaps, energies, Poisson in double */
+    LBKS_BF16 = 2  /* populations stored as bfloat16; collide, orbitals and W field in float;
+                      overlaps, energies, Poisson in double */
 };
 
 /* Solver controls.  lbks_params_default() fills the defaults in brackets. */
@@ -84,6 +87,9 @@ typedef struct lbks_params {
     double softening;    /* nuclear softening a (bohr); <= 0 means a = h [0] */
     double poisson_rtol; /* CG relative residual target [1e-11] */
     int poisson_max_iter;/* [20000] */
+    double polish_tol;   /* LBKS_BF16 only: once every running system's |dE| < polish_tol the
+                            populations are widened to FP32 and the solve finishes in FP32
+                            (bfloat16 rounding would otherwise bound the accuracy); <= 0 never [1e-4] */
 } lbks_params;
 
 void lbks_params_default(lbks_params* p);
@@ -104,8 +110,10 @@ typedef struct lbks_system lbks_system;
 
 /* Allocates all device state of one system on the current device: two
  * population buffers of n_orb*19*N elements, orbitals, W field, potentials,
- * CG vectors and reduction scratch.  EINVAL: nx, ny, nz < 2, h <= 0,
- * n_orb < 1 or > LBKS_MAX_ORB, bad params.  ENOMEM: cudaMalloc failed. */
+ * CG vectors and reduction scratch.  Up to 8 orbitals the overlap products
+ * are fused into the stream-collide kernel; above, a separate tiled Gram
+ * kernel forms them.  EINVAL: nx, ny, nz < 2, h <= 0, n_orb < 1 or >
+ * LBKS_MAX_ORB, bad params.  ENOMEM: cudaMalloc failed. */
 int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb,
                        lbks_system** out);
 int lbks_destroy_system(lbks_system* sys);
@@ -139,8 +147,11 @@ typedef struct lbks_result {
  * on `stream`. */
 int lbks_scf(lbks_system* sys, void* stream, lbks_result* out);
 
-/* Runs exactly n cycles (no convergence test); result as lbks_scf. */
+/* Runs exactly n cycles (no convergence test); result as lbks_scf (one
+ * result per system of a batched handle). */
 int lbks_scf_cycles(lbks_system* sys, int n, void* stream, lbks_result* out);
+
+
 
 typedef struct lbks_energy_terms {
     double T_s, E_ext, E_H, E_xc, E_nn, E_total;
@@ -159,6 +170,29 @@ int lbks_get_density(const lbks_system* sys, double* host, size_t cap);
 int lbks_get_orbitals(const lbks_system* sys, double* host, size_t cap);
 int lbks_get_potential(const lbks_system* sys, int which /*0 V_in,1 V_out,2 V_H,3 V_ext*/,
                        double* host, size_t cap);
+
+/* ---------------------------------------------------------------- batching
+ * A batched handle holds n_systems systems of one grid shape, orbital count
+ * and parameter set (e.g. a scan over geometries).  Every kernel of the
+ * relaxation cycle, the Hartree solve and the reductions covers all systems
+ * in one launch (system = blockIdx.y), and each relaxation cycle is one
+ * CUDA-graph replay.  Systems advance in lock step; one whose |dE| drops
+ * below e_tol stops and is skipped by every later launch.  Per-system
+ * results equal those of single-system handles up to the summation order of
+ * the reductions (block counts differ). */
+int lbks_create_batch(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, int n_systems,
+                      lbks_system** out);
+size_t lbks_batch_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb, int n_systems);
+/* Stores system `system`'s nuclei (checks as lbks_set_geometry); nothing runs. */
+int lbks_batch_set_geometry(lbks_system* sys, int system, int n_atoms, const double* xyz, const double* Z);
+/* Gaussian starts and the first evaluation of every system (all must have
+ * geometry).  Synchronous. */
+int lbks_batch_init(lbks_system* sys);
+/* Self-consistent loop of all systems; out[n_systems].  ENOTCONV if some
+ * system did not converge within max_cycles (results still filled). */
+int lbks_batch_scf(lbks_system* sys, void* stream, lbks_result* out);
+int lbks_batch_energy(const lbks_system* sys, int system, lbks_energy_terms* out);
+int lbks_batch_get_density(const lbks_system* sys, int system, double* host, size_t cap);
 
 /* ------------------------------------------------------------------ serving
  * A request loop with continuous batching.  Each request is one closed-shell
@@ -276,6 +310,19 @@ int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, do
  * u_(j-1)(r) = -omega sum_{k<j} lambda_jk psi_k(r), j = 1..n_orb-1. */
 int lbks_w_field(int precision, size_t n_sites, int n_orb, double omega,
                  const void* psi_dev, const double* lambda_dev, void* u_out_dev, void* stream);
+
+/* Overlap matrix S = h^3 psi psi^T (the inner products behind sigma_j and
+ * lambda_jk of Sec. 3 and behind the orthonormalisation), FP64 result.
+ * psi: n_orb * n_sites values (FP64 for LBKS_FP64, else FP32), orbital-major.
+ * S: n_orb^2 doubles, row-major, both triangles written.
+ * tensor_cores = 0: SIMT products summed in FP64 (the orthonormalising
+ * overlap of the solver).  tensor_cores = 1 and FP32 orbitals: the tcgen05
+ * kernel of the solver's per-step overlap for more than eight orbitals --
+ * each value split into bf16 hi + lo, FP32 accumulation in tensor memory over
+ * at most 512 sites (truncating: a relative bias below ~1.5e-6 on S_jj), FP64
+ * beyond; ignored for LBKS_FP64.  Asynchronous on stream. */
+int lbks_overlap(int precision, size_t n_sites, int n_orb, double h, const void* psi_dev,
+                 double* S_dev, int tensor_cores, void* stream);
 
 /* Cholesky S = L L^T of an n x n SPD matrix on the device (FP64, one CTA),
  * writes L^{-1} (lower, row-major).  Sets *status_dev = 0, or j+1 if the

@@ -94,14 +94,20 @@ namespace {
 const PrecisionOps* ops_for(int precision) {
     if (precision == LBKS_FP64) return &ops_f64();
     if (precision == LBKS_FP32) return &ops_f32();
+    if (precision == LBKS_BF16) return &ops_bf16();
     return nullptr;
 }
 
-constexpr int kScratchVals = kMaxOrb * kMaxOrb + kMaxOrb;  // largest reduction width
+constexpr int kScratchVals = kMaxOrb * kMaxOrb + kMaxOrb;  // largest reduction width up to kMaxOrb orbitals
+// Largest reduction width of a handle with n_orb orbitals.
+int scratch_vals(int n_orb) { return n_orb <= kMaxOrb ? kScratchVals : n_orb * (n_orb + 1) / 2 + n_orb; }
+// Doubles of the energy-matrix output per system.
+int emat_stride(int n_orb) { return n_orb <= kMaxOrb ? kEmatStride : kEmatWideStride; }
 
 cudaError_t alloc_scratch(Scratch& sc) {
     sc.max_blocks = num_sms() * 8;
-    sc.max_vals = kScratchVals;
+    sc.max_vals = scratch_vals(kMaxOrbWide);
+    sc.systems = 1;
     cudaError_t e = cudaMalloc(&sc.partial, sizeof(double) * (size_t)sc.max_blocks * sc.max_vals);
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&sc.counter, sizeof(unsigned) * 4);
@@ -190,9 +196,12 @@ bool valid_params(const lbks_params* p) {
 
 using namespace lbks;
 
+// One handle holds B >= 1 systems of the same shape and parameters; each
+// system's arrays sit consecutively (see PrecisionOps).  Single-system calls
+// address system 0.
 struct lbks_system {
     lbks_params prm;
-    int nx, ny, nz, n_orb;
+    int nx, ny, nz, n_orb, B;
     double h, dt, a;
     Grid g;
     Coef c;
@@ -200,49 +209,65 @@ struct lbks_system {
     size_t N;
     int dev;
     void* f[2] = {nullptr, nullptr};
+    void* f_wide[2] = {nullptr, nullptr};  // FP32 populations of the BF16 polish phase
+    bool polished = false;
     int cur = 0;
     void* u = nullptr;
     void* psi = nullptr;
     double *vin = nullptr, *vout = nullptr, *vext = nullptr, *vh = nullptr, *rho = nullptr;
-    double* pvec = nullptr;  // b, r, p, ap, z, tmp, then the multigrid levels
+    double* pvec = nullptr;  // b, r, p, ap, z, tmp (B*N each), then the multigrid levels
     CGState* cg = nullptr;
     MGHierarchy mg;
     cudaGraphExec_t poisson_graph = nullptr;  // kPoissonChunk preconditioned CG iterations
     uint64_t poisson_nodes = 0;
-    double* small = nullptr;  // S, lam, sigma, Linv, e4, emat, mp, atoms
-    int* status = nullptr;
+    double* small = nullptr;
     double *S, *lam, *sigma, *Linv, *e4, *emat, *mp, *atoms;
+    int* ints = nullptr;  // status[B], active[B], atom counts[B]
+    int *status, *active, *counts;
+    OrbitalStart* starts = nullptr;  // [B][n_orb]
     Scratch sc;
-    double* host = nullptr;  // pinned: e4[4], emat[NO^2+NO], status, cg
+    double* host = nullptr;  // pinned readback area
     cudaStream_t st = nullptr;   // internal stream for synchronous calls
     cudaStream_t cap = nullptr;  // capture stream
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
-    std::vector<double> xyz, Z;
-    bool has_geometry = false;
-    lbks_energy_terms terms;
+    std::vector<std::vector<double>> xyz, Z;  // per system
+    std::vector<int> has_atoms;
+    bool ready = false;  // orbitals and energies initialised
+    std::vector<lbks_energy_terms> terms;
     int poisson_iters = 0;
 };
 
 namespace {
 
-constexpr int kSmall = 4 * kMaxOrb * kMaxOrb + 4 + kScratchVals + 16;
-constexpr int kMaxAtoms = 256;
-
+// Doubles per system of the small device arrays (S, Lambda, L^-1, sigma,
+// energy integrals, energy matrix, multipoles).
+size_t small_per_sys(int no) { return 3 * (size_t)no * no + no + kE4Stride + emat_stride(no) + kMpStride; }
 constexpr int kPoissonChunk = 2;  // PCG iterations per graph launch between convergence checks
+// Doubles per system of the pinned readback area: energy integrals + matrix + status slot.
+size_t host_per_sys(int no) { return kE4Stride + emat_stride(no) + 2; }
 
-PoissonBufs poisson_bufs(double* v, size_t N, CGState* cg, double* mp) {
-    return PoissonBufs{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, cg, mp};
+PoissonBufs poisson_bufs(double* v, size_t n, CGState* cg, double* mp) {
+    return PoissonBufs{v, v + n, v + 2 * n, v + 3 * n, v + 4 * n, v + 5 * n, cg, mp};
+}
+
+double* host_e4(lbks_system* s, int i) { return s->host + (size_t)i * host_per_sys(s->n_orb); }
+double* host_emat(lbks_system* s, int i) { return host_e4(s, i) + kE4Stride; }
+int* host_status(lbks_system* s) { return reinterpret_cast<int*>(s->host + (size_t)s->B * host_per_sys(s->n_orb)); }
+int* host_active(lbks_system* s) { return host_status(s) + s->B; }
+CGState* host_cg(lbks_system* s) {
+    return reinterpret_cast<CGState*>(s->host + (size_t)s->B * host_per_sys(s->n_orb) + s->B + 1);
 }
 
 int poisson_graph(lbks_system* s) {
     if (s->poisson_graph) return LBKS_OK;
-    const PoissonBufs pb = poisson_bufs(s->pvec, s->N, s->cg, s->mp);
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp);
     cudaGraph_t gr = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
     g_capturing = true;
-    cudaError_t ee = launch_poisson_iterate(s->g, s->vh, s->prm.poisson_rtol, kPoissonChunk, pb, s->mg, s->sc, s->cap);
+    cudaError_t ee =
+        launch_poisson_iterate(s->g, s->vh, s->prm.poisson_rtol, kPoissonChunk, pb, s->mg, s->sc, s->B, s->cap);
     g_capturing = false;
     e = cudaStreamEndCapture(s->cap, &gr);
     if (ee != cudaSuccess) {
@@ -260,100 +285,116 @@ int poisson_graph(lbks_system* s) {
 }
 
 int hartree_solve(lbks_system* s, cudaStream_t st) {
-    const PoissonBufs pb = poisson_bufs(s->pvec, s->N, s->cg, s->mp);
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp);
     int rc = poisson_graph(s);
     if (rc != LBKS_OK) return rc;
-    cudaError_t e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, st);
+    cudaError_t e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, s->B, st);
     if (e != cudaSuccess) return cuda_fail(e, "poisson start");
-    CGState* hcg = reinterpret_cast<CGState*>(s->host + 8 + kScratchVals);
+    CGState* hcg = host_cg(s);
+    const int* act = host_active(s);
     int done_iters = 0;
     while (true) {
-        e = cudaMemcpyAsync(hcg, s->cg, sizeof(CGState), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(hcg, s->cg, sizeof(CGState) * s->B, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "poisson readback");
-        if (hcg->done) break;
-        if (done_iters >= s->prm.poisson_max_iter) {
-            s->poisson_iters += hcg->iters;
-            return fail(LBKS_ENOTCONV, "Hartree PCG: relative residual %.3e after %d iterations", hcg->relres,
-                        hcg->iters);
-        }
+        int pending = -1;
+        for (int i = 0; i < s->B; ++i)
+            if (act[i] && !hcg[i].done) pending = i;
+        if (pending < 0) break;
+        if (done_iters >= s->prm.poisson_max_iter)
+            return fail(LBKS_ENOTCONV, "Hartree PCG (system %d): relative residual %.3e after %d iterations",
+                        pending, hcg[pending].relres, hcg[pending].iters);
         e = cudaGraphLaunch(s->poisson_graph, st);
         if (e != cudaSuccess) return cuda_fail(e, "poisson iterate");
         count_launches(s->poisson_nodes);
         done_iters += kPoissonChunk;
     }
-    s->poisson_iters += hcg->iters;
+    int most = 0;
+    for (int i = 0; i < s->B; ++i)
+        if (act[i]) most = std::max(most, hcg[i].iters);
+    s->poisson_iters += most;
     return LBKS_OK;
 }
 
 // Density, Hartree, xc, potential (mixed unless first), energies of the
-// current orthonormal orbitals.
+// current orthonormal orbitals of every active system.
 int evaluate(lbks_system* s, cudaStream_t st, int first) {
-    cudaError_t e = s->ops->density(s->n_orb, s->g, s->h, s->psi, s->rho, s->mp, s->sc, st);
+    const int B = s->B;
+    cudaError_t e = s->ops->density(s->n_orb, s->g, s->h, s->psi, s->rho, s->mp, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "density");
     int rc = hartree_solve(s, st);
     if (rc != LBKS_OK) return rc;
-    e = launch_potential(s->g, s->h, s->rho, s->vext, s->vh, s->vout, s->vin, first, s->prm.mix, s->e4, s->sc, st);
+    e = launch_potential(s->g, s->h, s->rho, s->vext, s->vh, s->vout, s->vin, first, s->prm.mix, s->e4, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "potential");
-    e = s->ops->energy_matrix(s->n_orb, s->g, s->c, s->psi, s->vout, s->emat, s->sc, st);
+    e = s->ops->energy_matrix(s->n_orb, s->g, s->c, s->psi, s->vout, s->emat, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "energy matrix");
     const int no = s->n_orb;
-    double* h4 = s->host;
-    double* hm = s->host + 4;
-    int* hstat = reinterpret_cast<int*>(s->host + 4 + kScratchVals);
-    e = cudaMemcpyAsync(h4, s->e4, sizeof(double) * 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(hm, s->emat, sizeof(double) * (no * no + no), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hstat, s->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    for (int i = 0; i < B && e == cudaSuccess; ++i) {
+        e = cudaMemcpyAsync(host_e4(s, i), s->e4 + (size_t)i * kE4Stride, sizeof(double) * kE4Stride,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_emat(s, i), s->emat + (size_t)i * emat_stride(no), sizeof(double) * (no * no + no),
+                                cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_status(s), s->status, sizeof(int) * B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "energy readback");
-    if (*hstat != 0) return fail(LBKS_ENOTCONV, "overlap matrix not positive definite at orbital %d", *hstat - 1);
-
-    lbks_energy_terms& t = s->terms;
-    memset(&t, 0, sizeof t);
-    double ts = 0.0;
-    for (int j = 0; j < no; ++j) ts += hm[no * no + j];
-    t.T_s = 2.0 * ts;
-    t.E_ext = h4[0];
-    t.E_H = 0.5 * h4[1];
-    t.E_xc = h4[2];
-    t.n_electrons = h4[3];
-    double enn = 0.0;
-    const int na = (int)s->Z.size();
-    for (int i = 0; i < na; ++i)
-        for (int j = 0; j < i; ++j) {
-            const double dx = s->xyz[3 * i] - s->xyz[3 * j], dy = s->xyz[3 * i + 1] - s->xyz[3 * j + 1],
-                         dz = s->xyz[3 * i + 2] - s->xyz[3 * j + 2];
-            enn += s->Z[i] * s->Z[j] / std::sqrt(dx * dx + dy * dy + dz * dz);
+    const int* act = host_active(s);
+    for (int i = 0; i < B; ++i) {
+        if (!act[i]) continue;
+        if (host_status(s)[i] != 0)
+            return fail(LBKS_ENOTCONV, "system %d: overlap matrix not positive definite at orbital %d", i,
+                        host_status(s)[i] - 1);
+        const double* h4 = host_e4(s, i);
+        const double* hm = host_emat(s, i);
+        lbks_energy_terms& t = s->terms[i];
+        memset(&t, 0, sizeof t);
+        double ts = 0.0;
+        for (int j = 0; j < no; ++j) ts += hm[no * no + j];
+        t.T_s = 2.0 * ts;
+        t.E_ext = h4[0];
+        t.E_H = 0.5 * h4[1];
+        t.E_xc = h4[2];
+        t.n_electrons = h4[3];
+        double enn = 0.0;
+        const std::vector<double>& xyz = s->xyz[i];
+        const std::vector<double>& Z = s->Z[i];
+        const int na = (int)Z.size();
+        for (int a = 0; a < na; ++a)
+            for (int b = 0; b < a; ++b) {
+                const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                             dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+                enn += Z[a] * Z[b] / std::sqrt(dx * dx + dy * dy + dz * dz);
+            }
+        t.E_nn = enn;
+        t.E_total = t.T_s + t.E_ext + t.E_H + t.E_xc + t.E_nn;
+        std::vector<double> H(no * no);
+        for (int j = 0; j < no; ++j) {
+            t.orbital_energies[j] = hm[j * no + j];
+            for (int k = 0; k < no; ++k) H[j * no + k] = 0.5 * (hm[j * no + k] + hm[k * no + j]);
         }
-    t.E_nn = enn;
-    t.E_total = t.T_s + t.E_ext + t.E_H + t.E_xc + t.E_nn;
-    std::vector<double> H(no * no);
-    for (int j = 0; j < no; ++j) {
-        t.orbital_energies[j] = hm[j * no + j];
-        for (int k = 0; k < no; ++k) H[j * no + k] = 0.5 * (hm[j * no + k] + hm[k * no + j]);
+        jacobi_eigenvalues(no, H, t.eigenvalues);
     }
-    jacobi_eigenvalues(no, H, t.eigenvalues);
     return LBKS_OK;
 }
 
 // n_inner - 1 steps of Eq. KSLB and one orthonormalising step, starting from f[start].
 cudaError_t enqueue_cycle(lbks_system* s, cudaStream_t st, int start) {
     int cur = start;
-    const int n = s->prm.n_inner;
+    const int n = s->prm.n_inner, B = s->B;
     for (int t = 0; t < n; ++t) {
         RelaxIO io{s->f[cur], t == 0 ? nullptr : s->u, s->vin, s->sigma, s->f[1 - cur], s->psi, s->S, s->lam, s->sigma};
-        cudaError_t e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, st);
+        cudaError_t e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, B, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
         if (t < n - 1) {
-            e = s->ops->w_field(s->n_orb, s->N, s->prm.omega, s->psi, s->lam, s->u, st);
+            e = s->ops->w_field(s->n_orb, s->g, s->prm.omega, s->psi, s->lam, s->u, B, st);
             if (e != cudaSuccess) return e;
         }
     }
-    cudaError_t e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, st);
-    if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->N, s->Linv, s->f[cur], s->psi, st);
-    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb, 1.0, st);
+    cudaError_t e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, s->active, B, st);
+    if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->g, s->Linv, s->f[cur], s->psi, B, st);
+    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * B, 1.0, st);
     return e;
 }
 
@@ -380,14 +421,45 @@ int cycle_graph(lbks_system* s, int start) {
     return LBKS_OK;
 }
 
+int upload_active(lbks_system* s, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(s->active, host_active(s), sizeof(int) * s->B, cudaMemcpyHostToDevice, st);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "upload active flags");
+}
+
+// BF16 -> FP32 switch: widen the current populations, continue with FP32
+// kernels (orbitals, W field and scalars are float already).
+int polish(lbks_system* s, cudaStream_t st) {
+    cudaError_t e = launch_bf16_to_f32(s->f[s->cur], s->f_wide[s->cur], s->N * s->B * 19 * s->n_orb, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "polish switch");
+    for (int k = 0; k < 2; ++k) {
+        if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+        s->graph[k] = nullptr;
+        std::swap(s->f[k], s->f_wide[k]);
+    }
+    s->ops = &ops_f32();
+    s->polished = true;
+    return LBKS_OK;
+}
+
+// Relaxation cycles of all systems in lock step; a system stops (drops out
+// of every launch) once its |dE| < e_tol, unless `fixed`.
 int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* out) {
-    if (!s->has_geometry) return fail(LBKS_EINVAL, "lbks_set_geometry has not been called");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    const int B = s->B;
     const auto t0 = std::chrono::steady_clock::now();
-    double prev = s->terms.E_total, de = INFINITY;
-    int cycles = 0, converged = 0, rc = LBKS_OK;
-    const int start_iters = s->poisson_iters;
+    std::vector<double> prev(B), de(B, INFINITY);
+    std::vector<int> cycles(B, 0), converged(B, 0), p0(B, 0);
+    int* act = host_active(s);
+    for (int i = 0; i < B; ++i) {
+        prev[i] = s->terms[i].E_total;
+        act[i] = 1;
+    }
+    int rc = upload_active(s, st);
+    if (rc != LBKS_OK) return rc;
     const int limit = fixed ? n : s->prm.max_cycles;
-    int steps = 0;
+    const int start_iters = s->poisson_iters;
+    int cycles_polished = 0;
     for (int c = 0; c < limit; ++c) {
         rc = cycle_graph(s, s->cur);
         if (rc != LBKS_OK) return rc;
@@ -395,31 +467,142 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
         count_launches(s->graph_nodes[s->cur]);
         s->cur ^= (s->prm.n_inner & 1);
-        steps += s->prm.n_inner;
         rc = evaluate(s, st, 0);
         if (rc != LBKS_OK) return rc;
-        ++cycles;
-        de = std::fabs(s->terms.E_total - prev);
-        prev = s->terms.E_total;
-        if (!std::isfinite(s->terms.E_total)) return fail(LBKS_ENOTCONV, "total energy is not finite");
-        if (!fixed && de < s->prm.e_tol) {
-            converged = 1;
-            break;
+        // A BF16 handle with a polish phase converges only in FP32, and only
+        // after two FP32 cycles have washed the bfloat16 rounding out of the
+        // orbitals (the energy is second order in it, eigenvalues first order).
+        const bool wait_polish = s->f_wide[0] && !fixed && (!s->polished || cycles_polished < 2);
+        int remaining = 0;
+        bool ready = true;
+        for (int i = 0; i < B; ++i) {
+            if (!act[i]) continue;
+            ++cycles[i];
+            de[i] = std::fabs(s->terms[i].E_total - prev[i]);
+            prev[i] = s->terms[i].E_total;
+            if (!std::isfinite(s->terms[i].E_total)) return fail(LBKS_ENOTCONV, "system %d: energy not finite", i);
+            if (!(de[i] < s->prm.polish_tol)) ready = false;
+            if (!fixed && !wait_polish && de[i] < s->prm.e_tol) {
+                converged[i] = 1;
+                act[i] = 0;
+            } else {
+                ++remaining;
+            }
+        }
+        if (s->polished) ++cycles_polished;
+        if (!remaining) break;
+        if (!s->polished && s->f_wide[0] && !fixed && ready) {
+            rc = polish(s, st);
+            if (rc != LBKS_OK) return rc;
+        }
+        if (!fixed) {
+            rc = upload_active(s, st);
+            if (rc != LBKS_OK) return rc;
         }
     }
-    if (out) {
-        memset(out, 0, sizeof *out);
-        out->E_total = s->terms.E_total;
-        out->dE = de;
-        for (int j = 0; j < s->n_orb; ++j) out->eigenvalues[j] = s->terms.eigenvalues[j];
-        out->n_electrons = s->terms.n_electrons;
-        out->cycles = cycles;
-        out->steps = steps;
-        out->converged = converged;
-        out->poisson_iters = s->poisson_iters - start_iters;
-        out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int all = 1;
+    for (int i = 0; i < B; ++i) {
+        all &= converged[i] || fixed;
+        if (!out) continue;
+        lbks_result& r = out[i];
+        memset(&r, 0, sizeof r);
+        r.E_total = s->terms[i].E_total;
+        r.dE = de[i];
+        for (int j = 0; j < s->n_orb; ++j) r.eigenvalues[j] = s->terms[i].eigenvalues[j];
+        r.n_electrons = s->terms[i].n_electrons;
+        r.cycles = cycles[i];
+        r.steps = cycles[i] * s->prm.n_inner;
+        r.converged = converged[i];
+        r.poisson_iters = s->poisson_iters - start_iters;
+        r.wall_s = wall;
     }
-    if (!fixed && !converged) return fail(LBKS_ENOTCONV, "not converged after %d cycles (|dE| = %.3e)", cycles, de);
+    (void)p0;
+    if (!all) return fail(LBKS_ENOTCONV, "not every system converged within %d cycles", limit);
+    return LBKS_OK;
+}
+
+// Gaussian starts, orthonormalisation, equilibrium populations and the first
+// evaluation for every system of the handle (all must have atoms).
+int initialise(lbks_system* s) {
+    const int B = s->B;
+    if (s->polished) {  // start again in bfloat16
+        for (int k = 0; k < 2; ++k) {
+            if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+            std::swap(s->f[k], s->f_wide[k]);
+        }
+        s->ops = ops_for(s->prm.precision);
+        s->polished = false;
+    }
+    for (int i = 0; i < B; ++i)
+        if (!s->has_atoms[i]) return fail(LBKS_EINVAL, "system %d has no geometry", i);
+    cudaStream_t st = s->st;
+    std::vector<double> atoms((size_t)B * kMaxAtoms * 4, 0.0);
+    std::vector<int> counts(B);
+    std::vector<OrbitalStart> starts((size_t)B * s->n_orb);
+    for (int i = 0; i < B; ++i) {
+        const std::vector<double>& xyz = s->xyz[i];
+        const std::vector<double>& Z = s->Z[i];
+        const int na = (int)Z.size();
+        counts[i] = na;
+        for (int a = 0; a < na; ++a) {
+            double* d = &atoms[((size_t)i * kMaxAtoms + a) * 4];
+            d[0] = xyz[3 * a];
+            d[1] = xyz[3 * a + 1];
+            d[2] = xyz[3 * a + 2];
+            d[3] = Z[a];
+        }
+        std::vector<int> order(na);
+        for (int a = 0; a < na; ++a) order[a] = a;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Z[a] > Z[b]; });
+        for (int j = 0; j < s->n_orb; ++j) {
+            const int I = order[j % na], m = j / na;
+            OrbitalStart& o = starts[(size_t)i * s->n_orb + j];
+            o.cx = xyz[3 * I] + 0.25 * std::sin(1.0 + 2.1 * j);
+            o.cy = xyz[3 * I + 1] + 0.25 * std::sin(2.0 + 3.3 * j);
+            o.cz = xyz[3 * I + 2] + 0.25 * std::sin(3.0 + 4.7 * j);
+            o.width = 1.2 * (1.0 + 0.35 * m);
+        }
+    }
+    int* act = host_active(s);
+    for (int i = 0; i < B; ++i) act[i] = 1;
+    cudaError_t e = cudaMemcpyAsync(s->atoms, atoms.data(), sizeof(double) * atoms.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->counts, counts.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->starts, starts.data(), sizeof(OrbitalStart) * starts.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->active, act, sizeof(int) * B, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_vext(s->g, s->h, s->counts, s->atoms, s->a, s->vext, B, st);
+    if (e == cudaSuccess) e = s->ops->init_orbitals(s->n_orb, s->g, s->h, s->starts, s->psi, B, st);
+    if (e == cudaSuccess) e = s->ops->gram(s->n_orb, s->g, s->h, s->psi, s->S, s->sc, B, st);
+    if (e == cudaSuccess) e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, s->active, B, st);
+    if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->g, s->Linv, nullptr, s->psi, B, st);
+    if (e == cudaSuccess) e = s->ops->equilibrium(s->n_orb, s->g, s->c, s->psi, s->f[0], B, st);
+    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * B, 1.0, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->vh, 0, sizeof(double) * s->N * B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "initialise orbitals");
+    s->cur = 0;
+    s->poisson_iters = 0;
+    s->ready = true;
+    int rc = evaluate(s, st, 1);
+    if (rc != LBKS_OK) s->ready = false;
+    return rc;
+}
+
+int check_atoms(const lbks_system* s, int n_atoms, const double* xyz, const double* Z) {
+    if (!xyz || !Z) return fail(LBKS_EINVAL, "null argument");
+    if (n_atoms < 1 || n_atoms > kMaxAtoms) return fail(LBKS_EINVAL, "n_atoms must be in [1, %d]", kMaxAtoms);
+    double zsum = 0.0;
+    const double hx = 0.5 * (s->nx - 1) * s->h, hy = 0.5 * (s->ny - 1) * s->h, hz = 0.5 * (s->nz - 1) * s->h;
+    for (int i = 0; i < n_atoms; ++i) {
+        if (!(std::fabs(xyz[3 * i]) <= hx && std::fabs(xyz[3 * i + 1]) <= hy && std::fabs(xyz[3 * i + 2]) <= hz))
+            return fail(LBKS_EINVAL, "atom %d lies outside the box", i);
+        if (!(Z[i] > 0.0)) return fail(LBKS_EINVAL, "atom %d has non-positive charge", i);
+        zsum += Z[i];
+    }
+    if (std::fabs(zsum - 2.0 * s->n_orb) > 1e-9)
+        return fail(LBKS_EINVAL, "sum of Z (%g) must equal 2 n_orb (%d): closed-shell neutral systems only", zsum,
+                    2 * s->n_orb);
     return LBKS_OK;
 }
 
@@ -427,16 +610,125 @@ void free_system(lbks_system* s) {
     for (int k = 0; k < 2; ++k) {
         if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
         if (s->f[k]) cudaFree(s->f[k]);
+        if (s->f_wide[k]) cudaFree(s->f_wide[k]);
     }
     if (s->poisson_graph) cudaGraphExecDestroy(s->poisson_graph);
-    void* ptrs[] = {s->u, s->psi, s->vin, s->vout, s->vext, s->vh, s->rho, s->pvec, s->cg, s->small, s->status,
-                    s->sc.partial, s->sc.counter};
+    void* ptrs[] = {s->u,   s->psi,   s->vin,    s->vout,          s->vext,          s->vh, s->rho, s->pvec,
+                    s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->host) cudaFreeHost(s->host);
     if (s->st) cudaStreamDestroy(s->st);
     if (s->cap) cudaStreamDestroy(s->cap);
     delete s;
+}
+
+size_t bytes_of(const lbks_params* p, int nx, int ny, int nz, int n_orb, int B) {
+    const size_t N = (size_t)nx * ny * nz;
+    const size_t e = ops_for(p->precision)->elem, ep = ops_for(p->precision)->psi_elem;
+    const size_t per = e * N * (size_t)n_orb * 19 * 2 + ep * N * ((size_t)std::max(1, n_orb - 1) + n_orb) +
+                       sizeof(double) * N * 11 + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
+                       sizeof(double) * ((size_t)num_sms() * 8 * scratch_vals(n_orb) + small_per_sys(n_orb) +
+                                         4 * kMaxAtoms) +
+                       ((p->precision == LBKS_BF16 && p->polish_tol > 0.0) ? sizeof(float) * N * n_orb * 19 * 2 : 0);
+    return per * B;
+}
+
+int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, int B, lbks_system** out) {
+    if (!out) return fail(LBKS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!valid_params(p)) return fail(LBKS_EINVAL, "invalid lbks_params");
+    if (nx < 2 || ny < 2 || nz < 2) return fail(LBKS_EINVAL, "grid must be at least 2 sites per axis");
+    if (!(h > 0.0)) return fail(LBKS_EINVAL, "h must be positive");
+    if (n_orb < 1 || n_orb > kMaxOrbWide) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrbWide);
+    if (B < 1 || B > 4096) return fail(LBKS_EINVAL, "n_systems must be in [1, 4096]");
+    if ((size_t)nx * ny * nz >= (1ull << 31)) return fail(LBKS_EINVAL, "grid has 2^31 sites or more");
+    lbks_system* s = new lbks_system();
+    s->prm = *p;
+    s->nx = nx;
+    s->ny = ny;
+    s->nz = nz;
+    s->n_orb = n_orb;
+    s->B = B;
+    s->h = h;
+    s->dt = p->theta * h * h * (2.0 - p->omega) / p->omega;
+    s->a = p->softening > 0.0 ? p->softening : h;
+    s->g = make_grid(nx, ny, nz);
+    s->c = make_coef(p->omega, p->theta, s->dt, h);
+    s->ops = ops_for(p->precision);
+    s->N = (size_t)nx * ny * nz;
+    cudaGetDevice(&s->dev);
+    s->terms.assign(B, lbks_energy_terms{});
+    s->xyz.assign(B, {});
+    s->Z.assign(B, {});
+    s->has_atoms.assign(B, 0);
+    const size_t e = s->ops->elem, ep = s->ops->psi_elem, N = s->N, NB = N * B;
+    cudaError_t err = cudaSuccess;
+    auto A = [&](void** ptr, size_t bytes) {
+        if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
+    };
+    A(&s->f[0], e * NB * 19 * n_orb);
+    A(&s->f[1], e * NB * 19 * n_orb);
+    if (p->precision == LBKS_BF16 && p->polish_tol > 0.0) {
+        A(&s->f_wide[0], sizeof(float) * NB * 19 * n_orb);
+        A(&s->f_wide[1], sizeof(float) * NB * 19 * n_orb);
+    }
+    A(&s->u, ep * NB * std::max(1, n_orb - 1));
+    A(&s->psi, ep * NB * n_orb);
+    A((void**)&s->vin, 8 * NB);
+    A((void**)&s->vout, 8 * NB);
+    A((void**)&s->vext, 8 * NB);
+    A((void**)&s->vh, 8 * NB);
+    A((void**)&s->rho, 8 * NB);
+    A((void**)&s->pvec, 8 * (6 * NB + B * mg_coarse_doubles(nx, ny, nz)));
+    A((void**)&s->cg, sizeof(CGState) * B);
+    A((void**)&s->small, sizeof(double) * (small_per_sys(n_orb) + 4 * kMaxAtoms) * B);
+    A((void**)&s->ints, sizeof(int) * 3 * B);
+    A((void**)&s->starts, sizeof(OrbitalStart) * n_orb * B);
+    if (err == cudaSuccess) {
+        s->sc.max_blocks = num_sms() * 8;
+        s->sc.max_vals = scratch_vals(n_orb);
+        s->sc.systems = B;
+        err = cudaMalloc(&s->sc.partial, sizeof(double) * (size_t)s->sc.max_blocks * s->sc.max_vals * B);
+    }
+    A((void**)&s->sc.counter, sizeof(unsigned) * B);
+    if (err == cudaSuccess) err = cudaMemset(s->sc.counter, 0, sizeof(unsigned) * B);
+    if (err == cudaSuccess)
+        err = cudaMallocHost((void**)&s->host, sizeof(double) * (host_per_sys(n_orb) * B + B + 1) +
+                                                   sizeof(CGState) * B + sizeof(int) * 2 * B + 64);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaMemset(s->vh, 0, 8 * NB);
+    if (err == cudaSuccess) err = cudaMemset(s->u, 0, ep * NB * std::max(1, n_orb - 1));
+    if (err == cudaSuccess) err = cudaMemset(s->ints, 0, sizeof(int) * 3 * B);
+    if (err != cudaSuccess) {
+        int rc = cuda_fail(err, "create system");
+        free_system(s);
+        return rc;
+    }
+    s->status = s->ints;
+    s->active = s->ints + B;
+    s->counts = s->ints + 2 * B;
+    s->g.active = s->active;
+    s->mg = make_hierarchy(s->g, s->pvec + 6 * NB, B);
+    const size_t M = (size_t)n_orb * n_orb;
+    s->S = s->small;
+    s->lam = s->S + M * B;
+    s->Linv = s->lam + M * B;
+    s->sigma = s->Linv + M * B;
+    s->e4 = s->sigma + (size_t)n_orb * B;
+    s->emat = s->e4 + (size_t)kE4Stride * B;
+    s->mp = s->emat + (size_t)emat_stride(n_orb) * B;
+    s->atoms = s->mp + (size_t)kMpStride * B;
+    *out = s;
+    return LBKS_OK;
+}
+
+int copy_field(const lbks_system* s, int system, const double* base, double* host, size_t cap, const char* what) {
+    if (system < 0 || system >= s->B) return fail(LBKS_EINVAL, "system index out of range");
+    if (cap < s->N) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, s->N);
+    cudaError_t e = cudaMemcpy(host, base + (size_t)system * s->N, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, what);
 }
 
 }  // namespace
@@ -455,6 +747,7 @@ void lbks_params_default(lbks_params* p) {
     p->softening = 0.0;
     p->poisson_rtol = 1e-11;
     p->poisson_max_iter = 20000;
+    p->polish_tol = 1e-4;
 }
 
 int lbks_last_error(char* buf, size_t cap) {
@@ -466,84 +759,28 @@ int lbks_last_error(char* buf, size_t cap) {
     return (int)g_err.size();
 }
 
-const char* lbks_version(void) { return "lbks 0.1 (sm_103a)"; }
+const char* lbks_version(void) { return "lbks 0.2 (sm_103a)"; }
 
 uint64_t lbks_kernel_launches(void) { return g_launches.load(); }
 
 size_t lbks_system_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb) {
-    if (!valid_params(p) || nx < 2 || ny < 2 || nz < 2 || n_orb < 1 || n_orb > kMaxOrb) return 0;
-    const size_t N = (size_t)nx * ny * nz;
-    const size_t e = ops_for(p->precision)->elem;
-    return e * N * ((size_t)n_orb * 19 * 2 + (size_t)std::max(1, n_orb - 1) + n_orb) + sizeof(double) * N * 11 +
-           sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
-           sizeof(double) * ((size_t)num_sms() * 8 * kScratchVals + kSmall);
+    if (!valid_params(p) || nx < 2 || ny < 2 || nz < 2 || n_orb < 1 || n_orb > kMaxOrbWide) return 0;
+    return bytes_of(p, nx, ny, nz, n_orb, 1);
+}
+
+size_t lbks_batch_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb, int n_systems) {
+    if (!valid_params(p) || nx < 2 || ny < 2 || nz < 2 || n_orb < 1 || n_orb > kMaxOrbWide || n_systems < 1)
+        return 0;
+    return bytes_of(p, nx, ny, nz, n_orb, n_systems);
 }
 
 int lbks_create_system(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, lbks_system** out) {
-    if (!out) return fail(LBKS_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!valid_params(p)) return fail(LBKS_EINVAL, "invalid lbks_params");
-    if (nx < 2 || ny < 2 || nz < 2) return fail(LBKS_EINVAL, "grid must be at least 2 sites per axis");
-    if (!(h > 0.0)) return fail(LBKS_EINVAL, "h must be positive");
-    if (n_orb < 1 || n_orb > kMaxOrb) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrb);
-    if ((size_t)nx * ny * nz >= (1ull << 31)) return fail(LBKS_EINVAL, "grid has 2^31 sites or more");
-    lbks_system* s = new lbks_system();
-    s->prm = *p;
-    s->nx = nx;
-    s->ny = ny;
-    s->nz = nz;
-    s->n_orb = n_orb;
-    s->h = h;
-    s->dt = p->theta * h * h * (2.0 - p->omega) / p->omega;
-    s->a = p->softening > 0.0 ? p->softening : h;
-    s->g = make_grid(nx, ny, nz);
-    s->c = make_coef(p->omega, p->theta, s->dt, h);
-    s->ops = ops_for(p->precision);
-    s->N = (size_t)nx * ny * nz;
-    cudaGetDevice(&s->dev);
-    memset(&s->terms, 0, sizeof s->terms);
-    const size_t e = s->ops->elem, N = s->N;
-    cudaError_t err = cudaSuccess;
-    auto A = [&](void** ptr, size_t bytes) {
-        if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
-    };
-    A(&s->f[0], e * N * 19 * n_orb);
-    A(&s->f[1], e * N * 19 * n_orb);
-    A(&s->u, e * N * std::max(1, n_orb - 1));
-    A(&s->psi, e * N * n_orb);
-    A((void**)&s->vin, 8 * N);
-    A((void**)&s->vout, 8 * N);
-    A((void**)&s->vext, 8 * N);
-    A((void**)&s->vh, 8 * N);
-    A((void**)&s->rho, 8 * N);
-    A((void**)&s->pvec, 8 * (6 * N + mg_coarse_doubles(nx, ny, nz)));
-    A((void**)&s->cg, sizeof(CGState));
-    A((void**)&s->small, sizeof(double) * (kSmall + 4 * kMaxAtoms));
-    A((void**)&s->status, sizeof(int) * 4);
-    if (err == cudaSuccess) err = alloc_scratch(s->sc);
-    if (err == cudaSuccess) err = cudaMallocHost((void**)&s->host, sizeof(double) * (16 + kScratchVals + 16));
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
-    if (err == cudaSuccess) err = cudaMemset(s->vh, 0, 8 * N);
-    if (err == cudaSuccess) err = cudaMemset(s->u, 0, e * N * std::max(1, n_orb - 1));
-    if (err == cudaSuccess) err = cudaMemset(s->status, 0, sizeof(int) * 4);
-    if (err != cudaSuccess) {
-        int rc = cuda_fail(err, "lbks_create_system");
-        free_system(s);
-        return rc;
-    }
-    s->mg = make_hierarchy(s->g, s->pvec + 6 * N);
-    const int M = kMaxOrb * kMaxOrb;
-    s->S = s->small;
-    s->lam = s->S + M;
-    s->Linv = s->lam + M;
-    s->sigma = s->Linv + M;
-    s->e4 = s->sigma + M;
-    s->emat = s->e4 + 4;
-    s->mp = s->emat + kScratchVals;
-    s->atoms = s->mp + 16;
-    *out = s;
-    return LBKS_OK;
+    return create(p, nx, ny, nz, h, n_orb, 1, out);
+}
+
+int lbks_create_batch(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, int n_systems,
+                      lbks_system** out) {
+    return create(p, nx, ny, nz, h, n_orb, n_systems, out);
 }
 
 int lbks_destroy_system(lbks_system* s) {
@@ -557,61 +794,36 @@ int lbks_destroy_system(lbks_system* s) {
 }
 
 int lbks_set_geometry(lbks_system* s, int n_atoms, const double* xyz, const double* Z) {
-    if (!s || !xyz || !Z) return fail(LBKS_EINVAL, "null argument");
-    if (n_atoms < 1 || n_atoms > kMaxAtoms) return fail(LBKS_EINVAL, "n_atoms must be in [1, %d]", kMaxAtoms);
-    double zsum = 0.0;
-    const double hx = 0.5 * (s->nx - 1) * s->h, hy = 0.5 * (s->ny - 1) * s->h, hz = 0.5 * (s->nz - 1) * s->h;
-    for (int i = 0; i < n_atoms; ++i) {
-        if (!(std::fabs(xyz[3 * i]) <= hx && std::fabs(xyz[3 * i + 1]) <= hy && std::fabs(xyz[3 * i + 2]) <= hz))
-            return fail(LBKS_EINVAL, "atom %d lies outside the box", i);
-        if (!(Z[i] > 0.0)) return fail(LBKS_EINVAL, "atom %d has non-positive charge", i);
-        zsum += Z[i];
-    }
-    if (std::fabs(zsum - 2.0 * s->n_orb) > 1e-9)
-        return fail(LBKS_EINVAL, "sum of Z (%g) must equal 2 n_orb (%d): closed-shell neutral systems only", zsum,
-                    2 * s->n_orb);
-    s->xyz.assign(xyz, xyz + 3 * n_atoms);
-    s->Z.assign(Z, Z + n_atoms);
-    std::vector<double> atoms(4 * n_atoms);
-    for (int i = 0; i < n_atoms; ++i) {
-        atoms[4 * i] = xyz[3 * i];
-        atoms[4 * i + 1] = xyz[3 * i + 1];
-        atoms[4 * i + 2] = xyz[3 * i + 2];
-        atoms[4 * i + 3] = Z[i];
-    }
-    cudaStream_t st = s->st;
-    cudaError_t e = cudaMemcpyAsync(s->atoms, atoms.data(), sizeof(double) * 4 * n_atoms, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_vext(s->g, s->h, n_atoms, s->atoms, s->a, s->vext, st);
-    // Gaussian start (see include/lbks.h)
-    std::vector<int> order(n_atoms);
-    for (int i = 0; i < n_atoms; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Z[a] > Z[b]; });
-    OrbitalStart starts[kMaxOrb];
-    for (int j = 0; j < s->n_orb; ++j) {
-        const int I = order[j % n_atoms], m = j / n_atoms;
-        starts[j].cx = xyz[3 * I] + 0.25 * std::sin(1.0 + 2.1 * j);
-        starts[j].cy = xyz[3 * I + 1] + 0.25 * std::sin(2.0 + 3.3 * j);
-        starts[j].cz = xyz[3 * I + 2] + 0.25 * std::sin(3.0 + 4.7 * j);
-        starts[j].width = 1.2 * (1.0 + 0.35 * m);
-    }
-    if (e == cudaSuccess) e = s->ops->init_orbitals(s->n_orb, s->g, s->h, starts, s->psi, st);
-    if (e == cudaSuccess) e = s->ops->gram(s->n_orb, s->g, s->h, s->psi, s->S, s->sc, st);
-    if (e == cudaSuccess) e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, st);
-    if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->N, s->Linv, nullptr, s->psi, st);
-    if (e == cudaSuccess) e = s->ops->equilibrium(s->n_orb, s->N, s->c, s->psi, s->f[0], st);
-    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb, 1.0, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->vh, 0, sizeof(double) * s->N, st);
-    if (e != cudaSuccess) return cuda_fail(e, "lbks_set_geometry");
-    s->cur = 0;
-    s->has_geometry = true;
-    s->poisson_iters = 0;
-    int rc = evaluate(s, st, 1);
-    if (rc != LBKS_OK) s->has_geometry = false;
-    return rc;
+    if (!s) return fail(LBKS_EINVAL, "system is NULL");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: use lbks_batch_set_geometry and lbks_batch_init");
+    int rc = check_atoms(s, n_atoms, xyz, Z);
+    if (rc != LBKS_OK) return rc;
+    s->xyz[0].assign(xyz, xyz + 3 * n_atoms);
+    s->Z[0].assign(Z, Z + n_atoms);
+    s->has_atoms[0] = 1;
+    return initialise(s);
+}
+
+int lbks_batch_set_geometry(lbks_system* s, int system, int n_atoms, const double* xyz, const double* Z) {
+    if (!s) return fail(LBKS_EINVAL, "system is NULL");
+    if (system < 0 || system >= s->B) return fail(LBKS_EINVAL, "system index out of range");
+    int rc = check_atoms(s, n_atoms, xyz, Z);
+    if (rc != LBKS_OK) return rc;
+    s->xyz[system].assign(xyz, xyz + 3 * n_atoms);
+    s->Z[system].assign(Z, Z + n_atoms);
+    s->has_atoms[system] = 1;
+    s->ready = false;
+    return LBKS_OK;
+}
+
+int lbks_batch_init(lbks_system* s) {
+    if (!s) return fail(LBKS_EINVAL, "system is NULL");
+    return initialise(s);
 }
 
 int lbks_scf(lbks_system* s, void* stream, lbks_result* out) {
     if (!s) return fail(LBKS_EINVAL, "system is NULL");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: use lbks_batch_scf");
     return run_cycles(s, 0, 0, (cudaStream_t)stream, out);
 }
 
@@ -620,25 +832,33 @@ int lbks_scf_cycles(lbks_system* s, int n, void* stream, lbks_result* out) {
     return run_cycles(s, 1, n, (cudaStream_t)stream, out);
 }
 
-int lbks_energy(const lbks_system* s, lbks_energy_terms* out) {
+int lbks_batch_scf(lbks_system* s, void* stream, lbks_result* out) {
+    if (!s) return fail(LBKS_EINVAL, "system is NULL");
+    return run_cycles(s, 0, 0, (cudaStream_t)stream, out);
+}
+
+int lbks_batch_energy(const lbks_system* s, int system, lbks_energy_terms* out) {
     if (!s || !out) return fail(LBKS_EINVAL, "null argument");
-    if (!s->has_geometry) return fail(LBKS_EINVAL, "lbks_set_geometry has not been called");
-    *out = s->terms;
+    if (system < 0 || system >= s->B) return fail(LBKS_EINVAL, "system index out of range");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    *out = s->terms[system];
     return LBKS_OK;
 }
 
-int lbks_get_density(const lbks_system* s, double* host, size_t cap) {
+int lbks_energy(const lbks_system* s, lbks_energy_terms* out) { return lbks_batch_energy(s, 0, out); }
+
+int lbks_batch_get_density(const lbks_system* s, int system, double* host, size_t cap) {
     if (!s || !host) return fail(LBKS_EINVAL, "null argument");
-    if (cap < s->N) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, s->N);
-    cudaError_t e = cudaMemcpy(host, s->rho, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_get_density");
+    return copy_field(s, system, s->rho, host, cap, "lbks_get_density");
 }
+
+int lbks_get_density(const lbks_system* s, double* host, size_t cap) { return lbks_batch_get_density(s, 0, host, cap); }
 
 int lbks_get_orbitals(const lbks_system* s, double* host, size_t cap) {
     if (!s || !host) return fail(LBKS_EINVAL, "null argument");
     const size_t n = s->N * s->n_orb;
     if (cap < n) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, n);
-    if (s->ops->elem == sizeof(double)) {
+    if (s->ops->psi_elem == sizeof(double)) {
         cudaError_t e = cudaMemcpy(host, s->psi, sizeof(double) * n, cudaMemcpyDeviceToHost);
         return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_get_orbitals");
     }
@@ -651,11 +871,9 @@ int lbks_get_orbitals(const lbks_system* s, double* host, size_t cap) {
 
 int lbks_get_potential(const lbks_system* s, int which, double* host, size_t cap) {
     if (!s || !host) return fail(LBKS_EINVAL, "null argument");
-    if (cap < s->N) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, s->N);
     const double* src = which == 0 ? s->vin : which == 1 ? s->vout : which == 2 ? s->vh : which == 3 ? s->vext : nullptr;
     if (!src) return fail(LBKS_EINVAL, "which must be 0..3");
-    cudaError_t e = cudaMemcpy(host, src, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_get_potential");
+    return copy_field(s, 0, src, host, cap, "lbks_get_potential");
 }
 
 // ------------------------------------------------------------- step-level calls
@@ -667,7 +885,7 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h, 
     if (!ops) return fail(LBKS_EINVAL, "unknown precision %d", precision);
     if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= (1ull << 31))
         return fail(LBKS_EINVAL, "bad grid %d x %d x %d", nx, ny, nz);
-    if (n_orb < 1 || n_orb > kMaxOrb) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrb);
+    if (n_orb < 1 || n_orb > kMaxOrbWide) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrbWide);
     if (!f_in || !V || !sigma_in || !f_out || !psi_out || !S_out || !lambda_out || !sigma_out)
         return fail(LBKS_EINVAL, "null device pointer");
     if (f_in == f_out) return fail(LBKS_EINVAL, "f_in and f_out must not alias");
@@ -676,25 +894,44 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h, 
     int rc = workspace(stream, 0, &w);
     if (rc != LBKS_OK) return rc;
     RelaxIO io{f_in, u_in, V, sigma_in, f_out, psi_out, S_out, lambda_out, sigma_out};
-    cudaError_t e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, w->sc,
+    cudaError_t e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, w->sc, 1,
                                (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step");
+}
+
+int lbks_overlap(int precision, size_t n_sites, int n_orb, double h, const void* psi, double* S, int tensor_cores,
+                 void* stream) {
+    const PrecisionOps* ops = ops_for(precision);
+    if (!ops) return fail(LBKS_EINVAL, "unknown precision %d", precision);
+    if (n_orb < 1 || n_orb > kMaxOrbWide || !psi || !S || !(h > 0.0)) return fail(LBKS_EINVAL, "bad argument");
+    if (n_sites == 0 || n_sites >= (1ull << 31)) return fail(LBKS_EINVAL, "n_sites must be in [1, 2^31)");
+    Workspace* w = nullptr;
+    int rc = workspace(stream, 0, &w);
+    if (rc != LBKS_OK) return rc;
+    const Grid g = make_grid((int)n_sites, 1, 1);
+    cudaError_t e = tensor_cores && precision != LBKS_FP64
+                        ? launch_gram_tc(n_orb, g, h, (const float*)psi, S, nullptr, nullptr, w->sc, 1,
+                                         (cudaStream_t)stream)
+                        : ops->gram(n_orb, g, h, psi, S, w->sc, 1, (cudaStream_t)stream);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_overlap");
 }
 
 int lbks_w_field(int precision, size_t n_sites, int n_orb, double omega, const void* psi, const double* lambda,
                  void* u_out, void* stream) {
     const PrecisionOps* ops = ops_for(precision);
     if (!ops) return fail(LBKS_EINVAL, "unknown precision %d", precision);
-    if (n_orb < 1 || n_orb > kMaxOrb || !psi || !lambda || (n_orb > 1 && !u_out))
+    if (n_orb < 1 || n_orb > kMaxOrbWide || !psi || !lambda || (n_orb > 1 && !u_out))
         return fail(LBKS_EINVAL, "bad argument");
     if (n_sites == 0) return LBKS_OK;
-    cudaError_t e = ops->w_field(n_orb, n_sites, omega, psi, lambda, u_out, (cudaStream_t)stream);
+    if (n_sites >= (1ull << 31)) return fail(LBKS_EINVAL, "n_sites must be below 2^31");
+    cudaError_t e = ops->w_field(n_orb, make_grid((int)n_sites, 1, 1), omega, psi, lambda, u_out, 1,
+                                 (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_w_field");
 }
 
 int lbks_cholesky_inverse(int n, const double* S, double* Linv, int* status, void* stream) {
-    if (n < 1 || n > kMaxOrb || !S || !Linv || !status) return fail(LBKS_EINVAL, "bad argument");
-    cudaError_t e = launch_cholesky(n, S, Linv, status, (cudaStream_t)stream);
+    if (n < 1 || n > kMaxOrbWide || !S || !Linv || !status) return fail(LBKS_EINVAL, "bad argument");
+    cudaError_t e = launch_cholesky(n, S, Linv, status, nullptr, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_cholesky_inverse");
 }
 
@@ -702,9 +939,10 @@ int lbks_orth_apply(int precision, size_t n_sites, int n_orb, const double* Linv
                     void* stream) {
     const PrecisionOps* ops = ops_for(precision);
     if (!ops) return fail(LBKS_EINVAL, "unknown precision %d", precision);
-    if (n_orb < 1 || n_orb > kMaxOrb || !Linv) return fail(LBKS_EINVAL, "bad argument");
+    if (n_orb < 1 || n_orb > kMaxOrbWide || !Linv) return fail(LBKS_EINVAL, "bad argument");
     if (n_sites == 0 || (!f && !psi)) return LBKS_OK;
-    cudaError_t e = ops->orth_apply(n_orb, n_sites, Linv, f, psi, (cudaStream_t)stream);
+    if (n_sites >= (1ull << 31)) return fail(LBKS_EINVAL, "n_sites must be below 2^31");
+    cudaError_t e = ops->orth_apply(n_orb, make_grid((int)n_sites, 1, 1), Linv, f, psi, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_orth_apply");
 }
 
@@ -719,9 +957,9 @@ int lbks_hartree(int nx, int ny, int nz, double h, const double* rho, double* v,
     if (rc != LBKS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const PoissonBufs pb = poisson_bufs(w->pvec, g.N, w->cg, w->mp);
-    const MGHierarchy H = make_hierarchy(g, w->pvec + 6 * (size_t)g.N);
-    cudaError_t e = launch_multipoles_from_rho(g, h, rho, w->mp, w->sc, st);
-    if (e == cudaSuccess) e = launch_poisson_start(g, h, rho, v, rtol, pb, w->sc, st);
+    const MGHierarchy H = make_hierarchy(g, w->pvec + 6 * (size_t)g.N, 1);
+    cudaError_t e = launch_multipoles_from_rho(g, h, rho, w->mp, w->sc, 1, st);
+    if (e == cudaSuccess) e = launch_poisson_start(g, h, rho, v, rtol, pb, w->sc, 1, st);
     if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree");
     CGState hcg;
     int done = 0;
@@ -731,7 +969,7 @@ int lbks_hartree(int nx, int ny, int nz, double h, const double* rho, double* v,
         if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree readback");
         if (hcg.done || done >= max_iter) break;
         const int chunk = std::min(2, max_iter - done);
-        e = launch_poisson_iterate(g, v, rtol, chunk, pb, H, w->sc, st);
+        e = launch_poisson_iterate(g, v, rtol, chunk, pb, H, w->sc, 1, st);
         if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree iterate");
         done += chunk;
     }

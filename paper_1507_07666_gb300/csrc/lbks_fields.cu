@@ -28,12 +28,20 @@ int grid_for(size_t n, int cap_blocks) {
     return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap_blocks));
 }
 
-int red_cap(const Scratch& sc, int vals) { return sc.max_vals >= vals ? std::min(sc.max_blocks, num_sms() * 4) : 0; }
+// Blocks per system of a reduction kernel over B systems.
+int red_cap(const Scratch& sc, int vals, int B) {
+    if (sc.max_vals < vals || sc.systems < B) return 0;
+    return std::max(1, std::min(sc.max_blocks, num_sms() * 4 / std::max(B, 1)));
+}
 
 // ------------------------------------------------------------ external potential
 // V_ext(r) = -sum_I Z_I / sqrt(|r - R_I|^2 + a^2)   (softened nuclei)
-__global__ void __launch_bounds__(kThreads) k_vext(Grid g, double h, int n_atoms, const double* __restrict__ atoms,
-                                                   double a2, double* __restrict__ v) {
+__global__ void __launch_bounds__(kThreads) k_vext(Grid g, double h, const int* __restrict__ counts,
+                                                   const double* __restrict__ atoms, double a2, double* __restrict__ v) {
+    if (inactive(g)) return;
+    const int n_atoms = counts[sys_id()];
+    atoms += (size_t)sys_id() * kMaxAtoms * 4;
+    v += (size_t)sys_id() * g.N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         int x, y, z;
         double rx, ry, rz;
@@ -49,8 +57,13 @@ __global__ void __launch_bounds__(kThreads) k_vext(Grid g, double h, int n_atoms
 
 // --------------------------------------------------------------------- Cholesky
 // S = L L^T (one CTA), then L^{-1} by forward substitution, one column per thread.
-__global__ void k_cholesky(int n, const double* __restrict__ S, double* __restrict__ Linv, int* status) {
-    __shared__ double L[kMaxOrb * kMaxOrb];
+__global__ void k_cholesky(int n, const double* __restrict__ S, double* __restrict__ Linv, int* status,
+                           const int* active) {
+    if (active && !active[blockIdx.y]) return;
+    S += (size_t)blockIdx.y * n * n;
+    Linv += (size_t)blockIdx.y * n * n;
+    status += blockIdx.y;
+    __shared__ double L[kMaxOrbWide * kMaxOrbWide];
     __shared__ int bad;
     if (threadIdx.x == 0) {
         bad = 0;
@@ -142,6 +155,12 @@ __global__ void __launch_bounds__(kThreads) k_potential(Grid g, double h, const 
                                                         const double* __restrict__ vh, double* __restrict__ vout,
                                                         double* __restrict__ vin, int first, double mix, double* e4,
                                                         Scratch sc) {
+    if (inactive(g)) return;
+    {
+        const size_t o = (size_t)sys_id() * g.N;
+        rho += o; vext += o; vh += o; vout += o; vin += o;
+        e4 += (size_t)sys_id() * kE4Stride;
+    }
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         const double r = rho[s];
@@ -155,9 +174,10 @@ __global__ void __launch_bounds__(kThreads) k_potential(Grid g, double h, const 
         acc[2] += r * e;
         acc[3] += r;
     }
-    block_sum_store<4>(acc, sc.partial + (size_t)blockIdx.x * 4);
+    double* partial = sys_partial(sc);
+    block_sum_store<4>(acc, partial + (size_t)blockIdx.x * 4);
     __shared__ double tot[4];
-    if (grid_total<4>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<4>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = h * h * h;
         for (int k = 0; k < 4; ++k) e4[k] = h3 * tot[k];
     }
@@ -167,6 +187,9 @@ __global__ void __launch_bounds__(kThreads) k_potential(Grid g, double h, const 
 // Multipoles {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz} of rho.
 __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const double* __restrict__ rho, double* mp,
                                                          Scratch sc) {
+    if (inactive(g)) return;
+    rho += (size_t)sys_id() * g.N;
+    mp += (size_t)sys_id() * kMpStride;
     double acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
@@ -180,9 +203,10 @@ __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const
         acc[4] += r * rx * rx; acc[5] += r * ry * ry; acc[6] += r * rz * rz;
         acc[7] += r * rx * ry; acc[8] += r * rx * rz; acc[9] += r * ry * rz;
     }
-    block_sum_store<10>(acc, sc.partial + (size_t)blockIdx.x * 10);
+    double* partial = sys_partial(sc);
+    block_sum_store<10>(acc, partial + (size_t)blockIdx.x * 10);
     __shared__ double tot[10];
-    if (grid_total<10>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<10>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = h * h * h;
         const double tr = tot[4] + tot[5] + tot[6];
         mp[0] = h3 * tot[0];
@@ -195,16 +219,17 @@ __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const
 }  // namespace
 
 // ---------------------------------------------------------------------- launchers
-cudaError_t launch_vext(const Grid& g, double h, int n_atoms, const double* atoms, double a, double* v,
+cudaError_t launch_vext(const Grid& g, double h, const int* counts, const double* atoms, double a, double* v, int B,
                         cudaStream_t st) {
-    k_vext<<<grid_for(g.N, num_sms() * 8), kThreads, 0, st>>>(g, h, n_atoms, atoms, a * a, v);
+    k_vext<<<dim3(grid_for(g.N, std::max(1, num_sms() * 8 / B)), B), kThreads, 0, st>>>(g, h, counts, atoms, a * a, v);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, cudaStream_t st) {
-    if (n < 1 || n > kMaxOrb) return cudaErrorInvalidValue;
-    k_cholesky<<<1, 32, 0, st>>>(n, S, Linv, status);
+cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, const int* active, int B,
+                            cudaStream_t st) {
+    if (n < 1 || n > kMaxOrbWide) return cudaErrorInvalidValue;
+    k_cholesky<<<dim3(1, B), 64, 0, st>>>(n, S, Linv, status, active);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -222,20 +247,20 @@ cudaError_t launch_lda(size_t n, const double* rho, double* eps, double* v, cuda
 }
 
 cudaError_t launch_potential(const Grid& g, double h, const double* rho, const double* vext, const double* vh,
-                             double* vout, double* vin, int first, double mix, double* e4, const Scratch& sc,
+                             double* vout, double* vin, int first, double mix, double* e4, const Scratch& sc, int B,
                              cudaStream_t st) {
-    const int cap = red_cap(sc, 4);
+    const int cap = red_cap(sc, 4, B);
     if (cap < 1) return cudaErrorInvalidValue;
-    k_potential<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, vext, vh, vout, vin, first, mix, e4, sc);
+    k_potential<<<dim3(grid_for(g.N, cap), B), kThreads, 0, st>>>(g, h, rho, vext, vh, vout, vin, first, mix, e4, sc);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_multipoles_from_rho(const Grid& g, double h, const double* rho, double* mp, const Scratch& sc,
-                                       cudaStream_t st) {
-    const int cap = red_cap(sc, 10);
+                                       int B, cudaStream_t st) {
+    const int cap = red_cap(sc, 10, B);
     if (cap < 1) return cudaErrorInvalidValue;
-    k_multipoles<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, mp, sc);
+    k_multipoles<<<dim3(grid_for(g.N, cap), B), kThreads, 0, st>>>(g, h, rho, mp, sc);
     count_launches(1);
     return cudaGetLastError();
 }

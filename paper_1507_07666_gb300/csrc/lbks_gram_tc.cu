@@ -1,0 +1,343 @@
+// Overlap (Gram) matrix of more than eight FP32 orbitals on the fifth-
+// generation tensor cores: S = h^3 Psi Psi^T, the N_O x N_O x N contraction
+// behind the normalisation sigma_j = 1/||psi_j|| and the couplings
+// Lambda_jk = S_jk / S_kk of each relaxation step (Sec. 2, the normalised
+// update) and behind the Cholesky orthonormalisation that ends a cycle.
+//
+// Precision.  Every FP32 orbital value x is split into bf16 parts
+// hi = rn(x), lo = rn(x - hi).  A shared-memory tile of 64 sites holds hi in
+// rows 0..N_O-1 and lo in rows N_O..2N_O-1 (rows up to 127 are zero), and one
+// M = 128 tcgen05.mma with A = B = that tile leaves the four blocks hi.hi,
+// hi.lo, lo.hi, lo.lo in TMEM.  Their sum is the product of the FP32 values up
+// to the rounding of lo (2^-17 relative, unbiased).  TMEM accumulates in FP32
+// over kDrainTiles tiles; then the four blocks are folded and added to
+// per-thread FP64 sums, so no FP32 sum runs over more than 512 sites.  Blocks
+// and the grid finish in FP64 (the last block of each system, fixed order).
+//
+// Pipeline.  128 threads (warp w owns TMEM lanes 32w..32w+31) load the next
+// tile into registers while they split the current one into a 128-byte-
+// swizzled K-major tile (two stages); one thread issues the four K = 16 MMAs
+// of a tile and commits them to the stage's mbarrier.  Every wait on an
+// mbarrier is bounded: on expiry the block records a timeout, writes NaN
+// partial sums (so the solve fails with a non-finite energy), waits (bounded)
+// for its own MMAs, frees its TMEM and returns.
+#include "lbks_internal.cuh"
+#include "lbks_reduce.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+namespace lbks {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcSites = 64;                                 // sites per tile: 64 bf16 = one 128-byte row
+constexpr int kTcRows = 128;                                 // MMA M
+constexpr int kTcStages = 2;
+constexpr int kTcTileBytes = kTcRows * kTcSites * 2;         // 16 KB
+constexpr int kTcQuads = kMaxOrbWide * (kTcSites / 4) / kTcThreads;  // 4-site groups per thread (at most)
+constexpr int kTcMaxPairs = (kMaxOrbWide * (kMaxOrbWide + 1) / 2 + kTcThreads - 1) / kTcThreads;
+constexpr int kDrainTiles = 8;
+constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kTmemColumnsPerSm = 512;
+
+__device__ unsigned g_tc_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, groups of 8 rows 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu)   // start address
+           | ((uint64_t)1 << 16)                // leading-dimension offset (unused with this swizzle)
+           | ((uint64_t)(1024 >> 4) << 32)      // stride between 8-row groups
+           | ((uint64_t)1 << 46)                // descriptor version
+           | ((uint64_t)2 << 61);               // 128-byte swizzle
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B, both K-major; FP32 D; M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row r, site k) in a swizzled tile: 16-byte chunk
+// index XOR (row mod 8), the pattern the descriptor's swizzle mode reads.
+__device__ __forceinline__ uint32_t tile_off(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + (((k >> 3) ^ (r & 7)) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+        :
+        : "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit TMEM columns, one lane per thread of the warp.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
+}  // namespace
+
+// One block per group of tiles of one system (system = blockIdx.y).  VEC:
+// N % 4 == 0 and 16-byte aligned orbitals (float4 loads).  Dynamic shared
+// memory: 1 KB alignment slack, kTcStages tiles, the (2N_O) x (2N_O + 1) FP32
+// fold buffer (reused for the block totals).
+template <bool LAM, bool VEC>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
+              double* sigma, Scratch sc) {
+    if (inactive(g)) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    float* fold = reinterpret_cast<float*>(smem + kTcStages * kTcTileBytes);
+    __shared__ __align__(8) uint64_t mbar[kTcStages];
+    __shared__ uint32_t tmem_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t N = g.N;
+    const size_t y = sys_id();
+    psi += y * NO * (size_t)N;
+    const int R = 2 * NO;                       // tile rows in use: hi, then lo
+    const int NM = (R + 15) & ~15;              // MMA N (multiple of 16)
+    const uint32_t ncols = NM <= 32 ? 32u : NM <= 64 ? 64u : 128u;
+    const int ld = R + 1;                       // fold row pitch (floats)
+    const int NP = NO * (NO + 1) / 2;
+
+    for (int i = tid; i < kTcStages * kTcTileBytes / 16; i += kTcThreads)
+        reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_sh)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    const uint32_t idesc = idesc_bf16(kTcRows, NM);
+    const uint32_t tiles_u32 = smem_u32(smem);
+
+    double acc[kTcMaxPairs];
+    int pr[kTcMaxPairs];  // (a << 8) | b, or -1
+#pragma unroll
+    for (int q = 0; q < kTcMaxPairs; ++q) {
+        acc[q] = 0.0;
+        const int k = tid + q * kTcThreads;
+        int a = 0, b = 0;
+        if (k < NP) tri_pair(k, a, b);
+        pr[q] = k < NP ? (a << 8) | b : -1;
+    }
+
+    const int nq = NO * (kTcSites / 4);
+    const uint32_t ntiles = (N + kTcSites - 1) / kTcSites;
+    float4 cur[kTcQuads], nxt[kTcQuads];
+    auto load = [&](uint32_t ti, float4(&v)[kTcQuads]) {
+#pragma unroll
+        for (int q = 0; q < kTcQuads; ++q) {
+            const int i = tid + q * kTcThreads;
+            if (i >= nq) continue;
+            const uint32_t site = ti * kTcSites + 4 * (i & 15);
+            const float* p = psi + (size_t)(i >> 4) * N + site;
+            if (VEC && site < N) {
+                v[q] = __ldg(reinterpret_cast<const float4*>(p));
+            } else {
+                v[q].x = site < N ? __ldg(p) : 0.f;
+                v[q].y = site + 1 < N ? __ldg(p + 1) : 0.f;
+                v[q].z = site + 2 < N ? __ldg(p + 2) : 0.f;
+                v[q].w = site + 3 < N ? __ldg(p + 3) : 0.f;
+            }
+        }
+    };
+
+    bool failed = false;
+    int it = 0, in_chunk = 0;
+    uint32_t last_bar = 0, last_parity = 0;
+    load(blockIdx.x, cur);
+    for (uint32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+        const uint32_t tn = ti + gridDim.x;
+        if (tn < ntiles) load(tn, nxt);
+        const int s = it & 1;
+        const uint32_t bar = smem_u32(&mbar[s]);
+        // the MMAs of tile it-2 read this stage
+        const bool late = it >= kTcStages && !mbar_wait(bar, ((it >> 1) + 1) & 1);
+        unsigned char* st = smem + s * kTcTileBytes;
+#pragma unroll
+        for (int q = 0; q < kTcQuads; ++q) {
+            const int i = tid + q * kTcThreads;
+            if (i >= nq) continue;
+            const int r = i >> 4, k = 4 * (i & 15);
+            const float4 v = cur[q];
+            const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+            const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+            const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+            *reinterpret_cast<uint2*>(st + tile_off(r, k)) = make_uint2(bf2_bits(h01), bf2_bits(h23));
+            *reinterpret_cast<uint2*>(st + tile_off(NO + r, k)) = make_uint2(bf2_bits(l01), bf2_bits(l23));
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (__syncthreads_or(late)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            tc_fence_after();
+            const uint64_t d0 = sw128_desc(tiles_u32 + s * kTcTileBytes);
+#pragma unroll
+            for (int k = 0; k < kTcSites / 16; ++k)  // K = 16 bf16 = 32 bytes = 2 descriptor units
+                mma_bf16(tmem, d0 + 2 * k, d0 + 2 * k, idesc, (in_chunk > 0 || k > 0) ? 1u : 0u);
+            mma_commit(bar);
+        }
+        last_bar = bar;
+        last_parity = (it >> 1) & 1;
+        if (++in_chunk == drain_tiles || tn >= ntiles) {
+            in_chunk = 0;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity));
+            tc_fence_after();
+            if (ok && warp * 32 < R) {
+                for (int cb = 0; cb < NM; cb += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+                    if (tid < R) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (cb + e < R) fold[tid * ld + cb + e] = __uint_as_float(v[e]);
+                    }
+                }
+            }
+            tc_fence_before();
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+#pragma unroll
+            for (int q = 0; q < kTcMaxPairs; ++q) {
+                if (pr[q] < 0) continue;
+                const int a = pr[q] >> 8, b = pr[q] & 255;
+                const float d00 = fold[a * ld + b], d01 = fold[a * ld + NO + b];
+                const float d10 = fold[(NO + a) * ld + b], d11 = fold[(NO + a) * ld + NO + b];
+                acc[q] += (double)d00 + (double)((d01 + d10) + d11);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kTcQuads; ++q) cur[q] = nxt[q];
+    }
+
+    if (failed) {
+        if (tid == 0) atomicAdd(&g_tc_timeouts, 1u);
+        if (it > 0) mbar_wait(last_bar, last_parity);  // own MMAs in flight, bounded
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+
+    double* partial = sys_partial(sc);
+#pragma unroll
+    for (int q = 0; q < kTcMaxPairs; ++q) {
+        const int k = tid + q * kTcThreads;
+        if (k < NP) partial[(size_t)blockIdx.x * NP + k] = failed ? __longlong_as_double(0x7ff8000000000000ll) : acc[q];
+    }
+    double* tot = reinterpret_cast<double*>(fold);  // NP doubles fit in the fold buffer
+    if (grid_total_rt(partial, sys_counter(sc), tot, NP) && tid == 0)
+        store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, LAM ? sigma + y * NO : nullptr);
+}
+
+template <bool LAM, bool VEC>
+static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
+                                  double* sigma, const Scratch& sc, int B, int drain_tiles, cudaStream_t st) {
+    auto kern = k_gram_tc<LAM, VEC>;
+    const int R = 2 * NO, NM = (R + 15) & ~15;
+    const int ncols = NM <= 32 ? 32 : NM <= 64 ? 64 : 128;
+    size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (size_t)R * (R + 1) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    // co-resident blocks must not ask for more TMEM columns than an SM has
+    const int cap = kTmemColumnsPerSm / ncols;
+    for (int guard = 0; occ > cap && guard < 64; ++guard) {
+        smem += 4096;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (occ < 1 || occ > cap) return cudaErrorInvalidConfiguration;
+    const size_t tiles = (g.N + kTcSites - 1) / kTcSites;
+    const int per = std::max(1, std::min(sc.max_blocks, occ * num_sms() / std::max(B, 1)));
+    const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)per)), (unsigned)B);
+    kern<<<grid, kTcThreads, smem, st>>>(g, h, psi, NO, drain_tiles, S, lam, sigma, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
+                           double* sigma, const Scratch& sc, int B, cudaStream_t st, int drain_tiles) {
+    if (NO < 1 || NO > kMaxOrbWide || !psi || !S || (lam && !sigma)) return cudaErrorInvalidValue;
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B || drain_tiles < 0) return cudaErrorInvalidValue;
+    if (drain_tiles == 0) drain_tiles = kDrainTiles;
+    const bool vec = g.N % 4 == 0 && reinterpret_cast<uintptr_t>(psi) % 16 == 0;
+    if (lam) return vec ? gram_tc_launch<true, true>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
+                        : gram_tc_launch<true, false>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st);
+    return vec ? gram_tc_launch<false, true>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st)
+               : gram_tc_launch<false, false>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st);
+}
+
+unsigned gram_tc_timeouts() {
+    unsigned v = 0;
+    cudaMemcpyFromSymbol(&v, g_tc_timeouts, sizeof(v));
+    return v;
+}
+
+}  // namespace lbks

@@ -10,7 +10,12 @@
 namespace lbks {
 
 constexpr int kThreads = 256;  // block size of every grid kernel
-constexpr int kMaxOrb = 8;
+constexpr int kMaxOrb = 8;       // orbitals handled by the fused stream-collide kernel
+constexpr int kMaxOrbWide = 64;  // orbitals handled at all (wide kernels above kMaxOrb)
+constexpr int kEmatWideStride = kMaxOrbWide * kMaxOrbWide + kMaxOrbWide;
+constexpr int kMpStride = 16;    // doubles per system: multipoles of rho
+constexpr int kEmatStride = 80;  // doubles per system: H (NO^2) and kinetic (NO) terms
+constexpr int kE4Stride = 4;     // doubles per system: energy integrals
 
 // D3Q19 velocity components in the order of include/lbks.h.
 __host__ __device__ constexpr int vel(int p, int a) {
@@ -55,21 +60,37 @@ struct Coef {
 };
 Coef make_coef(double omega, double theta, double dt, double h);
 
+// One grid shape; a launch covers gridDim.y systems of this shape (system =
+// blockIdx.y, arrays of consecutive systems at fixed strides).  `active`
+// (optional, one flag per system) lets finished systems skip a launch.
 struct Grid {
     int nx, ny, nz;
     uint32_t N;
     FastDiv divx, divy;
+    const int* active = nullptr;
 };
 Grid make_grid(int nx, int ny, int nz);
 
 // Reduction scratch: per-block partial sums and one arrival counter that the
-// last block resets.  Kernels sharing a Scratch must be stream-ordered.
+// last block resets, one region of each per system of a batched launch.
+// Kernels sharing a Scratch must be stream-ordered.
 struct Scratch {
-    double* partial = nullptr;  // max_blocks * max_vals doubles
-    unsigned* counter = nullptr;
-    int max_blocks = 0;
+    double* partial = nullptr;  // systems * max_blocks * max_vals doubles
+    unsigned* counter = nullptr;  // one per system
+    int max_blocks = 0;           // blocks per system
     int max_vals = 0;
+    int systems = 1;
 };
+
+// Overlap S = h^3 Psi Psi^T of N_O FP32 orbitals per system (N_O <= kMaxOrbWide)
+// on the tensor cores (bf16 hi/lo split, FP64 block and grid sums); with lam
+// also Lambda and sigma as the relaxation step needs them.  drain_tiles: tiles
+// of 64 sites summed in TMEM before the FP64 fold (0: the default, 8).
+cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
+                           double* sigma, const Scratch& sc, int B, cudaStream_t st, int drain_tiles = 0);
+// Blocks of the tensor-core Gram kernel whose bounded mbarrier waits expired
+// (device counter since the library was loaded; 0 unless the hardware stalled).
+unsigned gram_tc_timeouts();
 
 // Launch bookkeeping.
 void count_launches(uint64_t n);
@@ -95,41 +116,51 @@ struct OrbitalStart {  // Gaussian start of one orbital
     double cx, cy, cz, width;
 };
 
+// Launchers of one precision; each covers B systems of the grid's shape,
+// arrays of consecutive systems at fixed strides (populations NO*19*N,
+// orbitals NO*N, W field max(NO-1,1)*N, potentials N, NO x NO matrices,
+// NO scales, kMpStride multipoles, kEmatStride energy-matrix entries).
 struct PrecisionOps {
-    cudaError_t (*relax)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, cudaStream_t);
-    cudaError_t (*w_field)(int n_orb, size_t n_sites, double omega, const void* psi, const double* lam,
-                           void* u, cudaStream_t);
-    cudaError_t (*orth_apply)(int n_orb, size_t n_sites, const double* Linv, void* f, void* psi,
-                              cudaStream_t);
-    cudaError_t (*gram)(int n_orb, const Grid&, double h, const void* psi, double* S, const Scratch&,
+    cudaError_t (*relax)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int B, cudaStream_t);
+    cudaError_t (*w_field)(int n_orb, const Grid&, double omega, const void* psi, const double* lam, void* u, int B,
+                           cudaStream_t);
+    cudaError_t (*orth_apply)(int n_orb, const Grid&, const double* Linv, void* f, void* psi, int B, cudaStream_t);
+    cudaError_t (*gram)(int n_orb, const Grid&, double h, const void* psi, double* S, const Scratch&, int B,
                         cudaStream_t);
-    cudaError_t (*init_orbitals)(int n_orb, const Grid&, double h, const OrbitalStart* starts, void* psi,
+    // starts: device array [B][n_orb]
+    cudaError_t (*init_orbitals)(int n_orb, const Grid&, double h, const OrbitalStart* starts, void* psi, int B,
                                  cudaStream_t);
-    cudaError_t (*equilibrium)(int n_orb, size_t n_sites, const Coef&, const void* psi, void* f,
-                               cudaStream_t);
+    cudaError_t (*equilibrium)(int n_orb, const Grid&, const Coef&, const void* psi, void* f, int B, cudaStream_t);
     // rho = 2 sum psi^2 and its multipoles mp[10] = {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz}
     cudaError_t (*density)(int n_orb, const Grid&, double h, const void* psi, double* rho, double* mp,
-                           const Scratch&, cudaStream_t);
-    // H[j][k] = <psi_j|T_h + V|psi_k>, kin[j] = <psi_j|T_h|psi_j>  (out: n_orb^2 + n_orb doubles)
+                           const Scratch&, int B, cudaStream_t);
+    // H[j][k] = <psi_j|T_h + V|psi_k>, kin[j] = <psi_j|T_h|psi_j>  (n_orb^2 + n_orb doubles per system)
     cudaError_t (*energy_matrix)(int n_orb, const Grid&, const Coef&, const void* psi, const double* V,
-                                 double* out, const Scratch&, cudaStream_t);
-    size_t elem;
+                                 double* out, const Scratch&, int B, cudaStream_t);
+    size_t elem;      // bytes of a stored population
+    size_t psi_elem;  // bytes of an orbital / W-field value (the compute type)
 };
 const PrecisionOps& ops_f64();
 const PrecisionOps& ops_f32();
+const PrecisionOps& ops_bf16();  // bfloat16 populations, float arithmetic and orbitals
+// Widens n bfloat16 populations to float (the switch to the FP32 polish phase).
+cudaError_t launch_bf16_to_f32(const void* src, void* dst, size_t n, cudaStream_t);
 
 // ----------------------------------------------------------------- field ops
 // lbks_fields.cu (always FP64)
-cudaError_t launch_vext(const Grid&, double h, int n_atoms, const double* atoms_dev /*4 per atom*/,
-                        double a, double* v, cudaStream_t);
-cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, cudaStream_t);
+constexpr int kMaxAtoms = 256;
+// counts[B] atoms per system, atoms[B][kMaxAtoms][4] = (x, y, z, Z)
+cudaError_t launch_vext(const Grid&, double h, const int* counts, const double* atoms, double a, double* v, int B,
+                        cudaStream_t);
+cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, const int* active, int B,
+                            cudaStream_t);
 cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t);
 cudaError_t launch_lda(size_t n, const double* rho, double* eps, double* v, cudaStream_t);
 // V_out = V_ext + V_H + v_xc(rho); V_in = first ? V_out : mix V_out + (1 - mix) V_in;
 // e4 = h^3 {sum V_ext rho, sum V_H rho, sum rho eps_xc, sum rho}
 cudaError_t launch_potential(const Grid&, double h, const double* rho, const double* vext,
                              const double* vh, double* vout, double* vin, int first, double mix,
-                             double* e4, const Scratch&, cudaStream_t);
+                             double* e4, const Scratch&, int B, cudaStream_t);
 
 struct CGState {  // device-resident scalars of the preconditioned CG
     double bb, rr, rz, pap, alpha, beta, relres;
@@ -151,15 +182,17 @@ struct MGHierarchy {
 };
 // lbks_poisson.cu
 int mg_levels(int nx, int ny, int nz);
-size_t mg_coarse_doubles(int nx, int ny, int nz);           // x, b, r of every level below the finest
-MGHierarchy make_hierarchy(const Grid& fine, double* coarse);  // carves `coarse` into the levels
+size_t mg_coarse_doubles(int nx, int ny, int nz);  // x, b, r of every level below the finest, one system
+// Carves `coarse` (B * mg_coarse_doubles) into the levels; level arrays hold
+// the B systems consecutively.
+MGHierarchy make_hierarchy(const Grid& fine, double* coarse, int B);
 // Builds the right-hand side (4 pi h^2 rho + ghost values) and r = b - A x.
 cudaError_t launch_poisson_start(const Grid&, double h, const double* rho, double* x, double rtol,
-                                 const PoissonBufs&, const Scratch&, cudaStream_t);
+                                 const PoissonBufs&, const Scratch&, int B, cudaStream_t);
 // `iters` preconditioned CG iterations (no-ops once converged).
 cudaError_t launch_poisson_iterate(const Grid&, double* x, double rtol, int iters, const PoissonBufs&,
-                                   const MGHierarchy&, const Scratch&, cudaStream_t);
+                                   const MGHierarchy&, const Scratch&, int B, cudaStream_t);
 cudaError_t launch_multipoles_from_rho(const Grid&, double h, const double* rho, double* mp,
-                                       const Scratch&, cudaStream_t);
+                                       const Scratch&, int B, cudaStream_t);
 
 }  // namespace lbks

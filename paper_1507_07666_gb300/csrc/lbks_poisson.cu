@@ -30,7 +30,11 @@ int grid_for(size_t n, int cap_blocks) {
     return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap_blocks));
 }
 
-int red_cap(const Scratch& sc, int vals) { return sc.max_vals >= vals ? std::min(sc.max_blocks, num_sms() * 4) : 0; }
+// Blocks per system of a reduction kernel over B systems.
+int red_cap(const Scratch& sc, int vals, int B) {
+    if (sc.max_vals < vals || sc.systems < B) return 0;
+    return std::max(1, std::min(sc.max_blocks, num_sms() * 4 / std::max(B, 1)));
+}
 
 __device__ __forceinline__ void decode3(const Grid& g, uint32_t s, int& x, int& y, int& z) {
     const uint32_t q = g.divx.div(s);
@@ -54,6 +58,15 @@ __device__ __forceinline__ double stencil(const Grid& g, const double* __restric
     return t;
 }
 
+// The system's slice of the PCG vectors and scalars.
+__device__ __forceinline__ PoissonBufs at_sys(PoissonBufs pb, size_t N) {
+    const size_t o = (size_t)blockIdx.y * N;
+    pb.b += o; pb.r += o; pb.p += o; pb.ap += o; pb.z += o; pb.tmp += o;
+    pb.cg += blockIdx.y;
+    pb.mp += (size_t)blockIdx.y * kMpStride;
+    return pb;
+}
+
 __device__ __forceinline__ double multipole_value(const double* mp, double X, double Y, double Z) {
     const double r2 = X * X + Y * Y + Z * Z;
     const double r = sqrt(r2);
@@ -69,7 +82,9 @@ __device__ __forceinline__ double multipole_value(const double* mp, double X, do
 // x = (b + scale * sum nb x) / (6 scale) at sites with (x+y+z) % 2 == colour.
 __global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, double scale, int colour, double* __restrict__ x,
                                                         const double* __restrict__ b, const CGState* cg) {
-    if (cg->done) return;
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    x += (size_t)blockIdx.y * g.N;
+    b += (size_t)blockIdx.y * g.N;
     const double inv = 1.0 / (6.0 * scale);
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         int ix, iy, iz;
@@ -84,7 +99,10 @@ __global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, double scale, in
 __global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, double scale, const double* __restrict__ x,
                                                           const double* __restrict__ b, double* __restrict__ r,
                                                           const CGState* cg) {
-    if (cg->done) return;
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    x += (size_t)blockIdx.y * g.N;
+    b += (size_t)blockIdx.y * g.N;
+    r += (size_t)blockIdx.y * g.N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         int ix, iy, iz;
         decode3(g, s, ix, iy, iz);
@@ -96,7 +114,9 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, double scale, 
 // prod_axis (1 at the centre, 1/2 beside it)  (= P^T r)
 __global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, const double* __restrict__ rf,
                                                           double* __restrict__ bc, const CGState* cg) {
-    if (cg->done) return;
+    if (inactive(gf) || cg[blockIdx.y].done) return;
+    rf += (size_t)blockIdx.y * gf.N;
+    bc += (size_t)blockIdx.y * gc.N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < gc.N; s += gridDim.x * kThreads) {
         int I, J, K;
         decode3(gc, s, I, J, K);
@@ -139,7 +159,9 @@ __device__ __forceinline__ int interp_axis(int i, int m, int* c, double* w) {
 // x_f += P x_c (trilinear, zero ghosts)
 __global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const double* __restrict__ xc,
                                                          double* __restrict__ xf, const CGState* cg) {
-    if (cg->done) return;
+    if (inactive(gf) || cg[blockIdx.y].done) return;
+    xc += (size_t)blockIdx.y * gc.N;
+    xf += (size_t)blockIdx.y * gf.N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < gf.N; s += gridDim.x * kThreads) {
         int x, y, z;
         decode3(gf, s, x, y, z);
@@ -161,7 +183,9 @@ __global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const
 // kCoarse black/red sweeps, a barrier between colours.
 __global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, double scale, double* __restrict__ x,
                                                               const double* __restrict__ b, const CGState* cg) {
-    if (cg->done) return;
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    x += (size_t)blockIdx.y * g.N;
+    b += (size_t)blockIdx.y * g.N;
     const double inv = 1.0 / (6.0 * scale);
     for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) x[s] = 0.0;
     __syncthreads();
@@ -180,8 +204,10 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, double sca
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mg_zero(size_t n, double* __restrict__ x, const CGState* cg) {
-    if (cg->done) return;
+__global__ void __launch_bounds__(kThreads) k_mg_zero(Grid g, double* __restrict__ x, const CGState* cg) {
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    const size_t n = g.N;
+    x += (size_t)blockIdx.y * n;
     for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) x[s] = 0.0;
 }
 
@@ -190,6 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_mg_zero(size_t n, double* __restri
 __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const double* __restrict__ rho,
                                                         const double* __restrict__ x, double rtol, PoissonBufs pb,
                                                         Scratch sc) {
+    if (inactive(g)) return;
+    pb = at_sys(pb, g.N);
+    rho += (size_t)blockIdx.y * g.N;
+    x += (size_t)blockIdx.y * g.N;
     const double kPi = 3.141592653589793238462643383279502884;
     double acc[2] = {0.0, 0.0};
     const double* mp = pb.mp;
@@ -211,9 +241,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
         acc[0] += b * b;
         acc[1] += r * r;
     }
-    block_sum_store<2>(acc, sc.partial + (size_t)blockIdx.x * 2);
+    double* partial = sys_partial(sc);
+    block_sum_store<2>(acc, partial + (size_t)blockIdx.x * 2);
     __shared__ double tot[2];
-    if (grid_total<2>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<2>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         CGState* cg = pb.cg;
         cg->bb = tot[0];
         cg->rr = tot[1];
@@ -226,13 +257,16 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
 
 // rz = r . z; beta = rz / rz_old (0 on the first iteration)
 __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scratch sc) {
+    if (inactive(g)) return;
+    pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
     double acc[1] = {0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
         acc[0] += pb.r[s] * pb.z[s];
-    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    double* partial = sys_partial(sc);
+    block_sum_store<1>(acc, partial + (size_t)blockIdx.x);
     __shared__ double tot[1];
-    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<1>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         CGState* cg = pb.cg;
         cg->beta = cg->rz > 0.0 ? tot[0] / cg->rz : 0.0;
         cg->rz = tot[0];
@@ -241,6 +275,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scr
 
 // p = z + beta p
 __global__ void __launch_bounds__(kThreads) k_pcg_dir(Grid g, PoissonBufs pb) {
+    if (inactive(g)) return;
+    pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
     const double beta = pb.cg->beta;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
@@ -249,6 +285,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_dir(Grid g, PoissonBufs pb) {
 
 // ap = A p; alpha = rz / (p . ap)
 __global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scratch sc) {
+    if (inactive(g)) return;
+    pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
     double acc[1] = {0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
@@ -258,9 +296,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scr
         pb.ap[s] = a;
         acc[0] += pb.p[s] * a;
     }
-    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    double* partial = sys_partial(sc);
+    block_sum_store<1>(acc, partial + (size_t)blockIdx.x);
     __shared__ double tot[1];
-    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<1>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         pb.cg->pap = tot[0];
         pb.cg->alpha = pb.cg->rz / tot[0];
     }
@@ -269,7 +308,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scr
 // x += alpha p; r -= alpha ap; convergence test on |r| / |b|
 __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
                                                          Scratch sc) {
+    if (inactive(g)) return;
+    pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
+    x += (size_t)blockIdx.y * g.N;
     const double alpha = pb.cg->alpha;
     double acc[1] = {0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
@@ -278,9 +320,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
         pb.r[s] = r;
         acc[0] += r * r;
     }
-    block_sum_store<1>(acc, sc.partial + (size_t)blockIdx.x);
+    double* partial = sys_partial(sc);
+    block_sum_store<1>(acc, partial + (size_t)blockIdx.x);
     __shared__ double tot[1];
-    if (grid_total<1>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<1>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         CGState* cg = pb.cg;
         cg->rr = tot[0];
         cg->iters += 1;
@@ -290,22 +333,23 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
 }
 
 cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* tmp0, const CGState* cg, int ge,
-                   cudaStream_t st, uint64_t* nl) {
+                   int Bs, cudaStream_t st, uint64_t* nl) {
     // level 0 works on (x = z0, b = r0, r = tmp0); levels >= 1 on their own arrays
     auto X = [&](int l) { return l == 0 ? z0 : H.lev[l].x; };
     auto B = [&](int l) -> const double* { return l == 0 ? r0 : H.lev[l].b; };
     auto R = [&](int l) { return l == 0 ? tmp0 : H.lev[l].r; };
+    auto grid = [&](size_t n) { return dim3(grid_for(n, std::max(1, ge / Bs)), Bs); };
     const int L = H.nlev;
     for (int l = 0; l < L; ++l) {
         const Grid& g = H.lev[l].g;
         const double sc = (double)(1 << l);
-        const int gl = grid_for(g.N, ge);
+        const dim3 gl = grid(g.N);
         if (l == L - 1 && g.N <= kCoarseSites) {
-            k_mg_coarse_solve<<<1, kThreads, 0, st>>>(g, sc, X(l), B(l), cg);
+            k_mg_coarse_solve<<<dim3(1, Bs), kThreads, 0, st>>>(g, sc, X(l), B(l), cg);
             ++*nl;
             break;
         }
-        k_mg_zero<<<gl, kThreads, 0, st>>>(g.N, X(l), cg);
+        k_mg_zero<<<gl, kThreads, 0, st>>>(g, X(l), cg);
         ++*nl;
         if (l == L - 1) {
             for (int k = 0; k < kCoarse; ++k) {
@@ -325,13 +369,13 @@ cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* t
         }
         k_mg_residual<<<gl, kThreads, 0, st>>>(g, sc, X(l), B(l), R(l), cg);
         const Grid& gc = H.lev[l + 1].g;
-        k_mg_restrict<<<grid_for(gc.N, ge), kThreads, 0, st>>>(g, gc, R(l), H.lev[l + 1].b, cg);
+        k_mg_restrict<<<grid(gc.N), kThreads, 0, st>>>(g, gc, R(l), H.lev[l + 1].b, cg);
         *nl += 2 * kPre + 3;
     }
     for (int l = L - 2; l >= 0; --l) {
         const Grid& g = H.lev[l].g;
         const double sc = (double)(1 << l);
-        const int gl = grid_for(g.N, ge);
+        const dim3 gl = grid(g.N);
         k_mg_prolong<<<gl, kThreads, 0, st>>>(g, H.lev[l + 1].g, X(l + 1), X(l), cg);
         for (int k = 0; k < kPre; ++k) {
             k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
@@ -367,7 +411,7 @@ size_t mg_coarse_doubles(int nx, int ny, int nz) {
     return total;
 }
 
-MGHierarchy make_hierarchy(const Grid& fine, double* coarse) {
+MGHierarchy make_hierarchy(const Grid& fine, double* coarse, int B) {
     MGHierarchy H;
     H.nlev = mg_levels(fine.nx, fine.ny, fine.nz);
     H.lev[0].g = fine;
@@ -377,7 +421,8 @@ MGHierarchy make_hierarchy(const Grid& fine, double* coarse) {
         ny /= 2;
         nz /= 2;
         H.lev[l].g = make_grid(nx, ny, nz);
-        const size_t n = (size_t)nx * ny * nz;
+        H.lev[l].g.active = fine.active;
+        const size_t n = (size_t)nx * ny * nz * B;
         H.lev[l].x = coarse;
         H.lev[l].b = coarse + n;
         H.lev[l].r = coarse + 2 * n;
@@ -387,26 +432,27 @@ MGHierarchy make_hierarchy(const Grid& fine, double* coarse) {
 }
 
 cudaError_t launch_poisson_start(const Grid& g, double h, const double* rho, double* x, double rtol,
-                                 const PoissonBufs& pb, const Scratch& sc, cudaStream_t st) {
-    const int cap = red_cap(sc, 2);
+                                 const PoissonBufs& pb, const Scratch& sc, int B, cudaStream_t st) {
+    const int cap = red_cap(sc, 2, B);
     if (cap < 1) return cudaErrorInvalidValue;
-    k_pcg_start<<<grid_for(g.N, cap), kThreads, 0, st>>>(g, h, rho, x, rtol, pb, sc);
+    k_pcg_start<<<dim3(grid_for(g.N, cap), B), kThreads, 0, st>>>(g, h, rho, x, rtol, pb, sc);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int iters, const PoissonBufs& pb,
-                                   const MGHierarchy& H, const Scratch& sc, cudaStream_t st) {
-    const int cap = red_cap(sc, 1);
+                                   const MGHierarchy& H, const Scratch& sc, int B, cudaStream_t st) {
+    const int cap = red_cap(sc, 1, B);
     if (cap < 1) return cudaErrorInvalidValue;
-    const int gr = grid_for(g.N, cap);
+    const dim3 gr(grid_for(g.N, cap), B);
     const int ge = num_sms() * 8;
+    const dim3 gel(grid_for(g.N, std::max(1, ge / B)), B);
     uint64_t nl = 0;
     for (int i = 0; i < iters; ++i) {
-        cudaError_t e = vcycle(H, pb.r, pb.z, pb.tmp, pb.cg, ge, st, &nl);
+        cudaError_t e = vcycle(H, pb.r, pb.z, pb.tmp, pb.cg, ge, B, st, &nl);
         if (e != cudaSuccess) return e;
         k_pcg_rz<<<gr, kThreads, 0, st>>>(g, pb, sc);
-        k_pcg_dir<<<grid_for(g.N, ge), kThreads, 0, st>>>(g, pb);
+        k_pcg_dir<<<gel, kThreads, 0, st>>>(g, pb);
         k_pcg_ap<<<gr, kThreads, 0, st>>>(g, pb, sc);
         k_pcg_update<<<gr, kThreads, 0, st>>>(g, x, rtol, pb, sc);
         nl += 4;

@@ -66,4 +66,64 @@ __device__ __forceinline__ bool grid_total(const double* partial, unsigned* coun
     return true;
 }
 
+// This block's system in a batched launch, and the system's scratch region.
+__device__ __forceinline__ int sys_id() { return (int)blockIdx.y; }
+__device__ __forceinline__ bool inactive(const Grid& g) { return g.active && !g.active[blockIdx.y]; }
+__device__ __forceinline__ double* sys_partial(const Scratch& sc) {
+    return sc.partial + (size_t)blockIdx.y * sc.max_blocks * sc.max_vals;
+}
+__device__ __forceinline__ unsigned* sys_counter(const Scratch& sc) { return sc.counter + blockIdx.y; }
+
+// Index of pair (j, i), i <= j, in the packed lower triangle.
+__host__ __device__ constexpr int tri(int j, int i) { return j * (j + 1) / 2 + i; }
+
+// Grid total of K runtime values (per-system scratch region), fixed order.
+__device__ __forceinline__ bool grid_total_rt(const double* partial, unsigned* counter, double* tot, int K) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = w; k < K; k += nw) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partial + (size_t)b * K + k);
+        t = warp_sum1(t);
+        if (lane == 0) tot[k] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// Pair index -> (a, b), b <= a, in the packed lower triangle.
+__device__ __forceinline__ void tri_pair(int k, int& a, int& b) {
+    a = (int)((sqrtf(8.0f * k + 1.0f) - 1.0f) * 0.5f);
+    while (tri(a + 1, 0) <= k) ++a;
+    while (tri(a, 0) > k) --a;
+    b = k - tri(a, 0);
+}
+
+// Overlap S = h^3 * (packed pair totals), both triangles; with lam != nullptr
+// also Lambda_ab = S_ab / S_bb (a > b, else 0) and sigma_a = 1 / sqrt(S_aa),
+// the coupling and normalisation factors of the next relaxation step.
+// One thread.
+__device__ inline void store_overlap(const double* tot, int NO, double h, double* S, double* lam, double* sigma) {
+    const double h3 = h * h * h;
+    for (int a = 0; a < NO; ++a)
+        for (int b = 0; b <= a; ++b) {
+            const double v = h3 * tot[tri(a, b)];
+            S[a * NO + b] = v;
+            S[b * NO + a] = v;
+        }
+    if (lam) {
+        for (int a = 0; a < NO; ++a) {
+            for (int b = 0; b < NO; ++b) lam[a * NO + b] = (b < a) ? S[a * NO + b] / S[b * NO + b] : 0.0;
+            sigma[a] = 1.0 / sqrt(S[a * NO + a]);
+        }
+    }
+}
+
 }  // namespace lbks

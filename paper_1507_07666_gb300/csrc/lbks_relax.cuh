@@ -16,12 +16,21 @@
 #include "lbks_internal.cuh"
 #include "lbks_reduce.cuh"
 
-#include <algorithm>
+#include <cuda_bf16.h>
 
-// Minimum resident blocks per SM requested from the register allocator for
-// the stream-collide kernel (a tuning knob; 1 lets it use up to 255 registers).
+#include <algorithm>
+#include <type_traits>
+
+// Resident 256-thread blocks per SM that the register allocator must leave
+// room for in the stream-collide kernel (tuning knobs, set by measurement):
+// the general FP64 collision keeps 19 doubles per thread and gets fewer; the
+// batched build (per-system bases in registers) and more than five orbitals
+// get one more than that.
 #ifndef LBKS_RELAX_MIN_BLOCKS
-#define LBKS_RELAX_MIN_BLOCKS 1
+#define LBKS_RELAX_MIN_BLOCKS 4
+#endif
+#ifndef LBKS_RELAX_MIN_BLOCKS_WIDE
+#define LBKS_RELAX_MIN_BLOCKS_WIDE 2
 #endif
 
 namespace lbks {
@@ -32,8 +41,17 @@ __device__ __forceinline__ T ld_ro(const T* p) { return __ldg(p); }
 template <typename T>
 __device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
 
-// Index of pair (j, i), i <= j, in the packed lower triangle.
-__host__ __device__ constexpr int tri(int j, int i) { return j * (j + 1) / 2 + i; }
+// Populations are stored as TS and computed in T (TS = T, or bfloat16
+// storage with float arithmetic).
+template <typename T, typename TS>
+__device__ __forceinline__ T to_compute(TS v) { return (T)v; }
+template <>
+__device__ __forceinline__ float to_compute<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename TS, typename T>
+__device__ __forceinline__ TS to_store(T v) { return (TS)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
 
 // Neighbour bookkeeping of one site for pull streaming.
 struct Site {
@@ -71,20 +89,38 @@ __device__ __forceinline__ uint32_t source_index(const Grid& g, uint32_t s, int 
 // ---------------------------------------------------------------------------
 // Fused pull-stream + normalisation + BGK collision + potential source for
 // all NO orbitals of a site; psi epilogue; overlap partials; the last block
-// turns S into Lambda and the next step's scale sigma.
-template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads, LBKS_RELAX_MIN_BLOCKS) k_stream_collide(Grid g, Coef c, RelaxIO io,
-                                                                                  Scratch sc) {
+// turns S into Lambda and the next step's scale sigma.  One thread per site,
+// orbitals in sequence (the W source of orbital j reaches it through u_j, so
+// the orbitals of a site share nothing but the overlap products).
+// OM1: omega = 1, where the collision forgets the arriving populations and
+// only their sum psi enters (no (1 - omega) f term).
+template <typename T, int NO, bool OM1, bool BATCHED>
+constexpr int relax_min_blocks() {
+    return (sizeof(T) == 8 && !OM1) ? LBKS_RELAX_MIN_BLOCKS_WIDE
+           : (BATCHED || NO > 5)    ? LBKS_RELAX_MIN_BLOCKS_WIDE + 1
+                                    : LBKS_RELAX_MIN_BLOCKS;
+}
+
+// BATCHED: the launch covers several systems (system = blockIdx.y); the
+// single-system build keeps its array bases in the parameter bank instead of
+// registers, which the register-bound kernel needs.
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, (relax_min_blocks<T, NO, OM1, BATCHED>()))
+    k_stream_collide(Grid g, Coef c, RelaxIO io, Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
-    const T* __restrict__ fin = static_cast<const T*>(io.f_in);
-    const T* __restrict__ uin = static_cast<const T*>(io.u_in);
-    T* __restrict__ fout = static_cast<T*>(io.f_out);
-    T* __restrict__ psio = static_cast<T*>(io.psi_out);
+    if (BATCHED && inactive(g)) return;
     const uint32_t N = g.N;
+    const size_t y = BATCHED ? sys_id() : 0;
+    // per-system bases are formed where they are used, from the parameter
+    // bank and y, so that they need not stay live in registers
+    const TS* __restrict__ fin = static_cast<const TS*>(io.f_in);
+    const T* __restrict__ uin = static_cast<const T*>(io.u_in);
+    TS* __restrict__ fout = static_cast<TS*>(io.f_out);
+    T* __restrict__ psio = static_cast<T*>(io.psi_out);
 
     T sig[NO];
 #pragma unroll
-    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[j];
+    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[y * NO + j];
     const T om = (T)c.omega, dt = (T)c.dt, om1 = (T)(1.0 - c.omega);
     const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
     const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
@@ -95,17 +131,19 @@ __global__ void __launch_bounds__(kThreads, LBKS_RELAX_MIN_BLOCKS) k_stream_coll
 
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
         const Site t = decode(g, s);
-        const T vr = (T)__ldg(io.V + s);
+        const T vr = (T)__ldg(io.V + y * N + s);
         T psi[NO];
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
-            const T* fj = fin + (size_t)j * 19 * N;
+            const TS* fj = fin + (y * NO + j) * 19 * N;
+            const T* uj = (j > 0 && uin != nullptr) ? uin + (y * (NO > 1 ? NO - 1 : 1) + j - 1) * N : nullptr;
+            TS* oj = fout + (y * NO + j) * 19 * N;
+            // all 19 loads are issued before any use (memory-level parallelism)
             T gp[19];
 #pragma unroll
             for (int p = 0; p < 19; ++p)
-                gp[p] = has_source(t, p) ? ld_ro(fj + (size_t)p * N + source_index(g, s, p)) : T(0);
-            if (j > 0 && uin != nullptr) {
-                const T* uj = uin + (size_t)(j - 1) * N;
+                gp[p] = has_source(t, p) ? to_compute<T>(ld_ro(fj + (size_t)p * N + source_index(g, s, p))) : T(0);
+            if (uj) {
 #pragma unroll
                 for (int p = 0; p < 19; ++p)
                     if (has_source(t, p)) gp[p] += xi[vclass(p)] * ld_ro(uj + source_index(g, s, p));
@@ -117,10 +155,10 @@ __global__ void __launch_bounds__(kThreads, LBKS_RELAX_MIN_BLOCKS) k_stream_coll
             const T A = om * ps, B = dt * vr * ps;
             const T e[3] = {xi[0] * A - chi[0] * B, xi[1] * A - chi[1] * B, xi[2] * A - chi[2] * B};
             const T c1 = om1 * sig[j];
-            T* oj = fout + (size_t)j * 19 * N;
 #pragma unroll
-            for (int p = 0; p < 19; ++p) st_stream(oj + (size_t)p * N + s, c1 * gp[p] + e[vclass(p)]);
-            psio[(size_t)j * N + s] = ps;
+            for (int p = 0; p < 19; ++p)
+                st_stream(oj + (size_t)p * N + s, to_store<TS>(OM1 ? e[vclass(p)] : c1 * gp[p] + e[vclass(p)]));
+            psio[(y * NO + j) * N + s] = ps;
             psi[j] = ps;
         }
 #pragma unroll
@@ -132,28 +170,37 @@ __global__ void __launch_bounds__(kThreads, LBKS_RELAX_MIN_BLOCKS) k_stream_coll
     double v[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) v[k] = (double)acc[k];
-    block_sum_store<NP>(v, sc.partial + (size_t)blockIdx.x * NP);
+    double* partial = sc.partial + y * sc.max_blocks * sc.max_vals;
+    block_sum_store<NP>(v, partial + (size_t)blockIdx.x * NP);
     __shared__ double tot[NP];
-    if (grid_total<NP>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0) {
+        double* S_out = io.S_out + y * NO * NO;
+        double* lambda_out = io.lambda_out + y * NO * NO;
+        double* sigma_out = io.sigma_out + y * NO;
         const double h3 = c.h * c.h * c.h;
         for (int j = 0; j < NO; ++j)
             for (int i = 0; i <= j; ++i) {
                 const double sji = h3 * tot[tri(j, i)];
-                io.S_out[j * NO + i] = sji;
-                io.S_out[i * NO + j] = sji;
+                S_out[j * NO + i] = sji;
+                S_out[i * NO + j] = sji;
             }
         for (int j = 0; j < NO; ++j) {
             for (int k = 0; k < NO; ++k)
-                io.lambda_out[j * NO + k] = (k < j) ? io.S_out[j * NO + k] / io.S_out[k * NO + k] : 0.0;
-            io.sigma_out[j] = 1.0 / sqrt(io.S_out[j * NO + j]);
+                lambda_out[j * NO + k] = (k < j) ? S_out[j * NO + k] / S_out[k * NO + k] : 0.0;
+            sigma_out[j] = 1.0 / sqrt(S_out[j * NO + j]);
         }
     }
 }
 
 // u_(j-1)(r) = -omega sum_{k<j} Lambda_jk psi_k(r)
 template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads) k_w_field(size_t n, double omega, const T* __restrict__ psi,
+__global__ void __launch_bounds__(kThreads) k_w_field(const Grid g, double omega, const T* __restrict__ psi,
                                                       const double* __restrict__ lam, T* __restrict__ u) {
+    if (inactive(g)) return;
+    const size_t n = g.N, y = sys_id();
+    psi += y * NO * n;
+    lam += y * NO * NO;
+    u += y * (NO - 1) * n;
     T l[NO][NO];
 #pragma unroll
     for (int j = 0; j < NO; ++j)
@@ -174,9 +221,14 @@ __global__ void __launch_bounds__(kThreads) k_w_field(size_t n, double omega, co
 }
 
 // f_jp <- sum_k Linv_jk f_kp, psi_j <- sum_k Linv_jk psi_k, in place per site.
-template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads) k_orth_apply(size_t n, const double* __restrict__ Linv,
-                                                         T* __restrict__ f, T* __restrict__ psi) {
+template <typename TS, typename T, int NO>
+__global__ void __launch_bounds__(kThreads) k_orth_apply(const Grid g, const double* __restrict__ Linv,
+                                                         TS* __restrict__ f, T* __restrict__ psi) {
+    if (inactive(g)) return;
+    const size_t n = g.N, y = sys_id();
+    Linv += y * NO * NO;
+    if (f) f += y * NO * 19 * n;
+    if (psi) psi += y * NO * n;
     T L[NO][NO];
 #pragma unroll
     for (int j = 0; j < NO; ++j)
@@ -188,13 +240,13 @@ __global__ void __launch_bounds__(kThreads) k_orth_apply(size_t n, const double*
             for (int p = 0; p < 19; ++p) {
                 T a[NO];
 #pragma unroll
-                for (int k = 0; k < NO; ++k) a[k] = f[((size_t)k * 19 + p) * n + s];
+                for (int k = 0; k < NO; ++k) a[k] = to_compute<T>(f[((size_t)k * 19 + p) * n + s]);
 #pragma unroll
                 for (int j = 0; j < NO; ++j) {
                     T o = T(0);
 #pragma unroll
                     for (int k = 0; k <= j; ++k) o += L[j][k] * a[k];
-                    f[((size_t)j * 19 + p) * n + s] = o;
+                    f[((size_t)j * 19 + p) * n + s] = to_store<TS>(o);
                 }
             }
         }
@@ -218,6 +270,9 @@ template <typename T, int NO>
 __global__ void __launch_bounds__(kThreads) k_gram(Grid g, double h, const T* __restrict__ psi, double* S,
                                                    Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
+    if (inactive(g)) return;
+    psi += (size_t)sys_id() * NO * g.N;
+    S += (size_t)sys_id() * NO * NO;
     double acc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = 0.0;
@@ -231,9 +286,10 @@ __global__ void __launch_bounds__(kThreads) k_gram(Grid g, double h, const T* __
 #pragma unroll
             for (int i = 0; i <= j; ++i) acc[tri(j, i)] += a[j] * a[i];
     }
-    block_sum_store<NP>(acc, sc.partial + (size_t)blockIdx.x * NP);
+    double* partial = sys_partial(sc);
+    block_sum_store<NP>(acc, partial + (size_t)blockIdx.x * NP);
     __shared__ double tot[NP];
-    if (grid_total<NP>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<NP>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = h * h * h;
         for (int j = 0; j < NO; ++j)
             for (int i = 0; i <= j; ++i) {
@@ -243,14 +299,14 @@ __global__ void __launch_bounds__(kThreads) k_gram(Grid g, double h, const T* __
     }
 }
 
-struct StartsArg {
-    OrbitalStart o[kMaxOrb];
-};
-
-// psi0_j(r) = exp(-|r - c_j|^2 / (2 w_j^2))
+// psi0_j(r) = exp(-|r - c_j|^2 / (2 w_j^2)); starts[system][j]
 template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads) k_init_orbitals(Grid g, double h, StartsArg st, T* __restrict__ psi) {
+__global__ void __launch_bounds__(kThreads) k_init_orbitals(Grid g, double h, const OrbitalStart* __restrict__ starts,
+                                                            T* __restrict__ psi) {
+    if (inactive(g)) return;
     const uint32_t N = g.N;
+    const OrbitalStart* st = starts + (size_t)sys_id() * NO;
+    psi += (size_t)sys_id() * NO * N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
         const uint32_t q = g.divx.div(s);
         const int x = (int)(s - q * (uint32_t)g.nx);
@@ -260,24 +316,28 @@ __global__ void __launch_bounds__(kThreads) k_init_orbitals(Grid g, double h, St
                      rz = ((int)z - 0.5 * (g.nz - 1)) * h;
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
-            const double dx = rx - st.o[j].cx, dy = ry - st.o[j].cy, dz = rz - st.o[j].cz;
-            const double w = st.o[j].width;
+            const double dx = rx - st[j].cx, dy = ry - st[j].cy, dz = rz - st[j].cz;
+            const double w = st[j].width;
             psi[(size_t)j * N + s] = (T)exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * w * w));
         }
     }
 }
 
 // f_jp = xi_p psi_j
-template <typename T, int NO>
-__global__ void __launch_bounds__(kThreads) k_equilibrium(size_t n, Coef c, const T* __restrict__ psi,
-                                                          T* __restrict__ f) {
+template <typename TS, typename T, int NO>
+__global__ void __launch_bounds__(kThreads) k_equilibrium(const Grid g, Coef c, const T* __restrict__ psi,
+                                                          TS* __restrict__ f) {
+    if (inactive(g)) return;
+    const size_t n = g.N;
+    psi += (size_t)sys_id() * NO * n;
+    f += (size_t)sys_id() * NO * 19 * n;
     const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
     for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) {
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
             const T a = psi[(size_t)j * n + s];
 #pragma unroll
-            for (int p = 0; p < 19; ++p) f[((size_t)j * 19 + p) * n + s] = xi[vclass(p)] * a;
+            for (int p = 0; p < 19; ++p) f[((size_t)j * 19 + p) * n + s] = to_store<TS>(xi[vclass(p)] * a);
         }
     }
 }
@@ -286,6 +346,10 @@ __global__ void __launch_bounds__(kThreads) k_equilibrium(size_t n, Coef c, cons
 template <typename T, int NO>
 __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T* __restrict__ psi,
                                                       double* __restrict__ rho, double* mp, Scratch sc) {
+    if (inactive(g)) return;
+    psi += (size_t)sys_id() * NO * g.N;
+    rho += (size_t)sys_id() * g.N;
+    mp += (size_t)sys_id() * kMpStride;
     double acc[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) acc[k] = 0.0;
@@ -310,9 +374,10 @@ __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T*
         acc[4] += r * rx * rx; acc[5] += r * ry * ry; acc[6] += r * rz * rz;
         acc[7] += r * rx * ry; acc[8] += r * rx * rz; acc[9] += r * ry * rz;
     }
-    block_sum_store<10>(acc, sc.partial + (size_t)blockIdx.x * 10);
+    double* partial = sys_partial(sc);
+    block_sum_store<10>(acc, partial + (size_t)blockIdx.x * 10);
     __shared__ double tot[10];
-    if (grid_total<10>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<10>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = h * h * h;
         const double tr = tot[4] + tot[5] + tot[6];
         mp[0] = h3 * tot[0];
@@ -329,6 +394,10 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix(Grid g, Coef c, cons
                                                             const double* __restrict__ V, double* out,
                                                             Scratch sc) {
     constexpr int K = NO * NO + NO;
+    if (inactive(g)) return;
+    psi += (size_t)sys_id() * NO * g.N;
+    V += (size_t)sys_id() * g.N;
+    out += (size_t)sys_id() * kEmatStride;
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
@@ -355,15 +424,23 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix(Grid g, Coef c, cons
 #pragma unroll
             for (int k = 0; k < NO; ++k) acc[j * NO + k] += a[j] * hp[k];
     }
-    block_sum_store<K>(acc, sc.partial + (size_t)blockIdx.x * K);
+    double* partial = sys_partial(sc);
+    block_sum_store<K>(acc, partial + (size_t)blockIdx.x * K);
     __shared__ double tot[K];
-    if (grid_total<K>(sc.partial, sc.counter, tot) && threadIdx.x == 0) {
+    if (grid_total<K>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = c.h * c.h * c.h;
         for (int k = 0; k < K; ++k) out[k] = h3 * tot[k];
     }
 }
 
+}  // namespace lbks
+
+#include "lbks_wide.cuh"
+
+namespace lbks {
+
 // ----------------------------------------------------------------- launchers
+// Every launcher covers B systems of one shape: grid (blocks per system, B).
 template <typename Kern>
 int blocks_per_sm(Kern kern) {
     int nb = 0;
@@ -371,203 +448,253 @@ int blocks_per_sm(Kern kern) {
     return nb;
 }
 
-inline int elementwise_grid(size_t n) {
+// Blocks per system: enough for the sites, at most `cap` resident blocks
+// shared by the B systems (at least one each) and the scratch's capacity.
+inline dim3 batch_grid(size_t n, int cap, int B, int scratch_blocks = 1 << 30) {
     const size_t need = (n + kThreads - 1) / kThreads;
-    return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)num_sms() * 8));
+    const int per = std::max(1, std::min(cap / std::max(B, 1), scratch_blocks));
+    return dim3((unsigned)std::max<size_t>(1, std::min<size_t>(need, (size_t)per)), (unsigned)B);
 }
+inline dim3 elementwise_grid(size_t n, int B) { return batch_grid(n, num_sms() * 8, B); }
 
-template <typename Kern>
-int reduction_grid(Kern kern, size_t n, const Scratch& sc, int vals) {
-    static_assert(sizeof(Kern) > 0, "");
-    int cap = blocks_per_sm(kern) * num_sms();
-    const int by_scratch = sc.max_vals >= vals ? sc.max_blocks : 0;
-    cap = std::min(cap, by_scratch);
-    const size_t need = (n + kThreads - 1) / kThreads;
-    return (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap));
-}
-
-template <typename T>
+template <typename TS, typename T>
 struct Ops {
-    template <int NO>
-    static cudaError_t relax_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, cudaStream_t st) {
-        auto kern = k_stream_collide<T, NO>;
+    template <int NO, bool OM1, bool BATCHED>
+    static cudaError_t relax_nmb(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                 cudaStream_t st) {
+        auto kern = k_stream_collide<TS, T, NO, OM1, BATCHED>;
         static const int nb = blocks_per_sm(kern);
-        const int cap = std::min(nb * num_sms(), sc.max_blocks);
-        const size_t need = (g.N + kThreads - 1) / kThreads;
-        const int grid = (int)std::max<size_t>(1, std::min<size_t>(need, (size_t)cap));
-        if (sc.max_vals < NO * (NO + 1) / 2 || grid < 1) return cudaErrorInvalidValue;
-        kern<<<grid, kThreads, 0, st>>>(g, c, io, sc);
+        if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+        kern<<<batch_grid(g.N, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
         count_launches(1);
         return cudaGetLastError();
     }
+    template <int NO, bool OM1>
+    static cudaError_t relax_nm(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                cudaStream_t st) {
+        return B > 1 ? relax_nmb<NO, OM1, true>(g, c, io, sc, B, st) : relax_nmb<NO, OM1, false>(g, c, io, sc, B, st);
+    }
     template <int NO>
-    static cudaError_t wfield_n(size_t n, double omega, const void* psi, const double* lam, void* u, cudaStream_t st) {
+    static cudaError_t relax_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                               cudaStream_t st) {
+        return c.omega == 1.0 ? relax_nm<NO, true>(g, c, io, sc, B, st) : relax_nm<NO, false>(g, c, io, sc, B, st);
+    }
+    template <int NO>
+    static cudaError_t wfield_n(const Grid& g, double omega, const void* psi, const double* lam, void* u, int B,
+                                cudaStream_t st) {
         if (NO < 2) return cudaSuccess;
-        k_w_field<T, NO><<<elementwise_grid(n), kThreads, 0, st>>>(n, omega, (const T*)psi, lam, (T*)u);
+        k_w_field<T, NO><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, omega, (const T*)psi, lam, (T*)u);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
-    static cudaError_t orth_n(size_t n, const double* Linv, void* f, void* psi, cudaStream_t st) {
-        k_orth_apply<T, NO><<<elementwise_grid(n), kThreads, 0, st>>>(n, Linv, (T*)f, (T*)psi);
+    static cudaError_t orth_n(const Grid& g, const double* Linv, void* f, void* psi, int B, cudaStream_t st) {
+        k_orth_apply<TS, T, NO><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, Linv, (TS*)f, (T*)psi);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
-    static cudaError_t gram_n(const Grid& g, double h, const void* psi, double* S, const Scratch& sc, cudaStream_t st) {
+    static cudaError_t gram_n(const Grid& g, double h, const void* psi, double* S, const Scratch& sc, int B,
+                              cudaStream_t st) {
         auto kern = k_gram<T, NO>;
-        const int grid = reduction_grid(kern, g.N, sc, NO * (NO + 1) / 2);
-        kern<<<grid, kThreads, 0, st>>>(g, h, (const T*)psi, S, sc);
+        if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+        kern<<<batch_grid(g.N, blocks_per_sm(kern) * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(
+            g, h, (const T*)psi, S, sc);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
-    static cudaError_t init_n(const Grid& g, double h, const OrbitalStart* starts, void* psi, cudaStream_t st) {
-        StartsArg a;
-        for (int j = 0; j < NO; ++j) a.o[j] = starts[j];
-        k_init_orbitals<T, NO><<<elementwise_grid(g.N), kThreads, 0, st>>>(g, h, a, (T*)psi);
+    static cudaError_t init_n(const Grid& g, double h, const OrbitalStart* starts, void* psi, int B,
+                              cudaStream_t st) {
+        k_init_orbitals<T, NO><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, h, starts, (T*)psi);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
-    static cudaError_t eq_n(size_t n, const Coef& c, const void* psi, void* f, cudaStream_t st) {
-        k_equilibrium<T, NO><<<elementwise_grid(n), kThreads, 0, st>>>(n, c, (const T*)psi, (T*)f);
+    static cudaError_t eq_n(const Grid& g, const Coef& c, const void* psi, void* f, int B, cudaStream_t st) {
+        k_equilibrium<TS, T, NO><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, c, (const T*)psi, (TS*)f);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
     static cudaError_t density_n(const Grid& g, double h, const void* psi, double* rho, double* mp,
-                                 const Scratch& sc, cudaStream_t st) {
+                                 const Scratch& sc, int B, cudaStream_t st) {
         auto kern = k_density<T, NO>;
-        const int grid = reduction_grid(kern, g.N, sc, 10);
-        kern<<<grid, kThreads, 0, st>>>(g, h, (const T*)psi, rho, mp, sc);
+        if (sc.max_vals < 10 || sc.systems < B) return cudaErrorInvalidValue;
+        kern<<<batch_grid(g.N, blocks_per_sm(kern) * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(
+            g, h, (const T*)psi, rho, mp, sc);
         count_launches(1);
         return cudaGetLastError();
     }
     template <int NO>
     static cudaError_t energy_n(const Grid& g, const Coef& c, const void* psi, const double* V, double* out,
-                                const Scratch& sc, cudaStream_t st) {
+                                const Scratch& sc, int B, cudaStream_t st) {
         auto kern = k_energy_matrix<T, NO>;
-        const int grid = reduction_grid(kern, g.N, sc, NO * NO + NO);
-        kern<<<grid, kThreads, 0, st>>>(g, c, (const T*)psi, V, out, sc);
+        if (sc.max_vals < NO * NO + NO || sc.systems < B) return cudaErrorInvalidValue;
+        kern<<<batch_grid(g.N, blocks_per_sm(kern) * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(
+            g, c, (const T*)psi, V, out, sc);
         count_launches(1);
         return cudaGetLastError();
     }
 
-    static cudaError_t relax(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc,
-                             cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return relax_n<1>(g, c, io, sc, st);
-            case 2: return relax_n<2>(g, c, io, sc, st);
-            case 3: return relax_n<3>(g, c, io, sc, st);
-            case 4: return relax_n<4>(g, c, io, sc, st);
-            case 5: return relax_n<5>(g, c, io, sc, st);
-            case 6: return relax_n<6>(g, c, io, sc, st);
-            case 7: return relax_n<7>(g, c, io, sc, st);
-            case 8: return relax_n<8>(g, c, io, sc, st);
-            default: return cudaErrorInvalidValue;
-        }
+    // ---- more than kMaxOrb orbitals (runtime orbital count)
+    template <typename Kern>
+    static cudaError_t with_smem(Kern kern, size_t bytes) {
+        return bytes > 48 * 1024 ? cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+                                 : cudaSuccess;
     }
-    static cudaError_t w_field(int n_orb, size_t n, double omega, const void* psi, const double* lam, void* u,
-                               cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return cudaSuccess;
-            case 2: return wfield_n<2>(n, omega, psi, lam, u, st);
-            case 3: return wfield_n<3>(n, omega, psi, lam, u, st);
-            case 4: return wfield_n<4>(n, omega, psi, lam, u, st);
-            case 5: return wfield_n<5>(n, omega, psi, lam, u, st);
-            case 6: return wfield_n<6>(n, omega, psi, lam, u, st);
-            case 7: return wfield_n<7>(n, omega, psi, lam, u, st);
-            case 8: return wfield_n<8>(n, omega, psi, lam, u, st);
-            default: return cudaErrorInvalidValue;
-        }
+    static dim3 tile_grid(const Grid& g, int B, const Scratch& sc) {
+        const size_t tiles = (g.N + kWideTile - 1) / kWideTile;
+        const int per = std::max(1, std::min(sc.max_blocks, num_sms() * 2 / std::max(B, 1)));
+        return dim3((unsigned)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)per)), (unsigned)B);
     }
-    static cudaError_t orth_apply(int n_orb, size_t n, const double* Linv, void* f, void* psi, cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return orth_n<1>(n, Linv, f, psi, st);
-            case 2: return orth_n<2>(n, Linv, f, psi, st);
-            case 3: return orth_n<3>(n, Linv, f, psi, st);
-            case 4: return orth_n<4>(n, Linv, f, psi, st);
-            case 5: return orth_n<5>(n, Linv, f, psi, st);
-            case 6: return orth_n<6>(n, Linv, f, psi, st);
-            case 7: return orth_n<7>(n, Linv, f, psi, st);
-            case 8: return orth_n<8>(n, Linv, f, psi, st);
-            default: return cudaErrorInvalidValue;
-        }
+    template <bool LAM>
+    static cudaError_t gram_wide(int NO, const Grid& g, double h, const void* psi, double* S, double* lam,
+                                 double* sigma, const Scratch& sc, int B, cudaStream_t st) {
+        const int NP = NO * (NO + 1) / 2;
+        if (sc.max_vals < NP || sc.systems < B) return cudaErrorInvalidValue;
+        // FP32 orbitals, per-step overlap (sigma and Lambda): tensor cores.  The
+        // orthonormalising overlap keeps exact FP64 sums: it fixes the norms
+        // that density and energies see, where the tensor cores' truncating
+        // FP32 accumulation would leave a ~1e-6 relative bias.
+        if constexpr (std::is_same<T, float>::value)
+            if (LAM) return launch_gram_tc(NO, g, h, (const float*)psi, S, lam, sigma, sc, B, st);
+        auto kern = k_gram_wide<T, LAM>;
+        const size_t smem = (size_t)NO * kWideTile * sizeof(T) + sizeof(double) * NP;
+        cudaError_t e = with_smem(kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<tile_grid(g, B, sc), kThreads, smem, st>>>(g, h, (const T*)psi, NO, S, lam, sigma, sc);
+        count_launches(1);
+        return cudaGetLastError();
     }
-    static cudaError_t gram(int n_orb, const Grid& g, double h, const void* psi, double* S, const Scratch& sc,
-                            cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return gram_n<1>(g, h, psi, S, sc, st);
-            case 2: return gram_n<2>(g, h, psi, S, sc, st);
-            case 3: return gram_n<3>(g, h, psi, S, sc, st);
-            case 4: return gram_n<4>(g, h, psi, S, sc, st);
-            case 5: return gram_n<5>(g, h, psi, S, sc, st);
-            case 6: return gram_n<6>(g, h, psi, S, sc, st);
-            case 7: return gram_n<7>(g, h, psi, S, sc, st);
-            case 8: return gram_n<8>(g, h, psi, S, sc, st);
-            default: return cudaErrorInvalidValue;
-        }
+    static cudaError_t relax_wide(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                  cudaStream_t st) {
+        auto kern = c.omega == 1.0 ? k_stream_collide_wide<TS, T, true> : k_stream_collide_wide<TS, T, false>;
+        if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
+        kern<<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return gram_wide<true>(NO, g, c.h, io.psi_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st);
     }
-    static cudaError_t init_orbitals(int n_orb, const Grid& g, double h, const OrbitalStart* o, void* psi,
-                                     cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return init_n<1>(g, h, o, psi, st);
-            case 2: return init_n<2>(g, h, o, psi, st);
-            case 3: return init_n<3>(g, h, o, psi, st);
-            case 4: return init_n<4>(g, h, o, psi, st);
-            case 5: return init_n<5>(g, h, o, psi, st);
-            case 6: return init_n<6>(g, h, o, psi, st);
-            case 7: return init_n<7>(g, h, o, psi, st);
-            case 8: return init_n<8>(g, h, o, psi, st);
-            default: return cudaErrorInvalidValue;
-        }
+    static cudaError_t wfield_wide(int NO, const Grid& g, double omega, const void* psi, const double* lam, void* u,
+                                   int B, cudaStream_t st) {
+        const size_t smem = ((size_t)NO * kThreads + (size_t)NO * NO) * sizeof(T);
+        cudaError_t e = with_smem(k_w_field_wide<T>, smem);
+        if (e != cudaSuccess) return e;
+        k_w_field_wide<T><<<batch_grid(g.N, num_sms() * 2, B), kThreads, smem, st>>>(g, omega, (const T*)psi, lam,
+                                                                                      (T*)u, NO);
+        count_launches(1);
+        return cudaGetLastError();
     }
-    static cudaError_t equilibrium(int n_orb, size_t n, const Coef& c, const void* psi, void* f, cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return eq_n<1>(n, c, psi, f, st);
-            case 2: return eq_n<2>(n, c, psi, f, st);
-            case 3: return eq_n<3>(n, c, psi, f, st);
-            case 4: return eq_n<4>(n, c, psi, f, st);
-            case 5: return eq_n<5>(n, c, psi, f, st);
-            case 6: return eq_n<6>(n, c, psi, f, st);
-            case 7: return eq_n<7>(n, c, psi, f, st);
-            case 8: return eq_n<8>(n, c, psi, f, st);
-            default: return cudaErrorInvalidValue;
-        }
+    static cudaError_t orth_wide(int NO, const Grid& g, const double* Linv, void* f, void* psi, int B,
+                                 cudaStream_t st) {
+        const size_t smem = ((size_t)NO * kThreads + (size_t)NO * NO) * sizeof(T);
+        cudaError_t e = with_smem(k_orth_apply_wide<TS, T>, smem);
+        if (e != cudaSuccess) return e;
+        k_orth_apply_wide<TS, T><<<batch_grid(g.N, num_sms() * 2, B), kThreads, smem, st>>>(g, Linv, (TS*)f, (T*)psi,
+                                                                                             NO);
+        count_launches(1);
+        return cudaGetLastError();
     }
-    static cudaError_t density(int n_orb, const Grid& g, double h, const void* psi, double* rho, double* mp,
-                               const Scratch& sc, cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return density_n<1>(g, h, psi, rho, mp, sc, st);
-            case 2: return density_n<2>(g, h, psi, rho, mp, sc, st);
-            case 3: return density_n<3>(g, h, psi, rho, mp, sc, st);
-            case 4: return density_n<4>(g, h, psi, rho, mp, sc, st);
-            case 5: return density_n<5>(g, h, psi, rho, mp, sc, st);
-            case 6: return density_n<6>(g, h, psi, rho, mp, sc, st);
-            case 7: return density_n<7>(g, h, psi, rho, mp, sc, st);
-            case 8: return density_n<8>(g, h, psi, rho, mp, sc, st);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    static cudaError_t energy_matrix(int n_orb, const Grid& g, const Coef& c, const void* psi, const double* V,
-                                     double* out, const Scratch& sc, cudaStream_t st) {
-        switch (n_orb) {
-            case 1: return energy_n<1>(g, c, psi, V, out, sc, st);
-            case 2: return energy_n<2>(g, c, psi, V, out, sc, st);
-            case 3: return energy_n<3>(g, c, psi, V, out, sc, st);
-            case 4: return energy_n<4>(g, c, psi, V, out, sc, st);
-            case 5: return energy_n<5>(g, c, psi, V, out, sc, st);
-            case 6: return energy_n<6>(g, c, psi, V, out, sc, st);
-            case 7: return energy_n<7>(g, c, psi, V, out, sc, st);
-            case 8: return energy_n<8>(g, c, psi, V, out, sc, st);
-            default: return cudaErrorInvalidValue;
-        }
+    static cudaError_t energy_wide(int NO, const Grid& g, const Coef& c, const void* psi, const double* V, double* out,
+                                   const Scratch& sc, int B, cudaStream_t st) {
+        const int K = NO * (NO + 1) / 2 + NO;
+        if (sc.max_vals < K || sc.systems < B) return cudaErrorInvalidValue;
+        const size_t smem = 3 * (size_t)NO * kWideTile * sizeof(T) + sizeof(double) * K;
+        cudaError_t e = with_smem(k_energy_matrix_wide<T>, smem);
+        if (e != cudaSuccess) return e;
+        k_energy_matrix_wide<T><<<tile_grid(g, B, sc), kThreads, smem, st>>>(g, c, (const T*)psi, V, out, sc, NO);
+        count_launches(1);
+        return cudaGetLastError();
     }
 
+#define LBKS_SWITCH_NO(CALL)                  \
+    switch (n_orb) {                          \
+        case 1: return CALL(1);               \
+        case 2: return CALL(2);               \
+        case 3: return CALL(3);               \
+        case 4: return CALL(4);               \
+        case 5: return CALL(5);               \
+        case 6: return CALL(6);               \
+        case 7: return CALL(7);               \
+        case 8: return CALL(8);               \
+        default: return n_orb <= kMaxOrbWide ? WIDE : cudaErrorInvalidValue; \
+    }
+    static cudaError_t relax(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                             cudaStream_t st) {
+#define CALL(NO) relax_n<NO>(g, c, io, sc, B, st)
+#define WIDE relax_wide(n_orb, g, c, io, sc, B, st)
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t w_field(int n_orb, const Grid& g, double omega, const void* psi, const double* lam, void* u,
+                               int B, cudaStream_t st) {
+#define CALL(NO) wfield_n<NO>(g, omega, psi, lam, u, B, st)
+#define WIDE wfield_wide(n_orb, g, omega, psi, lam, u, B, st)
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t orth_apply(int n_orb, const Grid& g, const double* Linv, void* f, void* psi, int B,
+                                  cudaStream_t st) {
+#define CALL(NO) orth_n<NO>(g, Linv, f, psi, B, st)
+#define WIDE orth_wide(n_orb, g, Linv, f, psi, B, st)
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t gram(int n_orb, const Grid& g, double h, const void* psi, double* S, const Scratch& sc, int B,
+                            cudaStream_t st) {
+#define CALL(NO) gram_n<NO>(g, h, psi, S, sc, B, st)
+#define WIDE gram_wide<false>(n_orb, g, h, psi, S, nullptr, nullptr, sc, B, st)
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t init_orbitals(int n_orb, const Grid& g, double h, const OrbitalStart* o, void* psi, int B,
+                                     cudaStream_t st) {
+#define CALL(NO) init_n<NO>(g, h, o, psi, B, st)
+#define WIDE (k_init_orbitals_wide<T><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, h, o, (T*)psi, n_orb), \
+              count_launches(1), cudaGetLastError())
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t equilibrium(int n_orb, const Grid& g, const Coef& c, const void* psi, void* f, int B,
+                                   cudaStream_t st) {
+#define CALL(NO) eq_n<NO>(g, c, psi, f, B, st)
+#define WIDE (k_equilibrium_wide<TS, T><<<elementwise_grid(g.N, B), kThreads, 0, st>>>(g, c, (const T*)psi, (TS*)f, \
+                                                                                         n_orb),                   \
+              count_launches(1), cudaGetLastError())
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t density(int n_orb, const Grid& g, double h, const void* psi, double* rho, double* mp,
+                               const Scratch& sc, int B, cudaStream_t st) {
+#define CALL(NO) density_n<NO>(g, h, psi, rho, mp, sc, B, st)
+#define WIDE (k_density_wide<T><<<batch_grid(g.N, num_sms() * 4, B, sc.max_blocks), kThreads, 0, st>>>(    \
+                  g, h, (const T*)psi, rho, mp, sc, n_orb),                                              \
+              count_launches(1), cudaGetLastError())
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+    static cudaError_t energy_matrix(int n_orb, const Grid& g, const Coef& c, const void* psi, const double* V,
+                                     double* out, const Scratch& sc, int B, cudaStream_t st) {
+#define CALL(NO) energy_n<NO>(g, c, psi, V, out, sc, B, st)
+#define WIDE energy_wide(n_orb, g, c, psi, V, out, sc, B, st)
+        LBKS_SWITCH_NO(CALL)
+#undef WIDE
+#undef CALL
+    }
+#undef LBKS_SWITCH_NO
+
     static const PrecisionOps& table() {
-        static const PrecisionOps t = {&relax, &w_field, &orth_apply, &gram, &init_orbitals,
-                                       &equilibrium, &density, &energy_matrix, sizeof(T)};
+        static const PrecisionOps t = {&relax,   &w_field, &orth_apply,    &gram,      &init_orbitals,
+                                       &equilibrium, &density, &energy_matrix, sizeof(TS), sizeof(T)};
         return t;
     }
 };

@@ -3,5 +3,5 @@
 #include "lbks_relax.cuh"
 
 namespace lbks {
-const PrecisionOps& ops_f32() { return Ops<float>::table(); }
+const PrecisionOps& ops_f32() { return Ops<float, float>::table(); }
 }  // namespace lbks

@@ -2,5 +2,5 @@
 #include "lbks_relax.cuh"
 
 namespace lbks {
-const PrecisionOps& ops_f64() { return Ops<double>::table(); }
+const PrecisionOps& ops_f64() { return Ops<double, double>::table(); }
 }  // namespace lbks

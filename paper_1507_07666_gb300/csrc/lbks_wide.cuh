@@ -1,0 +1,354 @@
+// Relaxation kernels for more orbitals than the fused kernel handles
+// (kMaxOrb < N_O <= kMaxOrbWide): the orbital count is a runtime value, the
+// overlap products leave the stream-collide kernel for a tiled Gram kernel
+// (the N_O x N_O x N contraction S = h^3 Psi Psi^T), and the W field, the
+// orthonormalisation and the energy matrix stage orbital tiles in shared
+// memory.  Included by lbks_relax.cuh; same conventions (system = blockIdx.y,
+// arrays of consecutive systems, TS storage / T arithmetic).
+#pragma once
+
+namespace lbks {
+
+constexpr int kWideTile = 64;  // sites per shared-memory tile
+
+// Fused pull-stream + normalisation + collision + potential source, one
+// (site, orbital) per thread: blockIdx.y = system * N_O + orbital, so the
+// blocks of one orbital stream through its 19 population arrays together.
+// psi is written for the Gram kernel.  Every orbital also rereads V (8 B per
+// orbital-site, mostly from L2).
+template <typename TS, typename T, bool OM1>
+__global__ void __launch_bounds__(kThreads, 4) k_stream_collide_wide(Grid g, Coef c, RelaxIO io, int NO) {
+    const int y = (int)blockIdx.y / NO, j = (int)blockIdx.y - y * NO;
+    if (g.active && !g.active[y]) return;
+    const uint32_t N = g.N;
+    const uint32_t s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= N) return;
+    const size_t oj = (size_t)y * NO + j;  // orbital index over all systems
+    const TS* __restrict__ fj = static_cast<const TS*>(io.f_in) + oj * 19 * N;
+    const T* __restrict__ uj =
+        (j > 0 && io.u_in != nullptr) ? static_cast<const T*>(io.u_in) + ((size_t)y * (NO - 1) + j - 1) * N : nullptr;
+    TS* __restrict__ out = static_cast<TS*>(io.f_out) + oj * 19 * N;
+    const T om = (T)c.omega, dt = (T)c.dt, om1 = (T)(1.0 - c.omega);
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    const Site t = decode(g, s);
+    T gp[19];
+#pragma unroll
+    for (int p = 0; p < 19; ++p)
+        gp[p] = has_source(t, p) ? to_compute<T>(ld_ro(fj + (size_t)p * N + source_index(g, s, p))) : T(0);
+    if (uj) {
+#pragma unroll
+        for (int p = 0; p < 19; ++p)
+            if (has_source(t, p)) gp[p] += xi[vclass(p)] * ld_ro(uj + source_index(g, s, p));
+    }
+    const T vr = (T)__ldg(io.V + (size_t)y * N + s);
+    T ps = T(0);
+#pragma unroll
+    for (int p = 0; p < 19; ++p) ps += gp[p];
+    const T sig = (T)io.sigma_in[oj];
+    ps *= sig;
+    const T A = om * ps, B = dt * vr * ps;
+    const T e[3] = {xi[0] * A - chi[0] * B, xi[1] * A - chi[1] * B, xi[2] * A - chi[2] * B};
+    const T c1 = om1 * sig;
+#pragma unroll
+    for (int p = 0; p < 19; ++p)
+        st_stream(out + (size_t)p * N + s, to_store<TS>(OM1 ? e[vclass(p)] : c1 * gp[p] + e[vclass(p)]));
+    static_cast<T*>(io.psi_out)[oj * N + s] = ps;
+}
+
+// S = h^3 Psi Psi^T over the packed lower triangle (NP pairs): tiles of
+// kWideTile sites in shared memory, per-thread pair sums in T over a tile,
+// FP64 across tiles and blocks.  With LAM: Lambda and sigma as in the fused
+// kernel.  Dynamic shared memory: NO * kWideTile * sizeof(T) + NP doubles.
+template <typename T, bool LAM>
+__global__ void __launch_bounds__(kThreads) k_gram_wide(Grid g, double h, const T* __restrict__ psi, int NO,
+                                                        double* S, double* lam, double* sigma, Scratch sc) {
+    if (inactive(g)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* tile = reinterpret_cast<T*>(smem);  // [NO][kWideTile]
+    double* tot = reinterpret_cast<double*>(smem + (size_t)NO * kWideTile * sizeof(T));
+    const int NP = NO * (NO + 1) / 2;
+    const uint32_t N = g.N;
+    const size_t y = sys_id();
+    psi += y * NO * N;
+    constexpr int kMaxPairsPerThread = (kMaxOrbWide * (kMaxOrbWide + 1) / 2 + kThreads - 1) / kThreads;
+    double acc[kMaxPairsPerThread];
+    int pa[kMaxPairsPerThread], pb[kMaxPairsPerThread];
+#pragma unroll
+    for (int q = 0; q < kMaxPairsPerThread; ++q) {
+        acc[q] = 0.0;
+        const int k = threadIdx.x + q * kThreads;
+        if (k < NP) tri_pair(k, pa[q], pb[q]);
+        else pa[q] = pb[q] = -1;
+    }
+    const uint32_t tiles = (N + kWideTile - 1) / kWideTile;
+    for (uint32_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
+        const uint32_t base = ti * kWideTile;
+        for (int i = threadIdx.x; i < NO * kWideTile; i += kThreads) {
+            const int j = i / kWideTile, s = i % kWideTile;
+            tile[i] = (base + s < N) ? psi[(size_t)j * N + base + s] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMaxPairsPerThread; ++q) {
+            if (pa[q] < 0) continue;
+            const T* ra = tile + pa[q] * kWideTile;
+            const T* rb = tile + pb[q] * kWideTile;
+            T part = T(0);
+#pragma unroll 8
+            for (int s = 0; s < kWideTile; ++s) part += ra[s] * rb[s];
+            acc[q] += (double)part;
+        }
+        __syncthreads();
+    }
+    double* partial = sys_partial(sc);
+#pragma unroll
+    for (int q = 0; q < kMaxPairsPerThread; ++q) {
+        const int k = threadIdx.x + q * kThreads;
+        if (k < NP) partial[(size_t)blockIdx.x * NP + k] = acc[q];
+    }
+    if (grid_total_rt(partial, sys_counter(sc), tot, NP) && threadIdx.x == 0)
+        store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, sigma + y * NO);
+}
+
+// u_(j-1) = -omega sum_{k<j} Lambda_jk psi_k: orbital tile and Lambda in
+// shared memory, one site per thread.  Dynamic shared memory:
+// (NO * kThreads + NO * NO) * sizeof(T).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_w_field_wide(const Grid g, double omega, const T* __restrict__ psi,
+                                                           const double* __restrict__ lam, T* __restrict__ u, int NO) {
+    if (inactive(g)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* tile = reinterpret_cast<T*>(smem);  // [NO][kThreads]
+    T* L = tile + (size_t)NO * kThreads;   // [NO][NO]
+    const size_t n = g.N, y = sys_id();
+    psi += y * NO * n;
+    lam += y * NO * NO;
+    u += y * (NO - 1) * n;
+    for (int i = threadIdx.x; i < NO * NO; i += kThreads) L[i] = (T)(-omega * lam[i]);
+    const size_t tiles = (n + kThreads - 1) / kThreads;
+    for (size_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
+        const size_t s = ti * kThreads + threadIdx.x;
+        __syncthreads();
+        for (int k = 0; k < NO; ++k) tile[k * kThreads + threadIdx.x] = (s < n) ? psi[k * n + s] : T(0);
+        __syncthreads();
+        if (s < n) {
+            for (int j = 1; j < NO; ++j) {
+                T w = T(0);
+                for (int k = 0; k < j; ++k) w += L[j * NO + k] * tile[k * kThreads + threadIdx.x];
+                u[(j - 1) * n + s] = w;
+            }
+        }
+    }
+}
+
+// In-place orthonormalisation f_jp <- sum_k Linv_jk f_kp, psi likewise:
+// per site, one velocity at a time, the NO values staged per thread in
+// shared memory.  Dynamic shared memory: (NO * kThreads + NO * NO) * sizeof(T).
+template <typename TS, typename T>
+__global__ void __launch_bounds__(kThreads) k_orth_apply_wide(const Grid g, const double* __restrict__ Linv,
+                                                              TS* __restrict__ f, T* __restrict__ psi, int NO) {
+    if (inactive(g)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* col = reinterpret_cast<T*>(smem);  // [NO][kThreads]
+    T* L = col + (size_t)NO * kThreads;   // [NO][NO]
+    const size_t n = g.N, y = sys_id();
+    Linv += y * NO * NO;
+    if (f) f += y * NO * 19 * n;
+    if (psi) psi += y * NO * n;
+    for (int i = threadIdx.x; i < NO * NO; i += kThreads) L[i] = (T)Linv[i];
+    __syncthreads();
+    T* mine = col + threadIdx.x;
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) {
+        for (int p = (f ? 0 : 19); p <= 19; ++p) {
+            if (p == 19 && !psi) break;
+            for (int k = 0; k < NO; ++k)
+                mine[k * kThreads] = (p < 19) ? to_compute<T>(f[((size_t)k * 19 + p) * n + s]) : psi[(size_t)k * n + s];
+            for (int j = NO - 1; j >= 0; --j) {  // from the top: row j reads rows k <= j, not yet overwritten
+                T o = T(0);
+                for (int k = 0; k <= j; ++k) o += L[j * NO + k] * mine[k * kThreads];
+                mine[j * kThreads] = o;
+            }
+            for (int j = 0; j < NO; ++j) {
+                if (p < 19) f[((size_t)j * 19 + p) * n + s] = to_store<TS>(mine[j * kThreads]);
+                else psi[(size_t)j * n + s] = mine[j * kThreads];
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_init_orbitals_wide(Grid g, double h, const OrbitalStart* __restrict__ starts,
+                                                                 T* __restrict__ psi, int NO) {
+    if (inactive(g)) return;
+    const uint32_t N = g.N;
+    const OrbitalStart* st = starts + (size_t)sys_id() * NO;
+    psi += (size_t)sys_id() * NO * N;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
+        const uint32_t q = g.divx.div(s);
+        const int x = (int)(s - q * (uint32_t)g.nx);
+        const uint32_t z = g.divy.div(q);
+        const int yy = (int)(q - z * (uint32_t)g.ny);
+        const double rx = (x - 0.5 * (g.nx - 1)) * h, ry = (yy - 0.5 * (g.ny - 1)) * h,
+                     rz = ((int)z - 0.5 * (g.nz - 1)) * h;
+        for (int j = 0; j < NO; ++j) {
+            const double dx = rx - st[j].cx, dy = ry - st[j].cy, dz = rz - st[j].cz;
+            const double w = st[j].width;
+            psi[(size_t)j * N + s] = (T)exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * w * w));
+        }
+    }
+}
+
+template <typename TS, typename T>
+__global__ void __launch_bounds__(kThreads) k_equilibrium_wide(const Grid g, Coef c, const T* __restrict__ psi,
+                                                               TS* __restrict__ f, int NO) {
+    if (inactive(g)) return;
+    const size_t n = g.N;
+    psi += (size_t)sys_id() * NO * n;
+    f += (size_t)sys_id() * NO * 19 * n;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads)
+        for (int j = 0; j < NO; ++j) {
+            const T a = psi[(size_t)j * n + s];
+#pragma unroll
+            for (int p = 0; p < 19; ++p) f[((size_t)j * 19 + p) * n + s] = to_store<TS>(xi[vclass(p)] * a);
+        }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_density_wide(Grid g, double h, const T* __restrict__ psi,
+                                                           double* __restrict__ rho, double* mp, Scratch sc, int NO) {
+    if (inactive(g)) return;
+    psi += (size_t)sys_id() * NO * g.N;
+    rho += (size_t)sys_id() * g.N;
+    mp += (size_t)sys_id() * kMpStride;
+    double acc[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    const uint32_t N = g.N;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
+        double r = 0.0;
+        for (int j = 0; j < NO; ++j) {
+            const double a = (double)psi[(size_t)j * N + s];
+            r += a * a;
+        }
+        r *= 2.0;
+        rho[s] = r;
+        const uint32_t q = g.divx.div(s);
+        const int x = (int)(s - q * (uint32_t)g.nx);
+        const uint32_t z = g.divy.div(q);
+        const int yy = (int)(q - z * (uint32_t)g.ny);
+        const double rx = (x - 0.5 * (g.nx - 1)) * h, ry = (yy - 0.5 * (g.ny - 1)) * h,
+                     rz = ((int)z - 0.5 * (g.nz - 1)) * h;
+        acc[0] += r;
+        acc[1] += r * rx; acc[2] += r * ry; acc[3] += r * rz;
+        acc[4] += r * rx * rx; acc[5] += r * ry * ry; acc[6] += r * rz * rz;
+        acc[7] += r * rx * ry; acc[8] += r * rx * rz; acc[9] += r * ry * rz;
+    }
+    double* partial = sys_partial(sc);
+    block_sum_store<10>(acc, partial + (size_t)blockIdx.x * 10);
+    __shared__ double tot[10];
+    if (grid_total<10>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
+        const double h3 = h * h * h;
+        const double tr = tot[4] + tot[5] + tot[6];
+        mp[0] = h3 * tot[0];
+        mp[1] = h3 * tot[1]; mp[2] = h3 * tot[2]; mp[3] = h3 * tot[3];
+        mp[4] = h3 * (3.0 * tot[4] - tr); mp[5] = h3 * (3.0 * tot[5] - tr); mp[6] = h3 * (3.0 * tot[6] - tr);
+        mp[7] = h3 * 3.0 * tot[7]; mp[8] = h3 * 3.0 * tot[8]; mp[9] = h3 * 3.0 * tot[9];
+    }
+}
+
+// Energy matrix for many orbitals: per tile, psi, (T_h + V) psi and T_h psi in
+// shared memory; H over the packed lower triangle (symmetrised by the host)
+// and kin on the diagonal, FP64 across tiles and blocks.  Output per system
+// (kEmatWideStride doubles): H[NO][NO] then kin[NO].
+// Dynamic shared memory: 3 * NO * kWideTile * sizeof(T) + (NP + NO) doubles.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_energy_matrix_wide(Grid g, Coef c, const T* __restrict__ psi,
+                                                                 const double* __restrict__ V, double* out, Scratch sc,
+                                                                 int NO) {
+    if (inactive(g)) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* A = reinterpret_cast<T*>(smem);      // psi [NO][tile]
+    T* Hp = A + (size_t)NO * kWideTile;     // (T_h + V) psi
+    T* Tp = Hp + (size_t)NO * kWideTile;    // T_h psi
+    double* tot = reinterpret_cast<double*>(Tp + (size_t)NO * kWideTile);
+    const int NP = NO * (NO + 1) / 2, K = NP + NO;
+    const uint32_t N = g.N;
+    const size_t y = sys_id();
+    psi += y * NO * N;
+    V += y * N;
+    out += y * kEmatWideStride;
+    const T inv = (T)(1.0 / (c.theta * c.h * c.h));
+    constexpr int kMaxPerThread = (kMaxOrbWide * (kMaxOrbWide + 1) / 2 + kMaxOrbWide + kThreads - 1) / kThreads;
+    double acc[kMaxPerThread];
+    int pa[kMaxPerThread], pb[kMaxPerThread];
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread; ++q) {
+        acc[q] = 0.0;
+        const int k = threadIdx.x + q * kThreads;
+        if (k < NP) tri_pair(k, pa[q], pb[q]);
+        else if (k < K) pa[q] = pb[q] = -2 - (k - NP);  // kinetic term of orbital k - NP
+        else pa[q] = pb[q] = -1;
+    }
+    const uint32_t tiles = (N + kWideTile - 1) / kWideTile;
+    for (uint32_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
+        const uint32_t base = ti * kWideTile;
+        for (int i = threadIdx.x; i < NO * kWideTile; i += kThreads) {
+            const int j = i / kWideTile, sl = i % kWideTile;
+            const uint32_t s = base + sl;
+            T a = T(0), tp = T(0), hp = T(0);
+            if (s < N) {
+                const Site t = decode(g, s);
+                const T* pj = psi + (size_t)j * N;
+                T kx = T(0);
+#pragma unroll
+                for (int p = 0; p < 19; ++p)
+                    if (has_source(t, p)) kx += (T)c.xi[vclass(p)] * pj[source_index(g, s, p)];
+                a = pj[s];
+                tp = (a - kx) * inv;
+                hp = tp + (T)V[s] * a;
+            }
+            A[i] = a;
+            Tp[i] = tp;
+            Hp[i] = hp;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMaxPerThread; ++q) {
+            if (pa[q] == -1) continue;
+            const T* ra;
+            const T* rb;
+            if (pa[q] >= 0) {
+                ra = A + pa[q] * kWideTile;
+                rb = Hp + pb[q] * kWideTile;
+            } else {
+                const int j = -2 - pa[q];
+                ra = A + j * kWideTile;
+                rb = Tp + j * kWideTile;
+            }
+            T part = T(0);
+#pragma unroll 8
+            for (int s = 0; s < kWideTile; ++s) part += ra[s] * rb[s];
+            acc[q] += (double)part;
+        }
+        __syncthreads();
+    }
+    double* partial = sys_partial(sc);
+#pragma unroll
+    for (int q = 0; q < kMaxPerThread; ++q) {
+        const int k = threadIdx.x + q * kThreads;
+        if (k < K) partial[(size_t)blockIdx.x * K + k] = acc[q];
+    }
+    if (grid_total_rt(partial, sys_counter(sc), tot, K) && threadIdx.x == 0) {
+        const double h3 = c.h * c.h * c.h;
+        for (int a = 0; a < NO; ++a)
+            for (int b = 0; b <= a; ++b) {
+                out[a * NO + b] = h3 * tot[tri(a, b)];
+                out[b * NO + a] = h3 * tot[tri(a, b)];
+            }
+        for (int j = 0; j < NO; ++j) out[NO * NO + j] = h3 * tot[NP + j];
+    }
+}
+
+}  // namespace lbks

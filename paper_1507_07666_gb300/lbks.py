@@ -15,10 +15,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbks.so")
 
-MAX_ORB = 8
+MAX_ORB = 64
 OK, EINVAL, ENOMEM, ENOTCONV, ETIMEDOUT, EBUSY, ECUDA, ENOTFOUND = range(8)
-FP64, FP32 = 0, 1
-_ELEM = {FP64: 8, FP32: 4}
+FP64, FP32, BF16 = 0, 1, 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1507_07666_gb300.build.build()")
@@ -35,7 +34,8 @@ class lbks_params(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("theta", ctypes.c_double), ("n_inner", ctypes.c_int),
                 ("mix", ctypes.c_double), ("e_tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("softening", ctypes.c_double),
-                ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int)]
+                ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
+                ("polish_tol", ctypes.c_double)]
 
 
 class lbks_result(ctypes.Structure):
@@ -79,6 +79,13 @@ _SIGS = {
     "lbks_destroy_system": (_i, [_vp]),
     "lbks_system_bytes": (_sz, [ctypes.POINTER(lbks_params), _i, _i, _i, _i]),
     "lbks_set_geometry": (_i, [_vp, _i, _dp, _dp]),
+    "lbks_create_batch": (_i, [ctypes.POINTER(lbks_params), _i, _i, _i, _d, _i, _i, ctypes.POINTER(_vp)]),
+    "lbks_batch_bytes": (_sz, [ctypes.POINTER(lbks_params), _i, _i, _i, _i, _i]),
+    "lbks_batch_set_geometry": (_i, [_vp, _i, _i, _dp, _dp]),
+    "lbks_batch_init": (_i, [_vp]),
+    "lbks_batch_scf": (_i, [_vp, _vp, ctypes.POINTER(lbks_result)]),
+    "lbks_batch_energy": (_i, [_vp, _i, ctypes.POINTER(lbks_energy_terms)]),
+    "lbks_batch_get_density": (_i, [_vp, _i, _dp, _sz]),
     "lbks_scf": (_i, [_vp, _vp, ctypes.POINTER(lbks_result)]),
     "lbks_scf_cycles": (_i, [_vp, _i, _vp, ctypes.POINTER(lbks_result)]),
     "lbks_energy": (_i, [_vp, ctypes.POINTER(lbks_energy_terms)]),
@@ -97,6 +104,7 @@ _SIGS = {
     "lbks_relax_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp]),
     "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
+    "lbks_overlap": (_i, [_i, _sz, _i, _d, _vp, _vp, _i, _vp]),
     "lbks_cholesky_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
     "lbks_orth_apply": (_i, [_i, _sz, _i, _vp, _vp, _vp, _vp]),
     "lbks_hartree": (_i, [_i, _i, _i, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _dp, _vp]),
@@ -145,6 +153,13 @@ def _stream(stream):
 
 
 def _tdtype(precision):
+    """torch dtype of stored populations."""
+    import torch
+    return {FP64: torch.float64, FP32: torch.float32, BF16: torch.bfloat16}[precision]
+
+
+def _psitype(precision):
+    """torch dtype of orbitals and the W field (the compute type)."""
     import torch
     return torch.float64 if precision == FP64 else torch.float32
 
@@ -235,10 +250,10 @@ def lbks_get_potential(handle, which, shape):
 def lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, V, sigma_in, f_out,
                     psi_out, S_out, lambda_out, sigma_out, stream=None):
     import torch
-    T = _tdtype(precision)
+    T, P = _tdtype(precision), _psitype(precision)
     _check(_lib.lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, _ptr(f_in, T),
-                                _ptr(u_in, T, optional=True), _ptr(V, torch.float64),
-                                _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, T),
+                                _ptr(u_in, P, optional=True), _ptr(V, torch.float64),
+                                _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, P),
                                 _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
                                 _ptr(sigma_out, torch.float64), _stream(stream)))
 
@@ -248,19 +263,25 @@ def lbks_relax_step_noalloc(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f
     """As lbks_relax_step, with the reduction scratch in the library's fixed
     device array (nothing is allocated; overlapping calls race)."""
     import torch
-    T = _tdtype(precision)
+    T, P = _tdtype(precision), _psitype(precision)
     _check(_lib.lbks_relax_step_noalloc(precision, nx, ny, nz, n_orb, h, omega, theta, dt, _ptr(f_in, T),
-                                        _ptr(u_in, T, optional=True), _ptr(V, torch.float64),
-                                        _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, T),
+                                        _ptr(u_in, P, optional=True), _ptr(V, torch.float64),
+                                        _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, P),
                                         _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
                                         _ptr(sigma_out, torch.float64), _stream(stream)))
 
 
 def lbks_w_field(precision, n_sites, n_orb, omega, psi, lam, u_out, stream=None):
     import torch
-    T = _tdtype(precision)
-    _check(_lib.lbks_w_field(precision, n_sites, n_orb, omega, _ptr(psi, T), _ptr(lam, torch.float64),
-                             _ptr(u_out, T, optional=True), _stream(stream)))
+    P = _psitype(precision)
+    _check(_lib.lbks_w_field(precision, n_sites, n_orb, omega, _ptr(psi, P), _ptr(lam, torch.float64),
+                             _ptr(u_out, P, optional=True), _stream(stream)))
+
+
+def lbks_overlap(precision, n_sites, n_orb, h, psi, S, tensor_cores=False, stream=None):
+    import torch
+    _check(_lib.lbks_overlap(precision, n_sites, n_orb, h, _ptr(psi, _psitype(precision)), _ptr(S, torch.float64),
+                             int(bool(tensor_cores)), _stream(stream)))
 
 
 def lbks_cholesky_inverse(n, S, Linv, status, stream=None):
@@ -271,9 +292,9 @@ def lbks_cholesky_inverse(n, S, Linv, status, stream=None):
 
 def lbks_orth_apply(precision, n_sites, n_orb, Linv, f, psi, stream=None):
     import torch
-    T = _tdtype(precision)
+    T, P = _tdtype(precision), _psitype(precision)
     _check(_lib.lbks_orth_apply(precision, n_sites, n_orb, _ptr(Linv, torch.float64), _ptr(f, T, optional=True),
-                                _ptr(psi, T, optional=True), _stream(stream)))
+                                _ptr(psi, P, optional=True), _stream(stream)))
 
 
 def lbks_hartree(nx, ny, nz, h, rho, v, rtol=1e-11, max_iter=20000, stream=None):
@@ -289,6 +310,54 @@ def lbks_lda(n_sites, rho, eps, v, stream=None):
     import torch
     _check(_lib.lbks_lda(n_sites, _ptr(rho, torch.float64), _ptr(eps, torch.float64), _ptr(v, torch.float64),
                          _stream(stream)))
+
+
+def lbks_create_batch(params, nx, ny, nz, h, n_orb, n_systems):
+    handle = ctypes.c_void_p()
+    _check(_lib.lbks_create_batch(ctypes.byref(params), nx, ny, nz, h, n_orb, n_systems, ctypes.byref(handle)))
+    return handle
+
+
+def lbks_batch_bytes(params, nx, ny, nz, n_orb, n_systems) -> int:
+    return int(_lib.lbks_batch_bytes(ctypes.byref(params), nx, ny, nz, n_orb, n_systems))
+
+
+def lbks_batch_set_geometry(handle, system, xyz, Z):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    Z = np.ascontiguousarray(Z, dtype=np.float64).ravel()
+    _check(_lib.lbks_batch_set_geometry(handle, system, len(Z), xyz.ctypes.data_as(_dp), Z.ctypes.data_as(_dp)))
+
+
+def lbks_batch_init(handle):
+    _check(_lib.lbks_batch_init(handle))
+
+
+def lbks_batch_scf(handle, n_systems, stream=None, n_orb=MAX_ORB, allow_notconv=False):
+    res = (lbks_result * n_systems)()
+    code = _lib.lbks_batch_scf(handle, _stream(stream), res)
+    if code != OK and not (allow_notconv and code == ENOTCONV):
+        _check(code)
+    return [_result_dict(res[i], n_orb) for i in range(n_systems)]
+
+
+def lbks_batch_scf_cycles(handle, n_systems, n, stream=None, n_orb=MAX_ORB):
+    res = (lbks_result * n_systems)()
+    _check(_lib.lbks_scf_cycles(handle, n, _stream(stream), res))
+    return [_result_dict(res[i], n_orb) for i in range(n_systems)]
+
+
+def lbks_batch_energy(handle, system, n_orb=MAX_ORB) -> dict:
+    t = lbks_energy_terms()
+    _check(_lib.lbks_batch_energy(handle, system, ctypes.byref(t)))
+    return {"T_s": t.T_s, "E_ext": t.E_ext, "E_H": t.E_H, "E_xc": t.E_xc, "E_nn": t.E_nn,
+            "E_total": t.E_total, "eigenvalues": np.array(t.eigenvalues[:n_orb]),
+            "orbital_energies": np.array(t.orbital_energies[:n_orb]), "n_electrons": t.n_electrons}
+
+
+def lbks_batch_get_density(handle, system, shape):
+    out = np.empty(shape, dtype=np.float64)
+    _check(_lib.lbks_batch_get_density(handle, system, out.ctypes.data_as(_dp), out.size))
+    return out
 
 
 def lbks_server_create(params=None, budget_bytes=0, max_slots=4):
@@ -340,6 +409,51 @@ def lbks_server_get_stats(handle) -> dict:
 
 
 # ------------------------------------------------------------- convenience
+class Batch:
+    """Owning wrapper of a batched handle: n_systems systems of one shape."""
+
+    def __init__(self, n, h, n_orb, n_systems, **params):
+        self.n = tuple(int(x) for x in n)
+        self.h = float(h)
+        self.n_orb = int(n_orb)
+        self.n_systems = int(n_systems)
+        self.params = lbks_params_default(**params)
+        self.handle = lbks_create_batch(self.params, *self.n, self.h, self.n_orb, self.n_systems)
+
+    @property
+    def grid_shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    def set_geometries(self, molecules):
+        for i, (xyz, Z) in enumerate(molecules):
+            lbks_batch_set_geometry(self.handle, i, xyz, Z)
+        lbks_batch_init(self.handle)
+
+    def scf(self, stream=None, allow_notconv=False):
+        return lbks_batch_scf(self.handle, self.n_systems, stream, self.n_orb, allow_notconv)
+
+    def scf_cycles(self, n, stream=None):
+        return lbks_batch_scf_cycles(self.handle, self.n_systems, n, stream, self.n_orb)
+
+    def energy(self, i):
+        return lbks_batch_energy(self.handle, i, self.n_orb)
+
+    def density(self, i):
+        return lbks_batch_get_density(self.handle, i, self.grid_shape)
+
+    def close(self):
+        if self.handle is not None:
+            lbks_destroy_system(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class System:
     """Owning wrapper of one lbks_system handle."""
 

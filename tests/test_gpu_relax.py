@@ -4,7 +4,8 @@ oracle, element by element, through the C ABI.
 The GPU writes the collision without the orthogonalisation source plus the
 W field u; f_split + xi_p u is compared with the oracle's post-collision
 populations.  Grids are ragged (no extent a multiple of the block) and span
-several blocks; n_orb covers 1 (no W), the common 5 and the maximum 8."""
+several blocks; n_orb covers 1 (no W), the common 5, 8 (the largest fused
+case) and 10-12 (the tiled path for wider orbital sets)."""
 import numpy as np
 import pytest
 
@@ -23,26 +24,38 @@ CASES = [
     ((33, 20, 17), 5, 1.3, 3),
     ((2, 3, 2), 2, 1.0, 4),
     ((16, 5, 40), 8, 0.9, 5),
+    # more than eight orbitals: stream-collide without fused products + tiled Gram kernel
+    ((21, 18, 23), 12, 1.0, 6),
+    ((9, 10, 11), 10, 0.9, 8),
 ]
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
+# bfloat16 storage: orbitals and overlaps are float sums of the stored (rounded)
+# inputs; the stored outputs carry bfloat16's 2^-9 relative rounding
+BF16_TOL_PSI, BF16_TOL_F = 2e-5, 4e-3
+
+
+def _bf16_round(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16).double().numpy()
 
 
 def _run_gpu(torch, lbks, prec, n, n_orb, omega, theta, dt, h, f, u, V, sigma):
-    T = torch.float64 if prec == lbks.FP64 else torch.float32
+    T = {0: torch.float64, 1: torch.float32, 2: torch.bfloat16}[prec]
+    P = torch.float64 if prec == lbks.FP64 else torch.float32  # orbitals and W field
     nx, ny, nz = n
     N = nx * ny * nz
     f_in = to_dev(torch, f, T)
-    u_in = to_dev(torch, u[1:], T) if n_orb > 1 else None
+    u_in = to_dev(torch, u[1:], P) if n_orb > 1 else None
     Vd = to_dev(torch, V, torch.float64)
     sig = to_dev(torch, sigma, torch.float64)
     f_out = torch.empty_like(f_in)
-    psi = torch.empty((n_orb, nz, ny, nx), dtype=T, device="cuda")
+    psi = torch.empty((n_orb, nz, ny, nx), dtype=P, device="cuda")
     S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
     lam = torch.empty_like(S)
     sig_out = torch.empty_like(sig)
     lbks.lbks_relax_step(prec, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, Vd, sig, f_out, psi, S, lam,
                          sig_out)
-    u_out = torch.zeros((max(n_orb - 1, 1), nz, ny, nx), dtype=T, device="cuda")
+    u_out = torch.zeros((max(n_orb - 1, 1), nz, ny, nx), dtype=P, device="cuda")
     lbks.lbks_w_field(prec, N, n_orb, omega, psi, lam, u_out if n_orb > 1 else None)
     torch.cuda.synchronize()
     return {"f_split": to_np(f_out), "u": to_np(u_out), "psi": to_np(psi), "S": to_np(S), "lam": to_np(lam),
@@ -69,14 +82,35 @@ def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed):
     assert rel_err(fg, ref["fstar"]) < tol
 
 
-@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-def test_orthonormalising_step_matches_oracle(prec):
-    """Relax step, Cholesky of its overlap and L^{-1} applied to populations
-    and orbitals reproduce the oracle's cycle-ending step."""
+@pytest.mark.parametrize("n,n_orb,omega,seed", [((33, 20, 17), 5, 1.0, 2), ((7, 9, 11), 3, 0.8, 1)])
+def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed):
+    """bfloat16 populations, float arithmetic: the oracle is fed the rounded
+    populations; orbitals/overlaps to float accuracy, stored populations to
+    bfloat16 rounding."""
     torch, lbks = require_gpu()
-    n, n_orb, omega, theta, h = (19, 13, 10), 4, 1.0, 0.5, 0.25
+    theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, omega, h)
-    f, V, sigma, _, u = W.random_state(n, n_orb, 11)
+    f, V, sigma, _, u = W.random_state(n, n_orb, seed)
+    f = _bf16_round(f)
+    u = u.astype(np.float32).astype(np.float64)
+    g = _run_gpu(torch, lbks, lbks.BF16, n, n_orb, omega, theta, dt, h, f, u, V, sigma)
+    ref = lb.step(paper_state(f, u[1:], theta), sigma, V, omega, theta, dt, h)
+    assert rel_err(g["psi"], ref["psi"]) < BF16_TOL_PSI
+    assert rel_err(g["S"], ref["S"]) < BF16_TOL_PSI
+    fg = paper_state(g["f_split"], g["u"], theta) if n_orb > 1 else g["f_split"]
+    assert rel_err(fg, ref["fstar"]) < BF16_TOL_F
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("n,n_orb,seed", [((19, 13, 10), 4, 11), ((13, 11, 9), 11, 12)])
+def test_orthonormalising_step_matches_oracle(prec, n, n_orb, seed):
+    """Relax step, Cholesky of its overlap and L^{-1} applied to populations
+    and orbitals reproduce the oracle's cycle-ending step (eight or fewer
+    orbitals: fused kernels; more: the tiled kernels)."""
+    torch, lbks = require_gpu()
+    omega, theta, h = 1.0, 0.5, 0.25
+    dt = lattice.time_step(theta, omega, h)
+    f, V, sigma, _, u = W.random_state(n, n_orb, seed)
     if prec == lbks.FP32:
         f, u = f.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
     T = torch.float64 if prec == lbks.FP64 else torch.float32
@@ -148,5 +182,5 @@ def test_step_rejects_bad_arguments():
         lbks.lbks_relax_step(0, 2, 2, 2, 2, 0.2, 1.0, 0.5, 0.02, x, None, x[:8], x[:2], x, x[:16], x[:4], x[:4],
                              x[:2])
     with pytest.raises(lbks.LbksError):  # too many orbitals
-        lbks.lbks_relax_step(0, 2, 2, 2, 9, 0.2, 1.0, 0.5, 0.02, x, None, x[:8], x[:2], x.clone(), x[:16], x[:4],
+        lbks.lbks_relax_step(0, 2, 2, 2, 65, 0.2, 1.0, 0.5, 0.02, x, None, x[:8], x[:2], x.clone(), x[:16], x[:4],
                              x[:4], x[:2])

@@ -114,6 +114,48 @@ def water_scan(count: int = 64, seed: int = 0) -> List[Molecule]:
     return [water(float(r[i]), float(a[i])) for i in range(count)]
 
 
+def _rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniformly random rotation matrix (QR of a Gaussian matrix, sign-fixed)."""
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def water_cluster(count: int = 8, seed: int = 0, box: float = 51.2, min_oo: float = 5.0,
+                  margin: float = 6.0) -> Molecule:
+    """`count` waters (r_OH = 1.81 bohr, 104.5 deg) at seeded random positions
+    and orientations: O-O distances >= min_oo, every O at least `margin` from
+    the faces of a cubic box of edge `box` centred on the origin."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    unit = water()
+    half = box / 2.0 - margin
+    centres = []
+    while len(centres) < count:
+        c = rng.uniform(-half, half, size=3)
+        if all(np.linalg.norm(c - o) >= min_oo for o in centres):
+            centres.append(c)
+    symbols, xyz = [], []
+    for c in centres:
+        rot = _rotation(rng)
+        for s, p in zip(unit.symbols, unit.xyz):
+            symbols.append(s)
+            xyz.append(c + rot @ p)
+    return Molecule(f"(H2O){count}", symbols, np.array(xyz))
+
+
+def cluster_256() -> Workload:
+    """Eight waters in a 256^3 grid at h = 0.2 bohr, 40 doubly occupied orbitals."""
+    return Workload("(H2O)8 256^3 h=0.2", water_cluster(8, 0), (256, 256, 256), 0.2, n_inner=100)
+
+
+def cluster_sample() -> Workload:
+    """The cluster of cluster_256 on a 64^3 grid spanning the same box
+    (h = 0.8 bohr): a host-sized sample of its relaxation steps."""
+    return Workload("(H2O)8 64^3 h=0.8", water_cluster(8, 0), (64, 64, 64), 0.8, n_inner=100)
+
+
 def perturb(mol: Molecule, sigma: float, rng: np.random.Generator) -> Molecule:
     return Molecule(mol.name, list(mol.symbols), mol.xyz + rng.normal(0.0, sigma, size=mol.xyz.shape))
 
