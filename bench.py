@@ -77,6 +77,11 @@ def parse_args():
                     help="time only the fused stream-collide kernel (for profiling)")
     ap.add_argument("--kernel-n", type=int, default=0, help="cubic grid edge for --kernel-only (0: workload's)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--kernel", choices=["stream_collide", "overlap_tc", "overlap_exact"], default="stream_collide",
+                    help="--kernel-only: which step to launch alone")
+    ap.add_argument("--relax-variant", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="stream-collide variant: 0 tuned per shape, 1 one site per thread, 2 site pairs, "
+                         "3 one site with the next orbital prefetched")
     return ap.parse_args()
 
 
@@ -256,21 +261,50 @@ def time_stream_collide(torch, lbks, w, prec, stream, launches=20):
     return statistics.mean(ms), N * no
 
 
+def time_overlap(torch, lbks, w, prec, stream, tensor_cores, launches=20):
+    """Average duration of the overlap (Gram) step S = h^3 Psi Psi^T alone."""
+    nx, ny, nz = w.n
+    N = nx * ny * nz
+    P = torch.float64 if prec == lbks.FP64 else torch.float32
+    with torch.cuda.stream(stream):
+        psi = torch.randn((w.n_orb, N), dtype=P, device="cuda")
+        S = torch.empty((w.n_orb, w.n_orb), dtype=torch.float64, device="cuda")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i in range(3 + launches):
+        if i == 3:
+            evs[0].record(stream)
+        lbks.lbks_overlap(prec, N, w.n_orb, w.h, psi, S, tensor_cores=tensor_cores, stream=stream)
+    evs[1].record(stream)
+    stream.synchronize()
+    return evs[0].elapsed_time(evs[1]) / launches, N * w.n_orb, psi.element_size()
+
+
 def main_kernel_only(args):
-    """Stream-collide launches alone (3 untimed + --launches timed), for ncu."""
+    """One step launched alone (3 untimed + --launches timed), for ncu: the
+    stream-collide, or the overlap on the tensor cores / with exact sums."""
     import torch
     from paper_1507_07666_gb300 import build as build_mod
     build_mod.build()
     from paper_1507_07666_gb300 import lbks
-    w = WORKLOADS[args.workload]()
+    w = (WORKLOADS.get(args.workload) or CYCLES[args.workload])()
     if args.kernel_n:
         w.n = (args.kernel_n,) * 3
     prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
+    lbks.lbks_set_relax_variant(args.relax_variant)
     stream = torch.cuda.Stream()
+    if args.kernel != "stream_collide":
+        ms, units, esz = time_overlap(torch, lbks, w, prec, stream, args.kernel == "overlap_tc", args.launches)
+        print(json.dumps({"kernel": "k_gram_tc" if args.kernel == "overlap_tc" and prec != lbks.FP64 else "k_gram",
+                          "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision, "ms_per_launch": ms,
+                          "algorithmic_GBps": units * esz / (ms / 1e3) / 1e9, "launches": args.launches}),
+              flush=True)
+        return 0
     ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
     gbs = 38 * elem * units / (ms / 1e3) / 1e9
-    print(json.dumps({"kernel": "k_stream_collide", "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
+    print(json.dumps({"kernel": "k_stream_collide_pair" if args.relax_variant == 2 else "k_stream_collide",
+                      "variant": ("sites (untuned)", "sites", "pairs", "prefetch")[args.relax_variant],
+                      "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
                       "ms_per_launch": ms, "algorithmic_GBps": gbs, "launches": args.launches}), flush=True)
     return 0
 
@@ -309,6 +343,7 @@ def main_batch(args):
     clk = clocks.stop()
     launches = lbks.lbks_kernel_launches() - l0
     elapsed_ms = ev0.elapsed_time(ev1)
+    tuned = lbks.lbks_get_relax_variant(b.handle)
     updates = sum(r["steps"] for res in results for r in res) * w.n_orb * w.sites
     last = results[-1]
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
@@ -325,7 +360,7 @@ def main_batch(args):
         "batch": {"converged": sum(r["converged"] for r in last), "cycles_max": max(r["cycles"] for r in last),
                   "cycles_min": min(r["cycles"] for r in last),
                   "E_total_range": [min(r["E_total"] for r in last), max(r["E_total"] for r in last)]},
-        "gpu_launches": int(launches), "clocks": clk,
+        "gpu_launches": int(launches), "clocks": clk, "stream_collide_variant": tuned,
     }
     print(json.dumps(line), flush=True)
     b.close()
@@ -473,6 +508,7 @@ def main_lbks(args):
            "h2d_bytes_per_step": int(xyz.nbytes + Z.nbytes),
            "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
 
+    tuned = lbks.lbks_get_relax_variant(sysm.handle)
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration
@@ -517,6 +553,7 @@ def main_lbks(args):
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "stream_collide_variant": tuned,
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -535,6 +572,11 @@ def main():
         return main_reference(args)
     if args.kernel_only:
         return main_kernel_only(args)
+    if args.relax_variant:
+        from paper_1507_07666_gb300 import build as build_mod
+        build_mod.build()
+        from paper_1507_07666_gb300 import lbks
+        lbks.lbks_set_relax_variant(args.relax_variant)
     if args.workload in BATCHES:
         return main_batch(args)
     if args.workload in SERVING:

@@ -87,8 +87,10 @@ typedef struct lbks_params {
     double softening;    /* nuclear softening a (bohr); <= 0 means a = h [0] */
     double poisson_rtol; /* CG relative residual target [1e-11] */
     int poisson_max_iter;/* [20000] */
-    double polish_tol;   /* LBKS_BF16 only: once every running system's |dE| < polish_tol the
-                            populations are widened to FP32 and the solve finishes in FP32
+    double polish_tol;   /* LBKS_BF16 only: once every running system's |dE| < polish_tol, or
+                            has stalled below 100 polish_tol (no longer halving over two cycles:
+                            the bfloat16 noise floor), the populations are widened to FP32 and the
+                            solve finishes in FP32, converging only after two FP32 cycles
                             (bfloat16 rounding would otherwise bound the accuracy); <= 0 never [1e-4] */
 } lbks_params;
 
@@ -159,6 +161,26 @@ typedef struct lbks_energy_terms {
     double orbital_energies[LBKS_MAX_ORB]; /* <psi_j|H|psi_j> per orbital */
     double n_electrons;
 } lbks_energy_terms;
+
+/* Stream-collide kernel variant (up to 8 orbitals; more use one kernel):
+ *   0  one site per thread;
+ *   1  two x-neighbouring sites per thread, two-element loads, x-shifted
+ *      populations by warp shuffle (nx even and arrays 16-byte aligned, else 0);
+ *   2  one site per thread, the next orbital's populations loaded before the
+ *      current orbital collides (more loads in flight, fewer threads).
+ * mode 0 (default), tuned: the first lbks_set_geometry of each shape
+ * (precision, orbitals, omega == 1 or not, grid, systems) times every
+ * variant on the handle's buffers (a few launches, before they hold state)
+ * and keeps the fastest for every later handle of that shape and for
+ * lbks_relax_step of that shape (untuned shapes: variant 0).  mode 1 + v:
+ * variant v forced.  Process-wide.  Returns the previous mode, or -1 for a
+ * bad mode. */
+int lbks_set_relax_variant(int mode);
+
+/* Variant the handle's stream-collide runs, and the tuner's ms per launch of
+ * each variant in ms[0..2] (may be NULL; negative: not measured by this
+ * handle). */
+int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
 
 /* Energy terms of the last evaluation (after lbks_set_geometry or a cycle). */
 int lbks_energy(const lbks_system* sys, lbks_energy_terms* out);

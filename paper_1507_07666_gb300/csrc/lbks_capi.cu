@@ -104,7 +104,9 @@ int scratch_vals(int n_orb) { return n_orb <= kMaxOrb ? kScratchVals : n_orb * (
 // Doubles of the energy-matrix output per system.
 int emat_stride(int n_orb) { return n_orb <= kMaxOrb ? kEmatStride : kEmatWideStride; }
 
-cudaError_t alloc_scratch(Scratch& sc) {
+// The counter is zeroed on `st`, the stream the scratch is then used on: a
+// legacy-stream cudaMemset is not ordered before work on non-blocking streams.
+cudaError_t alloc_scratch(Scratch& sc, cudaStream_t st) {
     sc.max_blocks = num_sms() * 8;
     sc.max_vals = scratch_vals(kMaxOrbWide);
     sc.systems = 1;
@@ -112,7 +114,7 @@ cudaError_t alloc_scratch(Scratch& sc) {
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&sc.counter, sizeof(unsigned) * 4);
     if (e != cudaSuccess) return e;
-    return cudaMemset(sc.counter, 0, sizeof(unsigned) * 4);
+    return cudaMemsetAsync(sc.counter, 0, sizeof(unsigned) * 4, st);
 }
 
 // Library-managed workspace of the step-level entry points, one per
@@ -134,7 +136,7 @@ int workspace(void* stream, size_t n_pvec, Workspace** out) {
     Workspace*& w = g_ws[{dev, stream}];
     if (!w) {
         w = new Workspace();
-        cudaError_t e = alloc_scratch(w->sc);
+        cudaError_t e = alloc_scratch(w->sc, (cudaStream_t)stream);
         if (e == cudaSuccess) e = cudaMalloc(&w->cg, sizeof(CGState));
         if (e == cudaSuccess) e = cudaMalloc(&w->mp, sizeof(double) * 16);
         if (e != cudaSuccess) {
@@ -155,7 +157,7 @@ int workspace(void* stream, size_t n_pvec, Workspace** out) {
     return LBKS_OK;
 }
 
-// Symmetric eigenvalues by cyclic Jacobi rotations (n <= 8), ascending.
+// Symmetric eigenvalues by cyclic Jacobi rotations (n <= 64), ascending.
 void jacobi_eigenvalues(int n, std::vector<double> a, double* out) {
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0.0;
@@ -229,6 +231,8 @@ struct lbks_system {
     double* host = nullptr;  // pinned readback area
     cudaStream_t st = nullptr;   // internal stream for synchronous calls
     cudaStream_t cap = nullptr;  // capture stream
+    int variant = kRelaxSites;   // stream-collide variant (tuned per shape)
+    double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
     std::vector<std::vector<double>> xyz, Z;  // per system
@@ -384,7 +388,8 @@ cudaError_t enqueue_cycle(lbks_system* s, cudaStream_t st, int start) {
     const int n = s->prm.n_inner, B = s->B;
     for (int t = 0; t < n; ++t) {
         RelaxIO io{s->f[cur], t == 0 ? nullptr : s->u, s->vin, s->sigma, s->f[1 - cur], s->psi, s->S, s->lam, s->sigma};
-        cudaError_t e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, B, st);
+        const int v = s->variant | (t == n - 1 ? kRelaxExactOverlap : 0);  // the last overlap feeds the Cholesky
+        cudaError_t e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, B, v, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
         if (t < n - 1) {
@@ -448,7 +453,7 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
     if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
     const int B = s->B;
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<double> prev(B), de(B, INFINITY);
+    std::vector<double> prev(B), de(B, INFINITY), de1(B, INFINITY), de2(B, INFINITY);
     std::vector<int> cycles(B, 0), converged(B, 0), p0(B, 0);
     int* act = host_active(s);
     for (int i = 0; i < B; ++i) {
@@ -478,10 +483,15 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         for (int i = 0; i < B; ++i) {
             if (!act[i]) continue;
             ++cycles[i];
+            de2[i] = de1[i];
+            de1[i] = de[i];
             de[i] = std::fabs(s->terms[i].E_total - prev[i]);
             prev[i] = s->terms[i].E_total;
             if (!std::isfinite(s->terms[i].E_total)) return fail(LBKS_ENOTCONV, "system %d: energy not finite", i);
-            if (!(de[i] < s->prm.polish_tol)) ready = false;
+            // ready for FP32 storage: below polish_tol, or stalled at the
+            // bfloat16 noise floor (|dE| no longer halving over two cycles)
+            const bool stalled = de[i] < 100.0 * s->prm.polish_tol && de[i] > 0.5 * de2[i];
+            if (!(de[i] < s->prm.polish_tol || stalled)) ready = false;
             if (!fixed && !wait_polish && de[i] < s->prm.e_tol) {
                 converged[i] = 1;
                 act[i] = 0;
@@ -519,6 +529,88 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
     }
     (void)p0;
     if (!all) return fail(LBKS_ENOTCONV, "not every system converged within %d cycles", limit);
+    return LBKS_OK;
+}
+
+// ---------------------------------------------------------- kernel tuner
+// The stream-collide variant (one site per thread, two x-neighbouring sites
+// per thread, one site with the next orbital prefetched) is chosen per shape
+// by timing all on the first handle of that shape, process-wide: key
+// (precision, orbitals, omega == 1, nx, ny, nz, systems).  Up to kMaxOrb
+// orbitals only; wider sets have one kernel.
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+std::atomic<int> g_variant_mode{0};  // 0 tuned, else 1 + the forced variant
+
+TuneKey tune_key(int precision, int n_orb, double omega, int nx, int ny, int nz, int B) {
+    return TuneKey(precision, n_orb, omega == 1.0 ? 1 : 0, nx, ny, nz, B);
+}
+
+// Variant for a launch outside a handle (lbks_relax_step): forced, tuned for
+// the shape, else one site per thread.
+int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) {
+    const int mode = g_variant_mode.load();
+    if (n_orb > kMaxOrb) return kRelaxSites;
+    if (mode > 0) return mode - 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(precision, n_orb, omega, nx, ny, nz, 1));
+    return it == g_tuned.end() ? kRelaxSites : it->second;
+}
+
+// Times both variants on the handle's own buffers before they hold state
+// (called at the start of initialise: populations, orbitals, S, Lambda and
+// sigma are all rewritten afterwards).  A few launches, once per shape.
+int tune_relax(lbks_system* s) {
+    const int mode = g_variant_mode.load();
+    if (s->n_orb > kMaxOrb) {
+        s->variant = kRelaxSites;
+        return LBKS_OK;
+    }
+    if (mode > 0) {
+        s->variant = mode - 1;
+        return LBKS_OK;
+    }
+    const TuneKey key = tune_key(s->prm.precision, s->n_orb, s->prm.omega, s->nx, s->ny, s->nz, s->B);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            s->variant = it->second;
+            return LBKS_OK;
+        }
+    }
+    cudaStream_t st = s->st;
+    const size_t NB = s->N * s->B;
+    cudaError_t e = cudaMemsetAsync(s->f[0], 0, s->ops->elem * NB * 19 * s->n_orb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->vin, 0, sizeof(double) * NB, st);
+    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * s->B, 1.0, st);
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    const RelaxIO io{s->f[0], s->n_orb > 1 ? s->u : nullptr, s->vin, s->sigma, s->f[1], s->psi, s->S, s->lam,
+                     s->sigma};
+    constexpr int kReps = 3;
+    float ms[kRelaxVariants] = {0.f, 0.f, 0.f};
+    bool tried[kRelaxVariants] = {true, s->nx % 2 == 0, s->n_orb > 1};  // variants that differ from one site
+    for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
+        if (!tried[v]) continue;
+        e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
+    }
+    for (int k = 0; k < 3; ++k)
+        if (ev[k]) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return cuda_fail(e, "stream-collide tuning");
+    s->variant = kRelaxSites;
+    for (int v = 0; v < kRelaxVariants; ++v) {
+        s->tune_ms[v] = tried[v] ? ms[v] / kReps : -1.0;
+        if (tried[v] && ms[v] < ms[s->variant]) s->variant = v;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.emplace(key, s->variant);
     return LBKS_OK;
 }
 
@@ -572,6 +664,9 @@ int initialise(lbks_system* s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->starts, starts.data(), sizeof(OrbitalStart) * starts.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->active, act, sizeof(int) * B, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "initialise orbitals");
+    int trc = tune_relax(s);
+    if (trc != LBKS_OK) return trc;
     if (e == cudaSuccess) e = launch_vext(s->g, s->h, s->counts, s->atoms, s->a, s->vext, B, st);
     if (e == cudaSuccess) e = s->ops->init_orbitals(s->n_orb, s->g, s->h, s->starts, s->psi, B, st);
     if (e == cudaSuccess) e = s->ops->gram(s->n_orb, s->g, s->h, s->psi, s->S, s->sc, B, st);
@@ -692,15 +787,20 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
         err = cudaMalloc(&s->sc.partial, sizeof(double) * (size_t)s->sc.max_blocks * s->sc.max_vals * B);
     }
     A((void**)&s->sc.counter, sizeof(unsigned) * B);
-    if (err == cudaSuccess) err = cudaMemset(s->sc.counter, 0, sizeof(unsigned) * B);
     if (err == cudaSuccess)
         err = cudaMallocHost((void**)&s->host, sizeof(double) * (host_per_sys(n_orb) * B + B + 1) +
                                                    sizeof(CGState) * B + sizeof(int) * 2 * B + 64);
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
-    if (err == cudaSuccess) err = cudaMemset(s->vh, 0, 8 * NB);
-    if (err == cudaSuccess) err = cudaMemset(s->u, 0, ep * NB * std::max(1, n_orb - 1));
-    if (err == cudaSuccess) err = cudaMemset(s->ints, 0, sizeof(int) * 3 * B);
+    // Zeroed on the handle's own stream and waited for: a legacy-stream
+    // cudaMemset returns before it runs and is not ordered before work on
+    // non-blocking streams (the caller's, or a server slot's), which could
+    // then see the arrival counters or the active flags reset mid-solve.
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->sc.counter, 0, sizeof(unsigned) * B, s->st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->vh, 0, 8 * NB, s->st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->u, 0, ep * NB * std::max(1, n_orb - 1), s->st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->ints, 0, sizeof(int) * 3 * B, s->st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s->st);
     if (err != cudaSuccess) {
         int rc = cuda_fail(err, "create system");
         free_system(s);
@@ -727,13 +827,32 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
 int copy_field(const lbks_system* s, int system, const double* base, double* host, size_t cap, const char* what) {
     if (system < 0 || system >= s->B) return fail(LBKS_EINVAL, "system index out of range");
     if (cap < s->N) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, s->N);
-    cudaError_t e = cudaMemcpy(host, base + (size_t)system * s->N, sizeof(double) * s->N, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(host, base + (size_t)system * s->N, sizeof(double) * s->N,
+                                    cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, what);
 }
 
 }  // namespace
 
+int lbks::relax_variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) {
+    return variant_for(precision, n_orb, omega, nx, ny, nz);
+}
+
 extern "C" {
+
+int lbks_set_relax_variant(int mode) {
+    if (mode < 0 || mode > kRelaxVariants) return -1;
+    return g_variant_mode.exchange(mode);
+}
+
+int lbks_get_relax_variant(const lbks_system* s, int* variant, double* ms) {
+    if (!s || !variant) return fail(LBKS_EINVAL, "null argument");
+    *variant = s->variant;
+    if (ms)
+        for (int v = 0; v < kRelaxVariants; ++v) ms[v] = s->tune_ms[v];
+    return LBKS_OK;
+}
 
 void lbks_params_default(lbks_params* p) {
     if (!p) return;
@@ -859,11 +978,13 @@ int lbks_get_orbitals(const lbks_system* s, double* host, size_t cap) {
     const size_t n = s->N * s->n_orb;
     if (cap < n) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, n);
     if (s->ops->psi_elem == sizeof(double)) {
-        cudaError_t e = cudaMemcpy(host, s->psi, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpyAsync(host, s->psi, sizeof(double) * n, cudaMemcpyDeviceToHost, s->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
         return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_get_orbitals");
     }
     std::vector<float> tmp(n);
-    cudaError_t e = cudaMemcpy(tmp.data(), s->psi, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpyAsync(tmp.data(), s->psi, sizeof(float) * n, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return cuda_fail(e, "lbks_get_orbitals");
     for (size_t i = 0; i < n; ++i) host[i] = tmp[i];
     return LBKS_OK;
@@ -895,7 +1016,7 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h, 
     if (rc != LBKS_OK) return rc;
     RelaxIO io{f_in, u_in, V, sigma_in, f_out, psi_out, S_out, lambda_out, sigma_out};
     cudaError_t e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, w->sc, 1,
-                               (cudaStream_t)stream);
+                               variant_for(precision, n_orb, omega, nx, ny, nz), (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step");
 }
 

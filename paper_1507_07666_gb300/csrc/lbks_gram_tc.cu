@@ -39,6 +39,7 @@ constexpr int kTcTileBytes = kTcRows * kTcSites * 2;         // 16 KB
 constexpr int kTcQuads = kMaxOrbWide * (kTcSites / 4) / kTcThreads;  // 4-site groups per thread (at most)
 constexpr int kTcMaxPairs = (kMaxOrbWide * (kMaxOrbWide + 1) / 2 + kTcThreads - 1) / kTcThreads;
 constexpr int kDrainTiles = 8;
+constexpr int kInStages = 4;                                 // staged FP32 tiles in flight (bulk-copy path)
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int kTmemColumnsPerSm = 512;
 
@@ -118,11 +119,27 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinter
 
 }  // namespace
 
-// One block per group of tiles of one system (system = blockIdx.y).  VEC:
-// N % 4 == 0 and 16-byte aligned orbitals (float4 loads).  Dynamic shared
-// memory: 1 KB alignment slack, kTcStages tiles, the (2N_O) x (2N_O + 1) FP32
-// fold buffer (reused for the block totals).
-template <bool LAM, bool VEC>
+// 16-byte asynchronous copy global -> shared (zero-filled when src_bytes = 0).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One block per group of tiles of one system (system = blockIdx.y); tile i of
+// the block is global tile blockIdx.x + i * gridDim.x.
+//
+// BULK (N % 4 == 0, 16-byte aligned orbitals): every thread streams its 16-byte
+// pieces of the tiles kInStages - 1 ahead into a staging ring with cp.async,
+// so the loads in flight do not depend on registers.  Otherwise every thread
+// loads its values for the next tile into registers while it converts the
+// current one.
+//
+// Dynamic shared memory: 1 KB alignment slack, kTcStages bf16 tiles, the
+// staging ring (BULK), the (2N_O) x (2N_O + 1) FP32 fold buffer (reused for
+// the block totals).
+template <bool LAM, bool BULK>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
               double* sigma, Scratch sc) {
@@ -130,7 +147,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
-    float* fold = reinterpret_cast<float*>(smem + kTcStages * kTcTileBytes);
+    const uint32_t stage_bytes = (uint32_t)NO * kTcSites * 4;  // one staged FP32 tile
+    unsigned char* ring = smem + kTcStages * kTcTileBytes;
+    float* fold = reinterpret_cast<float*>(ring + (BULK ? kInStages * stage_bytes : 0));
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_sh;
 
@@ -143,6 +162,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t ncols = NM <= 32 ? 32u : NM <= 64 ? 64u : 128u;
     const int ld = R + 1;                       // fold row pitch (floats)
     const int NP = NO * (NO + 1) / 2;
+    const uint32_t ntiles = (N + kTcSites - 1) / kTcSites;
+    const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // >= 1: gridDim.x <= ntiles
 
     for (int i = tid; i < kTcStages * kTcTileBytes / 16; i += kTcThreads)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -165,6 +186,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t idesc = idesc_bf16(kTcRows, NM);
     const uint32_t tiles_u32 = smem_u32(smem);
 
+    const int nq = NO * (kTcSites / 4);
+    // Staged copy of local tile `it` into ring slot it % kInStages: this
+    // thread's 16-byte pieces, one commit group per tile (empty past the end).
+    auto issue = [&](int it) {
+        if (it < my_tiles) {
+            const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
+            const uint32_t slot = smem_u32(ring + (it % kInStages) * stage_bytes);
+#pragma unroll
+            for (int q = 0; q < kTcQuads; ++q) {
+                const int i = tid + q * kTcThreads;
+                if (i >= nq) continue;
+                const uint32_t site = base + 4 * (i & 15);
+                const bool in = site < N;  // N % 4 == 0: a piece is all in or all out
+                cp_async16(slot + (uint32_t)((i >> 4) * kTcSites + 4 * (i & 15)) * 4u,
+                           in ? psi + (size_t)(i >> 4) * N + site : psi, in ? 16u : 0u);
+            }
+        }
+        cp_async_commit();
+    };
+    if (BULK)
+        for (int it = 0; it < kInStages - 1; ++it) issue(it);
+
     double acc[kTcMaxPairs];
     int pr[kTcMaxPairs];  // (a << 8) | b, or -1
 #pragma unroll
@@ -176,38 +219,51 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         pr[q] = k < NP ? (a << 8) | b : -1;
     }
 
-    const int nq = NO * (kTcSites / 4);
-    const uint32_t ntiles = (N + kTcSites - 1) / kTcSites;
     float4 cur[kTcQuads], nxt[kTcQuads];
-    auto load = [&](uint32_t ti, float4(&v)[kTcQuads]) {
+    // Register path: values of local tile `it` (zero past N).
+    auto load = [&](int it, float4(&v)[kTcQuads]) {
+        const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
             const int i = tid + q * kTcThreads;
             if (i >= nq) continue;
-            const uint32_t site = ti * kTcSites + 4 * (i & 15);
+            const uint32_t site = base + 4 * (i & 15);
             const float* p = psi + (size_t)(i >> 4) * N + site;
-            if (VEC && site < N) {
-                v[q] = __ldg(reinterpret_cast<const float4*>(p));
-            } else {
-                v[q].x = site < N ? __ldg(p) : 0.f;
-                v[q].y = site + 1 < N ? __ldg(p + 1) : 0.f;
-                v[q].z = site + 2 < N ? __ldg(p + 2) : 0.f;
-                v[q].w = site + 3 < N ? __ldg(p + 3) : 0.f;
-            }
+            v[q].x = site < N ? __ldg(p) : 0.f;
+            v[q].y = site + 1 < N ? __ldg(p + 1) : 0.f;
+            v[q].z = site + 2 < N ? __ldg(p + 2) : 0.f;
+            v[q].w = site + 3 < N ? __ldg(p + 3) : 0.f;
         }
     };
 
     bool failed = false;
-    int it = 0, in_chunk = 0;
+    int in_chunk = 0;
     uint32_t last_bar = 0, last_parity = 0;
-    load(blockIdx.x, cur);
-    for (uint32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
-        const uint32_t tn = ti + gridDim.x;
-        if (tn < ntiles) load(tn, nxt);
+    if (!BULK) load(0, cur);
+    for (int it = 0; it < my_tiles; ++it) {
+        const bool last_tile = it + 1 == my_tiles;
+        bool late = false;
+        if (BULK) {
+            cp_async_wait<kInStages - 2>();  // this thread's pieces of tile `it` have landed
+            __syncthreads();                 // everyone's; and slot (it - 1) % kInStages is free
+            issue(it + kInStages - 1);
+            const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
+            const float* stg = reinterpret_cast<const float*>(ring + (it % kInStages) * stage_bytes);
+#pragma unroll
+            for (int q = 0; q < kTcQuads; ++q) {
+                const int i = tid + q * kTcThreads;
+                if (i >= nq) continue;
+                const uint32_t site = base + 4 * (i & 15);
+                cur[q] = site < N ? *reinterpret_cast<const float4*>(stg + (i >> 4) * kTcSites + 4 * (i & 15))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else if (!last_tile) {
+            load(it + 1, nxt);
+        }
         const int s = it & 1;
         const uint32_t bar = smem_u32(&mbar[s]);
         // the MMAs of tile it-2 read this stage
-        const bool late = it >= kTcStages && !mbar_wait(bar, ((it >> 1) + 1) & 1);
+        late = late || (it >= kTcStages && !mbar_wait(bar, ((it >> 1) + 1) & 1));
         unsigned char* st = smem + s * kTcTileBytes;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
@@ -237,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         last_bar = bar;
         last_parity = (it >> 1) & 1;
-        if (++in_chunk == drain_tiles || tn >= ntiles) {
+        if (++in_chunk == drain_tiles || last_tile) {
             in_chunk = 0;
             const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity));
             tc_fence_after();
@@ -266,14 +322,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 acc[q] += (double)d00 + (double)((d01 + d10) + d11);
             }
         }
+        if (!BULK) {
 #pragma unroll
-        for (int q = 0; q < kTcQuads; ++q) cur[q] = nxt[q];
+            for (int q = 0; q < kTcQuads; ++q) cur[q] = nxt[q];
+        }
     }
 
     if (failed) {
         if (tid == 0) atomicAdd(&g_tc_timeouts, 1u);
-        if (it > 0) mbar_wait(last_bar, last_parity);  // own MMAs in flight, bounded
+        if (last_bar) mbar_wait(last_bar, last_parity);  // own MMAs in flight, bounded
     }
+    if (BULK) cp_async_wait<0>();  // no copy may land after the block's shared memory is gone
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -292,13 +351,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, LAM ? sigma + y * NO : nullptr);
 }
 
-template <bool LAM, bool VEC>
+template <bool LAM, bool BULK>
 static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
                                   double* sigma, const Scratch& sc, int B, int drain_tiles, cudaStream_t st) {
-    auto kern = k_gram_tc<LAM, VEC>;
+    auto kern = k_gram_tc<LAM, BULK>;
     const int R = 2 * NO, NM = (R + 15) & ~15;
     const int ncols = NM <= 32 ? 32 : NM <= 64 ? 64 : 128;
-    size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (size_t)R * (R + 1) * sizeof(float);
+    size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (BULK ? (size_t)kInStages * NO * kTcSites * 4 : 0) +
+                  (size_t)R * (R + 1) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -327,11 +387,11 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
     if (NO < 1 || NO > kMaxOrbWide || !psi || !S || (lam && !sigma)) return cudaErrorInvalidValue;
     if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B || drain_tiles < 0) return cudaErrorInvalidValue;
     if (drain_tiles == 0) drain_tiles = kDrainTiles;
-    const bool vec = g.N % 4 == 0 && reinterpret_cast<uintptr_t>(psi) % 16 == 0;
-    if (lam) return vec ? gram_tc_launch<true, true>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
-                        : gram_tc_launch<true, false>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st);
-    return vec ? gram_tc_launch<false, true>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st)
-               : gram_tc_launch<false, false>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st);
+    const bool bulk = g.N % 4 == 0 && reinterpret_cast<uintptr_t>(psi) % 16 == 0;
+    if (lam) return bulk ? gram_tc_launch<true, true>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
+                         : gram_tc_launch<true, false>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st);
+    return bulk ? gram_tc_launch<false, true>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st)
+                : gram_tc_launch<false, false>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st);
 }
 
 unsigned gram_tc_timeouts() {

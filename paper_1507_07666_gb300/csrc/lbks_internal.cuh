@@ -98,6 +98,25 @@ void count_launches(uint64_t n);
 int set_last_error(int code, const char* msg);
 int num_sms();
 
+// Stream-collide variants (up to kMaxOrb orbitals): one site per thread; two
+// x-neighbouring sites per thread with two-element loads (needs an even nx
+// and aligned arrays, else the one-site kernel runs); one site per thread
+// with the next orbital's populations loaded before the current one collides.
+constexpr int kRelaxSites = 0;
+constexpr int kRelaxPairs = 1;
+constexpr int kRelaxPrefetch = 2;
+constexpr int kRelaxVariants = 3;
+constexpr int kRelaxVariantMask = 3;
+// Flag or-ed into the variant by the cycle-ending step: its overlap feeds the
+// Cholesky orthonormalisation, which fixes the orbital norms that density and
+// energies see, so it is summed exactly (FP64) even where the per-step
+// overlap runs on the tensor cores (more than kMaxOrb FP32 orbitals).
+constexpr int kRelaxExactOverlap = 4;
+
+// Variant for a stream-collide launch outside a handle: forced by
+// lbks_set_relax_variant, else the tuned choice for the shape, else one site.
+int relax_variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz);
+
 // ------------------------------------------------------------------ relax ops
 // Implemented per precision (lbks_relax_f64.cu, lbks_relax_f32.cu).
 struct RelaxIO {
@@ -121,7 +140,8 @@ struct OrbitalStart {  // Gaussian start of one orbital
 // orbitals NO*N, W field max(NO-1,1)*N, potentials N, NO x NO matrices,
 // NO scales, kMpStride multipoles, kEmatStride energy-matrix entries).
 struct PrecisionOps {
-    cudaError_t (*relax)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int B, cudaStream_t);
+    cudaError_t (*relax)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int B, int variant,
+                         cudaStream_t);
     cudaError_t (*w_field)(int n_orb, const Grid&, double omega, const void* psi, const double* lam, void* u, int B,
                            cudaStream_t);
     cudaError_t (*orth_apply)(int n_orb, const Grid&, const double* Linv, void* f, void* psi, int B, cudaStream_t);

@@ -78,7 +78,8 @@ extern "C" int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, in
     cudaError_t e = cudaMemsetAsync(sc.counter, 0, sizeof(unsigned), st);
     if (e == cudaSuccess) {
         RelaxIO io{f_in, u_in, V, sigma_in, f_out, psi_out, S_out, lambda_out, sigma_out};
-        e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, sc, 1, st);
+        e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, sc, 1,
+                       relax_variant_for(precision, n_orb, omega, nx, ny, nz), st);
     }
     if (e != cudaSuccess) return fail(LBKS_ECUDA, std::string("lbks_relax_step_noalloc: ") + cudaGetErrorString(e));
     return LBKS_OK;

@@ -1,0 +1,194 @@
+// Stream-collide over pairs of x-neighbouring sites (nx even): the same
+// update as k_stream_collide, but every population of both sites arrives in
+// one aligned two-element load (bfloat16 x 2 = 4 bytes, float x 2 = 8 bytes),
+// which halves the load and store instructions per byte -- the limit of the
+// one-site kernel with 2-byte bfloat16 populations.
+//
+// Pull streaming with a velocity of x-component +1 needs, for the pair's
+// first site, the element left of the pair's source pair: the lane to the
+// left loaded it (its pair lies two sites to the left in the same source
+// row), so it arrives by warp shuffle; lane 0 loads it itself.  x-component
+// -1 mirrors this with the lane to the right and lane 31.  Where the
+// neighbouring lane sits in another row the element is not needed: the site
+// is on the box face and has no source there.  Every lane of a warp runs the
+// shuffles (lanes past the last pair load nothing).
+// Included by lbks_relax.cuh.
+#pragma once
+
+namespace lbks {
+
+template <typename TS>
+struct Pack2;
+template <>
+struct Pack2<float> {
+    using type = float2;
+    __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+    __device__ static float lo(float2 v) { return v.x; }
+    __device__ static float hi(float2 v) { return v.y; }
+    __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct Pack2<__nv_bfloat16> {
+    using type = __nv_bfloat162;
+    __device__ static __nv_bfloat162 zero() { return __floats2bfloat162_rn(0.f, 0.f); }
+    __device__ static float lo(__nv_bfloat162 v) { return __low2float(v); }
+    __device__ static float hi(__nv_bfloat162 v) { return __high2float(v); }
+    __device__ static __nv_bfloat162 make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <>
+struct Pack2<double> {
+    using type = double2;
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+    __device__ static double lo(double2 v) { return v.x; }
+    __device__ static double hi(double2 v) { return v.y; }
+    __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+};
+
+// Values of population array `src` (element type E) arriving along velocity
+// p at the two sites of the pair: x-shift by shuffle as described above.
+// row: index of the pair's source pair (s0 - offset of v_p without its x part).
+// ok: the source row exists and the lane is live; v0 / v1: the x-source of
+// site 0 / site 1 exists.
+template <typename E, typename T, int VX>
+__device__ __forceinline__ void pull_pair(const E* __restrict__ src, uint32_t row, bool ok, bool v0, bool v1,
+                                          int lane, T& g0, T& g1) {
+    using P = Pack2<E>;
+    const typename P::type q = ok ? __ldg(reinterpret_cast<const typename P::type*>(src + row)) : P::zero();
+    const T a = (T)P::lo(q), b = (T)P::hi(q);
+    if (VX == 0) {
+        g0 = a;
+        g1 = b;
+    } else if (VX > 0) {  // source x - 1
+        T left = __shfl_up_sync(0xffffffffu, b, 1);
+        if (lane == 0) left = (ok && v0) ? to_compute<T>(__ldg(src + row - 1)) : T(0);
+        g0 = v0 ? left : T(0);
+        g1 = a;
+    } else {  // source x + 1
+        T right = __shfl_down_sync(0xffffffffu, a, 1);
+        if (lane == 31) right = (ok && v1) ? to_compute<T>(__ldg(src + row + 2)) : T(0);
+        g0 = b;
+        g1 = v1 ? right : T(0);
+    }
+}
+
+// Resident 256-thread blocks per SM the register allocator must allow: two
+// sites per thread hold twice the populations of the one-site kernel, so two
+// blocks (1024 sites per SM in flight, as the one-site kernel's four).
+template <typename TS, int NO, bool BATCHED>
+constexpr int pair_min_blocks() {
+    return 2;
+}
+
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>()))
+    k_stream_collide_pair(Grid g, Coef c, RelaxIO io, Scratch sc) {
+    constexpr int NP = NO * (NO + 1) / 2;
+    using PS = Pack2<TS>;
+    using PT = Pack2<T>;
+    if (BATCHED && inactive(g)) return;
+    const uint32_t N = g.N, NH = N >> 1;
+    const size_t y = BATCHED ? sys_id() : 0;
+    const TS* __restrict__ fin = static_cast<const TS*>(io.f_in);
+    const T* __restrict__ uin = static_cast<const T*>(io.u_in);
+    TS* __restrict__ fout = static_cast<TS*>(io.f_out);
+    T* __restrict__ psio = static_cast<T*>(io.psi_out);
+    const int lane = threadIdx.x & 31;
+    const int nxy = g.nx * g.ny;
+
+    T sig[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[y * NO + j];
+    const T om = (T)c.omega, dt = (T)c.dt, om1 = (T)(1.0 - c.omega);
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+
+    T acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = T(0);
+
+    // block-uniform trip count: every lane of a warp takes part in the shuffles
+    for (uint32_t i0 = blockIdx.x * kThreads; i0 < NH; i0 += gridDim.x * kThreads) {
+        const uint32_t i = i0 + threadIdx.x;
+        const bool live = i < NH;
+        const uint32_t s0 = live ? 2 * i : 0;
+        const Site t = decode(g, s0);
+        const bool x0_has_left = t.xm;                        // site 0 pulls from x - 1
+        const bool x1_has_right = t.x + 2 < g.nx;             // site 1 pulls from x + 1
+        T vr0 = T(0), vr1 = T(0);
+        if (live) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(io.V + y * N + s0));
+            vr0 = (T)v.x;
+            vr1 = (T)v.y;
+        }
+        T psi0[NO], psi1[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+            const TS* fj = fin + (y * NO + j) * 19 * N;
+            const T* uj = (j > 0 && uin != nullptr) ? uin + (y * (NO > 1 ? NO - 1 : 1) + j - 1) * N : nullptr;
+            TS* oj = fout + (y * NO + j) * 19 * N;
+            T g0[19], g1[19];
+#pragma unroll
+            for (int p = 0; p < 19; ++p) {
+                const int vy = vel(p, 1), vz = vel(p, 2);
+                const bool rowok = live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
+                const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
+                const TS* src = fj + (size_t)p * N;
+                if (vel(p, 0) == 0) pull_pair<TS, T, 0>(src, row, rowok, true, true, lane, g0[p], g1[p]);
+                else if (vel(p, 0) > 0) pull_pair<TS, T, 1>(src, row, rowok, x0_has_left, true, lane, g0[p], g1[p]);
+                else pull_pair<TS, T, -1>(src, row, rowok, true, x1_has_right, lane, g0[p], g1[p]);
+            }
+            if (uj) {  // warp-uniform
+#pragma unroll
+                for (int p = 0; p < 19; ++p) {
+                    const int vy = vel(p, 1), vz = vel(p, 2);
+                    const bool rowok =
+                        live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
+                    const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
+                    T w0, w1;
+                    if (vel(p, 0) == 0) pull_pair<T, T, 0>(uj, row, rowok, true, true, lane, w0, w1);
+                    else if (vel(p, 0) > 0) pull_pair<T, T, 1>(uj, row, rowok, x0_has_left, true, lane, w0, w1);
+                    else pull_pair<T, T, -1>(uj, row, rowok, true, x1_has_right, lane, w0, w1);
+                    g0[p] += xi[vclass(p)] * w0;
+                    g1[p] += xi[vclass(p)] * w1;
+                }
+            }
+            T ps0 = T(0), ps1 = T(0);
+#pragma unroll
+            for (int p = 0; p < 19; ++p) {
+                ps0 += g0[p];
+                ps1 += g1[p];
+            }
+            ps0 *= sig[j];
+            ps1 *= sig[j];
+            const T A0 = om * ps0, B0 = dt * vr0 * ps0, A1 = om * ps1, B1 = dt * vr1 * ps1;
+            const T c1 = om1 * sig[j];
+            if (live) {
+#pragma unroll
+                for (int p = 0; p < 19; ++p) {
+                    const int k = vclass(p);
+                    const T e0 = xi[k] * A0 - chi[k] * B0, e1 = xi[k] * A1 - chi[k] * B1;
+                    const T o0 = OM1 ? e0 : c1 * g0[p] + e0, o1 = OM1 ? e1 : c1 * g1[p] + e1;
+                    __stcs(reinterpret_cast<typename PS::type*>(oj + (size_t)p * N + s0), PS::make(o0, o1));
+                }
+                *reinterpret_cast<typename PT::type*>(psio + (y * NO + j) * N + s0) = PT::make(ps0, ps1);
+            }
+            psi0[j] = live ? ps0 : T(0);
+            psi1[j] = live ? ps1 : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < NO; ++j)
+#pragma unroll
+            for (int k = 0; k <= j; ++k) acc[tri(j, k)] += psi0[j] * psi0[k] + psi1[j] * psi1[k];
+    }
+
+    double v[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v[k] = (double)acc[k];
+    double* partial = sc.partial + y * sc.max_blocks * sc.max_vals;
+    block_sum_store<NP>(v, partial + (size_t)blockIdx.x * NP);
+    __shared__ double tot[NP];
+    if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0)
+        store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
+}
+
+}  // namespace lbks

@@ -56,6 +56,7 @@ __device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16, float>(float v)
 // Neighbour bookkeeping of one site for pull streaming.
 struct Site {
     uint32_t s;
+    int x;
     bool xm, xp, ym, yp, zm, zp;  // a source exists at x-1, x+1, ...
 };
 
@@ -67,6 +68,7 @@ __device__ __forceinline__ Site decode(const Grid& g, uint32_t s) {
     const uint32_t zz = g.divy.div(q);
     const int y = (int)(q - zz * (uint32_t)g.ny);
     const int z = (int)zz;
+    t.x = x;
     t.xm = x > 0; t.xp = x < g.nx - 1;
     t.ym = y > 0; t.yp = y < g.ny - 1;
     t.zm = z > 0; t.zp = z < g.nz - 1;
@@ -94,18 +96,26 @@ __device__ __forceinline__ uint32_t source_index(const Grid& g, uint32_t s, int 
 // the orbitals of a site share nothing but the overlap products).
 // OM1: omega = 1, where the collision forgets the arriving populations and
 // only their sum psi enters (no (1 - omega) f term).
-template <typename T, int NO, bool OM1, bool BATCHED>
+// PF: the populations of orbital j + 1 are loaded before orbital j is
+// collided (twice the loads in flight per thread, one block fewer per SM).
+template <typename T, int NO, bool OM1, bool BATCHED, bool PF = false>
 constexpr int relax_min_blocks() {
-    return (sizeof(T) == 8 && !OM1) ? LBKS_RELAX_MIN_BLOCKS_WIDE
+    return PF                       ? LBKS_RELAX_MIN_BLOCKS_WIDE + (sizeof(T) == 8 ? 0 : 1)
+           : (sizeof(T) == 8 && !OM1) ? LBKS_RELAX_MIN_BLOCKS_WIDE
            : (BATCHED || NO > 5)    ? LBKS_RELAX_MIN_BLOCKS_WIDE + 1
                                     : LBKS_RELAX_MIN_BLOCKS;
 }
 
+template <typename TS>
+__device__ __forceinline__ TS zero_store() { return TS(0); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 zero_store<__nv_bfloat16>() { return __float2bfloat16_rn(0.f); }
+
 // BATCHED: the launch covers several systems (system = blockIdx.y); the
 // single-system build keeps its array bases in the parameter bank instead of
 // registers, which the register-bound kernel needs.
-template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
-__global__ void __launch_bounds__(kThreads, (relax_min_blocks<T, NO, OM1, BATCHED>()))
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED, bool PF>
+__global__ void __launch_bounds__(kThreads, (relax_min_blocks<T, NO, OM1, BATCHED, PF>()))
     k_stream_collide(Grid g, Coef c, RelaxIO io, Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
     if (BATCHED && inactive(g)) return;
@@ -133,6 +143,13 @@ __global__ void __launch_bounds__(kThreads, (relax_min_blocks<T, NO, OM1, BATCHE
         const Site t = decode(g, s);
         const T vr = (T)__ldg(io.V + y * N + s);
         T psi[NO];
+        TS raw[19];  // PF: the next orbital's populations, in flight
+        if (PF) {
+#pragma unroll
+            for (int p = 0; p < 19; ++p)
+                raw[p] = has_source(t, p) ? ld_ro(fin + y * NO * 19 * N + (size_t)p * N + source_index(g, s, p))
+                                          : zero_store<TS>();
+        }
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
             const TS* fj = fin + (y * NO + j) * 19 * N;
@@ -140,9 +157,20 @@ __global__ void __launch_bounds__(kThreads, (relax_min_blocks<T, NO, OM1, BATCHE
             TS* oj = fout + (y * NO + j) * 19 * N;
             // all 19 loads are issued before any use (memory-level parallelism)
             T gp[19];
+            if (PF) {
 #pragma unroll
-            for (int p = 0; p < 19; ++p)
-                gp[p] = has_source(t, p) ? to_compute<T>(ld_ro(fj + (size_t)p * N + source_index(g, s, p))) : T(0);
+                for (int p = 0; p < 19; ++p) gp[p] = to_compute<T>(raw[p]);
+                if (j + 1 < NO) {
+#pragma unroll
+                    for (int p = 0; p < 19; ++p)
+                        raw[p] = has_source(t, p) ? ld_ro(fj + 19 * (size_t)N + (size_t)p * N + source_index(g, s, p))
+                                                  : zero_store<TS>();
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < 19; ++p)
+                    gp[p] = has_source(t, p) ? to_compute<T>(ld_ro(fj + (size_t)p * N + source_index(g, s, p))) : T(0);
+            }
             if (uj) {
 #pragma unroll
                 for (int p = 0; p < 19; ++p)
@@ -436,6 +464,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix(Grid g, Coef c, cons
 }  // namespace lbks
 
 #include "lbks_wide.cuh"
+#include "lbks_pair.cuh"
 
 namespace lbks {
 
@@ -457,27 +486,63 @@ inline dim3 batch_grid(size_t n, int cap, int B, int scratch_blocks = 1 << 30) {
 }
 inline dim3 elementwise_grid(size_t n, int B) { return batch_grid(n, num_sms() * 8, B); }
 
+// The two-site kernel needs an even row length (pairs never straddle rows)
+// and arrays aligned for two-element loads of every type it reads.
+inline bool pairs_apply(const Grid& g, const RelaxIO& io) {
+    auto al = [](const void* p, uintptr_t a) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % a == 0; };
+    return g.nx % 2 == 0 && al(io.f_in, 16) && al(io.f_out, 16) && al(io.u_in, 16) && al(io.psi_out, 16) &&
+           al(io.V, 16);
+}
+
+// One launch of the one-site kernel (PF: next orbital prefetched) / of the
+// two-site kernel for NO orbitals of B systems.
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED, bool PF>
+cudaError_t launch_stream_collide(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                  cudaStream_t st) {
+    auto kern = k_stream_collide<TS, T, NO, OM1, BATCHED, PF>;
+    static const int nb = blocks_per_sm(kern);
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    kern<<<batch_grid(g.N, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
+cudaError_t launch_stream_collide_pair(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                       cudaStream_t st) {
+    auto kern = k_stream_collide_pair<TS, T, NO, OM1, BATCHED>;
+    static const int nb = blocks_per_sm(kern);
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    kern<<<batch_grid(g.N / 2, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// The two-site and the prefetching variants for NO <= kMaxOrb orbitals, each
+// compiled in a translation unit of its own (lbks_relax_<precision>_<variant>.cu)
+// so that the per-precision units stay small enough to build in parallel.
+template <typename TS, typename T>
+cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                               const Scratch& sc, int B, cudaStream_t st);
+template <typename TS, typename T>
+cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                                  const Scratch& sc, int B, cudaStream_t st);
+
 template <typename TS, typename T>
 struct Ops {
-    template <int NO, bool OM1, bool BATCHED>
-    static cudaError_t relax_nmb(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                                 cudaStream_t st) {
-        auto kern = k_stream_collide<TS, T, NO, OM1, BATCHED>;
-        static const int nb = blocks_per_sm(kern);
-        if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
-        kern<<<batch_grid(g.N, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
-        count_launches(1);
-        return cudaGetLastError();
-    }
     template <int NO, bool OM1>
     static cudaError_t relax_nm(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                                cudaStream_t st) {
-        return B > 1 ? relax_nmb<NO, OM1, true>(g, c, io, sc, B, st) : relax_nmb<NO, OM1, false>(g, c, io, sc, B, st);
+                                int variant, cudaStream_t st) {
+        const int v = variant & kRelaxVariantMask;
+        if (v == kRelaxPairs && pairs_apply(g, io)) return launch_relax_pairs<TS, T>(NO, OM1, g, c, io, sc, B, st);
+        if (v == kRelaxPrefetch && NO > 1) return launch_relax_prefetch<TS, T>(NO, OM1, g, c, io, sc, B, st);
+        return B > 1 ? launch_stream_collide<TS, T, NO, OM1, true, false>(g, c, io, sc, B, st)
+                     : launch_stream_collide<TS, T, NO, OM1, false, false>(g, c, io, sc, B, st);
     }
     template <int NO>
     static cudaError_t relax_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                               cudaStream_t st) {
-        return c.omega == 1.0 ? relax_nm<NO, true>(g, c, io, sc, B, st) : relax_nm<NO, false>(g, c, io, sc, B, st);
+                               int variant, cudaStream_t st) {
+        return c.omega == 1.0 ? relax_nm<NO, true>(g, c, io, sc, B, variant, st)
+                              : relax_nm<NO, false>(g, c, io, sc, B, variant, st);
     }
     template <int NO>
     static cudaError_t wfield_n(const Grid& g, double omega, const void* psi, const double* lam, void* u, int B,
@@ -548,17 +613,17 @@ struct Ops {
         const int per = std::max(1, std::min(sc.max_blocks, num_sms() * 2 / std::max(B, 1)));
         return dim3((unsigned)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)per)), (unsigned)B);
     }
+    // FP32 orbitals, per-step overlap (sigma and Lambda, which every step
+    // measures again): tensor cores.  exact: FP64 sums of SIMT products (the
+    // orthonormalising overlaps, where the tensor cores' truncating FP32
+    // accumulation would leave a ~1e-6 relative bias on the norms).
     template <bool LAM>
     static cudaError_t gram_wide(int NO, const Grid& g, double h, const void* psi, double* S, double* lam,
-                                 double* sigma, const Scratch& sc, int B, cudaStream_t st) {
+                                 double* sigma, const Scratch& sc, int B, cudaStream_t st, bool exact = !LAM) {
         const int NP = NO * (NO + 1) / 2;
         if (sc.max_vals < NP || sc.systems < B) return cudaErrorInvalidValue;
-        // FP32 orbitals, per-step overlap (sigma and Lambda): tensor cores.  The
-        // orthonormalising overlap keeps exact FP64 sums: it fixes the norms
-        // that density and energies see, where the tensor cores' truncating
-        // FP32 accumulation would leave a ~1e-6 relative bias.
         if constexpr (std::is_same<T, float>::value)
-            if (LAM) return launch_gram_tc(NO, g, h, (const float*)psi, S, lam, sigma, sc, B, st);
+            if (!exact) return launch_gram_tc(NO, g, h, (const float*)psi, S, lam, sigma, sc, B, st);
         auto kern = k_gram_wide<T, LAM>;
         const size_t smem = (size_t)NO * kWideTile * sizeof(T) + sizeof(double) * NP;
         cudaError_t e = with_smem(kern, smem);
@@ -568,14 +633,15 @@ struct Ops {
         return cudaGetLastError();
     }
     static cudaError_t relax_wide(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                                  cudaStream_t st) {
+                                  int variant, cudaStream_t st) {
         auto kern = c.omega == 1.0 ? k_stream_collide_wide<TS, T, true> : k_stream_collide_wide<TS, T, false>;
         if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
         kern<<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return gram_wide<true>(NO, g, c.h, io.psi_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st);
+        return gram_wide<true>(NO, g, c.h, io.psi_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
+                               (variant & kRelaxExactOverlap) != 0);
     }
     static cudaError_t wfield_wide(int NO, const Grid& g, double omega, const void* psi, const double* lam, void* u,
                                    int B, cudaStream_t st) {
@@ -622,9 +688,9 @@ struct Ops {
         default: return n_orb <= kMaxOrbWide ? WIDE : cudaErrorInvalidValue; \
     }
     static cudaError_t relax(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                             cudaStream_t st) {
-#define CALL(NO) relax_n<NO>(g, c, io, sc, B, st)
-#define WIDE relax_wide(n_orb, g, c, io, sc, B, st)
+                             int variant, cudaStream_t st) {
+#define CALL(NO) relax_n<NO>(g, c, io, sc, B, variant, st)
+#define WIDE relax_wide(n_orb, g, c, io, sc, B, variant, st)
         LBKS_SWITCH_NO(CALL)
 #undef WIDE
 #undef CALL

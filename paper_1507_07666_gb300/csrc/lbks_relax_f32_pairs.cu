@@ -1,0 +1,7 @@
+// FP32 instantiation of the two-site stream-collide kernels.
+#include "lbks_relax_variants.cuh"
+
+namespace lbks {
+template cudaError_t launch_relax_pairs<float, float>(int, bool, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int,
+                                     cudaStream_t);
+}  // namespace lbks

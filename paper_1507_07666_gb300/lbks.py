@@ -105,6 +105,8 @@ _SIGS = {
                                      _vp, _vp]),
     "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
     "lbks_overlap": (_i, [_i, _sz, _i, _d, _vp, _vp, _i, _vp]),
+    "lbks_set_relax_variant": (_i, [_i]),
+    "lbks_get_relax_variant": (_i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "lbks_cholesky_inverse": (_i, [_i, _vp, _vp, _vp, _vp]),
     "lbks_orth_apply": (_i, [_i, _sz, _i, _vp, _vp, _vp, _vp]),
     "lbks_hartree": (_i, [_i, _i, _i, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _dp, _vp]),
@@ -282,6 +284,25 @@ def lbks_overlap(precision, n_sites, n_orb, h, psi, S, tensor_cores=False, strea
     import torch
     _check(_lib.lbks_overlap(precision, n_sites, n_orb, h, _ptr(psi, _psitype(precision)), _ptr(S, torch.float64),
                              int(bool(tensor_cores)), _stream(stream)))
+
+
+RELAX_VARIANTS = ("sites", "pairs", "prefetch")
+
+
+def lbks_set_relax_variant(mode: int) -> int:
+    """0: tuned per shape (default); 1 + v: variant v of RELAX_VARIANTS forced. Returns the previous mode."""
+    prev = _lib.lbks_set_relax_variant(int(mode))
+    if prev < 0:
+        raise LbksError(EINVAL, f"bad relax variant mode {mode}")
+    return prev
+
+
+def lbks_get_relax_variant(handle) -> dict:
+    v, ms = ctypes.c_int(), (ctypes.c_double * len(RELAX_VARIANTS))()
+    _check(_lib.lbks_get_relax_variant(handle, ctypes.byref(v), ms))
+    out = {"variant": RELAX_VARIANTS[v.value]}
+    out.update({f"ms_{name}": ms[k] for k, name in enumerate(RELAX_VARIANTS)})
+    return out
 
 
 def lbks_cholesky_inverse(n, S, Linv, status, stream=None):

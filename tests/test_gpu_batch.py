@@ -30,13 +30,16 @@ def test_batched_water_scan_matches_single_solves(prec):
         s.set_geometry(m.xyz, m.Z)
         ref = s.scf()
         assert res[i]["converged"]
+        # FP32: the batched and the single launches may run different tuned
+        # kernels and sum the overlaps in another order; a run can then stop
+        # one cycle earlier or later, so agreement is to a few e_tol.
         if prec == 0:
             assert res[i]["cycles"] == ref["cycles"]
-        assert abs(res[i]["E_total"] - ref["E_total"]) <= (1e-9 if prec == 0 else 1e-6)
+        assert abs(res[i]["E_total"] - ref["E_total"]) <= (1e-9 if prec == 0 else 5e-6)
         np.testing.assert_allclose(res[i]["eigenvalues"][:5], ref["eigenvalues"][:5],
-                                   atol=1e-9 if prec == 0 else 1e-6)
+                                   atol=1e-9 if prec == 0 else 1e-5)
         rho_b, rho_s = b.density(i), s.density()
-        assert np.linalg.norm(rho_b - rho_s) / np.linalg.norm(rho_s) <= (1e-9 if prec == 0 else 1e-6)
+        assert np.linalg.norm(rho_b - rho_s) / np.linalg.norm(rho_s) <= (1e-9 if prec == 0 else 1e-5)
         s.close()
     b.close()
 

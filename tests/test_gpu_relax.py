@@ -27,7 +27,12 @@ CASES = [
     # more than eight orbitals: stream-collide without fused products + tiled Gram kernel
     ((21, 18, 23), 12, 1.0, 6),
     ((9, 10, 11), 10, 0.9, 8),
+    # even nx: the two-site kernel applies (x-shifts cross lanes and warps)
+    ((34, 20, 17), 5, 1.0, 9),
+    ((66, 7, 5), 2, 1.2, 10),
+    ((10, 9, 11), 8, 0.8, 11),
 ]
+VARIANTS = [1, 2, 3]  # lbks_set_relax_variant: one site, two sites, one site with the next orbital prefetched
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
 # bfloat16 storage: orbitals and overlaps are float sums of the stored (rounded)
 # inputs; the stored outputs carry bfloat16's 2^-9 relative rounding
@@ -62,9 +67,18 @@ def _run_gpu(torch, lbks, prec, n, n_orb, omega, theta, dt, h, f, u, V, sigma):
             "sigma": to_np(sig_out)}
 
 
+@pytest.fixture
+def relax_variant(request):
+    from paper_1507_07666_gb300 import lbks
+    prev = lbks.lbks_set_relax_variant(request.param)
+    yield request.param
+    lbks.lbks_set_relax_variant(prev)
+
+
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch"], indirect=True)
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("n,n_orb,omega,seed", CASES)
-def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed):
+def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed, relax_variant):
     torch, lbks = require_gpu()
     theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, omega, h)
@@ -82,8 +96,10 @@ def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed):
     assert rel_err(fg, ref["fstar"]) < tol
 
 
-@pytest.mark.parametrize("n,n_orb,omega,seed", [((33, 20, 17), 5, 1.0, 2), ((7, 9, 11), 3, 0.8, 1)])
-def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed):
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch"], indirect=True)
+@pytest.mark.parametrize("n,n_orb,omega,seed", [((33, 20, 17), 5, 1.0, 2), ((7, 9, 11), 3, 0.8, 1),
+                                                 ((34, 20, 17), 5, 1.0, 2), ((66, 7, 5), 2, 1.2, 10)])
+def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed, relax_variant):
     """bfloat16 populations, float arithmetic: the oracle is fed the rounded
     populations; orbitals/overlaps to float accuracy, stored populations to
     bfloat16 rounding."""

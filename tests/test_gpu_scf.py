@@ -173,3 +173,33 @@ def test_water_dimer_ten_orbitals_trajectory(prec):
     g = s.scf_cycles(3)
     _compare(g, ref, s.density(), st.rho, e_tol=1e-8 if prec == 0 else E_TOL)
     s.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["sites", "pairs", "prefetch"])
+def test_stream_collide_variants_give_the_oracle_trajectory(mode):
+    """Both stream-collide kernels (one site or two x-neighbouring sites per
+    thread), forced, follow the oracle's SCF trajectory; the tuner (mode 0)
+    reports the variant it chose and both timings."""
+    torch, lbks = require_gpu()
+    mol = W.water(1.8, 104.0)
+    n, h = (30, 26, 28), 0.4
+    st, ref = scf.scf(n, h, mol.xyz, mol.Z, 5, n_inner=12, poisson_rtol=1e-12, fixed_cycles=2)
+    prev = lbks.lbks_set_relax_variant(mode)
+    try:
+        for prec in (0, 1, 2):
+            s = lbks.System(n, h, 5, precision=prec, n_inner=12, poisson_rtol=1e-12, polish_tol=0.0)
+            s.set_geometry(mol.xyz, mol.Z)
+            assert lbks.lbks_get_relax_variant(s.handle)["variant"] == lbks.RELAX_VARIANTS[mode - 1]
+            g = s.scf_cycles(2)
+            tol = {0: 1e-8, 1: 1e-5, 2: 2e-3}[prec]
+            assert abs(g["E_total"] - ref["E_total"]) <= tol, (prec, g["E_total"], ref["E_total"])
+            s.close()
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+    lbks.lbks_set_relax_variant(0)
+    s = lbks.System((34, 22, 18), h, 5, precision=1, n_inner=12)  # a shape no other test uses
+    s.set_geometry(mol.xyz, mol.Z)
+    t = lbks.lbks_get_relax_variant(s.handle)
+    assert t["variant"] in lbks.RELAX_VARIANTS and min(t[f"ms_{v}"] for v in lbks.RELAX_VARIANTS) > 0
+    s.close()
+    lbks.lbks_set_relax_variant(prev)

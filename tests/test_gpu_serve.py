@@ -95,3 +95,22 @@ def test_serving_errors_are_reported_on_the_host():
         assert e.value.code == lbks.EINVAL
     finally:
         lbks.lbks_server_destroy(srv)
+
+
+def test_new_handle_is_ready_while_the_legacy_stream_is_busy():
+    """A handle zeroes its counters and flags on its own stream and waits for
+    them.  Zeroing them with legacy-stream cudaMemset left them unordered
+    with the solve's non-blocking streams: with the legacy stream held by a
+    long kernel, the zeroing landed mid-solve (reset arrival counters and
+    atom counts: failed Cholesky, energies without nuclear attraction)."""
+    torch, lbks = require_gpu()
+    _, mol, n, h = MIX[2]
+    ref = _alone(lbks, n, h, mol, 1)
+    torch.cuda._sleep(2_000_000_000)  # ~1 s spin on the legacy default stream
+    s = lbks.System(n, h, mol.n_orb, precision=1, n_inner=20)
+    s.set_geometry(mol.xyz, mol.Z)
+    r = s.scf(stream=torch.cuda.Stream())
+    s.close()
+    torch.cuda.synchronize()
+    assert r["converged"]
+    assert abs(r["E_total"] - ref["E_total"]) <= 1e-10
