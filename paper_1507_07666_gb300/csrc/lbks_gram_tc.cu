@@ -31,13 +31,18 @@
 namespace lbks {
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;                              // 8 warps; warp w reads TMEM lanes 32 (w % 4) ..
 constexpr int kTcSites = 64;                                 // sites per tile: 64 bf16 = one 128-byte row
 constexpr int kTcRows = 128;                                 // MMA M
 constexpr int kTcStages = 2;
 constexpr int kTcTileBytes = kTcRows * kTcSites * 2;         // 16 KB
-constexpr int kTcQuads = kMaxOrbWide * (kTcSites / 4) / kTcThreads;  // 4-site groups per thread (at most)
-constexpr int kTcMaxPairs = (kMaxOrbWide * (kMaxOrbWide + 1) / 2 + kTcThreads - 1) / kTcThreads;
+// Per-thread work bounds for at most MAXO orbitals: 4-site groups of a tile,
+// and overlap pairs of the packed lower triangle.
+template <int MAXO>
+struct TcBounds {
+    static constexpr int quads = (MAXO * (kTcSites / 4) + kTcThreads - 1) / kTcThreads;
+    static constexpr int pairs = (MAXO * (MAXO + 1) / 2 + kTcThreads - 1) / kTcThreads;
+};
 constexpr int kDrainTiles = 8;
 constexpr int kInStages = 4;                                 // staged FP32 tiles in flight (bulk-copy path)
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -139,8 +144,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Dynamic shared memory: 1 KB alignment slack, kTcStages bf16 tiles, the
 // staging ring (BULK), the (2N_O) x (2N_O + 1) FP32 fold buffer (reused for
 // the block totals).
-template <bool LAM, bool BULK>
-__global__ void __launch_bounds__(kTcThreads, 1)
+template <bool LAM, bool BULK, int MAXO>
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
               double* sigma, Scratch sc) {
     if (inactive(g)) return;
@@ -153,7 +158,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_sh;
 
+    constexpr int kTcQuads = TcBounds<MAXO>::quads, kTcMaxPairs = TcBounds<MAXO>::pairs;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int lane_base = (warp & 3) * 32, half = warp >> 2;  // TMEM lanes of this warp; column half it drains
     const uint32_t N = g.N;
     const size_t y = sys_id();
     psi += y * NO * (size_t)N;
@@ -297,14 +304,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             in_chunk = 0;
             const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity));
             tc_fence_after();
-            if (ok && warp * 32 < R) {
-                for (int cb = 0; cb < NM; cb += 16) {
+            if (ok && lane_base < R) {  // the two warp groups drain alternate 16-column blocks
+                const int row = lane_base + (tid & 31);
+                for (int cb = 16 * half; cb < NM; cb += 32) {
                     uint32_t v[16];
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
-                    if (tid < R) {
+                    tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)cb, v);
+                    if (row < R) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e)
-                            if (cb + e < R) fold[tid * ld + cb + e] = __uint_as_float(v[e]);
+                            if (cb + e < R) fold[row * ld + cb + e] = __uint_as_float(v[e]);
                     }
                 }
             }
@@ -351,19 +359,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, LAM ? sigma + y * NO : nullptr);
 }
 
-template <bool LAM, bool BULK>
+template <bool LAM, bool BULK, int MAXO>
 static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
                                   double* sigma, const Scratch& sc, int B, int drain_tiles, cudaStream_t st) {
-    auto kern = k_gram_tc<LAM, BULK>;
+    auto kern = k_gram_tc<LAM, BULK, MAXO>;
     const int R = 2 * NO, NM = (R + 15) & ~15;
     const int ncols = NM <= 32 ? 32 : NM <= 64 ? 64 : 128;
     size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (BULK ? (size_t)kInStages * NO * kTcSites * 4 : 0) +
                   (size_t)R * (R + 1) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the largest shared-memory carveout, so that two blocks fit beside each other
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem);
     if (e != cudaSuccess) return e;
+    // The occupancy query has reported one block per SM where two fit (shared
+    // memory and registers both allow two, and two run when launched): take
+    // the larger of it and the count from the per-SM limits.
+    {
+        static const int smem_sm = [] {
+            int dev = 0, v = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            return v;
+        }();
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0) {
+            const int regs = (fa.numRegs + 7) & ~7;
+            const int by_regs = 65536 / (regs * kTcThreads);
+            const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+            occ = std::max(occ, std::min(by_regs, by_smem));
+        }
+    }
     // co-resident blocks must not ask for more TMEM columns than an SM has
     const int cap = kTmemColumnsPerSm / ncols;
     for (int guard = 0; occ > cap && guard < 64; ++guard) {
@@ -388,10 +417,16 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
     if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B || drain_tiles < 0) return cudaErrorInvalidValue;
     if (drain_tiles == 0) drain_tiles = kDrainTiles;
     const bool bulk = g.N % 4 == 0 && reinterpret_cast<uintptr_t>(psi) % 16 == 0;
-    if (lam) return bulk ? gram_tc_launch<true, true>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
-                         : gram_tc_launch<true, false>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st);
-    return bulk ? gram_tc_launch<false, true>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st)
-                : gram_tc_launch<false, false>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st);
+#define LBKS_TC(MAXO)                                                                                          \
+    return lam ? (bulk ? gram_tc_launch<true, true, MAXO>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)  \
+                       : gram_tc_launch<true, false, MAXO>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)) \
+               : (bulk ? gram_tc_launch<false, true, MAXO>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st) \
+                       : gram_tc_launch<false, false, MAXO>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st));
+    if (NO <= 16) LBKS_TC(16)
+    if (NO <= 32) LBKS_TC(32)
+    if (NO <= 48) LBKS_TC(48)
+    LBKS_TC(kMaxOrbWide)
+#undef LBKS_TC
 }
 
 unsigned gram_tc_timeouts() {

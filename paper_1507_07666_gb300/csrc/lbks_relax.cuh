@@ -643,15 +643,23 @@ struct Ops {
         return gram_wide<true>(NO, g, c.h, io.psi_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
                                (variant & kRelaxExactOverlap) != 0);
     }
-    static cudaError_t wfield_wide(int NO, const Grid& g, double omega, const void* psi, const double* lam, void* u,
-                                   int B, cudaStream_t st) {
-        const size_t smem = ((size_t)NO * kThreads + (size_t)NO * NO) * sizeof(T);
-        cudaError_t e = with_smem(k_w_field_wide<T>, smem);
-        if (e != cudaSuccess) return e;
-        k_w_field_wide<T><<<batch_grid(g.N, num_sms() * 2, B), kThreads, smem, st>>>(g, omega, (const T*)psi, lam,
-                                                                                      (T*)u, NO);
+    template <int MAXO>
+    static cudaError_t wfield_wide_m(int NO, const Grid& g, double omega, const void* psi, const double* lam,
+                                     void* u, int B, cudaStream_t st) {
+        auto kern = k_w_field_wide<T, MAXO>;
+        static const int nb = blocks_per_sm(kern);
+        kern<<<batch_grid(g.N, nb * num_sms(), B), kThreads, 0, st>>>(g, omega, (const T*)psi, lam, (T*)u, NO);
         count_launches(1);
         return cudaGetLastError();
+    }
+    static cudaError_t wfield_wide(int NO, const Grid& g, double omega, const void* psi, const double* lam, void* u,
+                                   int B, cudaStream_t st) {
+        if (NO <= 16) return wfield_wide_m<16>(NO, g, omega, psi, lam, u, B, st);
+        if (NO <= 24) return wfield_wide_m<24>(NO, g, omega, psi, lam, u, B, st);
+        if (NO <= 32) return wfield_wide_m<32>(NO, g, omega, psi, lam, u, B, st);
+        if (NO <= 40) return wfield_wide_m<40>(NO, g, omega, psi, lam, u, B, st);
+        if (NO <= 48) return wfield_wide_m<48>(NO, g, omega, psi, lam, u, B, st);
+        return wfield_wide_m<kMaxOrbWide>(NO, g, omega, psi, lam, u, B, st);
     }
     static cudaError_t orth_wide(int NO, const Grid& g, const double* Linv, void* f, void* psi, int B,
                                  cudaStream_t st) {

@@ -111,33 +111,62 @@ __global__ void __launch_bounds__(kThreads) k_gram_wide(Grid g, double h, const 
         store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, sigma + y * NO);
 }
 
-// u_(j-1) = -omega sum_{k<j} Lambda_jk psi_k: orbital tile and Lambda in
-// shared memory, one site per thread.  Dynamic shared memory:
-// (NO * kThreads + NO * NO) * sizeof(T).
-template <typename T>
+// 16-byte shared-memory loads that the compiler may not hoist out of the
+// site loop (it would otherwise keep the whole coefficient matrix live in
+// registers and spill).
+__device__ __forceinline__ void lds16(const float* p, float (&v)[4]) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void lds16(const double* p, double (&v)[2]) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+
+// u_(j-1) = -omega sum_{k<j} Lambda_jk psi_k, one site per thread: the
+// site's N_O orbital values stay in registers (MAXO >= N_O, a compile-time
+// bound; loops unrolled and cut at the runtime N_O) and -omega Lambda sits in
+// shared memory (row pitch MAXO, zero beyond N_O and on and above the
+// diagonal), read 16 bytes at a time by broadcast.  Streams psi in and u out
+// once: HBM-bound.
+template <typename T, int MAXO>
 __global__ void __launch_bounds__(kThreads) k_w_field_wide(const Grid g, double omega, const T* __restrict__ psi,
                                                            const double* __restrict__ lam, T* __restrict__ u, int NO) {
+    constexpr int V = 16 / sizeof(T);  // coefficients per shared-memory load
+    static_assert(MAXO % V == 0, "row pitch must keep 16-byte alignment");
     if (inactive(g)) return;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* tile = reinterpret_cast<T*>(smem);  // [NO][kThreads]
-    T* L = tile + (size_t)NO * kThreads;   // [NO][NO]
+    __shared__ __align__(16) T L[MAXO * MAXO];
     const size_t n = g.N, y = sys_id();
     psi += y * NO * n;
     lam += y * NO * NO;
     u += y * (NO - 1) * n;
-    for (int i = threadIdx.x; i < NO * NO; i += kThreads) L[i] = (T)(-omega * lam[i]);
-    const size_t tiles = (n + kThreads - 1) / kThreads;
-    for (size_t ti = blockIdx.x; ti < tiles; ti += gridDim.x) {
-        const size_t s = ti * kThreads + threadIdx.x;
-        __syncthreads();
-        for (int k = 0; k < NO; ++k) tile[k * kThreads + threadIdx.x] = (s < n) ? psi[k * n + s] : T(0);
-        __syncthreads();
-        if (s < n) {
-            for (int j = 1; j < NO; ++j) {
-                T w = T(0);
-                for (int k = 0; k < j; ++k) w += L[j * NO + k] * tile[k * kThreads + threadIdx.x];
-                u[(j - 1) * n + s] = w;
+    for (int i = threadIdx.x; i < MAXO * MAXO; i += kThreads) {
+        const int j = i / MAXO, k = i % MAXO;
+        L[i] = (j < NO && k < j) ? (T)(-omega * lam[j * NO + k]) : T(0);
+    }
+    __syncthreads();
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) {
+        T ps[MAXO];
+        const T* pp = psi + s;
+#pragma unroll
+        for (int k = 0; k < MAXO; ++k) {
+            ps[k] = k < NO ? __ldcs(pp) : T(0);
+            pp += n;
+        }
+        T* up = u + s;
+#pragma unroll
+        for (int j = 1; j < MAXO; ++j) {
+            if (j >= NO) break;
+            T w = T(0);
+#pragma unroll
+            for (int kb = 0; kb < j; kb += V) {
+                T l[V];
+                lds16(&L[j * MAXO + kb], l);
+#pragma unroll
+                for (int e = 0; e < V; ++e) w += l[e] * ps[kb + e];
             }
+            __stcs(up, w);
+            up += n;
         }
     }
 }

@@ -42,6 +42,8 @@ def _scaled_err(S, ref):
     ((64, 48, 40), 64, True),
     ((23, 19, 17), 16, False),   # ragged N: scalar loads, partial last tile
     ((31, 7, 5), 33, False),
+    ((24, 20, 16), 20, False),   # each compile-time bound of the kernel: <= 16, 32, 48, 64 orbitals
+    ((12, 10, 8), 3, True),
 ])
 def test_fp32_overlap_tensor_cores(n, n_orb, smooth):
     torch, lbks = require_gpu()

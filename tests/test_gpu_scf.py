@@ -197,7 +197,7 @@ def test_stream_collide_variants_give_the_oracle_trajectory(mode):
     finally:
         lbks.lbks_set_relax_variant(prev)
     lbks.lbks_set_relax_variant(0)
-    s = lbks.System((34, 22, 18), h, 5, precision=1, n_inner=12)  # a shape no other test uses
+    s = lbks.System((34 + 2 * mode, 22, 18), h, 5, precision=1, n_inner=12)  # a shape no other test uses
     s.set_geometry(mol.xyz, mol.Z)
     t = lbks.lbks_get_relax_variant(s.handle)
     assert t["variant"] in lbks.RELAX_VARIANTS and min(t[f"ms_{v}"] for v in lbks.RELAX_VARIANTS) > 0
