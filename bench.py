@@ -39,6 +39,7 @@ import workloads as W  # noqa: E402
 METRIC = "GLUPS (orbital-site updates/s)"
 UNIT = "GLUPS"
 FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 KERNEL_SRC = os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_relax.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_ch4_128_fp32.json")
 
@@ -71,6 +72,9 @@ def parse_args():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CYCLES) + sorted(BATCHES) + sorted(SERVING), default="ch4_128")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent solve slots")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
+    ap.add_argument("--storage", choices=["populations", "psi"], default="populations",
+                    help="what a relaxation step keeps: the 19 populations per orbital-site (any omega), or, at "
+                         "omega = 1, the orbital alone (the same step as a 19-point stencil)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel-only", action="store_true",
@@ -226,6 +230,42 @@ def recorded_traffic():
     return None
 
 
+def time_relax_psi(torch, lbks, w, prec, stream, launches=20):
+    """Average duration of the orbital-storage step (omega = 1) in the
+    solver's launch configuration, CUDA events on the launching stream."""
+    P = torch.float64 if prec == lbks.FP64 else torch.float32
+    nx, ny, nz = w.n
+    N = nx * ny * nz
+    no = w.n_orb
+    with torch.cuda.stream(stream):
+        pa = torch.rand((no, nz, ny, nx), dtype=P, device="cuda")
+        pb = torch.empty_like(pa)
+        u = torch.rand((max(no - 1, 1), nz, ny, nx), dtype=P, device="cuda") * 0.1
+        V = -torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda")
+        sig = torch.full((no,), 1e-3, dtype=torch.float64, device="cuda")
+        S = torch.empty((no, no), dtype=torch.float64, device="cuda")
+        lam = torch.empty_like(S)
+        sig2 = torch.empty_like(sig)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dt = w.theta * w.h * w.h
+    bufs = [pa, pb]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches)]
+    for i in range(3 + launches):
+        src, dst = bufs[i % 2], bufs[(i + 1) % 2]
+        if i >= 3:
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))  # the working set can fit in L2: evict it before every timed launch
+            evs[2 * (i - 3)].record(stream)
+        lbks.lbks_relax_step_psi(prec, nx, ny, nz, no, w.h, w.theta, dt, src, u if no > 1 else None, V, sig, dst, S,
+                                 lam, sig2, stream=stream)
+        if i >= 3:
+            evs[2 * (i - 3) + 1].record(stream)
+    stream.synchronize()
+    ms = [evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(launches)]
+    del pa, pb, u, V, flush
+    return statistics.mean(ms), N * no
+
+
 def time_stream_collide(torch, lbks, w, prec, stream, launches=20):
     """Average duration of the fused stream-collide kernel in the solver's own
     launch configuration, CUDA events on the launching stream."""
@@ -321,7 +361,8 @@ def main_batch(args):
     w = W.water_96(mols[0])
     prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
     b = lbks.Batch(w.n, w.h, w.n_orb, count, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
-                   omega=w.omega, mix=w.mix, max_cycles=w.max_cycles)
+                   omega=w.omega, mix=w.mix, max_cycles=w.max_cycles,
+                   storage=lbks.STORE_PSI if args.storage == "psi" else lbks.STORE_POPULATIONS)
     stream = torch.cuda.Stream()
     geoms = [(m.xyz, m.Z) for m in mols]
 
@@ -355,7 +396,11 @@ def main_batch(args):
         "config": {"workload": f"batched water scan: {count} geometries (seed {seed}), 96^3, h=0.2, one launch "
                                "per relaxation step for all geometries",
                    "grid": list(w.n), "n_orb": w.n_orb, "systems": count, "n_inner": w.n_inner,
-                   "l2": "inputs larger than L2 (populations %.1f GB)" % (2 * 19 * elem * w.n_orb * w.sites * count / 1e9)},
+                   "storage": args.storage,
+                   "l2": "inputs larger than L2 (%s %.1f GB)" % (
+                       ("psi pair", 2 * (8 if prec == lbks.FP64 else 4) * w.n_orb * w.sites * count / 1e9)
+                       if args.storage == "psi" else
+                       ("populations", 2 * 19 * elem * w.n_orb * w.sites * count / 1e9))},
         "solves_per_s": count * args.steps / (elapsed_ms / 1e3),
         "batch": {"converged": sum(r["converged"] for r in last), "cycles_max": max(r["cycles"] for r in last),
                   "cycles_min": min(r["cycles"] for r in last),
@@ -455,8 +500,10 @@ def main_lbks(args):
     per_cycle = args.workload in CYCLES
     w = (CYCLES if per_cycle else WORKLOADS)[args.workload]()
     prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.BF16}[args.precision]
+    psi_mode = args.storage == "psi"
     sysm = lbks.System(w.n, w.h, w.n_orb, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
-                       omega=w.omega, mix=w.mix, max_cycles=w.max_cycles)
+                       omega=w.omega, mix=w.mix, max_cycles=w.max_cycles,
+                       storage=lbks.STORE_PSI if psi_mode else lbks.STORE_POPULATIONS)
     xyz, Z = w.molecule.xyz, w.molecule.Z
     N = w.sites
     stream = torch.cuda.Stream()
@@ -512,19 +559,29 @@ def main_lbks(args):
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration
-    ms, units = time_stream_collide(torch, lbks, w, prec, stream)
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
     wide = w.n_orb > 8
     psi_elem = 8 if prec == lbks.FP64 else 4
-    # more than eight orbitals: the timed step is two kernels, stream-collide
-    # and the overlap (Gram) kernel that reads the orbitals it wrote back
-    bytes_per_launch = (38 * elem + (2 * psi_elem if wide else 0)) * units
+    gram_name = "k_gram_wide" if prec == lbks.FP64 else "k_gram_tc"
+    if psi_mode:
+        # orbital storage: psi in and out, the W field of orbitals 1.., the
+        # collision potential once per site (more than eight orbitals: plus the
+        # overlap kernel's read of psi)
+        ms, units = time_relax_psi(torch, lbks, w, prec, stream)
+        N = units // w.n_orb
+        bytes_per_launch = (psi_elem * (2 * w.n_orb + (w.n_orb - 1) + (w.n_orb if wide else 0)) + 8) * N
+        kname = ("k_relax_psi_wide + %s (one relaxation step)" % gram_name) if wide else "k_relax_psi"
+    else:
+        ms, units = time_stream_collide(torch, lbks, w, prec, stream)
+        # more than eight orbitals: the timed step is two kernels, stream-collide
+        # and the overlap (Gram) kernel that reads the orbitals it wrote back
+        bytes_per_launch = (38 * elem + (2 * psi_elem if wide else 0)) * units
+        kname = ("k_stream_collide_wide + %s (one relaxation step)" % gram_name) if wide else "k_stream_collide"
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_launch / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if wide else recorded_traffic(),
-                "kernel": ("k_stream_collide_wide + %s (one relaxation step)"
-                           % ("k_gram_wide" if prec == lbks.FP64 else "k_gram_tc")) if wide else "k_stream_collide",
+                "traffic": None if (wide or psi_mode) else recorded_traffic(),
+                "kernel": kname,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms,
                 "peak_source": f"hbm_gbs of {peak_kind}"}
 
@@ -543,8 +600,10 @@ def main_lbks(args):
                                  lbks.FP64: "FP64 throughout",
                                  lbks.BF16: "BF16 populations, FP32 collide, FP32 polish below |dE| 1e-4, "
                                             "FP64 overlaps/energies/Poisson"}[prec],
-                   "n_inner": w.n_inner, "e_tol": w.e_tol,
-                   "l2": "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * elem * units / 1e9),
+                   "n_inner": w.n_inner, "e_tol": w.e_tol, "storage": args.storage,
+                   "l2": ("orbital storage: a solve's working set (psi pair, W field, potentials, Poisson vectors) "
+                          "exceeds L2; the kernel timing writes 256 MB before every timed launch") if psi_mode else
+                         "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * elem * units / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "solves_per_s": world * args.steps / (elapsed_ms / 1e3),
         "solve": {"E_total": last["E_total"], "eigenvalues": [float(x) for x in last["eigenvalues"]],

@@ -74,6 +74,22 @@ enum lbks_precision {
                       overlaps, energies, Poisson in double */
 };
 
+/* What a relaxation step stores between steps.
+ * LBKS_STORE_POPULATIONS: the 19 post-collision populations of every orbital
+ *   (Eq. KSLB as written; any omega).
+ * LBKS_STORE_PSI: omega = 1 only.  There the collision forgets the arriving
+ *   populations and every post-collision population is xi_p psi - chi_p dt V psi
+ *   + xi_p u (Sec. 3), a fixed combination of the orbital, the potential and
+ *   the W field at its site.  The step keeps psi alone and applies the same
+ *   pull-and-sum as a 19-point stencil:
+ *     psi'(r) = sigma sum_p [(xi_p - dt chi_p Vc(r - v_p)) psi(r - v_p) + xi_p u(r - v_p)],
+ *   Vc the potential of the collision that produced psi.  Identical results up
+ *   to rounding; 2 orbital arrays instead of 38 population arrays.  FP64 or FP32. */
+enum lbks_storage {
+    LBKS_STORE_POPULATIONS = 0,
+    LBKS_STORE_PSI = 1
+};
+
 /* Solver controls.  lbks_params_default() fills the defaults in brackets. */
 typedef struct lbks_params {
     double omega;        /* BGK relaxation frequency, 0 < omega < 2 [1.0]; Sec. 3, Eq. LBeq */
@@ -92,6 +108,8 @@ typedef struct lbks_params {
                             the bfloat16 noise floor), the populations are widened to FP32 and the
                             solve finishes in FP32, converging only after two FP32 cycles
                             (bfloat16 rounding would otherwise bound the accuracy); <= 0 never [1e-4] */
+    int storage;         /* enum lbks_storage [LBKS_STORE_POPULATIONS]; LBKS_STORE_PSI needs omega = 1
+                            and LBKS_FP64 or LBKS_FP32 */
 } lbks_params;
 
 void lbks_params_default(lbks_params* p);
@@ -327,6 +345,21 @@ int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, do
                             const double* sigma_in_dev, void* f_out_dev, void* psi_out_dev,
                             double* S_out_dev, double* lambda_out_dev, double* sigma_out_dev,
                             void* stream);
+
+/* One relaxation step in orbital storage (LBKS_STORE_PSI, omega = 1; Sec. 3,
+ * Eq. KSLB with the populations written as xi_p psi - chi_p dt Vc psi + xi_p u):
+ *   psi_out_j(r) = sigma_in_j sum_p [(xi_p - dt chi_p Vc(r - v_p)) psi_in_j(r - v_p)
+ *                                    + xi_p u_(j-1)(r - v_p)]   (zero outside the box)
+ * and, as lbks_relax_step, S = h^3 psi_out psi_out^T, lambda_out and sigma_out.
+ * precision: LBKS_FP64 (psi, u double) or LBKS_FP32 (float).  psi_in, psi_out:
+ * n_orb*N values, orbital-major, must not alias.  u_in: (n_orb-1)*N values or
+ * NULL for u = 0.  Vc: N doubles, the potential of the collision that produced
+ * psi_in (zeros when psi_in is a start orbital: f = xi psi has no potential
+ * term).  sigma_in may alias sigma_out.  Asynchronous on stream. */
+int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double dt,
+                        const void* psi_in_dev, const void* u_in_dev, const double* Vc_dev,
+                        const double* sigma_in_dev, void* psi_out_dev, double* S_out_dev,
+                        double* lambda_out_dev, double* sigma_out_dev, void* stream);
 
 /* W field of the orthogonalisation source (Sec. 3, W_jp):
  * u_(j-1)(r) = -omega sum_{k<j} lambda_jk psi_k(r), j = 1..n_orb-1. */

@@ -190,7 +190,9 @@ void jacobi_eigenvalues(int n, std::vector<double> a, double* out) {
 bool valid_params(const lbks_params* p) {
     return p && p->omega > 0.0 && p->omega < 2.0 && p->theta > 0.0 && p->n_inner >= 2 && p->mix > 0.0 &&
            p->mix <= 1.0 && p->e_tol > 0.0 && p->max_cycles >= 1 && ops_for(p->precision) &&
-           p->poisson_rtol > 0.0 && p->poisson_max_iter >= 1;
+           p->poisson_rtol > 0.0 && p->poisson_max_iter >= 1 &&
+           (p->storage == LBKS_STORE_POPULATIONS ||
+            (p->storage == LBKS_STORE_PSI && p->omega == 1.0 && p->precision != LBKS_BF16));
 }
 
 }  // namespace
@@ -210,8 +212,10 @@ struct lbks_system {
     const PrecisionOps* ops;
     size_t N;
     int dev;
-    void* f[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};       // populations; orbital storage: psi ping-pong (psi aliases f[cur])
     void* f_wide[2] = {nullptr, nullptr};  // FP32 populations of the BF16 polish phase
+    bool psi_storage = false;              // lbks_params.storage == LBKS_STORE_PSI
+    double* vprev = nullptr;               // orbital storage: potential of the last collision
     bool polished = false;
     int cur = 0;
     void* u = nullptr;
@@ -382,8 +386,34 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
     return LBKS_OK;
 }
 
+// The same cycle in orbital storage (omega = 1): f[] hold psi; the first step
+// pulls with the previous cycle's collision potential (vprev), later steps
+// with this cycle's (vin); the cycle ends by keeping vin as vprev.
+cudaError_t enqueue_cycle_psi(lbks_system* s, cudaStream_t st, int start) {
+    int cur = start;
+    const int n = s->prm.n_inner, B = s->B;
+    for (int t = 0; t < n; ++t) {
+        RelaxIO io{s->f[cur], t == 0 ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma, s->f[1 - cur],
+                   s->f[1 - cur], s->S, s->lam, s->sigma};
+        const int v = t == n - 1 ? kRelaxExactOverlap : 0;  // the last overlap feeds the Cholesky
+        cudaError_t e = s->ops->relax_psi(s->n_orb, s->g, s->c, io, s->sc, B, v, st);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+        if (t < n - 1) {
+            e = s->ops->w_field(s->n_orb, s->g, s->prm.omega, s->f[cur], s->lam, s->u, B, st);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    cudaError_t e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, s->active, B, st);
+    if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->g, s->Linv, nullptr, s->f[cur], B, st);
+    if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * B, 1.0, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->vprev, s->vin, sizeof(double) * s->N * B, cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
 // n_inner - 1 steps of Eq. KSLB and one orthonormalising step, starting from f[start].
 cudaError_t enqueue_cycle(lbks_system* s, cudaStream_t st, int start) {
+    if (s->psi_storage) return enqueue_cycle_psi(s, st, start);
     int cur = start;
     const int n = s->prm.n_inner, B = s->B;
     for (int t = 0; t < n; ++t) {
@@ -472,6 +502,7 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
         count_launches(s->graph_nodes[s->cur]);
         s->cur ^= (s->prm.n_inner & 1);
+        if (s->psi_storage) s->psi = s->f[s->cur];
         rc = evaluate(s, st, 0);
         if (rc != LBKS_OK) return rc;
         // A BF16 handle with a polish phase converges only in FP32, and only
@@ -563,7 +594,7 @@ int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) 
 // sigma are all rewritten afterwards).  A few launches, once per shape.
 int tune_relax(lbks_system* s) {
     const int mode = g_variant_mode.load();
-    if (s->n_orb > kMaxOrb) {
+    if (s->n_orb > kMaxOrb || s->psi_storage) {
         s->variant = kRelaxSites;
         return LBKS_OK;
     }
@@ -668,11 +699,15 @@ int initialise(lbks_system* s) {
     int trc = tune_relax(s);
     if (trc != LBKS_OK) return trc;
     if (e == cudaSuccess) e = launch_vext(s->g, s->h, s->counts, s->atoms, s->a, s->vext, B, st);
+    if (s->psi_storage) {  // orbitals in f[0]; the start f = xi psi has no potential term: vprev = 0
+        s->psi = s->f[0];
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->vprev, 0, sizeof(double) * s->N * B, st);
+    }
     if (e == cudaSuccess) e = s->ops->init_orbitals(s->n_orb, s->g, s->h, s->starts, s->psi, B, st);
     if (e == cudaSuccess) e = s->ops->gram(s->n_orb, s->g, s->h, s->psi, s->S, s->sc, B, st);
     if (e == cudaSuccess) e = launch_cholesky(s->n_orb, s->S, s->Linv, s->status, s->active, B, st);
     if (e == cudaSuccess) e = s->ops->orth_apply(s->n_orb, s->g, s->Linv, nullptr, s->psi, B, st);
-    if (e == cudaSuccess) e = s->ops->equilibrium(s->n_orb, s->g, s->c, s->psi, s->f[0], B, st);
+    if (e == cudaSuccess && !s->psi_storage) e = s->ops->equilibrium(s->n_orb, s->g, s->c, s->psi, s->f[0], B, st);
     if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * B, 1.0, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vh, 0, sizeof(double) * s->N * B, st);
     if (e != cudaSuccess) return cuda_fail(e, "initialise orbitals");
@@ -708,8 +743,9 @@ void free_system(lbks_system* s) {
         if (s->f_wide[k]) cudaFree(s->f_wide[k]);
     }
     if (s->poisson_graph) cudaGraphExecDestroy(s->poisson_graph);
+    if (s->psi_storage) s->psi = nullptr;  // an alias of f[cur]
     void* ptrs[] = {s->u,   s->psi,   s->vin,    s->vout,          s->vext,          s->vh, s->rho, s->pvec,
-                    s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter};
+                    s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter, s->vprev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->host) cudaFreeHost(s->host);
@@ -721,8 +757,10 @@ void free_system(lbks_system* s) {
 size_t bytes_of(const lbks_params* p, int nx, int ny, int nz, int n_orb, int B) {
     const size_t N = (size_t)nx * ny * nz;
     const size_t e = ops_for(p->precision)->elem, ep = ops_for(p->precision)->psi_elem;
-    const size_t per = e * N * (size_t)n_orb * 19 * 2 + ep * N * ((size_t)std::max(1, n_orb - 1) + n_orb) +
-                       sizeof(double) * N * 11 + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
+    const bool psi = p->storage == LBKS_STORE_PSI;  // f[] hold psi, no separate psi array, one more field
+    const size_t per = (psi ? ep * N * (size_t)n_orb * 2 : e * N * (size_t)n_orb * 19 * 2) +
+                       ep * N * ((size_t)std::max(1, n_orb - 1) + (psi ? 0 : n_orb)) +
+                       sizeof(double) * N * (psi ? 12 : 11) + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
                        sizeof(double) * ((size_t)num_sms() * 8 * scratch_vals(n_orb) + small_per_sys(n_orb) +
                                          4 * kMaxAtoms) +
                        ((p->precision == LBKS_BF16 && p->polish_tol > 0.0) ? sizeof(float) * N * n_orb * 19 * 2 : 0);
@@ -762,14 +800,17 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     auto A = [&](void** ptr, size_t bytes) {
         if (err == cudaSuccess) err = cudaMalloc(ptr, bytes);
     };
-    A(&s->f[0], e * NB * 19 * n_orb);
-    A(&s->f[1], e * NB * 19 * n_orb);
+    s->psi_storage = p->storage == LBKS_STORE_PSI;
+    const size_t fbytes = s->psi_storage ? ep * NB * n_orb : e * NB * 19 * n_orb;
+    A(&s->f[0], fbytes);
+    A(&s->f[1], fbytes);
+    if (s->psi_storage) A((void**)&s->vprev, 8 * NB);
     if (p->precision == LBKS_BF16 && p->polish_tol > 0.0) {
         A(&s->f_wide[0], sizeof(float) * NB * 19 * n_orb);
         A(&s->f_wide[1], sizeof(float) * NB * 19 * n_orb);
     }
     A(&s->u, ep * NB * std::max(1, n_orb - 1));
-    A(&s->psi, ep * NB * n_orb);
+    if (!s->psi_storage) A(&s->psi, ep * NB * n_orb);
     A((void**)&s->vin, 8 * NB);
     A((void**)&s->vout, 8 * NB);
     A((void**)&s->vext, 8 * NB);
@@ -867,6 +908,7 @@ void lbks_params_default(lbks_params* p) {
     p->poisson_rtol = 1e-11;
     p->poisson_max_iter = 20000;
     p->polish_tol = 1e-4;
+    p->storage = LBKS_STORE_POPULATIONS;
 }
 
 int lbks_last_error(char* buf, size_t cap) {
@@ -1018,6 +1060,28 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h, 
     cudaError_t e = ops->relax(n_orb, make_grid(nx, ny, nz), make_coef(omega, theta, dt, h), io, w->sc, 1,
                                variant_for(precision, n_orb, omega, nx, ny, nz), (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step");
+}
+
+int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double dt,
+                        const void* psi_in, const void* u_in, const double* Vc, const double* sigma_in,
+                        void* psi_out, double* S_out, double* lambda_out, double* sigma_out, void* stream) {
+    if (precision != LBKS_FP64 && precision != LBKS_FP32)
+        return fail(LBKS_EINVAL, "orbital storage needs LBKS_FP64 or LBKS_FP32");
+    const PrecisionOps* ops = ops_for(precision);
+    if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= (1ull << 31))
+        return fail(LBKS_EINVAL, "bad grid %d x %d x %d", nx, ny, nz);
+    if (n_orb < 1 || n_orb > kMaxOrbWide) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrbWide);
+    if (!psi_in || !Vc || !sigma_in || !psi_out || !S_out || !lambda_out || !sigma_out)
+        return fail(LBKS_EINVAL, "null device pointer");
+    if (psi_in == psi_out) return fail(LBKS_EINVAL, "psi_in and psi_out must not alias");
+    if (!(h > 0.0) || !(theta > 0.0)) return fail(LBKS_EINVAL, "bad h or theta");
+    Workspace* w = nullptr;
+    int rc = workspace(stream, 0, &w);
+    if (rc != LBKS_OK) return rc;
+    RelaxIO io{psi_in, u_in, Vc, sigma_in, psi_out, psi_out, S_out, lambda_out, sigma_out};
+    cudaError_t e = ops->relax_psi(n_orb, make_grid(nx, ny, nz), make_coef(1.0, theta, dt, h), io, w->sc, 1, 0,
+                                   (cudaStream_t)stream);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step_psi");
 }
 
 int lbks_overlap(int precision, size_t n_sites, int n_orb, double h, const void* psi, double* S, int tensor_cores,

@@ -142,6 +142,10 @@ struct OrbitalStart {  // Gaussian start of one orbital
 struct PrecisionOps {
     cudaError_t (*relax)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int B, int variant,
                          cudaStream_t);
+    // omega = 1 only: the step in orbital storage (f_in / f_out hold psi in the
+    // compute type, V is the potential of the collision that produced f_in)
+    cudaError_t (*relax_psi)(int n_orb, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int B,
+                             int variant, cudaStream_t);
     cudaError_t (*w_field)(int n_orb, const Grid&, double omega, const void* psi, const double* lam, void* u, int B,
                            cudaStream_t);
     cudaError_t (*orth_apply)(int n_orb, const Grid&, const double* Linv, void* f, void* psi, int B, cudaStream_t);

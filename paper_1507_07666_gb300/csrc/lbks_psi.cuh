@@ -1,0 +1,163 @@
+// Relaxation in orbital storage at omega = 1 (tau = 1 of the paper's runs).
+//
+// At omega = 1 the collision forgets the arriving populations: the
+// post-collision state of Eq. KSLB is f*_p(r) = xi_p A(r) - chi_p B(r) +
+// xi_p u(r), with A = psi (this step's normalised orbital), B = dt V psi and
+// u the W field.  Every stored population is a fixed combination of three
+// site fields, so the next step's pull-and-sum collapses to a 19-point
+// stencil on psi:
+//
+//   psi'(r) = sigma * sum_p [ (xi_p - dt chi_p Vc(r - v_p)) psi(r - v_p) + xi_p u(r - v_p) ],
+//
+// zero outside the box, where Vc is the potential of the collision that
+// produced psi (the previous step's; zero for the start f = xi psi).  The
+// populations never exist in memory: a step reads psi, u and Vc and writes
+// psi' -- about 12 bytes of HBM traffic per orbital-site instead of 152.
+// The same normalisation, overlap, Lambda and W field follow as in the
+// population kernels.  Included by the lbks_relax_<precision>_psi.cu units.
+#pragma once
+
+#include "lbks_relax.cuh"
+
+namespace lbks {
+
+// out_j = sum_p [ (xi_p - dt chi_p Vc(r - v_p)) psi_j(r - v_p) + xi_p u_j(r - v_p) ]
+// for the J orbitals j0 .. j0 + J - 1 of one site (terms outside the box are
+// zero).  Velocities outermost: one source index and one weight live at a
+// time, the J orbital loads of a velocity are independent.
+// psi: orbital j0's array, u: the W field of orbital j0 (or nullptr when j0 has
+// none, i.e. j0 == 0 or no W field); orbitals are N apart in both.
+template <typename T, int J>
+__device__ __forceinline__ void psi_stencil(const Grid& g, const Site& t, uint32_t s, const double* __restrict__ Vc,
+                                            const T* __restrict__ psi, const T* __restrict__ u0,
+                                            const T* __restrict__ u1, size_t N, const T (&xi)[3],
+                                            const T (&chi)[3], T dt, T (&out)[J]) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) out[j] = T(0);
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        if (!has_source(t, p)) continue;
+        const uint32_t src = source_index(g, s, p);
+        const T a = xi[vclass(p)] - dt * chi[vclass(p)] * (T)__ldg(Vc + src);
+#pragma unroll
+        for (int j = 0; j < J; ++j) out[j] += a * __ldg(psi + (size_t)j * N + src);
+        // W field: orbital j0 takes u0 (may be null), orbitals j0 + 1 .. take u1 + (j - 1) N
+        if (u0) out[0] += xi[vclass(p)] * __ldg(u0 + src);
+        if (u1) {
+#pragma unroll
+            for (int j = 1; j < J; ++j) out[j] += xi[vclass(p)] * __ldg(u1 + (size_t)(j - 1) * N + src);
+        }
+    }
+}
+
+// Up to kMaxOrb orbitals: one site per thread, all orbitals, overlap partials
+// fused (as k_stream_collide); the last block writes S, Lambda and sigma.
+// io.f_in / io.f_out: psi in / out ([sys][j][z][y][x], T); io.V: Vc.
+// Resident blocks per SM the register allocator must allow: the unrolled
+// stencil keeps the loads of several velocities of every orbital in flight.
+template <typename T, int NO>
+constexpr int psi_min_blocks() {
+    return NO <= 2 ? 4 : (NO <= 5 && sizeof(T) == 4) ? 3 : 2;
+}
+
+template <typename T, int NO, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi(Grid g, Coef c, RelaxIO io,
+                                                                                    Scratch sc) {
+    constexpr int NP = NO * (NO + 1) / 2;
+    if (BATCHED && inactive(g)) return;
+    const uint32_t N = g.N;
+    const size_t y = BATCHED ? sys_id() : 0;
+    const T* __restrict__ pin = static_cast<const T*>(io.f_in);
+    const T* __restrict__ uin = static_cast<const T*>(io.u_in);
+    T* __restrict__ pout = static_cast<T*>(io.f_out);
+    T sig[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[y * NO + j];
+    const T dt = (T)c.dt;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    T acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = T(0);
+
+    // the W field of orbitals 1 .. NO-1 (orbital 0 has none)
+    const T* u1 = (NO > 1 && uin != nullptr) ? uin + y * (NO > 1 ? NO - 1 : 1) * N : nullptr;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
+        const Site t = decode(g, s);
+        T ps[NO];
+        psi_stencil<T, NO>(g, t, s, io.V + y * N, pin + y * NO * N, nullptr, u1, N, xi, chi, dt, ps);
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+            ps[j] *= sig[j];
+            pout[(y * NO + j) * N + s] = ps[j];
+        }
+#pragma unroll
+        for (int j = 0; j < NO; ++j)
+#pragma unroll
+            for (int i = 0; i <= j; ++i) acc[tri(j, i)] += ps[j] * ps[i];
+    }
+    double v[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v[k] = (double)acc[k];
+    double* partial = sc.partial + y * sc.max_blocks * sc.max_vals;
+    block_sum_store<NP>(v, partial + (size_t)blockIdx.x * NP);
+    __shared__ double tot[NP];
+    if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0)
+        store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
+}
+
+// More than kMaxOrb orbitals: one (site, orbital) per thread, blockIdx.y =
+// system * N_O + orbital; the overlap follows in its own kernel.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 4) k_relax_psi_wide(Grid g, Coef c, RelaxIO io, int NO) {
+    const int y = (int)blockIdx.y / NO, j = (int)blockIdx.y - y * NO;
+    if (g.active && !g.active[y]) return;
+    const uint32_t N = g.N;
+    const uint32_t s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= N) return;
+    const size_t oj = (size_t)y * NO + j;
+    const T dt = (T)c.dt;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    const Site t = decode(g, s);
+    const T* uj = (j > 0 && io.u_in != nullptr)
+                      ? static_cast<const T*>(io.u_in) + ((size_t)y * (NO - 1) + j - 1) * N
+                      : nullptr;
+    T ps[1];
+    psi_stencil<T, 1>(g, t, s, io.V + (size_t)y * N, static_cast<const T*>(io.f_in) + oj * N, uj, nullptr, N, xi,
+                      chi, dt, ps);
+    static_cast<T*>(io.f_out)[oj * N + s] = (T)io.sigma_in[oj] * ps[0];
+}
+
+template <typename T, int NO, bool BATCHED>
+cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                               cudaStream_t st) {
+    auto kern = k_relax_psi<T, NO, BATCHED>;
+    static const int nb = blocks_per_sm(kern);
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    kern<<<batch_grid(g.N, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                             cudaStream_t st) {
+    if (NO > kMaxOrb) {
+        if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
+        k_relax_psi_wide<T><<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io,
+                                                                                                           NO);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    const bool b = B > 1;
+    switch (NO) {
+#define LBKS_CASE(n) \
+    case n: return b ? launch_relax_psi_n<T, n, true>(g, c, io, sc, B, st) : launch_relax_psi_n<T, n, false>(g, c, io, sc, B, st);
+        LBKS_CASE(1) LBKS_CASE(2) LBKS_CASE(3) LBKS_CASE(4) LBKS_CASE(5) LBKS_CASE(6) LBKS_CASE(7) LBKS_CASE(8)
+#undef LBKS_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbks

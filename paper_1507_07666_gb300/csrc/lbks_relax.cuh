@@ -526,6 +526,12 @@ cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, c
 template <typename TS, typename T>
 cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
                                   const Scratch& sc, int B, cudaStream_t st);
+// Orbital-storage relaxation at omega = 1 (lbks_psi.cuh; io.f_in / f_out hold
+// psi, io.V the potential of the collision that produced psi), compiled in
+// lbks_relax_<precision>_psi.cu.
+template <typename T>
+cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                             cudaStream_t st);
 
 template <typename TS, typename T>
 struct Ops {
@@ -766,8 +772,15 @@ struct Ops {
     }
 #undef LBKS_SWITCH_NO
 
+    static cudaError_t relax_psi(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc,
+                                 int B, int variant, cudaStream_t st) {
+        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, st);
+        if (e != cudaSuccess || n_orb <= kMaxOrb) return e;  // up to kMaxOrb: overlap fused
+        return gram_wide<true>(n_orb, g, c.h, io.f_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
+                               (variant & kRelaxExactOverlap) != 0);
+    }
     static const PrecisionOps& table() {
-        static const PrecisionOps t = {&relax,   &w_field, &orth_apply,    &gram,      &init_orbitals,
+        static const PrecisionOps t = {&relax,   &relax_psi, &w_field, &orth_apply,    &gram,      &init_orbitals,
                                        &equilibrium, &density, &energy_matrix, sizeof(TS), sizeof(T)};
         return t;
     }

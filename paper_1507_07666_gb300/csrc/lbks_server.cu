@@ -34,7 +34,7 @@ struct Job {
     Clock::time_point t_submit, t_start, t_end;
 };
 
-using ShapeKey = std::tuple<int, int, int, int, int, int, double, double, double, long long>;
+using ShapeKey = std::tuple<int, int, int, int, int, int, double, double, double, long long, int>;
 
 }  // namespace
 
@@ -60,7 +60,7 @@ namespace {
 
 ShapeKey key_of(const lbks_params& p, const lbks_request& r) {
     return ShapeKey(r.nx, r.ny, r.nz, r.n_orb, p.precision, p.n_inner, r.h, p.theta, p.omega,
-                    (long long)(p.e_tol * 1e15));
+                    (long long)(p.e_tol * 1e15), p.storage);
 }
 
 lbks_params params_of(const lbks_server* s, const lbks_request& r) {

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "liblbks.so")
 MAX_ORB = 64
 OK, EINVAL, ENOMEM, ENOTCONV, ETIMEDOUT, EBUSY, ECUDA, ENOTFOUND = range(8)
 FP64, FP32, BF16 = 0, 1, 2
+STORE_POPULATIONS, STORE_PSI = 0, 1
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with paper_1507_07666_gb300.build.build()")
@@ -35,7 +36,7 @@ class lbks_params(ctypes.Structure):
                 ("mix", ctypes.c_double), ("e_tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("softening", ctypes.c_double),
                 ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
-                ("polish_tol", ctypes.c_double)]
+                ("polish_tol", ctypes.c_double), ("storage", ctypes.c_int)]
 
 
 class lbks_result(ctypes.Structure):
@@ -101,6 +102,7 @@ _SIGS = {
     "lbks_server_get_stats": (_i, [_vp, ctypes.POINTER(lbks_server_stats)]),
     "lbks_relax_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                              _vp]),
+    "lbks_relax_step_psi": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lbks_relax_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp]),
     "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
@@ -258,6 +260,17 @@ def lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_i
                                 _ptr(sigma_in, torch.float64), _ptr(f_out, T), _ptr(psi_out, P),
                                 _ptr(S_out, torch.float64), _ptr(lambda_out, torch.float64),
                                 _ptr(sigma_out, torch.float64), _stream(stream)))
+
+
+def lbks_relax_step_psi(precision, nx, ny, nz, n_orb, h, theta, dt, psi_in, u_in, Vc, sigma_in, psi_out, S_out,
+                        lambda_out, sigma_out, stream=None):
+    import torch
+    P = _psitype(precision)
+    _check(_lib.lbks_relax_step_psi(precision, nx, ny, nz, n_orb, h, theta, dt, _ptr(psi_in, P),
+                                    _ptr(u_in, P, optional=True), _ptr(Vc, torch.float64),
+                                    _ptr(sigma_in, torch.float64), _ptr(psi_out, P), _ptr(S_out, torch.float64),
+                                    _ptr(lambda_out, torch.float64), _ptr(sigma_out, torch.float64),
+                                    _stream(stream)))
 
 
 def lbks_relax_step_noalloc(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_in, V, sigma_in, f_out,

@@ -1,0 +1,135 @@
+"""Orbital storage at omega = 1 (LBKS_STORE_PSI): the step keeps psi alone and
+applies the pull-and-sum of Eq. KSLB as a 19-point stencil.  Its results must
+equal the oracle's population step fed the populations that the psi state
+stands for, f*_p = xi_p psi - dt chi_p Vc psi + xi_p u, element by element,
+and an orbital-storage SCF must follow the oracle's trajectory."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import lattice, lb, scf
+
+from gpu_util import rel_err, require_gpu, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 2e-5}
+
+
+def _populations(A, u, Vc, theta, dt):
+    """The post-collision populations the psi-state (A, Vc, u) stands for."""
+    xi = lattice.xi(theta)[None, :, None, None, None]
+    chi = lattice.chi()[None, :, None, None, None]
+    f = xi * A[:, None] - dt * chi * (Vc[None, None] * A[:, None])
+    if A.shape[0] > 1:
+        f[1:] += xi * u[:, None]
+    return f
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("n,n_orb,seed", [
+    ((7, 9, 11), 1, 0), ((33, 20, 17), 5, 1), ((16, 5, 40), 8, 2), ((2, 3, 2), 3, 3),
+    ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5),
+])
+def test_psi_step_matches_population_oracle(prec, n, n_orb, seed):
+    torch, lbks = require_gpu()
+    theta, h = 0.5, 0.3
+    dt = lattice.time_step(theta, 1.0, h)
+    nx, ny, nz = n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    A = rng.uniform(-0.5, 1.0, size=(n_orb, nz, ny, nx))
+    Vc = rng.uniform(-3.0, 1.0, size=(nz, ny, nx))
+    u = rng.uniform(-0.2, 0.2, size=(max(n_orb - 1, 1), nz, ny, nx))
+    sigma = rng.uniform(0.5, 2.0, size=n_orb)
+    if prec == 1:  # the oracle sees the values the GPU stores
+        A, u = A.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+    P = torch.float64 if prec == 0 else torch.float32
+    psi_in = to_dev(torch, A, P)
+    u_in = to_dev(torch, u, P) if n_orb > 1 else None
+    psi_out = torch.empty_like(psi_in)
+    S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
+    lam, sig_out = torch.empty_like(S), torch.empty(n_orb, dtype=torch.float64, device="cuda")
+    lbks.lbks_relax_step_psi(prec, nx, ny, nz, n_orb, h, theta, dt, psi_in, u_in, to_dev(torch, Vc, torch.float64),
+                             to_dev(torch, sigma, torch.float64), psi_out, S, lam, sig_out)
+    torch.cuda.synchronize()
+    ref = lb.step(_populations(A, u, Vc, theta, dt), sigma, np.zeros_like(Vc), 1.0, theta, dt, h)
+    tol = TOL[prec]
+    assert rel_err(to_np(psi_out), ref["psi"]) < tol
+    # more than 8 FP32 orbitals: the per-step overlap runs on the tensor cores (~1e-6 relative)
+    stol = 1e-5 if (prec == 1 and n_orb > 8) else tol
+    assert rel_err(to_np(S), ref["S"]) < stol
+    np.testing.assert_allclose(to_np(sig_out), ref["sigma"], rtol=stol)
+    np.testing.assert_allclose(to_np(lam), ref["lam"], atol=stol * max(1.0, np.abs(ref["lam"]).max()))
+
+
+def test_psi_step_rejects_bad_arguments():
+    torch, lbks = require_gpu()
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    xf = torch.zeros(64, dtype=torch.float32, device="cuda")
+    with pytest.raises(lbks.LbksError):  # bfloat16 has no orbital storage
+        lbks.lbks_relax_step_psi(2, 2, 2, 2, 1, 0.2, 0.5, 0.02, xf, None, x[:8], x[:1], xf.clone(), x[:1], x[:1],
+                                 x[:1])
+    with pytest.raises(lbks.LbksError):  # in and out alias
+        lbks.lbks_relax_step_psi(0, 2, 2, 2, 1, 0.2, 0.5, 0.02, x, None, x[:8], x[:1], x, x[:1], x[:1], x[:1])
+    with pytest.raises(lbks.LbksError):  # omega != 1
+        lbks.System((8, 8, 8), 0.4, 1, storage=lbks.STORE_PSI, omega=0.9)
+    with pytest.raises(lbks.LbksError):
+        lbks.System((8, 8, 8), 0.4, 1, storage=lbks.STORE_PSI, precision=lbks.BF16)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["ch4", "water_dimer"])
+def test_psi_storage_scf_follows_the_oracle(prec, case):
+    """Three fixed cycles from the Gaussian start: the first step pulls with no
+    potential term (the start is f = xi psi), every cycle's first step with
+    the previous cycle's collision potential."""
+    torch, lbks = require_gpu()
+    if case == "ch4":
+        mol, n, h, n_orb, n_inner = W.methane(), (30, 28, 26), 0.45, 5, 12
+    else:
+        mol = W.water_cluster(2, seed=3, box=11.0, min_oo=5.0, margin=2.5)
+        n, h, n_orb, n_inner = (36, 32, 34), 0.35, 10, 15
+    st, ref = scf.scf(n, h, mol.xyz, mol.Z, n_orb, n_inner=n_inner, poisson_rtol=1e-12, fixed_cycles=3)
+    s = lbks.System(n, h, n_orb, precision=prec, n_inner=n_inner, poisson_rtol=1e-12, storage=lbks.STORE_PSI)
+    s.set_geometry(mol.xyz, mol.Z)
+    g = s.scf_cycles(3)
+    etol = 1e-8 if prec == 0 else 1e-5
+    assert abs(g["E_total"] - ref["E_total"]) <= etol, (g["E_total"], ref["E_total"])
+    np.testing.assert_allclose(np.sort(g["eigenvalues"][:n_orb]), np.sort(ref["eigenvalues"]), atol=etol)
+    rho = s.density()
+    assert np.linalg.norm(rho - st.rho) / np.linalg.norm(st.rho) <= (1e-8 if prec == 0 else 1e-5)
+    s.close()
+
+
+def test_psi_and_population_storage_converge_alike():
+    """Full FP64 solves in the two storages stop at the same cycle with the
+    same energy (the two differ only in rounding)."""
+    torch, lbks = require_gpu()
+    mol, n, h = W.water(1.8, 104.0), (30, 26, 28), 0.4
+    out = []
+    for storage in (lbks.STORE_POPULATIONS, lbks.STORE_PSI):
+        s = lbks.System(n, h, 5, precision=0, n_inner=20, storage=storage)
+        s.set_geometry(mol.xyz, mol.Z)
+        out.append(s.scf())
+        s.close()
+    a, b = out
+    assert a["converged"] and b["converged"] and a["cycles"] == b["cycles"]
+    assert abs(a["E_total"] - b["E_total"]) <= 1e-10
+    np.testing.assert_allclose(a["eigenvalues"][:5], b["eigenvalues"][:5], atol=1e-10)
+
+
+def test_psi_storage_batch_matches_single():
+    torch, lbks = require_gpu()
+    n, h = (28, 26, 30), 0.4
+    mols = W.water_scan(3, 2)
+    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=20, storage=lbks.STORE_PSI)
+    b.set_geometries([(m.xyz, m.Z) for m in mols])
+    res = b.scf()
+    for i, m in enumerate(mols):
+        s = lbks.System(n, h, 5, precision=0, n_inner=20, storage=lbks.STORE_PSI)
+        s.set_geometry(m.xyz, m.Z)
+        ref = s.scf()
+        assert res[i]["converged"] and res[i]["cycles"] == ref["cycles"]
+        assert abs(res[i]["E_total"] - ref["E_total"]) <= 1e-9
+        s.close()
+    b.close()
