@@ -209,6 +209,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def job_totals(dist, device, updates, seconds):
+    """Replicas (one independent solve per rank, no collective on the data
+    path): the whole job's orbital-site updates and the slowest rank's time.
+    dist: torch.distributed or None."""
+    if dist is None:
+        return float(updates), float(seconds)
+    import torch
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def measured_hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -240,10 +254,10 @@ def time_relax_psi(torch, lbks, w, prec, stream, launches=20):
     with torch.cuda.stream(stream):
         pa = torch.rand((no, nz, ny, nx), dtype=P, device="cuda")
         pb = torch.empty_like(pa)
-        u = torch.rand((max(no - 1, 1), nz, ny, nx), dtype=P, device="cuda") * 0.1
         V = -torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda")
         sig = torch.full((no,), 1e-3, dtype=torch.float64, device="cuda")
         S = torch.empty((no, no), dtype=torch.float64, device="cuda")
+        lam_in = torch.tril(torch.rand((no, no), dtype=torch.float64, device="cuda"), -1) * 0.01
         lam = torch.empty_like(S)
         sig2 = torch.empty_like(sig)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -256,13 +270,13 @@ def time_relax_psi(torch, lbks, w, prec, stream, launches=20):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))  # the working set can fit in L2: evict it before every timed launch
             evs[2 * (i - 3)].record(stream)
-        lbks.lbks_relax_step_psi(prec, nx, ny, nz, no, w.h, w.theta, dt, src, u if no > 1 else None, V, sig, dst, S,
-                                 lam, sig2, stream=stream)
+        lbks.lbks_relax_step_psi(prec, nx, ny, nz, no, w.h, w.theta, dt, src, lam_in, V, sig, dst, S, lam, sig2,
+                                 stream=stream)
         if i >= 3:
             evs[2 * (i - 3) + 1].record(stream)
     stream.synchronize()
     ms = [evs[2 * k].elapsed_time(evs[2 * k + 1]) for k in range(launches)]
-    del pa, pb, u, V, flush
+    del pa, pb, V, flush
     return statistics.mean(ms), N * no
 
 
@@ -338,6 +352,17 @@ def main_kernel_only(args):
                           "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision, "ms_per_launch": ms,
                           "algorithmic_GBps": units * esz / (ms / 1e3) / 1e9, "launches": args.launches}),
               flush=True)
+        return 0
+    if args.storage == "psi":
+        ms, units = time_relax_psi(torch, lbks, w, prec, stream, launches=args.launches)
+        pe = 8 if prec == lbks.FP64 else 4
+        N = units // w.n_orb
+        wide = w.n_orb > 8
+        nbytes = (pe * (2 * w.n_orb + (3 * w.n_orb - 2 if wide else 0)) + 8) * N
+        print(json.dumps({"kernel": "k_relax_psi_wide + overlap" if wide else "k_relax_psi", "grid": list(w.n),
+                          "n_orb": w.n_orb, "dtype": args.precision, "ms_per_launch": ms,
+                          "algorithmic_GBps": nbytes / (ms / 1e3) / 1e9,
+                          "orbital_site_updates_per_s": units / (ms / 1e3), "launches": args.launches}), flush=True)
         return 0
     ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
@@ -534,13 +559,10 @@ def main_lbks(args):
         dist.barrier()
     clk = clocks.stop()
     launches = lbks.lbks_kernel_launches() - l0
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    updates = sum(r["steps"] for r in results) * w.n_orb * N
-    value = world * updates / (elapsed_ms / 1e3) / 1e9
+    updates, elapsed_s = job_totals(dist, "cuda", sum(r["steps"] for r in results) * w.n_orb * N,
+                                    ev0.elapsed_time(ev1) / 1e3)
+    elapsed_ms = 1e3 * elapsed_s
+    value = updates / elapsed_s / 1e9
 
     # end to end: host geometry in, energies + density back to the host
     e2e_updates, t_e2e = 0, 0.0
@@ -551,7 +573,8 @@ def main_lbks(args):
         rho = sysm.density()
         t_e2e += time.perf_counter() - t0
         e2e_updates += r["steps"] * w.n_orb * N
-    e2e = {"value": world * e2e_updates / t_e2e / 1e9, "unit": UNIT,
+    e2e_updates, t_e2e = job_totals(dist, "cuda", e2e_updates, t_e2e)
+    e2e = {"value": e2e_updates / t_e2e / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": int(xyz.nbytes + Z.nbytes),
            "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
 
@@ -564,13 +587,13 @@ def main_lbks(args):
     psi_elem = 8 if prec == lbks.FP64 else 4
     gram_name = "k_gram_wide" if prec == lbks.FP64 else "k_gram_tc"
     if psi_mode:
-        # orbital storage: psi in and out, the W field of orbitals 1.., the
-        # collision potential once per site (more than eight orbitals: plus the
-        # overlap kernel's read of psi)
+        # orbital storage: psi in and out and the collision potential once per
+        # site; more than eight orbitals: the W field written and read and the
+        # overlap kernel's read of psi too (the W-field kernel is timed with it)
         ms, units = time_relax_psi(torch, lbks, w, prec, stream)
         N = units // w.n_orb
-        bytes_per_launch = (psi_elem * (2 * w.n_orb + (w.n_orb - 1) + (w.n_orb if wide else 0)) + 8) * N
-        kname = ("k_relax_psi_wide + %s (one relaxation step)" % gram_name) if wide else "k_relax_psi"
+        bytes_per_launch = (psi_elem * (2 * w.n_orb + (3 * w.n_orb - 2 if wide else 0)) + 8) * N
+        kname = ("k_w_field_wide + k_relax_psi_wide + %s (one relaxation step)" % gram_name) if wide else "k_relax_psi"
     else:
         ms, units = time_stream_collide(torch, lbks, w, prec, stream)
         # more than eight orbitals: the timed step is two kernels, stream-collide

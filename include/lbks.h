@@ -349,15 +349,19 @@ int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, do
 /* One relaxation step in orbital storage (LBKS_STORE_PSI, omega = 1; Sec. 3,
  * Eq. KSLB with the populations written as xi_p psi - chi_p dt Vc psi + xi_p u):
  *   psi_out_j(r) = sigma_in_j sum_p [(xi_p - dt chi_p Vc(r - v_p)) psi_in_j(r - v_p)
- *                                    + xi_p u_(j-1)(r - v_p)]   (zero outside the box)
+ *                                    + xi_p u_j(r - v_p)],   zero outside the box,
+ *   u_j = -sum_{k<j} lambda_in_jk psi_in_k   (the W source; omega = 1),
  * and, as lbks_relax_step, S = h^3 psi_out psi_out^T, lambda_out and sigma_out.
- * precision: LBKS_FP64 (psi, u double) or LBKS_FP32 (float).  psi_in, psi_out:
- * n_orb*N values, orbital-major, must not alias.  u_in: (n_orb-1)*N values or
- * NULL for u = 0.  Vc: N doubles, the potential of the collision that produced
- * psi_in (zeros when psi_in is a start orbital: f = xi psi has no potential
- * term).  sigma_in may alias sigma_out.  Asynchronous on stream. */
+ * precision: LBKS_FP64 (psi double) or LBKS_FP32 (float).  psi_in, psi_out:
+ * n_orb*N values, orbital-major, must not alias.  lambda_in: n_orb^2 doubles
+ * (strictly lower part used; may alias lambda_out) or NULL for no W source.
+ * Vc: N doubles, the potential of the collision that produced psi_in (zeros
+ * when psi_in is a start orbital: f = xi psi has no potential term).
+ * sigma_in may alias sigma_out.  Up to 8 orbitals the W source is formed
+ * inside the step; more orbitals use library-managed scratch for u.
+ * Asynchronous on stream. */
 int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double dt,
-                        const void* psi_in_dev, const void* u_in_dev, const double* Vc_dev,
+                        const void* psi_in_dev, const double* lambda_in_dev, const double* Vc_dev,
                         const double* sigma_in_dev, void* psi_out_dev, double* S_out_dev,
                         double* lambda_out_dev, double* sigma_out_dev, void* stream);
 

@@ -392,14 +392,17 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
 cudaError_t enqueue_cycle_psi(lbks_system* s, cudaStream_t st, int start) {
     int cur = start;
     const int n = s->prm.n_inner, B = s->B;
+    // up to kMaxOrb orbitals the kernel forms the W source from Lambda itself;
+    // wider sets pull it from the W field u
+    const bool fused_w = s->n_orb <= kMaxOrb;
     for (int t = 0; t < n; ++t) {
-        RelaxIO io{s->f[cur], t == 0 ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma, s->f[1 - cur],
-                   s->f[1 - cur], s->S, s->lam, s->sigma};
+        RelaxIO io{s->f[cur], (t == 0 || fused_w) ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma,
+                   s->f[1 - cur], s->f[1 - cur], s->S, s->lam, s->sigma, (t == 0 || !fused_w) ? nullptr : s->lam};
         const int v = t == n - 1 ? kRelaxExactOverlap : 0;  // the last overlap feeds the Cholesky
         cudaError_t e = s->ops->relax_psi(s->n_orb, s->g, s->c, io, s->sc, B, v, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
-        if (t < n - 1) {
+        if (t < n - 1 && !fused_w) {
             e = s->ops->w_field(s->n_orb, s->g, s->prm.omega, s->f[cur], s->lam, s->u, B, st);
             if (e != cudaSuccess) return e;
         }
@@ -1063,7 +1066,7 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h, 
 }
 
 int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double dt,
-                        const void* psi_in, const void* u_in, const double* Vc, const double* sigma_in,
+                        const void* psi_in, const double* lambda_in, const double* Vc, const double* sigma_in,
                         void* psi_out, double* S_out, double* lambda_out, double* sigma_out, void* stream) {
     if (precision != LBKS_FP64 && precision != LBKS_FP32)
         return fail(LBKS_EINVAL, "orbital storage needs LBKS_FP64 or LBKS_FP32");
@@ -1075,12 +1078,18 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
         return fail(LBKS_EINVAL, "null device pointer");
     if (psi_in == psi_out) return fail(LBKS_EINVAL, "psi_in and psi_out must not alias");
     if (!(h > 0.0) || !(theta > 0.0)) return fail(LBKS_EINVAL, "bad h or theta");
+    const size_t N = (size_t)nx * ny * nz;
+    const bool wide = n_orb > kMaxOrb && lambda_in;  // the W field goes through workspace scratch
     Workspace* w = nullptr;
-    int rc = workspace(stream, 0, &w);
+    int rc = workspace(stream, wide ? (ops->psi_elem * N * (n_orb - 1) + 7) / 8 : 0, &w);
     if (rc != LBKS_OK) return rc;
-    RelaxIO io{psi_in, u_in, Vc, sigma_in, psi_out, psi_out, S_out, lambda_out, sigma_out};
-    cudaError_t e = ops->relax_psi(n_orb, make_grid(nx, ny, nz), make_coef(1.0, theta, dt, h), io, w->sc, 1, 0,
-                                   (cudaStream_t)stream);
+    const Grid g = make_grid(nx, ny, nz);
+    cudaError_t e = cudaSuccess;
+    if (wide) e = ops->w_field(n_orb, make_grid((int)N, 1, 1), 1.0, psi_in, lambda_in, w->pvec, 1, (cudaStream_t)stream);
+    RelaxIO io{psi_in, wide ? w->pvec : nullptr, Vc, sigma_in, psi_out, psi_out, S_out, lambda_out, sigma_out,
+               wide ? nullptr : lambda_in};
+    if (e == cudaSuccess)
+        e = ops->relax_psi(n_orb, g, make_coef(1.0, theta, dt, h), io, w->sc, 1, 0, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step_psi");
 }
 

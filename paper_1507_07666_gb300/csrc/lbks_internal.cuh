@@ -129,6 +129,9 @@ struct RelaxIO {
     double* S_out;
     double* lambda_out;
     double* sigma_out;
+    // orbital storage, up to kMaxOrb orbitals: the W source from Lambda of the
+    // step that produced f_in (null: no W source), instead of the field u_in
+    const double* lambda_in = nullptr;
 };
 
 struct OrbitalStart {  // Gaussian start of one orbital

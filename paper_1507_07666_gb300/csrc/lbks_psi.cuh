@@ -53,6 +53,13 @@ __device__ __forceinline__ void psi_stencil(const Grid& g, const Site& t, uint32
 // Up to kMaxOrb orbitals: one site per thread, all orbitals, overlap partials
 // fused (as k_stream_collide); the last block writes S, Lambda and sigma.
 // io.f_in / io.f_out: psi in / out ([sys][j][z][y][x], T); io.V: Vc.
+//
+// The W source needs no field: a thread holds every orbital of its site, and
+// sum_p xi_p u_j(r - v_p) = -omega sum_{k<j} Lambda_jk (K_xi psi_k)(r) with
+// K_xi psi_k = sum_p xi_p psi_k(r - v_p), which the same loads give.  Lambda
+// is read from io.lambda_in (the previous step's, written by that step's
+// last block; null at a cycle's first step) before any block of this launch
+// arrives at the counter, so the last block may overwrite it.
 // Resident blocks per SM the register allocator must allow: the unrolled
 // stencil keeps the loads of several velocities of every orbital in flight.
 template <typename T, int NO>
@@ -80,14 +87,39 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = T(0);
 
-    // the W field of orbitals 1 .. NO-1 (orbital 0 has none)
-    const T* u1 = (NO > 1 && uin != nullptr) ? uin + y * (NO > 1 ? NO - 1 : 1) * N : nullptr;
+    // -omega Lambda (strictly lower), or no W source
+    constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
+    T wl[NL];
+    const bool with_w = NO > 1 && io.lambda_in != nullptr;
+#pragma unroll
+    for (int j = 1; j < NO; ++j)
+#pragma unroll
+        for (int k = 0; k < j; ++k)
+            wl[tri(j - 1, k)] = with_w ? (T)(-c.omega * io.lambda_in[y * NO * NO + j * NO + k]) : T(0);
+    (void)uin;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
         const Site t = decode(g, s);
-        T ps[NO];
-        psi_stencil<T, NO>(g, t, s, io.V + y * N, pin + y * NO * N, nullptr, u1, N, xi, chi, dt, ps);
+        T ps[NO], kx[NO];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) ps[j] = kx[j] = T(0);
+        const double* Vc = io.V + y * N;
+        const T* pj = pin + y * NO * N;
+#pragma unroll
+        for (int p = 0; p < 19; ++p) {
+            if (!has_source(t, p)) continue;
+            const uint32_t src = source_index(g, s, p);
+            const T a = xi[vclass(p)] - dt * chi[vclass(p)] * (T)__ldg(Vc + src);
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const T v = __ldg(pj + (size_t)j * N + src);
+                ps[j] += a * v;
+                kx[j] += xi[vclass(p)] * v;
+            }
+        }
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
+#pragma unroll
+            for (int k = 0; k < j; ++k) ps[j] += wl[tri(j - 1, k)] * kx[k];
             ps[j] *= sig[j];
             pout[(y * NO + j) * N + s] = ps[j];
         }
@@ -106,27 +138,43 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
 }
 
-// More than kMaxOrb orbitals: one (site, orbital) per thread, blockIdx.y =
-// system * N_O + orbital; the overlap follows in its own kernel.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 4) k_relax_psi_wide(Grid g, Coef c, RelaxIO io, int NO) {
-    const int y = (int)blockIdx.y / NO, j = (int)blockIdx.y - y * NO;
-    if (g.active && !g.active[y]) return;
-    const uint32_t N = g.N;
-    const uint32_t s = blockIdx.x * kThreads + threadIdx.x;
-    if (s >= N) return;
-    const size_t oj = (size_t)y * NO + j;
+// More than kMaxOrb orbitals: one site and a group of up to kPsiGroup orbitals
+// per thread (they share the source indices and the weights), blockIdx.y =
+// system * groups + group; the overlap follows in its own kernel.
+constexpr int kPsiGroup = 4;
+
+template <typename T, int J>
+__device__ __forceinline__ void psi_group(const Grid& g, const Coef& c, const RelaxIO& io, int NO, int y, int j0,
+                                          uint32_t s) {
+    const size_t N = g.N;
     const T dt = (T)c.dt;
     const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
     const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
     const Site t = decode(g, s);
-    const T* uj = (j > 0 && io.u_in != nullptr)
-                      ? static_cast<const T*>(io.u_in) + ((size_t)y * (NO - 1) + j - 1) * N
-                      : nullptr;
-    T ps[1];
-    psi_stencil<T, 1>(g, t, s, io.V + (size_t)y * N, static_cast<const T*>(io.f_in) + oj * N, uj, nullptr, N, xi,
-                      chi, dt, ps);
-    static_cast<T*>(io.f_out)[oj * N + s] = (T)io.sigma_in[oj] * ps[0];
+    const T* uw = static_cast<const T*>(io.u_in);
+    const T* ubase = uw ? uw + (size_t)y * (NO - 1) * N : nullptr;  // W field of orbital j is ubase + (j - 1) N
+    const T* u0 = (ubase && j0 > 0) ? ubase + (size_t)(j0 - 1) * N : nullptr;
+    const T* u1 = ubase ? ubase + (size_t)j0 * N : nullptr;
+    const size_t o0 = (size_t)y * NO + j0;
+    T ps[J];
+    psi_stencil<T, J>(g, t, s, io.V + (size_t)y * N, static_cast<const T*>(io.f_in) + o0 * N, u0, u1, N, xi, chi, dt,
+                      ps);
+#pragma unroll
+    for (int j = 0; j < J; ++j) static_cast<T*>(io.f_out)[(o0 + j) * N + s] = (T)io.sigma_in[o0 + j] * ps[j];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) k_relax_psi_wide(Grid g, Coef c, RelaxIO io, int NO) {
+    const int groups = (NO + kPsiGroup - 1) / kPsiGroup;
+    const int y = (int)blockIdx.y / groups, jg = (int)blockIdx.y - y * groups;
+    if (g.active && !g.active[y]) return;
+    const uint32_t s = blockIdx.x * kThreads + threadIdx.x;
+    if (s >= g.N) return;
+    const int j0 = jg * kPsiGroup, J = min(kPsiGroup, NO - j0);  // block-uniform
+    if (J == 4) psi_group<T, 4>(g, c, io, NO, y, j0, s);
+    else if (J == 3) psi_group<T, 3>(g, c, io, NO, y, j0, s);
+    else if (J == 2) psi_group<T, 2>(g, c, io, NO, y, j0, s);
+    else psi_group<T, 1>(g, c, io, NO, y, j0, s);
 }
 
 template <typename T, int NO, bool BATCHED>
@@ -144,9 +192,10 @@ template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                              cudaStream_t st) {
     if (NO > kMaxOrb) {
-        if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
-        k_relax_psi_wide<T><<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io,
-                                                                                                           NO);
+        const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
+        if (groups * B > 65535) return cudaErrorInvalidConfiguration;
+        k_relax_psi_wide<T><<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(groups * B)), kThreads, 0, st>>>(
+            g, c, io, NO);
         count_launches(1);
         return cudaGetLastError();
     }

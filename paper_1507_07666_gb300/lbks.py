@@ -262,12 +262,12 @@ def lbks_relax_step(precision, nx, ny, nz, n_orb, h, omega, theta, dt, f_in, u_i
                                 _ptr(sigma_out, torch.float64), _stream(stream)))
 
 
-def lbks_relax_step_psi(precision, nx, ny, nz, n_orb, h, theta, dt, psi_in, u_in, Vc, sigma_in, psi_out, S_out,
-                        lambda_out, sigma_out, stream=None):
+def lbks_relax_step_psi(precision, nx, ny, nz, n_orb, h, theta, dt, psi_in, lambda_in, Vc, sigma_in, psi_out,
+                        S_out, lambda_out, sigma_out, stream=None):
     import torch
     P = _psitype(precision)
     _check(_lib.lbks_relax_step_psi(precision, nx, ny, nz, n_orb, h, theta, dt, _ptr(psi_in, P),
-                                    _ptr(u_in, P, optional=True), _ptr(Vc, torch.float64),
+                                    _ptr(lambda_in, torch.float64, optional=True), _ptr(Vc, torch.float64),
                                     _ptr(sigma_in, torch.float64), _ptr(psi_out, P), _ptr(S_out, torch.float64),
                                     _ptr(lambda_out, torch.float64), _ptr(sigma_out, torch.float64),
                                     _stream(stream)))

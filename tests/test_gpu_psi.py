@@ -1,8 +1,9 @@
 """Orbital storage at omega = 1 (LBKS_STORE_PSI): the step keeps psi alone and
 applies the pull-and-sum of Eq. KSLB as a 19-point stencil.  Its results must
 equal the oracle's population step fed the populations that the psi state
-stands for, f*_p = xi_p psi - dt chi_p Vc psi + xi_p u, element by element,
-and an orbital-storage SCF must follow the oracle's trajectory."""
+stands for, f*_p = xi_p psi - dt chi_p Vc psi + xi_p u with the W field
+u_j = -sum_{k<j} Lambda_jk psi_k, element by element, and an orbital-storage
+SCF must follow the oracle's trajectory."""
 import numpy as np
 import pytest
 
@@ -31,7 +32,8 @@ def _populations(A, u, Vc, theta, dt):
     ((7, 9, 11), 1, 0), ((33, 20, 17), 5, 1), ((16, 5, 40), 8, 2), ((2, 3, 2), 3, 3),
     ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5),
 ])
-def test_psi_step_matches_population_oracle(prec, n, n_orb, seed):
+@pytest.mark.parametrize("with_w", [True, False], ids=["W", "noW"])
+def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w):
     torch, lbks = require_gpu()
     theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, 1.0, h)
@@ -39,18 +41,21 @@ def test_psi_step_matches_population_oracle(prec, n, n_orb, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     A = rng.uniform(-0.5, 1.0, size=(n_orb, nz, ny, nx))
     Vc = rng.uniform(-3.0, 1.0, size=(nz, ny, nx))
-    u = rng.uniform(-0.2, 0.2, size=(max(n_orb - 1, 1), nz, ny, nx))
+    lam_in = np.tril(rng.uniform(-0.3, 0.3, size=(n_orb, n_orb)), -1) * (1.0 if with_w else 0.0)
     sigma = rng.uniform(0.5, 2.0, size=n_orb)
     if prec == 1:  # the oracle sees the values the GPU stores
-        A, u = A.astype(np.float32).astype(np.float64), u.astype(np.float32).astype(np.float64)
+        A = A.astype(np.float32).astype(np.float64)
+    # the W field the step forms: u_j = -sum_{k<j} Lambda_jk psi_k (omega = 1)
+    u = -np.tensordot(lam_in, A, axes=(1, 0))[1:]
     P = torch.float64 if prec == 0 else torch.float32
     psi_in = to_dev(torch, A, P)
-    u_in = to_dev(torch, u, P) if n_orb > 1 else None
     psi_out = torch.empty_like(psi_in)
     S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
     lam, sig_out = torch.empty_like(S), torch.empty(n_orb, dtype=torch.float64, device="cuda")
-    lbks.lbks_relax_step_psi(prec, nx, ny, nz, n_orb, h, theta, dt, psi_in, u_in, to_dev(torch, Vc, torch.float64),
-                             to_dev(torch, sigma, torch.float64), psi_out, S, lam, sig_out)
+    lam_dev = to_dev(torch, lam_in, torch.float64) if with_w else None
+    lbks.lbks_relax_step_psi(prec, nx, ny, nz, n_orb, h, theta, dt, psi_in, lam_dev,
+                             to_dev(torch, Vc, torch.float64), to_dev(torch, sigma, torch.float64), psi_out, S, lam,
+                             sig_out)
     torch.cuda.synchronize()
     ref = lb.step(_populations(A, u, Vc, theta, dt), sigma, np.zeros_like(Vc), 1.0, theta, dt, h)
     tol = TOL[prec]
