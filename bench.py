@@ -579,6 +579,9 @@ def main_lbks(args):
            "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
 
     tuned = lbks.lbks_get_relax_variant(sysm.handle)
+    if psi_mode:  # orbital storage names its two kernels differently
+        tuned = {"variant": ("tiled", "direct", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
+                 "ms_direct": tuned["ms_pairs"]}
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration

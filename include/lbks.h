@@ -186,6 +186,8 @@ typedef struct lbks_energy_terms {
  *      populations by warp shuffle (nx even and arrays 16-byte aligned, else 0);
  *   2  one site per thread, the next orbital's populations loaded before the
  *      current orbital collides (more loads in flight, fewer threads).
+ * In orbital storage (LBKS_STORE_PSI) the variants are 0: the stencil staged
+ * in shared memory by tiles, 1: one site per thread from L1 (2 is taken as 0).
  * mode 0 (default), tuned: the first lbks_set_geometry of each shape
  * (precision, orbitals, omega == 1 or not, grid, systems) times every
  * variant on the handle's buffers (a few launches, before they hold state)

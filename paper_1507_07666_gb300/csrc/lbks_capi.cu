@@ -398,7 +398,7 @@ cudaError_t enqueue_cycle_psi(lbks_system* s, cudaStream_t st, int start) {
     for (int t = 0; t < n; ++t) {
         RelaxIO io{s->f[cur], (t == 0 || fused_w) ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma,
                    s->f[1 - cur], s->f[1 - cur], s->S, s->lam, s->sigma, (t == 0 || !fused_w) ? nullptr : s->lam};
-        const int v = t == n - 1 ? kRelaxExactOverlap : 0;  // the last overlap feeds the Cholesky
+        const int v = s->variant | (t == n - 1 ? kRelaxExactOverlap : 0);  // the last overlap feeds the Cholesky
         cudaError_t e = s->ops->relax_psi(s->n_orb, s->g, s->c, io, s->sc, B, v, st);
         if (e != cudaSuccess) return e;
         cur ^= 1;
@@ -597,7 +597,7 @@ int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) 
 // sigma are all rewritten afterwards).  A few launches, once per shape.
 int tune_relax(lbks_system* s) {
     const int mode = g_variant_mode.load();
-    if (s->n_orb > kMaxOrb || s->psi_storage) {
+    if (s->n_orb > kMaxOrb) {
         s->variant = kRelaxSites;
         return LBKS_OK;
     }
@@ -605,7 +605,9 @@ int tune_relax(lbks_system* s) {
         s->variant = mode - 1;
         return LBKS_OK;
     }
-    const TuneKey key = tune_key(s->prm.precision, s->n_orb, s->prm.omega, s->nx, s->ny, s->nz, s->B);
+    // orbital storage has its own two kernels (0: tiled in shared memory, 1: one site per thread)
+    const TuneKey key = tune_key(s->prm.precision + (s->psi_storage ? 16 : 0), s->n_orb, s->prm.omega, s->nx, s->ny,
+                                 s->nz, s->B);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -616,21 +618,26 @@ int tune_relax(lbks_system* s) {
     }
     cudaStream_t st = s->st;
     const size_t NB = s->N * s->B;
-    cudaError_t e = cudaMemsetAsync(s->f[0], 0, s->ops->elem * NB * 19 * s->n_orb, st);
+    cudaError_t e = cudaMemsetAsync(
+        s->f[0], 0, s->psi_storage ? s->ops->psi_elem * NB * s->n_orb : s->ops->elem * NB * 19 * s->n_orb, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vin, 0, sizeof(double) * NB, st);
     if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * s->B, 1.0, st);
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
-    const RelaxIO io{s->f[0], s->n_orb > 1 ? s->u : nullptr, s->vin, s->sigma, s->f[1], s->psi, s->S, s->lam,
-                     s->sigma};
+    const RelaxIO io = s->psi_storage
+                           ? RelaxIO{s->f[0], nullptr, s->vin, s->sigma, s->f[1], s->f[1], s->S, s->lam, s->sigma,
+                                     nullptr}
+                           : RelaxIO{s->f[0], s->n_orb > 1 ? s->u : nullptr, s->vin, s->sigma, s->f[1], s->psi, s->S,
+                                     s->lam, s->sigma};
+    auto relax = s->psi_storage ? s->ops->relax_psi : s->ops->relax;
     constexpr int kReps = 3;
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f};
-    bool tried[kRelaxVariants] = {true, s->nx % 2 == 0, s->n_orb > 1};  // variants that differ from one site
+    bool tried[kRelaxVariants] = {true, s->psi_storage || s->nx % 2 == 0, !s->psi_storage && s->n_orb > 1};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
-        e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);  // warm-up
+        e = relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = s->ops->relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);
+        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
@@ -1088,8 +1095,10 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     if (wide) e = ops->w_field(n_orb, make_grid((int)N, 1, 1), 1.0, psi_in, lambda_in, w->pvec, 1, (cudaStream_t)stream);
     RelaxIO io{psi_in, wide ? w->pvec : nullptr, Vc, sigma_in, psi_out, psi_out, S_out, lambda_out, sigma_out,
                wide ? nullptr : lambda_in};
+    const int mode = g_variant_mode.load();  // forced variant, else the tiled kernel
     if (e == cudaSuccess)
-        e = ops->relax_psi(n_orb, g, make_coef(1.0, theta, dt, h), io, w->sc, 1, 0, (cudaStream_t)stream);
+        e = ops->relax_psi(n_orb, g, make_coef(1.0, theta, dt, h), io, w->sc, 1, mode > 0 ? mode - 1 : 0,
+                           (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step_psi");
 }
 

@@ -177,6 +177,128 @@ __global__ void __launch_bounds__(kThreads, 3) k_relax_psi_wide(Grid g, Coef c, 
     else psi_group<T, 1>(g, c, io, NO, y, j0, s);
 }
 
+// The same step with the stencil's inputs staged in shared memory: a block
+// takes a tile of kTX x kTY x kTZ sites, loads the tile's box with a one-site
+// halo of every orbital's psi and of Vc once (zero outside the grid, which is
+// the empty-source rule), and sums the 19 neighbours from shared memory.
+// Each thread owns one (x, y) column of the tile and kTZ sites along z.
+// Tiles are taken in a block-stride loop (the grid stays within the overlap
+// scratch's block count).  Dynamic shared memory: (NO + 1) box values of T.
+constexpr int kTX = 32, kTY = 8, kTZ = 4;
+constexpr int kBX = kTX + 2, kBY = kTY + 2, kBZ = kTZ + 2, kBox = kBX * kBY * kBZ;
+
+template <typename T, int NO, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
+                                                                                         Scratch sc) {
+    constexpr int NP = NO * (NO + 1) / 2;
+    constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* box = reinterpret_cast<T*>(smem_raw);  // [NO + 1][kBox]: psi_0 .. psi_{NO-1}, then Vc
+    if (BATCHED && inactive(g)) return;
+    const uint32_t N = g.N;
+    const size_t y = BATCHED ? sys_id() : 0;
+    const T* __restrict__ pin = static_cast<const T*>(io.f_in) + y * NO * N;
+    T* __restrict__ pout = static_cast<T*>(io.f_out) + y * NO * N;
+    const double* __restrict__ Vc = io.V + y * N;
+    T sig[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[y * NO + j];
+    const T dt = (T)c.dt;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    T wl[NL];
+    const bool with_w = NO > 1 && io.lambda_in != nullptr;
+#pragma unroll
+    for (int j = 1; j < NO; ++j)
+#pragma unroll
+        for (int k = 0; k < j; ++k)
+            wl[tri(j - 1, k)] = with_w ? (T)(-c.omega * io.lambda_in[y * NO * NO + j * NO + k]) : T(0);
+    T acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = T(0);
+
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY, ntz = (g.nz + kTZ - 1) / kTZ;
+    const int ntiles = ntx * nty * ntz;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int bxi = tile % ntx, byi = (tile / ntx) % nty, bzi = tile / (ntx * nty);
+        const int x0 = bxi * kTX - 1, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;  // box origin (halo included)
+        __syncthreads();  // the previous tile's box is no longer read
+        for (int i = threadIdx.x; i < kBox; i += kThreads) {
+            const int bx = i % kBX, by = (i / kBX) % kBY, bz = i / (kBX * kBY);
+            const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+            const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+            const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+            for (int j = 0; j < NO; ++j) box[j * kBox + i] = in ? __ldg(pin + (size_t)j * N + gs) : T(0);
+            box[NO * kBox + i] = in ? (T)__ldg(Vc + gs) : T(0);
+        }
+        __syncthreads();
+        const int gx = x0 + 1 + tx, gy = y0 + 1 + ty;
+#pragma unroll 1
+        for (int dz = 0; dz < kTZ; ++dz) {
+            const int gz = z0 + 1 + dz;
+            const bool live = gx < g.nx && gy < g.ny && gz < g.nz;
+            const int b = ((dz + 1) * kBY + (ty + 1)) * kBX + (tx + 1);  // the site in the box
+            T ps[NO], kx[NO];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) ps[j] = kx[j] = T(0);
+#pragma unroll
+            for (int p = 0; p < 19; ++p) {
+                const int src = b - (vel(p, 0) + vel(p, 1) * kBX + vel(p, 2) * kBX * kBY);
+                const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[NO * kBox + src];
+#pragma unroll
+                for (int j = 0; j < NO; ++j) {
+                    const T v = box[j * kBox + src];
+                    ps[j] += a * v;
+                    kx[j] += xi[vclass(p)] * v;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+#pragma unroll
+                for (int k = 0; k < j; ++k) ps[j] += wl[tri(j - 1, k)] * kx[k];
+                ps[j] = live ? ps[j] * sig[j] : T(0);
+            }
+            if (live) {
+                const size_t s = ((size_t)gz * g.ny + gy) * g.nx + gx;
+#pragma unroll
+                for (int j = 0; j < NO; ++j) pout[(size_t)j * N + s] = ps[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j)
+#pragma unroll
+                for (int i = 0; i <= j; ++i) acc[tri(j, i)] += ps[j] * ps[i];
+        }
+    }
+    double v[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v[k] = (double)acc[k];
+    double* partial = sc.partial + y * sc.max_blocks * sc.max_vals;
+    block_sum_store<NP>(v, partial + (size_t)blockIdx.x * NP);
+    __shared__ double tot[NP];
+    if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0)
+        store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
+}
+
+template <typename T, int NO, bool BATCHED>
+cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                  cudaStream_t st) {
+    auto kern = k_relax_psi_tile<T, NO, BATCHED>;
+    const size_t smem = (size_t)(NO + 1) * kBox * sizeof(T);
+    // opted in whatever the size: static and dynamic shared memory together may exceed 48 KB
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    const size_t tiles = (size_t)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
+    const int per = std::max(1, std::min(sc.max_blocks, nb * num_sms() / std::max(B, 1)));
+    kern<<<dim3((unsigned)std::min<size_t>(tiles, (size_t)per), (unsigned)B), kThreads, smem, st>>>(g, c, io, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                cudaStream_t st) {
@@ -190,7 +312,7 @@ cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, 
 
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                             cudaStream_t st) {
+                             bool tiled, cudaStream_t st) {
     if (NO > kMaxOrb) {
         const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
         if (groups * B > 65535) return cudaErrorInvalidConfiguration;
@@ -201,8 +323,12 @@ cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO
     }
     const bool b = B > 1;
     switch (NO) {
-#define LBKS_CASE(n) \
-    case n: return b ? launch_relax_psi_n<T, n, true>(g, c, io, sc, B, st) : launch_relax_psi_n<T, n, false>(g, c, io, sc, B, st);
+#define LBKS_CASE(n)                                                                                  \
+    case n:                                                                                           \
+        if (tiled)                                                                                    \
+            return b ? launch_relax_psi_tile<T, n, true>(g, c, io, sc, B, st)                         \
+                     : launch_relax_psi_tile<T, n, false>(g, c, io, sc, B, st);                       \
+        return b ? launch_relax_psi_n<T, n, true>(g, c, io, sc, B, st) : launch_relax_psi_n<T, n, false>(g, c, io, sc, B, st);
         LBKS_CASE(1) LBKS_CASE(2) LBKS_CASE(3) LBKS_CASE(4) LBKS_CASE(5) LBKS_CASE(6) LBKS_CASE(7) LBKS_CASE(8)
 #undef LBKS_CASE
         default: return cudaErrorInvalidValue;

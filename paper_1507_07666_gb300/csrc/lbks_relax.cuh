@@ -531,7 +531,7 @@ cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c
 // lbks_relax_<precision>_psi.cu.
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                             cudaStream_t st);
+                             bool tiled, cudaStream_t st);
 
 template <typename TS, typename T>
 struct Ops {
@@ -774,7 +774,8 @@ struct Ops {
 
     static cudaError_t relax_psi(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc,
                                  int B, int variant, cudaStream_t st) {
-        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, st);
+        // variant kRelaxSites: the shared-memory tiled stencil; kRelaxPairs: one site per thread from L1
+        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, (variant & kRelaxVariantMask) != kRelaxPairs, st);
         if (e != cudaSuccess || n_orb <= kMaxOrb) return e;  // up to kMaxOrb: overlap fused
         return gram_wide<true>(n_orb, g, c.h, io.f_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
                                (variant & kRelaxExactOverlap) != 0);

@@ -2,6 +2,6 @@
 #include "lbks_psi.cuh"
 
 namespace lbks {
-template cudaError_t launch_relax_psi<float>(int, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int,
+template cudaError_t launch_relax_psi<float>(int, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int, bool,
                                           cudaStream_t);
 }  // namespace lbks

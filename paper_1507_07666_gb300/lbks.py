@@ -313,7 +313,7 @@ def lbks_set_relax_variant(mode: int) -> int:
 def lbks_get_relax_variant(handle) -> dict:
     v, ms = ctypes.c_int(), (ctypes.c_double * len(RELAX_VARIANTS))()
     _check(_lib.lbks_get_relax_variant(handle, ctypes.byref(v), ms))
-    out = {"variant": RELAX_VARIANTS[v.value]}
+    out = {"variant": RELAX_VARIANTS[v.value], "index": v.value}
     out.update({f"ms_{name}": ms[k] for k, name in enumerate(RELAX_VARIANTS)})
     return out
 

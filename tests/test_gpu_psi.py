@@ -33,8 +33,17 @@ def _populations(A, u, Vc, theta, dt):
     ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5),
 ])
 @pytest.mark.parametrize("with_w", [True, False], ids=["W", "noW"])
-def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w):
+@pytest.mark.parametrize("mode", [1, 2], ids=["tiled", "direct"])
+def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
     torch, lbks = require_gpu()
+    prev = lbks.lbks_set_relax_variant(mode)  # forced: the tiled or the one-site-per-thread kernel
+    try:
+        _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w)
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+
+
+def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w):
     theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, 1.0, h)
     nx, ny, nz = n
@@ -83,13 +92,22 @@ def test_psi_step_rejects_bad_arguments():
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["ch4", "water_dimer"])
+@pytest.mark.parametrize("case", ["ch4", "water_dimer", "ch4_direct"])
 def test_psi_storage_scf_follows_the_oracle(prec, case):
     """Three fixed cycles from the Gaussian start: the first step pulls with no
     potential term (the start is f = xi psi), every cycle's first step with
-    the previous cycle's collision potential."""
+    the previous cycle's collision potential.  ch4: the tuned kernel;
+    ch4_direct: the one-site-per-thread kernel forced."""
     torch, lbks = require_gpu()
-    if case == "ch4":
+    prev = lbks.lbks_set_relax_variant(2 if case == "ch4_direct" else 0)
+    try:
+        _psi_scf_case(torch, lbks, prec, case)
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+
+
+def _psi_scf_case(torch, lbks, prec, case):
+    if case.startswith("ch4"):
         mol, n, h, n_orb, n_inner = W.methane(), (30, 28, 26), 0.45, 5, 12
     else:
         mol = W.water_cluster(2, seed=3, box=11.0, min_oo=5.0, margin=2.5)
