@@ -299,6 +299,74 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
     return cudaGetLastError();
 }
 
+// More than kMaxOrb orbitals, staged in shared memory: a block takes one
+// tile and one group of up to kPsiGroup orbitals of one system (blockIdx.y =
+// system * groups + group), stages the group's psi and W field and Vc with a
+// one-site halo, and writes psi'; the overlap follows in its own kernel.
+// Dynamic shared memory: (2 kPsiGroup + 1) box values of T.
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_relax_psi_wide_tile(Grid g, Coef c, RelaxIO io, int NO) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* box = reinterpret_cast<T*>(smem_raw);  // [kPsiGroup psi][kPsiGroup u][Vc], kBox each
+    const int groups = (NO + kPsiGroup - 1) / kPsiGroup;
+    const int y = (int)blockIdx.y / groups, jg = (int)blockIdx.y - y * groups;
+    if (g.active && !g.active[y]) return;
+    const size_t N = g.N;
+    const int j0 = jg * kPsiGroup, J = min(kPsiGroup, NO - j0);
+    const T* __restrict__ pin = static_cast<const T*>(io.f_in) + ((size_t)y * NO + j0) * N;
+    const T* uw = static_cast<const T*>(io.u_in);
+    // W field of orbital j (j >= 1): u + (y (NO - 1) + j - 1) N
+    const T* ubase = uw ? uw + (size_t)y * (NO - 1) * N : nullptr;
+    const double* __restrict__ Vc = io.V + (size_t)y * N;
+    const T dt = (T)c.dt;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
+    const int tile = blockIdx.x;
+    const int bxi = tile % ntx, byi = (tile / ntx) % nty, bzi = tile / (ntx * nty);
+    const int x0 = bxi * kTX - 1, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;
+    for (int i = threadIdx.x; i < kBox; i += kThreads) {
+        const int bx = i % kBX, by = (i / kBX) % kBY, bz = i / (kBX * kBY);
+        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+        const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+        const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+        for (int j = 0; j < kPsiGroup; ++j) {
+            const bool has = in && j < J;
+            box[j * kBox + i] = has ? __ldg(pin + (size_t)j * N + gs) : T(0);
+            const int jj = j0 + j;  // the W field exists for orbitals >= 1
+            box[(kPsiGroup + j) * kBox + i] =
+                (has && ubase && jj > 0) ? __ldg(ubase + (size_t)(jj - 1) * N + gs) : T(0);
+        }
+        box[2 * kPsiGroup * kBox + i] = in ? (T)__ldg(Vc + gs) : T(0);
+    }
+    __syncthreads();
+    const int gx = x0 + 1 + tx, gy = y0 + 1 + ty;
+#pragma unroll 1
+    for (int dz = 0; dz < kTZ; ++dz) {
+        const int gz = z0 + 1 + dz;
+        if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
+        const int b = ((dz + 1) * kBY + (ty + 1)) * kBX + (tx + 1);
+        T ps[kPsiGroup];
+#pragma unroll
+        for (int j = 0; j < kPsiGroup; ++j) ps[j] = T(0);
+#pragma unroll
+        for (int p = 0; p < 19; ++p) {
+            const int src = b - (vel(p, 0) + vel(p, 1) * kBX + vel(p, 2) * kBX * kBY);
+            const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[2 * kPsiGroup * kBox + src];
+#pragma unroll
+            for (int j = 0; j < kPsiGroup; ++j)
+                ps[j] += a * box[j * kBox + src] + xi[vclass(p)] * box[(kPsiGroup + j) * kBox + src];
+        }
+        const size_t s = ((size_t)gz * g.ny + gy) * g.nx + gx;
+        const size_t o0 = (size_t)y * NO + j0;
+#pragma unroll
+        for (int j = 0; j < kPsiGroup; ++j)
+            if (j < J) static_cast<T*>(io.f_out)[(o0 + j) * N + s] = (T)io.sigma_in[o0 + j] * ps[j];
+    }
+}
+
 template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                cudaStream_t st) {
@@ -316,6 +384,18 @@ cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO
     if (NO > kMaxOrb) {
         const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
         if (groups * B > 65535) return cudaErrorInvalidConfiguration;
+        if (tiled) {
+            const size_t smem = (size_t)(2 * kPsiGroup + 1) * kBox * sizeof(T);
+            static const cudaError_t attr =
+                cudaFuncSetAttribute(k_relax_psi_wide_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (attr != cudaSuccess) return attr;
+            const size_t tiles =
+                (size_t)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
+            k_relax_psi_wide_tile<T><<<dim3((unsigned)tiles, (unsigned)(groups * B)), kThreads, smem, st>>>(g, c, io,
+                                                                                                        NO);
+            count_launches(1);
+            return cudaGetLastError();
+        }
         k_relax_psi_wide<T><<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(groups * B)), kThreads, 0, st>>>(
             g, c, io, NO);
         count_launches(1);
