@@ -30,7 +30,7 @@ def _populations(A, u, Vc, theta, dt):
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("n,n_orb,seed", [
     ((7, 9, 11), 1, 0), ((33, 20, 17), 5, 1), ((16, 5, 40), 8, 2), ((2, 3, 2), 3, 3),
-    ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5),
+    ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5), ((12, 10, 9), 64, 6), ((70, 3, 9), 6, 7),
 ])
 @pytest.mark.parametrize("with_w", [True, False], ids=["W", "noW"])
 @pytest.mark.parametrize("mode", [1, 2], ids=["tiled", "direct"])

@@ -31,6 +31,7 @@ CASES = [
     ((34, 20, 17), 5, 1.0, 9),
     ((66, 7, 5), 2, 1.2, 10),
     ((10, 9, 11), 8, 0.8, 11),
+    ((12, 10, 9), 64, 1.0, 12),  # the largest orbital count the library takes
 ]
 VARIANTS = [1, 2, 3]  # lbks_set_relax_variant: one site, two sites, one site with the next orbital prefetched
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
