@@ -84,9 +84,9 @@ def parse_args():
     ap.add_argument("--launches", type=int, default=20)
     ap.add_argument("--kernel", choices=["stream_collide", "overlap_tc", "overlap_exact"], default="stream_collide",
                     help="--kernel-only: which step to launch alone")
-    ap.add_argument("--relax-variant", type=int, choices=[0, 1, 2, 3], default=0,
+    ap.add_argument("--relax-variant", type=int, choices=[0, 1, 2, 3, 4], default=0,
                     help="stream-collide variant: 0 tuned per shape, 1 one site per thread, 2 site pairs, "
-                         "3 one site with the next orbital prefetched")
+                         "3 one site with the next orbital prefetched, 4 populations staged by cp.async")
     return ap.parse_args()
 
 
@@ -376,8 +376,9 @@ def main_kernel_only(args):
     ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
     gbs = 38 * elem * units / (ms / 1e3) / 1e9
-    print(json.dumps({"kernel": "k_stream_collide_pair" if args.relax_variant == 2 else "k_stream_collide",
-                      "variant": ("sites (untuned)", "sites", "pairs", "prefetch")[args.relax_variant],
+    print(json.dumps({"kernel": {2: "k_stream_collide_pair", 4: "k_stream_collide_async"}.get(args.relax_variant,
+                                                                                            "k_stream_collide"),
+                      "variant": ("sites (untuned)", "sites", "pairs", "prefetch", "async")[args.relax_variant],
                       "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
                       "ms_per_launch": ms, "algorithmic_GBps": gbs, "launches": args.launches}), flush=True)
     return 0

@@ -185,7 +185,10 @@ typedef struct lbks_energy_terms {
  *   1  two x-neighbouring sites per thread, two-element loads, x-shifted
  *      populations by warp shuffle (nx even and arrays 16-byte aligned, else 0);
  *   2  one site per thread, the next orbital's populations loaded before the
- *      current orbital collides (more loads in flight, fewer threads).
+ *      current orbital collides (more loads in flight, fewer threads);
+ *   3  one site per thread, the pulled populations of a 256-site tile staged
+ *      in shared memory by cp.async several tiles ahead (N % 8 == 0 and
+ *      16-byte aligned arrays, else 0).
  * In orbital storage (LBKS_STORE_PSI) the variants are 0: the stencil staged
  * in shared memory by tiles, 1: one site per thread from L1 (2 is taken as 0).
  * mode 0 (default), tuned: the first lbks_set_geometry of each shape
@@ -198,7 +201,7 @@ typedef struct lbks_energy_terms {
 int lbks_set_relax_variant(int mode);
 
 /* Variant the handle's stream-collide runs, and the tuner's ms per launch of
- * each variant in ms[0..2] (may be NULL; negative: not measured by this
+ * each variant in ms[0..3] (may be NULL; negative: not measured by this
  * handle). */
 int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
 

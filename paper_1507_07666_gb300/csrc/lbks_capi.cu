@@ -236,7 +236,7 @@ struct lbks_system {
     cudaStream_t st = nullptr;   // internal stream for synchronous calls
     cudaStream_t cap = nullptr;  // capture stream
     int variant = kRelaxSites;   // stream-collide variant (tuned per shape)
-    double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0};
+    double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0, -1.0};
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
     std::vector<std::vector<double>> xyz, Z;  // per system
@@ -631,8 +631,10 @@ int tune_relax(lbks_system* s) {
                                      s->lam, s->sigma};
     auto relax = s->psi_storage ? s->ops->relax_psi : s->ops->relax;
     constexpr int kReps = 3;
-    float ms[kRelaxVariants] = {0.f, 0.f, 0.f};
-    bool tried[kRelaxVariants] = {true, s->psi_storage || s->nx % 2 == 0, !s->psi_storage && s->n_orb > 1};
+    float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
+    // variants that differ from the first kernel on this shape
+    bool tried[kRelaxVariants] = {true, s->psi_storage || s->nx % 2 == 0, !s->psi_storage && s->n_orb > 1,
+                                  !s->psi_storage && s->N % 8 == 0};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
         e = relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);  // warm-up

@@ -105,7 +105,8 @@ int num_sms();
 constexpr int kRelaxSites = 0;
 constexpr int kRelaxPairs = 1;
 constexpr int kRelaxPrefetch = 2;
-constexpr int kRelaxVariants = 3;
+constexpr int kRelaxAsync = 3;  // populations staged in shared memory by cp.async (lbks_async.cuh)
+constexpr int kRelaxVariants = 4;
 constexpr int kRelaxVariantMask = 3;
 // Flag or-ed into the variant by the cycle-ending step: its overlap feeds the
 // Cholesky orthonormalisation, which fixes the orbital norms that density and

@@ -526,12 +526,21 @@ cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, c
 template <typename TS, typename T>
 cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
                                   const Scratch& sc, int B, cudaStream_t st);
+template <typename TS, typename T>
+cudaError_t launch_relax_async(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                               const Scratch& sc, int B, cudaStream_t st);
 // Orbital-storage relaxation at omega = 1 (lbks_psi.cuh; io.f_in / f_out hold
 // psi, io.V the potential of the collision that produced psi), compiled in
 // lbks_relax_<precision>_psi.cu.
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                              bool tiled, cudaStream_t st);
+
+// The staged (cp.async) kernel copies 16-byte pieces of whole index ranges.
+inline bool async_applies(const Grid& g, const RelaxIO& io, size_t elem) {
+    auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    return g.N % (16 / elem) == 0 && g.N % 4 == 0 && al(io.f_in) && al(io.u_in);
+}
 
 template <typename TS, typename T>
 struct Ops {
@@ -541,6 +550,8 @@ struct Ops {
         const int v = variant & kRelaxVariantMask;
         if (v == kRelaxPairs && pairs_apply(g, io)) return launch_relax_pairs<TS, T>(NO, OM1, g, c, io, sc, B, st);
         if (v == kRelaxPrefetch && NO > 1) return launch_relax_prefetch<TS, T>(NO, OM1, g, c, io, sc, B, st);
+        if (v == kRelaxAsync && async_applies(g, io, sizeof(TS)))
+            return launch_relax_async<TS, T>(NO, OM1, g, c, io, sc, B, st);
         return B > 1 ? launch_stream_collide<TS, T, NO, OM1, true, false>(g, c, io, sc, B, st)
                      : launch_stream_collide<TS, T, NO, OM1, false, false>(g, c, io, sc, B, st);
     }

@@ -1,0 +1,7 @@
+// FP64 instantiation of the staged (cp.async) stream-collide kernels.
+#include "lbks_relax_variants.cuh"
+
+namespace lbks {
+template cudaError_t launch_relax_async<double, double>(int, bool, const Grid&, const Coef&, const RelaxIO&,
+                                                   const Scratch&, int, cudaStream_t);
+}  // namespace lbks

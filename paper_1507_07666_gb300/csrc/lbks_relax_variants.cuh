@@ -4,6 +4,7 @@
 #pragma once
 
 #include "lbks_relax.cuh"
+#include "lbks_async.cuh"
 
 namespace lbks {
 
@@ -39,6 +40,20 @@ struct PrefetchLaunch {
         return launch_stream_collide<TS, T, NO, OM1, BATCHED, true>(g, c, io, sc, B, st);
     }
 };
+
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
+struct AsyncLaunch {
+    static cudaError_t run(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                           cudaStream_t st) {
+        return launch_stream_collide_async<TS, T, NO, OM1, BATCHED>(g, c, io, sc, B, st);
+    }
+};
+
+template <typename TS, typename T>
+cudaError_t launch_relax_async(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                               const Scratch& sc, int B, cudaStream_t st) {
+    return dispatch_variant<TS, T, AsyncLaunch>(NO, om1, g, c, io, sc, B, st);
+}
 
 template <typename TS, typename T>
 cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,

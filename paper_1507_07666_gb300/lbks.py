@@ -299,7 +299,7 @@ def lbks_overlap(precision, n_sites, n_orb, h, psi, S, tensor_cores=False, strea
                              int(bool(tensor_cores)), _stream(stream)))
 
 
-RELAX_VARIANTS = ("sites", "pairs", "prefetch")
+RELAX_VARIANTS = ("sites", "pairs", "prefetch", "async")
 
 
 def lbks_set_relax_variant(mode: int) -> int:

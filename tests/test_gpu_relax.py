@@ -33,7 +33,7 @@ CASES = [
     ((10, 9, 11), 8, 0.8, 11),
     ((12, 10, 9), 64, 1.0, 12),  # the largest orbital count the library takes
 ]
-VARIANTS = [1, 2, 3]  # lbks_set_relax_variant: one site, two sites, one site with the next orbital prefetched
+VARIANTS = [1, 2, 3, 4]  # lbks_set_relax_variant: one site, two sites, next orbital prefetched, staged by cp.async
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
 # bfloat16 storage: orbitals and overlaps are float sums of the stored (rounded)
 # inputs; the stored outputs carry bfloat16's 2^-9 relative rounding
@@ -76,7 +76,7 @@ def relax_variant(request):
     lbks.lbks_set_relax_variant(prev)
 
 
-@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch"], indirect=True)
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "async"], indirect=True)
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("n,n_orb,omega,seed", CASES)
 def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed, relax_variant):
@@ -97,7 +97,7 @@ def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed, relax_variant):
     assert rel_err(fg, ref["fstar"]) < tol
 
 
-@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch"], indirect=True)
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "async"], indirect=True)
 @pytest.mark.parametrize("n,n_orb,omega,seed", [((33, 20, 17), 5, 1.0, 2), ((7, 9, 11), 3, 0.8, 1),
                                                  ((34, 20, 17), 5, 1.0, 2), ((66, 7, 5), 2, 1.2, 10)])
 def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed, relax_variant):
