@@ -267,10 +267,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         } else if (!last_tile) {
             load(it + 1, nxt);
         }
-        const int s = it & 1;
+        const int s = it % kTcStages;
         const uint32_t bar = smem_u32(&mbar[s]);
-        // the MMAs of tile it-2 read this stage
-        late = late || (it >= kTcStages && !mbar_wait(bar, ((it >> 1) + 1) & 1));
+        // the MMAs of tile it - kTcStages read this stage
+        late = late || (it >= kTcStages && !mbar_wait(bar, (uint32_t)((it / kTcStages) + 1) & 1u));
         unsigned char* st = smem + s * kTcTileBytes;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             mma_commit(bar);
         }
         last_bar = bar;
-        last_parity = (it >> 1) & 1;
+        last_parity = (uint32_t)(it / kTcStages) & 1u;
         if (++in_chunk == drain_tiles || last_tile) {
             in_chunk = 0;
             const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity));
@@ -355,8 +355,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         if (k < NP) partial[(size_t)blockIdx.x * NP + k] = failed ? __longlong_as_double(0x7ff8000000000000ll) : acc[q];
     }
     double* tot = reinterpret_cast<double*>(fold);  // NP doubles fit in the fold buffer
-    if (grid_total_rt(partial, sys_counter(sc), tot, NP) && tid == 0)
-        store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, LAM ? sigma + y * NO : nullptr);
+    if (grid_total_rt(partial, sys_counter(sc), tot, NP))
+        store_overlap_block(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr,
+                            LAM ? sigma + y * NO : nullptr);
 }
 
 template <bool LAM, bool BULK, int MAXO>

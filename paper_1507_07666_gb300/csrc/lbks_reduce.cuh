@@ -41,6 +41,35 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double* dst) {
     }
 }
 
+// The last block's sum of the K values stored by each of the gridDim.x blocks
+// (partial[b*K + k]) into tot[k], in a fixed order.
+__device__ __forceinline__ void sum_over_blocks(const double* partial, double* tot, int K) {
+    const int nb = (int)gridDim.x;
+    if (K >= 64) {
+        // many values (overlaps of many orbitals): one value per thread, eight
+        // independent partial sums over the blocks in flight at a time, loads
+        // coalesced across threads (values are contiguous per block)
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            double t[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            int b = 0;
+            for (; b + 8 <= nb; b += 8) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] += __ldcg(partial + (size_t)(b + i) * K + k);
+            }
+            for (int i = 0; b < nb; ++b, ++i) t[i] += __ldcg(partial + (size_t)b * K + k);
+            tot[k] = ((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]));
+        }
+    } else {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int k = w; k < K; k += nw) {
+            double t = 0.0;
+            for (int b = lane; b < nb; b += 32) t += __ldcg(partial + (size_t)b * K + k);
+            t = warp_sum1(t);
+            if (lane == 0) tot[k] = t;
+        }
+    }
+}
+
 // After every block stored its K partials at partial[blockIdx.x*K ...], the
 // block that arrives last sums them over the grid in a fixed order into the
 // shared array `tot` and returns true (in all of its threads); the others
@@ -54,13 +83,7 @@ __device__ __forceinline__ bool grid_total(const double* partial, unsigned* coun
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = w; k < K; k += nw) {
-        double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partial + (size_t)b * K + k);
-        t = warp_sum1(t);
-        if (lane == 0) tot[k] = t;
-    }
+    sum_over_blocks(partial, tot, K);
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
     return true;
@@ -86,13 +109,7 @@ __device__ __forceinline__ bool grid_total_rt(const double* partial, unsigned* c
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = w; k < K; k += nw) {
-        double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(partial + (size_t)b * K + k);
-        t = warp_sum1(t);
-        if (lane == 0) tot[k] = t;
-    }
+    sum_over_blocks(partial, tot, K);
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
     return true;
@@ -124,6 +141,21 @@ __device__ inline void store_overlap(const double* tot, int NO, double h, double
             sigma[a] = 1.0 / sqrt(S[a * NO + a]);
         }
     }
+}
+
+// store_overlap by all threads of the (last) block, with the same arithmetic
+// (Lambda_ab = S_ab / S_bb, sigma_a = 1 / sqrt(S_aa)).  Every thread of the
+// block must call it.
+__device__ inline void store_overlap_block(const double* tot, int NO, double h, double* S, double* lam,
+                                           double* sigma) {
+    const double h3 = h * h * h;
+    for (int i = threadIdx.x; i < NO * NO; i += blockDim.x) {
+        const int a = i / NO, b = i - a * NO;
+        S[i] = h3 * tot[a >= b ? tri(a, b) : tri(b, a)];
+        if (lam) lam[i] = (b < a) ? (h3 * tot[tri(a, b)]) / (h3 * tot[tri(b, b)]) : 0.0;
+    }
+    if (lam)
+        for (int a = threadIdx.x; a < NO; a += blockDim.x) sigma[a] = 1.0 / sqrt(h3 * tot[tri(a, a)]);
 }
 
 }  // namespace lbks

@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(kThreads) k_gram_wide(Grid g, double h, const 
         const int k = threadIdx.x + q * kThreads;
         if (k < NP) partial[(size_t)blockIdx.x * NP + k] = acc[q];
     }
-    if (grid_total_rt(partial, sys_counter(sc), tot, NP) && threadIdx.x == 0)
-        store_overlap(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr, sigma + y * NO);
+    if (grid_total_rt(partial, sys_counter(sc), tot, NP))
+        store_overlap_block(tot, NO, h, S + y * NO * NO, LAM ? lam + y * NO * NO : nullptr,
+                            LAM ? sigma + y * NO : nullptr);
 }
 
 // 16-byte shared-memory loads that the compiler may not hoist out of the
