@@ -253,9 +253,39 @@ def recorded_traffic():
     return None
 
 
-def time_relax_psi(torch, lbks, w, prec, stream, launches=20):
+def psi_step_kernels(w, pe, index):
+    """Kernels of one orbital-storage step for kernel index (0 tiled, 1 direct,
+    2 TMA) and its algorithmic HBM bytes per site: psi in and out and the
+    collision potential once; more than eight orbitals add the overlap
+    kernel's read of psi' and, without the TMA kernel, the W-field kernel's
+    read of psi, its write of u and the step's read of u."""
+    no, wide = w.n_orb, w.n_orb > 8
+    name = ("k_relax_psi_tile", "k_relax_psi", "k_relax_psi_tma")[index]
+    if wide and index != 2:
+        name = "k_w_field_wide + " + name.replace("k_relax_psi", "k_relax_psi_wide")
+    words = 2 * no + ((no if index == 2 else 4 * no - 2) if wide else 0)
+    if wide:
+        name += " + " + ("k_gram_wide" if pe == 8 else "k_gram_tc") + " (one relaxation step)"
+    return name, pe * words + 8
+
+
+def psi_kernel_index(w, pe, mode):
+    """The kernel lbks_relax_step_psi runs under lbks_set_relax_variant(mode)."""
+    tma_ok = w.n[0] % (16 // pe) == 0
+    k = mode - 1 if mode > 0 else (2 if tma_ok else 0)
+    return 0 if k == 3 or (k == 2 and not tma_ok) else k
+
+
+def time_relax_psi(torch, lbks, w, prec, stream, launches=20, mode=None):
     """Average duration of the orbital-storage step (omega = 1) in the
-    solver's launch configuration, CUDA events on the launching stream."""
+    solver's launch configuration, CUDA events on the launching stream;
+    mode: the lbks_set_relax_variant mode to time under (None: as set)."""
+    if mode is not None:
+        prev = lbks.lbks_set_relax_variant(mode)
+        try:
+            return time_relax_psi(torch, lbks, w, prec, stream, launches)
+        finally:
+            lbks.lbks_set_relax_variant(prev)
     P = torch.float64 if prec == lbks.FP64 else torch.float32
     nx, ny, nz = w.n
     N = nx * ny * nz
@@ -366,9 +396,9 @@ def main_kernel_only(args):
         ms, units = time_relax_psi(torch, lbks, w, prec, stream, launches=args.launches)
         pe = 8 if prec == lbks.FP64 else 4
         N = units // w.n_orb
-        wide = w.n_orb > 8
-        nbytes = (pe * (2 * w.n_orb + (3 * w.n_orb - 2 if wide else 0)) + 8) * N
-        print(json.dumps({"kernel": "k_relax_psi_wide + overlap" if wide else "k_relax_psi", "grid": list(w.n),
+        kname, per_site = psi_step_kernels(w, pe, psi_kernel_index(w, pe, args.relax_variant))
+        nbytes = per_site * N
+        print(json.dumps({"kernel": kname, "grid": list(w.n),
                           "n_orb": w.n_orb, "dtype": args.precision, "ms_per_launch": ms,
                           "algorithmic_GBps": nbytes / (ms / 1e3) / 1e9,
                           "orbital_site_updates_per_s": units / (ms / 1e3), "launches": args.launches}), flush=True)
@@ -420,6 +450,9 @@ def main_batch(args):
     launches = lbks.lbks_kernel_launches() - l0
     elapsed_ms = ev0.elapsed_time(ev1)
     tuned = lbks.lbks_get_relax_variant(b.handle)
+    if args.storage == "psi":  # orbital storage names its kernels differently
+        tuned = {"variant": ("tiled", "direct", "tma", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
+                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"]}
     updates = sum(r["steps"] for res in results for r in res) * w.n_orb * w.sites
     last = results[-1]
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
@@ -592,9 +625,10 @@ def main_lbks(args):
            "d2h_bytes_per_step": int(rho.nbytes + 8 * (8 + 2 * w.n_orb + 8))}
 
     tuned = lbks.lbks_get_relax_variant(sysm.handle)
-    if psi_mode:  # orbital storage names its two kernels differently
-        tuned = {"variant": ("tiled", "direct", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
-                 "ms_direct": tuned["ms_pairs"]}
+    tuned_index = tuned["index"]
+    if psi_mode:  # orbital storage names its kernels differently
+        tuned = {"variant": ("tiled", "direct", "tma", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
+                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"]}
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration
@@ -603,13 +637,12 @@ def main_lbks(args):
     psi_elem = 8 if prec == lbks.FP64 else 4
     gram_name = "k_gram_wide" if prec == lbks.FP64 else "k_gram_tc"
     if psi_mode:
-        # orbital storage: psi in and out and the collision potential once per
-        # site; more than eight orbitals: the W field written and read and the
-        # overlap kernel's read of psi too (the W-field kernel is timed with it)
-        ms, units = time_relax_psi(torch, lbks, w, prec, stream)
+        # orbital storage: the step the solver runs (its tuned kernel), timed
+        # through lbks_relax_step_psi with that kernel forced
+        ms, units = time_relax_psi(torch, lbks, w, prec, stream, mode=1 + tuned_index)
         N = units // w.n_orb
-        bytes_per_launch = (psi_elem * (2 * w.n_orb + (3 * w.n_orb - 2 if wide else 0)) + 8) * N
-        kname = ("k_w_field_wide + k_relax_psi_wide + %s (one relaxation step)" % gram_name) if wide else "k_relax_psi"
+        kname, per_site = psi_step_kernels(w, psi_elem, tuned_index)
+        bytes_per_launch = per_site * N
     else:
         ms, units = time_stream_collide(torch, lbks, w, prec, stream)
         # more than eight orbitals: the timed step is two kernels, stream-collide

@@ -190,7 +190,11 @@ typedef struct lbks_energy_terms {
  *      in shared memory by cp.async several tiles ahead (N % 8 == 0 and
  *      16-byte aligned arrays, else 0).
  * In orbital storage (LBKS_STORE_PSI) the variants are 0: the stencil staged
- * in shared memory by tiles, 1: one site per thread from L1 (2 is taken as 0).
+ * in shared memory by tiles, 1: one site per thread from L1, 2: the stencil's
+ * boxes copied into shared memory by the tensor memory accelerator, which also
+ * forms the W source at any orbital count (nx a multiple of 16 / the orbital
+ * value's bytes and 16-byte aligned arrays, else 0; 3 is taken as 0).  More
+ * than 8 orbitals in orbital storage: 2 where it applies, else 0.
  * mode 0 (default), tuned: the first lbks_set_geometry of each shape
  * (precision, orbitals, omega == 1 or not, grid, systems) times every
  * variant on the handle's buffers (a few launches, before they hold state)
@@ -362,8 +366,11 @@ int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, do
  * (strictly lower part used; may alias lambda_out) or NULL for no W source.
  * Vc: N doubles, the potential of the collision that produced psi_in (zeros
  * when psi_in is a start orbital: f = xi psi has no potential term).
- * sigma_in may alias sigma_out.  Up to 8 orbitals the W source is formed
- * inside the step; more orbitals use library-managed scratch for u.
+ * sigma_in may alias sigma_out.  Kernel: the one lbks_set_relax_variant
+ * forces, else the TMA kernel where it applies (nx a multiple of 16 / the
+ * value's bytes, psi_in and Vc 16-byte aligned), else the tiled one.  The TMA
+ * kernel, and any kernel up to 8 orbitals, forms the W source inside the
+ * step; otherwise more than 8 orbitals use library-managed scratch for u.
  * Asynchronous on stream. */
 int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double dt,
                         const void* psi_in_dev, const double* lambda_in_dev, const double* Vc_dev,

@@ -392,9 +392,9 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
 cudaError_t enqueue_cycle_psi(lbks_system* s, cudaStream_t st, int start) {
     int cur = start;
     const int n = s->prm.n_inner, B = s->B;
-    // up to kMaxOrb orbitals the kernel forms the W source from Lambda itself;
-    // wider sets pull it from the W field u
-    const bool fused_w = s->n_orb <= kMaxOrb;
+    // up to kMaxOrb orbitals, and at any count with the TMA kernel, the step
+    // forms the W source from Lambda itself; otherwise it pulls the W field u
+    const bool fused_w = s->n_orb <= kMaxOrb || s->variant == kPsiKernelTma;
     for (int t = 0; t < n; ++t) {
         RelaxIO io{s->f[cur], (t == 0 || fused_w) ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma,
                    s->f[1 - cur], s->f[1 - cur], s->S, s->lam, s->sigma, (t == 0 || !fused_w) ? nullptr : s->lam};
@@ -597,15 +597,24 @@ int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) 
 // sigma are all rewritten afterwards).  A few launches, once per shape.
 int tune_relax(lbks_system* s) {
     const int mode = g_variant_mode.load();
-    if (s->n_orb > kMaxOrb) {
+    // orbital storage: the TMA kernel where its tensor maps apply
+    const bool tma_ok = s->psi_storage && psi_tma_applies(s->nx, s->f[0], s->vin, s->ops->psi_elem) &&
+                        psi_tma_applies(s->nx, s->f[1], s->vprev, s->ops->psi_elem);
+    if (mode > 0) {
+        s->variant = mode - 1;
+        if (s->psi_storage && (s->variant == kRelaxAsync || (s->variant == kPsiKernelTma && !tma_ok)))
+            s->variant = kPsiKernelTiled;
+        if (!s->psi_storage && s->n_orb > kMaxOrb) s->variant = kRelaxSites;
+        return LBKS_OK;
+    }
+    // more than kMaxOrb orbitals: one population kernel; in orbital storage the
+    // tiled step with its W-field pass is timed against the TMA step
+    const bool wide = s->n_orb > kMaxOrb;
+    if (wide && !tma_ok) {
         s->variant = kRelaxSites;
         return LBKS_OK;
     }
-    if (mode > 0) {
-        s->variant = mode - 1;
-        return LBKS_OK;
-    }
-    // orbital storage has its own two kernels (0: tiled in shared memory, 1: one site per thread)
+    // orbital storage has its own kernels (0: tiled in shared memory, 1: one site per thread, 2: TMA)
     const TuneKey key = tune_key(s->prm.precision + (s->psi_storage ? 16 : 0), s->n_orb, s->prm.omega, s->nx, s->ny,
                                  s->nz, s->B);
     {
@@ -622,6 +631,7 @@ int tune_relax(lbks_system* s) {
         s->f[0], 0, s->psi_storage ? s->ops->psi_elem * NB * s->n_orb : s->ops->elem * NB * 19 * s->n_orb, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->vin, 0, sizeof(double) * NB, st);
     if (e == cudaSuccess) e = launch_fill(s->sigma, (size_t)s->n_orb * s->B, 1.0, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->lam, 0, sizeof(double) * s->n_orb * s->n_orb * s->B, st);
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
     const RelaxIO io = s->psi_storage
@@ -630,16 +640,28 @@ int tune_relax(lbks_system* s) {
                            : RelaxIO{s->f[0], s->n_orb > 1 ? s->u : nullptr, s->vin, s->sigma, s->f[1], s->psi, s->S,
                                      s->lam, s->sigma};
     auto relax = s->psi_storage ? s->ops->relax_psi : s->ops->relax;
+    // one step of variant v; wide orbital storage: with the W source as the
+    // cycle forms it (the W-field kernel before the tiled step, Lambda inside the TMA step)
+    auto step = [&](int v) -> cudaError_t {
+        RelaxIO sio = io;
+        if (wide && v == kPsiKernelTma) sio.lambda_in = s->lam;
+        if (wide && v != kPsiKernelTma) {
+            sio.u_in = s->u;
+            cudaError_t we = s->ops->w_field(s->n_orb, s->g, s->prm.omega, s->f[0], s->lam, s->u, s->B, st);
+            if (we != cudaSuccess) return we;
+        }
+        return relax(s->n_orb, s->g, s->c, sio, s->sc, s->B, v, st);
+    };
     constexpr int kReps = 3;
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
     // variants that differ from the first kernel on this shape
-    bool tried[kRelaxVariants] = {true, s->psi_storage || s->nx % 2 == 0, !s->psi_storage && s->n_orb > 1,
-                                  !s->psi_storage && s->N % 8 == 0};
+    bool tried[kRelaxVariants] = {true, !wide && (s->psi_storage || s->nx % 2 == 0),
+                                  s->psi_storage ? tma_ok : s->n_orb > 1, !s->psi_storage && s->N % 8 == 0};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
-        e = relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);  // warm-up
+        e = step(v);  // warm-up
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = relax(s->n_orb, s->g, s->c, io, s->sc, s->B, v, st);
+        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = step(v);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
@@ -1088,7 +1110,13 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     if (psi_in == psi_out) return fail(LBKS_EINVAL, "psi_in and psi_out must not alias");
     if (!(h > 0.0) || !(theta > 0.0)) return fail(LBKS_EINVAL, "bad h or theta");
     const size_t N = (size_t)nx * ny * nz;
-    const bool wide = n_orb > kMaxOrb && lambda_in;  // the W field goes through workspace scratch
+    // forced kernel, else the TMA kernel where it applies, else the tiled one
+    const int mode = g_variant_mode.load();
+    const bool tma_ok = psi_tma_applies(nx, psi_in, Vc, ops->psi_elem);
+    int kernel = mode > 0 ? mode - 1 : (tma_ok ? kPsiKernelTma : kPsiKernelTiled);
+    if ((kernel == kPsiKernelTma && !tma_ok) || kernel == kRelaxAsync) kernel = kPsiKernelTiled;
+    // the W field goes through workspace scratch unless the kernel forms it
+    const bool wide = n_orb > kMaxOrb && lambda_in && kernel != kPsiKernelTma;
     Workspace* w = nullptr;
     int rc = workspace(stream, wide ? (ops->psi_elem * N * (n_orb - 1) + 7) / 8 : 0, &w);
     if (rc != LBKS_OK) return rc;
@@ -1097,10 +1125,8 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     if (wide) e = ops->w_field(n_orb, make_grid((int)N, 1, 1), 1.0, psi_in, lambda_in, w->pvec, 1, (cudaStream_t)stream);
     RelaxIO io{psi_in, wide ? w->pvec : nullptr, Vc, sigma_in, psi_out, psi_out, S_out, lambda_out, sigma_out,
                wide ? nullptr : lambda_in};
-    const int mode = g_variant_mode.load();  // forced variant, else the tiled kernel
     if (e == cudaSuccess)
-        e = ops->relax_psi(n_orb, g, make_coef(1.0, theta, dt, h), io, w->sc, 1, mode > 0 ? mode - 1 : 0,
-                           (cudaStream_t)stream);
+        e = ops->relax_psi(n_orb, g, make_coef(1.0, theta, dt, h), io, w->sc, 1, kernel, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_relax_step_psi");
 }
 

@@ -108,6 +108,20 @@ constexpr int kRelaxPrefetch = 2;
 constexpr int kRelaxAsync = 3;  // populations staged in shared memory by cp.async (lbks_async.cuh)
 constexpr int kRelaxVariants = 4;
 constexpr int kRelaxVariantMask = 3;
+// In orbital storage the same ids pick the stencil kernel: staged in shared
+// memory by the threads, one site per thread from L1, or staged by the tensor
+// memory accelerator (psi_tma_applies; forms the W source itself at any
+// orbital count, so no W field runs with it).
+constexpr int kPsiKernelTiled = kRelaxSites;
+constexpr int kPsiKernelDirect = kRelaxPairs;
+constexpr int kPsiKernelTma = kRelaxPrefetch;
+// The TMA kernel's tensor maps need rows of whole 16-byte units (nx a
+// multiple of 16 / elem, elem the bytes of an orbital value) and 16-byte
+// aligned orbitals and potential.
+inline bool psi_tma_applies(int nx, const void* psi, const void* V, size_t elem) {
+    auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    return elem > 0 && elem <= 16 && nx % (int)(16 / elem) == 0 && al(psi) && al(V);
+}
 // Flag or-ed into the variant by the cycle-ending step: its overlap feeds the
 // Cholesky orthonormalisation, which fixes the orbital norms that density and
 // energies see, so it is summed exactly (FP64) even where the per-step

@@ -378,9 +378,17 @@ cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, 
     return cudaGetLastError();
 }
 
+}  // namespace lbks
+
+#include "lbks_psi_tma.cuh"
+
+namespace lbks {
+
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                             bool tiled, cudaStream_t st) {
+                             int kernel, cudaStream_t st) {
+    if (kernel == kPsiKernelTma) return launch_relax_psi_tma<T>(NO, g, c, io, sc, B, st);
+    const bool tiled = kernel == kPsiKernelTiled;
     if (NO > kMaxOrb) {
         const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
         if (groups * B > 65535) return cudaErrorInvalidConfiguration;

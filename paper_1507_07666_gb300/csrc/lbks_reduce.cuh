@@ -21,14 +21,15 @@ __device__ __forceinline__ double warp_sum1(double t) {
     return t;
 }
 
-// Sums v over the block and stores the K totals at dst (block-contiguous).
-// Every thread of the block must call it.  blockDim.x == kThreads.
-template <int K>
+// Sums v over the first NW warps of the block and stores the K totals at dst
+// (block-contiguous).  Every thread of the block must call it; warps from NW
+// on (a producer warp) contribute nothing.  blockDim.x >= 32 NW.
+template <int K, int NW = kThreads / 32>
 __device__ __forceinline__ void block_sum_store(double (&v)[K], double* dst) {
-    __shared__ double sh[kThreads / 32][K];
+    __shared__ double sh[NW][K];
     warp_sum<K>(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) {
+    if (lane == 0 && w < NW) {
 #pragma unroll
         for (int k = 0; k < K; ++k) sh[w][k] = v[k];
     }
@@ -36,7 +37,7 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double* dst) {
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < kThreads / 32; ++i) t += sh[i][k];
+        for (int i = 0; i < NW; ++i) t += sh[i][k];
         dst[k] = t;
     }
 }

@@ -532,9 +532,11 @@ cudaError_t launch_relax_async(int NO, bool om1, const Grid& g, const Coef& c, c
 // Orbital-storage relaxation at omega = 1 (lbks_psi.cuh; io.f_in / f_out hold
 // psi, io.V the potential of the collision that produced psi), compiled in
 // lbks_relax_<precision>_psi.cu.
+// kernel: kPsiKernelTiled, kPsiKernelDirect or kPsiKernelTma (the last needs
+// psi_tma_applies and forms the W source from io.lambda_in at any orbital count).
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                             bool tiled, cudaStream_t st);
+                             int kernel, cudaStream_t st);
 
 // The staged (cp.async) kernel copies 16-byte pieces of whole index ranges.
 inline bool async_applies(const Grid& g, const RelaxIO& io, size_t elem) {
@@ -785,8 +787,10 @@ struct Ops {
 
     static cudaError_t relax_psi(int n_orb, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc,
                                  int B, int variant, cudaStream_t st) {
-        // variant kRelaxSites: the shared-memory tiled stencil; kRelaxPairs: one site per thread from L1
-        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, (variant & kRelaxVariantMask) != kRelaxPairs, st);
+        // variant kPsiKernelTiled: the shared-memory tiled stencil; kPsiKernelDirect: one site per thread
+        // from L1; kPsiKernelTma: boxes copied by the tensor memory accelerator (anything else: tiled)
+        const int v = variant & kRelaxVariantMask;
+        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, v == kPsiKernelDirect || v == kPsiKernelTma ? v : kPsiKernelTiled, st);
         if (e != cudaSuccess || n_orb <= kMaxOrb) return e;  // up to kMaxOrb: overlap fused
         return gram_wide<true>(n_orb, g, c.h, io.f_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
                                (variant & kRelaxExactOverlap) != 0);

@@ -31,12 +31,18 @@ def _populations(A, u, Vc, theta, dt):
 @pytest.mark.parametrize("n,n_orb,seed", [
     ((7, 9, 11), 1, 0), ((33, 20, 17), 5, 1), ((16, 5, 40), 8, 2), ((2, 3, 2), 3, 3),
     ((21, 18, 23), 12, 4), ((9, 10, 11), 10, 5), ((12, 10, 9), 64, 6), ((70, 3, 9), 6, 7),
+    # rows of whole 16-byte units (the TMA kernel's tensor maps): several tiles in x and y
+    # with ragged ends, two planes, grids smaller than a box, each orbital bucket
+    ((36, 11, 13), 5, 8), ((44, 9, 7), 12, 9), ((4, 3, 5), 3, 10), ((64, 17, 6), 40, 11),
+    ((40, 8, 3), 8, 12), ((8, 2, 2), 1, 13), ((32, 9, 2), 2, 14), ((12, 20, 4), 33, 15),
 ])
 @pytest.mark.parametrize("with_w", [True, False], ids=["W", "noW"])
-@pytest.mark.parametrize("mode", [1, 2], ids=["tiled", "direct"])
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["tiled", "direct", "tma"])
 def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
+    """mode 3 forces the TMA kernel where its tensor maps apply (nx a multiple
+    of 16 / the value's bytes), the tiled one elsewhere."""
     torch, lbks = require_gpu()
-    prev = lbks.lbks_set_relax_variant(mode)  # forced: the tiled or the one-site-per-thread kernel
+    prev = lbks.lbks_set_relax_variant(mode)  # forced: tiled, one site per thread, or TMA
     try:
         _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w)
     finally:
@@ -91,15 +97,21 @@ def test_psi_step_rejects_bad_arguments():
         lbks.System((8, 8, 8), 0.4, 1, storage=lbks.STORE_PSI, precision=lbks.BF16)
 
 
+SCF_MODE = {"ch4": 0, "ch4_direct": 2, "ch4_tma": 3, "water_dimer": 0, "water_dimer_tiled": 1}
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["ch4", "water_dimer", "ch4_direct"])
+@pytest.mark.parametrize("case", list(SCF_MODE))
 def test_psi_storage_scf_follows_the_oracle(prec, case):
     """Three fixed cycles from the Gaussian start: the first step pulls with no
     potential term (the start is f = xi psi), every cycle's first step with
     the previous cycle's collision potential.  ch4: the tuned kernel;
-    ch4_direct: the one-site-per-thread kernel forced."""
+    ch4_direct: one site per thread forced; ch4_tma: the TMA kernel forced on
+    a grid whose rows it takes; water_dimer (ten orbitals): the default, the
+    TMA kernel with the W source formed in the step; water_dimer_tiled: the
+    tiled kernel with the W field."""
     torch, lbks = require_gpu()
-    prev = lbks.lbks_set_relax_variant(2 if case == "ch4_direct" else 0)
+    prev = lbks.lbks_set_relax_variant(SCF_MODE[case])
     try:
         _psi_scf_case(torch, lbks, prec, case)
     finally:
@@ -108,7 +120,7 @@ def test_psi_storage_scf_follows_the_oracle(prec, case):
 
 def _psi_scf_case(torch, lbks, prec, case):
     if case.startswith("ch4"):
-        mol, n, h, n_orb, n_inner = W.methane(), (30, 28, 26), 0.45, 5, 12
+        mol, n, h, n_orb, n_inner = W.methane(), (32 if case == "ch4_tma" else 30, 28, 26), 0.45, 5, 12
     else:
         mol = W.water_cluster(2, seed=3, box=11.0, min_oo=5.0, margin=2.5)
         n, h, n_orb, n_inner = (36, 32, 34), 0.35, 10, 15
@@ -156,3 +168,36 @@ def test_psi_storage_batch_matches_single():
         assert abs(res[i]["E_total"] - ref["E_total"]) <= 1e-9
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,nx,n_orb", [
+    (1, 36, 10), (1, 34, 10), (0, 34, 10), (0, 35, 10), (1, 36, 5), (1, 34, 5),
+])
+def test_psi_kernel_choice(prec, nx, n_orb):
+    """The tuner times the orbital-storage kernels that apply to the shape and
+    keeps the fastest: up to eight orbitals tiled, one site per thread and TMA
+    (where its tensor maps apply: nx a multiple of 16 / the value's bytes);
+    more than eight the tiled step with its W-field pass against the TMA step,
+    which forms the W source itself."""
+    torch, lbks = require_gpu()
+    prev = lbks.lbks_set_relax_variant(0)
+    try:
+        s = lbks.System((nx, 12, 10), 0.4, n_orb, precision=prec, storage=lbks.STORE_PSI)
+        if n_orb == 5:
+            mol = W.methane()
+            s.set_geometry(mol.xyz, mol.Z)
+        else:  # two Z = 10 centres: ten doubly occupied orbitals
+            s.set_geometry(np.array([[-2.0, 0.0, 0.0], [2.0, 0.0, 0.0]]), np.array([10.0, 10.0]))
+        got = lbks.lbks_get_relax_variant(s.handle)
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+    names = lbks.RELAX_VARIANTS
+    tma_ok = nx % (4 if prec == 1 else 2) == 0
+    if n_orb > 8 and not tma_ok:  # nothing to choose: the tiled step
+        assert got["index"] == 0
+    else:
+        ms = {k: got["ms_" + names[k]] for k in range(3)}
+        timed = [k for k in range(3) if ms[k] >= 0]
+        assert (2 in timed) == tma_ok and 0 in timed and (1 in timed) == (n_orb <= 8)
+        assert got["index"] == min(timed, key=lambda k: ms[k])
+    s.close()
