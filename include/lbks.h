@@ -212,6 +212,40 @@ int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
 /* Energy terms of the last evaluation (after lbks_set_geometry or a cycle). */
 int lbks_energy(const lbks_system* sys, lbks_energy_terms* out);
 
+/* Hellmann-Feynman forces on the nuclei (Born-Oppenheimer, Sec. 3.1 with the
+ * nuclei then moved): minus the explicit derivative of the total energy,
+ *   F_I = Z_I h^3 sum_r rho(r) (r - R_I) / (|r - R_I|^2 + a^2)^(3/2)
+ *         + sum_{J != I} Z_I Z_J (R_I - R_J) / |R_I - R_J|^3     (Ha/bohr),
+ * at the density of the last evaluation (a is the softening).  At
+ * self-consistency this is -dE_total/dR_I up to the scheme's
+ * non-variational terms.  forces: host, 3 * n_atoms doubles (x, y, z per
+ * nucleus, the order of lbks_set_geometry); EINVAL when cap is smaller or no
+ * geometry is set.  The electron-nucleus sum runs on the device (one
+ * deterministic grid reduction), the nucleus-nucleus sum on the host.
+ * Synchronous. */
+int lbks_forces(lbks_system* sys, double* forces, size_t cap);
+int lbks_batch_forces(lbks_system* sys, int system, double* forces, size_t cap);
+
+/* Moves the nuclei of a single-system handle (same count and charges) and
+ * keeps the orbitals as the start of the next lbks_scf (warm start):
+ * rebuilds V_ext, and the potential and energies of the current orbitals at
+ * the new positions (unmixed).  xyz: 3 * n_atoms doubles, inside the box
+ * (EINVAL otherwise).  Synchronous. */
+int lbks_move_atoms(lbks_system* sys, const double* xyz);
+
+/* Born-Oppenheimer geometry relaxation of a single-system handle: SCF, forces,
+ * then steepest-descent moves R <- R + alpha F (no nucleus moved more than
+ * 0.2 bohr per move), each followed by a warm-started SCF; a move that lowers
+ * E_total is kept and alpha grows by 1.25, otherwise it is undone and alpha
+ * halves.  Stops when the largest |F_I| < fmax (Ha/bohr): LBKS_OK; after
+ * max_steps moves: LBKS_ENOTCONV with the results filled.  step: the initial
+ * alpha (bohr^2/Ha).  out: the SCF result at the returned geometry, with
+ * cycles, steps, poisson_iters and wall_s summed over every SCF run; xyz_out:
+ * 3 * n_atoms doubles (may be NULL); steps_out: moves tried (may be NULL).
+ * The handle is left at the returned geometry, relaxed there. */
+int lbks_relax_geometry(lbks_system* sys, int max_steps, double fmax, double step, void* stream,
+                        lbks_result* out, double* xyz_out, int* steps_out);
+
 /* Host copies (synchronous) of the last evaluation's density rho (N doubles),
  * orthonormal orbitals (n_orb*N doubles) and potentials (N doubles each).
  * EINVAL if cap (elements) is too small. */

@@ -227,7 +227,7 @@ struct lbks_system {
     cudaGraphExec_t poisson_graph = nullptr;  // kPoissonChunk preconditioned CG iterations
     uint64_t poisson_nodes = 0;
     double* small = nullptr;
-    double *S, *lam, *sigma, *Linv, *e4, *emat, *mp, *atoms;
+    double *S, *lam, *sigma, *Linv, *e4, *emat, *mp, *atoms, *forces;
     int* ints = nullptr;  // status[B], active[B], atom counts[B]
     int *status, *active, *counts;
     OrbitalStart* starts = nullptr;  // [B][n_orb]
@@ -679,6 +679,25 @@ int tune_relax(lbks_system* s) {
     return LBKS_OK;
 }
 
+// Device layout of the nuclei: atoms[B][kMaxAtoms][4] = (x, y, z, Z), counts[B].
+void pack_atoms(const lbks_system* s, std::vector<double>& atoms, std::vector<int>& counts) {
+    atoms.assign((size_t)s->B * kMaxAtoms * 4, 0.0);
+    counts.assign(s->B, 0);
+    for (int i = 0; i < s->B; ++i) {
+        const std::vector<double>& xyz = s->xyz[i];
+        const std::vector<double>& Z = s->Z[i];
+        const int na = (int)Z.size();
+        counts[i] = na;
+        for (int a = 0; a < na; ++a) {
+            double* d = &atoms[((size_t)i * kMaxAtoms + a) * 4];
+            d[0] = xyz[3 * a];
+            d[1] = xyz[3 * a + 1];
+            d[2] = xyz[3 * a + 2];
+            d[3] = Z[a];
+        }
+    }
+}
+
 // Gaussian starts, orthonormalisation, equilibrium populations and the first
 // evaluation for every system of the handle (all must have atoms).
 int initialise(lbks_system* s) {
@@ -695,21 +714,14 @@ int initialise(lbks_system* s) {
     for (int i = 0; i < B; ++i)
         if (!s->has_atoms[i]) return fail(LBKS_EINVAL, "system %d has no geometry", i);
     cudaStream_t st = s->st;
-    std::vector<double> atoms((size_t)B * kMaxAtoms * 4, 0.0);
-    std::vector<int> counts(B);
+    std::vector<double> atoms;
+    std::vector<int> counts;
+    pack_atoms(s, atoms, counts);
     std::vector<OrbitalStart> starts((size_t)B * s->n_orb);
     for (int i = 0; i < B; ++i) {
         const std::vector<double>& xyz = s->xyz[i];
         const std::vector<double>& Z = s->Z[i];
         const int na = (int)Z.size();
-        counts[i] = na;
-        for (int a = 0; a < na; ++a) {
-            double* d = &atoms[((size_t)i * kMaxAtoms + a) * 4];
-            d[0] = xyz[3 * a];
-            d[1] = xyz[3 * a + 1];
-            d[2] = xyz[3 * a + 2];
-            d[3] = Z[a];
-        }
         std::vector<int> order(na);
         for (int a = 0; a < na; ++a) order[a] = a;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Z[a] > Z[b]; });
@@ -796,7 +808,7 @@ size_t bytes_of(const lbks_params* p, int nx, int ny, int nz, int n_orb, int B) 
                        ep * N * ((size_t)std::max(1, n_orb - 1) + (psi ? 0 : n_orb)) +
                        sizeof(double) * N * (psi ? 12 : 11) + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
                        sizeof(double) * ((size_t)num_sms() * 8 * scratch_vals(n_orb) + small_per_sys(n_orb) +
-                                         4 * kMaxAtoms) +
+                                         7 * kMaxAtoms) +
                        ((p->precision == LBKS_BF16 && p->polish_tol > 0.0) ? sizeof(float) * N * n_orb * 19 * 2 : 0);
     return per * B;
 }
@@ -852,7 +864,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     A((void**)&s->rho, 8 * NB);
     A((void**)&s->pvec, 8 * (6 * NB + B * mg_coarse_doubles(nx, ny, nz)));
     A((void**)&s->cg, sizeof(CGState) * B);
-    A((void**)&s->small, sizeof(double) * (small_per_sys(n_orb) + 4 * kMaxAtoms) * B);
+    A((void**)&s->small, sizeof(double) * (small_per_sys(n_orb) + 7 * kMaxAtoms) * B);
     A((void**)&s->ints, sizeof(int) * 3 * B);
     A((void**)&s->starts, sizeof(OrbitalStart) * n_orb * B);
     if (err == cudaSuccess) {
@@ -895,6 +907,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     s->emat = s->e4 + (size_t)kE4Stride * B;
     s->mp = s->emat + (size_t)emat_stride(n_orb) * B;
     s->atoms = s->mp + (size_t)kMpStride * B;
+    s->forces = s->atoms + (size_t)4 * kMaxAtoms * B;  // [B][kMaxAtoms][3]
     *out = s;
     return LBKS_OK;
 }
@@ -1041,6 +1054,140 @@ int lbks_batch_energy(const lbks_system* s, int system, lbks_energy_terms* out) 
 }
 
 int lbks_energy(const lbks_system* s, lbks_energy_terms* out) { return lbks_batch_energy(s, 0, out); }
+
+int lbks_batch_forces(lbks_system* s, int system, double* forces, size_t cap) {
+    if (!s || !forces) return fail(LBKS_EINVAL, "null argument");
+    if (system < 0 || system >= s->B) return fail(LBKS_EINVAL, "system index out of range");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    const int na = (int)s->Z[system].size();
+    if (cap < (size_t)3 * na) return fail(LBKS_EINVAL, "capacity %zu < %d", cap, 3 * na);
+    int max_atoms = 1;
+    for (int i = 0; i < s->B; ++i) max_atoms = std::max(max_atoms, (int)s->Z[i].size());
+    Grid g = s->g;
+    g.active = nullptr;  // every system, converged or not
+    cudaError_t e = launch_forces(g, s->h, s->counts, s->atoms, s->a, s->rho, s->forces, max_atoms, s->sc, s->B, s->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(forces, s->forces + (size_t)system * 3 * kMaxAtoms, sizeof(double) * 3 * na,
+                            cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return cuda_fail(e, "lbks_forces");
+    // nucleus-nucleus term (bare Coulomb, as E_nn)
+    const std::vector<double>& xyz = s->xyz[system];
+    const std::vector<double>& Z = s->Z[system];
+    for (int a = 0; a < na; ++a)
+        for (int b = 0; b < na; ++b) {
+            if (b == a) continue;
+            const double d[3] = {xyz[3 * a] - xyz[3 * b], xyz[3 * a + 1] - xyz[3 * b + 1], xyz[3 * a + 2] - xyz[3 * b + 2]};
+            const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int k = 0; k < 3; ++k) forces[3 * a + k] += Z[a] * Z[b] * d[k] / (r * r * r);
+        }
+    return LBKS_OK;
+}
+
+int lbks_forces(lbks_system* s, double* forces, size_t cap) { return lbks_batch_forces(s, 0, forces, cap); }
+
+int lbks_move_atoms(lbks_system* s, const double* xyz) {
+    if (!s || !xyz) return fail(LBKS_EINVAL, "null argument");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: move atoms with lbks_batch_set_geometry");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    const int na = (int)s->Z[0].size();
+    int rc = check_atoms(s, na, xyz, s->Z[0].data());
+    if (rc != LBKS_OK) return rc;
+    s->xyz[0].assign(xyz, xyz + 3 * na);
+    std::vector<double> atoms;
+    std::vector<int> counts;
+    pack_atoms(s, atoms, counts);
+    cudaStream_t st = s->st;
+    host_active(s)[0] = 1;
+    cudaError_t e = cudaMemcpyAsync(s->atoms, atoms.data(), sizeof(double) * atoms.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_vext(s->g, s->h, s->counts, s->atoms, s->a, s->vext, 1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host atom array is a temporary
+    if (e != cudaSuccess) return cuda_fail(e, "lbks_move_atoms");
+    rc = upload_active(s, st);
+    if (rc != LBKS_OK) return rc;
+    return evaluate(s, st, 1);  // potential of the current orbitals at the new nuclei, unmixed
+}
+
+int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step, void* stream, lbks_result* out,
+                        double* xyz_out, int* steps_out) {
+    if (!s || max_steps < 0 || !(fmax > 0.0) || !(step > 0.0)) return fail(LBKS_EINVAL, "bad argument");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: one geometry per handle");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    const int na = (int)s->Z[0].size();
+    lbks_result res;
+    int total_cycles = 0, total_steps = 0, total_iters = 0;
+    double total_wall = 0.0;
+    auto solve = [&](lbks_result* r) {
+        const int code = lbks_scf(s, stream, r);
+        total_cycles += r->cycles;
+        total_steps += r->steps;
+        total_iters += r->poisson_iters;
+        total_wall += r->wall_s;
+        return code;
+    };
+    int rc = solve(&res);
+    if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
+    std::vector<double> R = s->xyz[0], F(3 * na), trial(3 * na);
+    rc = lbks_forces(s, F.data(), F.size());
+    if (rc != LBKS_OK) return rc;
+    double E = res.E_total, alpha = step;
+    int steps = 0, accepted = 0;
+    bool at_R = true, done = false;
+    auto fmax_of = [&](const std::vector<double>& f) {
+        double m = 0.0;
+        for (int a = 0; a < na; ++a)
+            m = std::max(m, std::sqrt(f[3 * a] * f[3 * a] + f[3 * a + 1] * f[3 * a + 1] + f[3 * a + 2] * f[3 * a + 2]));
+        return m;
+    };
+    while (steps < max_steps) {
+        if (fmax_of(F) < fmax) {
+            done = true;
+            break;
+        }
+        ++steps;
+        // steepest descent, no nucleus moved more than 0.2 bohr
+        double scale = alpha;
+        const double fm = fmax_of(F);
+        if (alpha * fm > 0.2) scale = 0.2 / fm;
+        for (int k = 0; k < 3 * na; ++k) trial[k] = R[k] + scale * F[k];
+        rc = lbks_move_atoms(s, trial.data());
+        if (rc != LBKS_OK) return rc;
+        lbks_result tr;
+        rc = solve(&tr);
+        if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
+        if (tr.E_total < E) {  // accept, and lengthen the step
+            R = trial;
+            E = tr.E_total;
+            res = tr;
+            rc = lbks_forces(s, F.data(), F.size());
+            if (rc != LBKS_OK) return rc;
+            alpha *= 1.25;
+            at_R = true;
+            ++accepted;
+        } else {  // reject, and halve it
+            alpha *= 0.5;
+            at_R = false;
+        }
+    }
+    if (!at_R) {  // leave the handle at the returned geometry, relaxed there
+        rc = lbks_move_atoms(s, R.data());
+        if (rc == LBKS_OK) rc = solve(&res);
+        if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
+        rc = lbks_forces(s, F.data(), F.size());
+        if (rc != LBKS_OK) return rc;
+        if (fmax_of(F) < fmax) done = true;
+    }
+    res.cycles = total_cycles;
+    res.steps = total_steps;
+    res.poisson_iters = total_iters;
+    res.wall_s = total_wall;
+    if (out) *out = res;
+    if (xyz_out) std::copy(R.begin(), R.end(), xyz_out);
+    if (steps_out) *steps_out = steps;
+    (void)accepted;
+    if (!done) return fail(LBKS_ENOTCONV, "largest force %.3e Ha/bohr after %d steps", fmax_of(F), steps);
+    return LBKS_OK;
+}
 
 int lbks_batch_get_density(const lbks_system* s, int system, double* host, size_t cap) {
     if (!s || !host) return fail(LBKS_EINVAL, "null argument");

@@ -55,6 +55,63 @@ __global__ void __launch_bounds__(kThreads) k_vext(Grid g, double h, const int* 
     }
 }
 
+// ------------------------------------------------------- Hellmann-Feynman forces
+// Electron-nucleus part of the force on each nucleus at the density rho,
+// F_I = Z_I h^3 sum_r rho(r) (r - R_I) / (|r - R_I|^2 + a^2)^(3/2)
+// (minus the derivative of h^3 sum rho V_ext with respect to R_I).  Nuclei in
+// chunks of kForceChunk, one pass over rho per chunk; per-thread FP64 sums,
+// block sums into a flat partial array (row pitch kp = 3 * nuclei rounded up
+// to whole chunks), the last block sums the rows in a fixed order and writes
+// out[3 I + c] (times h^3).
+constexpr int kForceChunk = 8;
+
+__host__ __device__ inline int force_pitch(int n_atoms) {
+    return 3 * ((n_atoms + kForceChunk - 1) / kForceChunk) * kForceChunk;
+}
+
+__global__ void __launch_bounds__(kThreads) k_forces(Grid g, double h, const int* __restrict__ counts,
+                                                     const double* __restrict__ atoms, double a2,
+                                                     const double* __restrict__ rho, double* __restrict__ out,
+                                                     Scratch sc) {
+    if (inactive(g)) return;
+    const int na = counts[sys_id()];
+    const int kp = force_pitch(na);
+    atoms += (size_t)sys_id() * kMaxAtoms * 4;
+    rho += (size_t)sys_id() * g.N;
+    out += (size_t)sys_id() * 3 * kMaxAtoms;
+    double* partial = sys_partial(sc);
+    for (int a0 = 0; a0 < na; a0 += kForceChunk) {
+        double acc[3 * kForceChunk];
+#pragma unroll
+        for (int k = 0; k < 3 * kForceChunk; ++k) acc[k] = 0.0;
+        for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+            int x, y, z;
+            double rx, ry, rz;
+            coords(g, h, s, x, y, z, rx, ry, rz);
+            const double r = rho[s];
+#pragma unroll
+            for (int c = 0; c < kForceChunk; ++c) {
+                const int I = a0 + c;
+                if (I >= na) break;
+                const double dx = rx - atoms[4 * I], dy = ry - atoms[4 * I + 1], dz = rz - atoms[4 * I + 2];
+                const double d2 = dx * dx + dy * dy + dz * dz + a2;
+                const double w = r * atoms[4 * I + 3] / (d2 * sqrt(d2));
+                acc[3 * c] += w * dx;
+                acc[3 * c + 1] += w * dy;
+                acc[3 * c + 2] += w * dz;
+            }
+        }
+        block_sum_store<3 * kForceChunk>(acc, partial + (size_t)blockIdx.x * kp + 3 * a0);
+        __syncthreads();  // the block sums' shared rows are reused by the next chunk
+    }
+    __shared__ double tot[3 * kMaxAtoms];
+    if (grid_total_rt(partial, sys_counter(sc), tot, kp)) {
+        const double h3 = h * h * h;
+        for (int k = threadIdx.x; k < 3 * na; k += blockDim.x) out[k] = h3 * tot[k];
+    }
+}
+
+
 // --------------------------------------------------------------------- Cholesky
 // S = L L^T (one CTA), then L^{-1} by forward substitution, one column per thread.
 __global__ void k_cholesky(int n, const double* __restrict__ S, double* __restrict__ Linv, int* status,
@@ -219,6 +276,18 @@ __global__ void __launch_bounds__(kThreads) k_multipoles(Grid g, double h, const
 }  // namespace
 
 // ---------------------------------------------------------------------- launchers
+cudaError_t launch_forces(const Grid& g, double h, const int* counts, const double* atoms, double a, const double* rho,
+                          double* out, int max_atoms, const Scratch& sc, int B, cudaStream_t st) {
+    if (max_atoms < 1 || max_atoms > kMaxAtoms || sc.systems < B) return cudaErrorInvalidValue;
+    // every block's row of the flat partial array fits the system's scratch region
+    const int rows = (int)std::min<size_t>((size_t)sc.max_blocks * sc.max_vals / force_pitch(max_atoms),
+                                           (size_t)num_sms() * 2 / std::max(B, 1));
+    if (rows < 1) return cudaErrorInvalidValue;
+    k_forces<<<dim3(grid_for(g.N, rows), B), kThreads, 0, st>>>(g, h, counts, atoms, a * a, rho, out, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vext(const Grid& g, double h, const int* counts, const double* atoms, double a, double* v, int B,
                         cudaStream_t st) {
     k_vext<<<dim3(grid_for(g.N, std::max(1, num_sms() * 8 / B)), B), kThreads, 0, st>>>(g, h, counts, atoms, a * a, v);

@@ -194,6 +194,10 @@ constexpr int kMaxAtoms = 256;
 // counts[B] atoms per system, atoms[B][kMaxAtoms][4] = (x, y, z, Z)
 cudaError_t launch_vext(const Grid&, double h, const int* counts, const double* atoms, double a, double* v, int B,
                         cudaStream_t);
+// Electron-nucleus Hellmann-Feynman forces at density rho: out[B][kMaxAtoms][3]
+// (rows 0 .. counts[b] - 1 written); max_atoms bounds counts[].
+cudaError_t launch_forces(const Grid&, double h, const int* counts, const double* atoms, double a, const double* rho,
+                          double* out, int max_atoms, const Scratch& sc, int B, cudaStream_t);
 cudaError_t launch_cholesky(int n, const double* S, double* Linv, int* status, const int* active, int B,
                             cudaStream_t);
 cudaError_t launch_fill(double* p, size_t n, double value, cudaStream_t);

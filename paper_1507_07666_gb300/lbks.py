@@ -90,6 +90,10 @@ _SIGS = {
     "lbks_scf": (_i, [_vp, _vp, ctypes.POINTER(lbks_result)]),
     "lbks_scf_cycles": (_i, [_vp, _i, _vp, ctypes.POINTER(lbks_result)]),
     "lbks_energy": (_i, [_vp, ctypes.POINTER(lbks_energy_terms)]),
+    "lbks_forces": (_i, [_vp, _dp, _sz]),
+    "lbks_batch_forces": (_i, [_vp, _i, _dp, _sz]),
+    "lbks_move_atoms": (_i, [_vp, _dp]),
+    "lbks_relax_geometry": (_i, [_vp, _i, _d, _d, _vp, ctypes.POINTER(lbks_result), _dp, ctypes.POINTER(_i)]),
     "lbks_get_density": (_i, [_vp, _dp, _sz]),
     "lbks_get_orbitals": (_i, [_vp, _dp, _sz]),
     "lbks_get_potential": (_i, [_vp, _i, _dp, _sz]),
@@ -231,6 +235,36 @@ def lbks_energy(handle, n_orb=MAX_ORB) -> dict:
     return {"T_s": t.T_s, "E_ext": t.E_ext, "E_H": t.E_H, "E_xc": t.E_xc, "E_nn": t.E_nn,
             "E_total": t.E_total, "eigenvalues": np.array(t.eigenvalues[:n_orb]),
             "orbital_energies": np.array(t.orbital_energies[:n_orb]), "n_electrons": t.n_electrons}
+
+
+def lbks_forces(handle, n_atoms):
+    out = np.empty((n_atoms, 3), dtype=np.float64)
+    _check(_lib.lbks_forces(handle, out.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def lbks_batch_forces(handle, system, n_atoms):
+    out = np.empty((n_atoms, 3), dtype=np.float64)
+    _check(_lib.lbks_batch_forces(handle, system, out.ctypes.data_as(_dp), out.size))
+    return out
+
+
+def lbks_move_atoms(handle, xyz):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    _check(_lib.lbks_move_atoms(handle, xyz.ctypes.data_as(_dp)))
+
+
+def lbks_relax_geometry(handle, n_atoms, max_steps, fmax, step, stream=None, n_orb=MAX_ORB, allow_notconv=False):
+    r = lbks_result()
+    xyz = np.empty((n_atoms, 3), dtype=np.float64)
+    steps = ctypes.c_int()
+    code = _lib.lbks_relax_geometry(handle, max_steps, fmax, step, _stream(stream), ctypes.byref(r),
+                                    xyz.ctypes.data_as(_dp), ctypes.byref(steps))
+    if code != OK and not (allow_notconv and code == ENOTCONV):
+        _check(code)
+    out = _result_dict(r, n_orb)
+    out.update({"xyz": xyz, "moves": steps.value, "relaxed": code == OK})
+    return out
 
 
 def lbks_get_density(handle, shape):
@@ -505,6 +539,17 @@ class System:
 
     def set_geometry(self, xyz, Z):
         lbks_set_geometry(self.handle, xyz, Z)
+        self.n_atoms = len(np.ravel(Z))
+
+    def forces(self):
+        return lbks_forces(self.handle, self.n_atoms)
+
+    def move_atoms(self, xyz):
+        lbks_move_atoms(self.handle, xyz)
+
+    def relax_geometry(self, max_steps=50, fmax=1e-3, step=0.5, stream=None, allow_notconv=False):
+        return lbks_relax_geometry(self.handle, self.n_atoms, max_steps, fmax, step, stream, self.n_orb,
+                                   allow_notconv)
 
     def scf(self, stream=None, allow_notconv=False):
         return lbks_scf(self.handle, stream, self.n_orb, allow_notconv)
