@@ -234,12 +234,13 @@ int lbks_batch_forces(lbks_system* sys, int system, double* forces, size_t cap);
 int lbks_move_atoms(lbks_system* sys, const double* xyz);
 
 /* Born-Oppenheimer geometry relaxation of a single-system handle: SCF, forces,
- * then steepest-descent moves R <- R + alpha F (no nucleus moved more than
- * 0.2 bohr per move), each followed by a warm-started SCF; a move that lowers
- * E_total is kept and alpha grows by 1.25, otherwise it is undone and alpha
- * halves.  Stops when the largest |F_I| < fmax (Ha/bohr): LBKS_OK; after
- * max_steps moves: LBKS_ENOTCONV with the results filled.  step: the initial
- * alpha (bohr^2/Ha).  out: the SCF result at the returned geometry, with
+ * then quasi-Newton moves R <- R + alpha H F (H: BFGS estimate of the inverse
+ * Hessian, starting from step * I; no nucleus moved more than 0.2 bohr per
+ * move), each followed by a warm-started SCF.  A move that lowers E_total is
+ * kept (H updated from the change of R and F, alpha back towards 1);
+ * otherwise it is undone and alpha halves.  Stops when the largest
+ * |F_I| < fmax (Ha/bohr): LBKS_OK; after max_steps moves: LBKS_ENOTCONV with
+ * the results filled.  step: the initial inverse-Hessian scale (bohr^2/Ha).  out: the SCF result at the returned geometry, with
  * cycles, steps, poisson_iters and wall_s summed over every SCF run; xyz_out:
  * 3 * n_atoms doubles (may be NULL); steps_out: moves tried (may be NULL).
  * The handle is left at the returned geometry, relaxed there. */

@@ -1130,9 +1130,13 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     std::vector<double> R = s->xyz[0], F(3 * na), trial(3 * na);
     rc = lbks_forces(s, F.data(), F.size());
     if (rc != LBKS_OK) return rc;
-    double E = res.E_total, alpha = step;
+    double E = res.E_total, alpha = 1.0;
     int steps = 0, accepted = 0;
     bool at_R = true, done = false;
+    // inverse Hessian estimate (BFGS), starting from step * identity
+    const int n3 = 3 * na;
+    std::vector<double> Hi((size_t)n3 * n3, 0.0), p(n3), Fnew(n3), hy(n3);
+    for (int k = 0; k < n3; ++k) Hi[(size_t)k * n3 + k] = step;
     auto fmax_of = [&](const std::vector<double>& f) {
         double m = 0.0;
         for (int a = 0; a < na; ++a)
@@ -1145,26 +1149,60 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
             break;
         }
         ++steps;
-        // steepest descent, no nucleus moved more than 0.2 bohr
-        double scale = alpha;
-        const double fm = fmax_of(F);
-        if (alpha * fm > 0.2) scale = 0.2 / fm;
-        for (int k = 0; k < 3 * na; ++k) trial[k] = R[k] + scale * F[k];
+        // quasi-Newton direction p = Hi F; no nucleus moved more than 0.2 bohr
+        double pf = 0.0;
+        for (int i = 0; i < n3; ++i) {
+            double t = 0.0;
+            for (int k = 0; k < n3; ++k) t += Hi[(size_t)i * n3 + k] * F[k];
+            p[i] = t;
+            pf += t * F[i];
+        }
+        if (!(pf > 0.0)) {  // not a descent direction: start the estimate again
+            for (int i = 0; i < n3; ++i)
+                for (int k = 0; k < n3; ++k) Hi[(size_t)i * n3 + k] = i == k ? step : 0.0;
+            for (int i = 0; i < n3; ++i) p[i] = step * F[i];
+        }
+        double pm = 0.0;
+        for (int a = 0; a < na; ++a)
+            pm = std::max(pm, std::sqrt(p[3 * a] * p[3 * a] + p[3 * a + 1] * p[3 * a + 1] + p[3 * a + 2] * p[3 * a + 2]));
+        const double scale = alpha * pm > 0.2 ? 0.2 / pm : alpha;
+        for (int k = 0; k < n3; ++k) trial[k] = R[k] + scale * p[k];
         rc = lbks_move_atoms(s, trial.data());
         if (rc != LBKS_OK) return rc;
         lbks_result tr;
         rc = solve(&tr);
         if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
-        if (tr.E_total < E) {  // accept, and lengthen the step
-            R = trial;
+        if (tr.E_total < E) {  // accept; update the inverse Hessian with s = dR, y = -dF
+            rc = lbks_forces(s, Fnew.data(), Fnew.size());
+            if (rc != LBKS_OK) return rc;
+            double sy = 0.0;
+            for (int k = 0; k < n3; ++k) {
+                trial[k] -= R[k];           // s
+                p[k] = F[k] - Fnew[k];      // y (gradient change)
+                sy += trial[k] * p[k];
+            }
+            if (sy > 1e-12) {  // curvature condition: H+ = (I - r s y^T) H (I - r y s^T) + r s s^T, r = 1 / s.y
+                double yhy = 0.0;
+                for (int i = 0; i < n3; ++i) {
+                    double t = 0.0;
+                    for (int k = 0; k < n3; ++k) t += Hi[(size_t)i * n3 + k] * p[k];
+                    hy[i] = t;
+                    yhy += p[i] * t;
+                }
+                const double r = 1.0 / sy;
+                for (int i = 0; i < n3; ++i)
+                    for (int k = 0; k < n3; ++k)
+                        Hi[(size_t)i * n3 + k] += (1.0 + r * yhy) * r * trial[i] * trial[k] -
+                                                  r * (hy[i] * trial[k] + trial[i] * hy[k]);
+            }
+            for (int k = 0; k < n3; ++k) R[k] += trial[k];
+            F = Fnew;
             E = tr.E_total;
             res = tr;
-            rc = lbks_forces(s, F.data(), F.size());
-            if (rc != LBKS_OK) return rc;
-            alpha *= 1.25;
+            alpha = std::min(1.0, alpha * 2.0);
             at_R = true;
             ++accepted;
-        } else {  // reject, and halve it
+        } else {  // undo, and halve the step along the same direction next time
             alpha *= 0.5;
             at_R = false;
         }

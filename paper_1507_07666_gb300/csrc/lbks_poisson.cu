@@ -273,12 +273,17 @@ __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scr
     }
 }
 
-// p = z + beta p
+// p = z + beta p; p = z on the first iteration of a solve (p is not read
+// then: it holds whatever the memory held, and 0 * NaN is NaN)
 __global__ void __launch_bounds__(kThreads) k_pcg_dir(Grid g, PoissonBufs pb) {
     if (inactive(g)) return;
     pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
     const double beta = pb.cg->beta;
+    if (pb.cg->iters == 0) {
+        for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) pb.p[s] = pb.z[s];
+        return;
+    }
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
         pb.p[s] = pb.z[s] + beta * pb.p[s];
 }

@@ -45,6 +45,29 @@ def test_hartree_reports_non_convergence():
     assert e.value.code == lbks.ENOTCONV
 
 
+def test_hartree_ignores_an_earlier_solves_direction():
+    """The first PCG direction is the preconditioned residual itself.  A
+    direction left non-finite in the shared scratch by an earlier solve (a NaN
+    density, stopped after two iterations) must not leak into the next one:
+    p = z + 0 * p would be NaN."""
+    torch, lbks = require_gpu()
+    n, h = (22, 18, 20), 0.45
+    nx, ny, nz = n
+    X, Y, Z = poisson.coords(n, h)
+    rho = np.exp(-(X * X + 0.5 * Y * Y + (Z - 0.3) ** 2))
+    stream = torch.cuda.Stream()  # one workspace for both solves
+    bad = torch.full((nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda")
+    v = torch.zeros_like(bad)
+    with pytest.raises(lbks.LbksError):
+        lbks.lbks_hartree(nx, ny, nz, h, bad, v, rtol=1e-12, max_iter=2, stream=stream)
+    v.zero_()
+    it, rr = lbks.lbks_hartree(nx, ny, nz, h, to_dev(torch, rho, torch.float64), v, rtol=1e-12, stream=stream)
+    stream.synchronize()
+    ref, _, _ = poisson.hartree(rho, h, rtol=1e-13)
+    assert rr <= 1e-12 and np.isfinite(to_np(v)).all()
+    assert rel_err(to_np(v), ref) < 1e-9
+
+
 def test_lda_matches_oracle():
     torch, lbks = require_gpu()
     rng = np.random.default_rng(0)
