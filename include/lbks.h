@@ -240,12 +240,14 @@ int lbks_move_atoms(lbks_system* sys, const double* xyz);
  * kept (H updated from the change of R and F, alpha back towards 1);
  * otherwise it is undone and alpha halves.  Stops when the largest
  * |F_I| < fmax (Ha/bohr): LBKS_OK; after max_steps moves: LBKS_ENOTCONV with
- * the results filled.  step: the initial inverse-Hessian scale (bohr^2/Ha).  out: the SCF result at the returned geometry, with
+ * the results filled.  step: the initial inverse-Hessian scale (bohr^2/Ha).
+ * fixed: n_atoms flags (non-zero: the nucleus stays where it is and its force
+ * is not counted), or NULL for none.  out: the SCF result at the returned geometry, with
  * cycles, steps, poisson_iters and wall_s summed over every SCF run; xyz_out:
  * 3 * n_atoms doubles (may be NULL); steps_out: moves tried (may be NULL).
  * The handle is left at the returned geometry, relaxed there. */
-int lbks_relax_geometry(lbks_system* sys, int max_steps, double fmax, double step, void* stream,
-                        lbks_result* out, double* xyz_out, int* steps_out);
+int lbks_relax_geometry(lbks_system* sys, int max_steps, double fmax, double step, const int* fixed,
+                        void* stream, lbks_result* out, double* xyz_out, int* steps_out);
 
 /* Host copies (synchronous) of the last evaluation's density rho (N doubles),
  * orthonormal orbitals (n_orb*N doubles) and potentials (N doubles each).

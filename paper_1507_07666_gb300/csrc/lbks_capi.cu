@@ -1108,8 +1108,8 @@ int lbks_move_atoms(lbks_system* s, const double* xyz) {
     return evaluate(s, st, 1);  // potential of the current orbitals at the new nuclei, unmixed
 }
 
-int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step, void* stream, lbks_result* out,
-                        double* xyz_out, int* steps_out) {
+int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step, const int* fixed, void* stream,
+                        lbks_result* out, double* xyz_out, int* steps_out) {
     if (!s || max_steps < 0 || !(fmax > 0.0) || !(step > 0.0)) return fail(LBKS_EINVAL, "bad argument");
     if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: one geometry per handle");
     if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
@@ -1128,7 +1128,15 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     int rc = solve(&res);
     if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
     std::vector<double> R = s->xyz[0], F(3 * na), trial(3 * na);
-    rc = lbks_forces(s, F.data(), F.size());
+    // forces with the fixed nuclei's rows zeroed (they neither move nor count for convergence)
+    auto free_forces = [&](std::vector<double>& f) {
+        const int code = lbks_forces(s, f.data(), f.size());
+        if (code == LBKS_OK && fixed)
+            for (int a = 0; a < na; ++a)
+                if (fixed[a]) f[3 * a] = f[3 * a + 1] = f[3 * a + 2] = 0.0;
+        return code;
+    };
+    rc = free_forces(F);
     if (rc != LBKS_OK) return rc;
     double E = res.E_total, alpha = 1.0;
     int steps = 0, accepted = 0;
@@ -1173,7 +1181,7 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
         rc = solve(&tr);
         if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
         if (tr.E_total < E) {  // accept; update the inverse Hessian with s = dR, y = -dF
-            rc = lbks_forces(s, Fnew.data(), Fnew.size());
+            rc = free_forces(Fnew);
             if (rc != LBKS_OK) return rc;
             double sy = 0.0;
             for (int k = 0; k < n3; ++k) {
@@ -1211,7 +1219,7 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
         rc = lbks_move_atoms(s, R.data());
         if (rc == LBKS_OK) rc = solve(&res);
         if (rc != LBKS_OK && rc != LBKS_ENOTCONV) return rc;
-        rc = lbks_forces(s, F.data(), F.size());
+        rc = free_forces(F);
         if (rc != LBKS_OK) return rc;
         if (fmax_of(F) < fmax) done = true;
     }

@@ -93,7 +93,8 @@ _SIGS = {
     "lbks_forces": (_i, [_vp, _dp, _sz]),
     "lbks_batch_forces": (_i, [_vp, _i, _dp, _sz]),
     "lbks_move_atoms": (_i, [_vp, _dp]),
-    "lbks_relax_geometry": (_i, [_vp, _i, _d, _d, _vp, ctypes.POINTER(lbks_result), _dp, ctypes.POINTER(_i)]),
+    "lbks_relax_geometry": (_i, [_vp, _i, _d, _d, ctypes.POINTER(_i), _vp, ctypes.POINTER(lbks_result), _dp,
+                                 ctypes.POINTER(_i)]),
     "lbks_get_density": (_i, [_vp, _dp, _sz]),
     "lbks_get_orbitals": (_i, [_vp, _dp, _sz]),
     "lbks_get_potential": (_i, [_vp, _i, _dp, _sz]),
@@ -254,11 +255,15 @@ def lbks_move_atoms(handle, xyz):
     _check(_lib.lbks_move_atoms(handle, xyz.ctypes.data_as(_dp)))
 
 
-def lbks_relax_geometry(handle, n_atoms, max_steps, fmax, step, stream=None, n_orb=MAX_ORB, allow_notconv=False):
+def lbks_relax_geometry(handle, n_atoms, max_steps, fmax, step, stream=None, n_orb=MAX_ORB, allow_notconv=False,
+                        fixed=None):
     r = lbks_result()
     xyz = np.empty((n_atoms, 3), dtype=np.float64)
     steps = ctypes.c_int()
-    code = _lib.lbks_relax_geometry(handle, max_steps, fmax, step, _stream(stream), ctypes.byref(r),
+    fx = None
+    if fixed is not None:
+        fx = (ctypes.c_int * n_atoms)(*[1 if f else 0 for f in fixed])
+    code = _lib.lbks_relax_geometry(handle, max_steps, fmax, step, fx, _stream(stream), ctypes.byref(r),
                                     xyz.ctypes.data_as(_dp), ctypes.byref(steps))
     if code != OK and not (allow_notconv and code == ENOTCONV):
         _check(code)
@@ -547,9 +552,9 @@ class System:
     def move_atoms(self, xyz):
         lbks_move_atoms(self.handle, xyz)
 
-    def relax_geometry(self, max_steps=50, fmax=1e-3, step=0.5, stream=None, allow_notconv=False):
+    def relax_geometry(self, max_steps=50, fmax=1e-3, step=0.5, stream=None, allow_notconv=False, fixed=None):
         return lbks_relax_geometry(self.handle, self.n_atoms, max_steps, fmax, step, stream, self.n_orb,
-                                   allow_notconv)
+                                   allow_notconv, fixed)
 
     def scf(self, stream=None, allow_notconv=False):
         return lbks_scf(self.handle, stream, self.n_orb, allow_notconv)

@@ -101,6 +101,20 @@ def test_relax_geometry_finds_the_oracle_force_zero():
     s.close()
 
 
+def test_relax_geometry_keeps_fixed_nuclei():
+    """One H2 nucleus fixed: it does not move, the other relaxes to zero force."""
+    torch, lbks = require_gpu()
+    s = lbks.System(H2_GRID, H2_H, 1, precision=0, n_inner=30, e_tol=1e-9)
+    xyz, Z = _h2(1.1)
+    s.set_geometry(xyz, Z)
+    r = s.relax_geometry(max_steps=40, fmax=1e-3, step=1.0, fixed=[1, 0])
+    assert r["relaxed"]
+    np.testing.assert_array_equal(r["xyz"][0], xyz[0])
+    F = s.forces()
+    assert np.linalg.norm(F[1]) < 1e-3 and np.linalg.norm(F[0]) > 1e-3  # the held nucleus still feels a force
+    s.close()
+
+
 def test_force_and_move_errors():
     torch, lbks = require_gpu()
     s = lbks.System(H2_GRID, H2_H, 1, precision=0)
