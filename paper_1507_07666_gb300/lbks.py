@@ -515,6 +515,9 @@ class Batch:
     def density(self, i):
         return lbks_batch_get_density(self.handle, i, self.grid_shape)
 
+    def forces(self, i, n_atoms):
+        return lbks_batch_forces(self.handle, i, n_atoms)
+
     def close(self):
         if self.handle is not None:
             lbks_destroy_system(self.handle)

@@ -37,6 +37,20 @@ def test_forces_match_the_oracle_at_the_solver_density(prec, waters):
     s.close()
 
 
+def test_batch_forces_match_the_oracle_per_system():
+    """Every system of a batch, converged or still running, at its own density."""
+    torch, lbks = require_gpu()
+    n, h = (28, 26, 30), 0.4
+    mols = W.water_scan(3, 5)
+    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=10)
+    b.set_geometries([(m.xyz, m.Z) for m in mols])
+    b.scf_cycles(1)
+    for i, m in enumerate(mols):
+        ref = forces.hf_forces(b.density(i), h, m.xyz, m.Z, h)
+        np.testing.assert_allclose(b.forces(i, len(m.Z)), ref, rtol=1e-10, atol=1e-11 * np.abs(ref).max())
+    b.close()
+
+
 def test_forces_follow_the_oracle_scf():
     """Three fixed cycles of H2 in FP64 on both sides: same density, same forces."""
     torch, lbks = require_gpu()
