@@ -233,6 +233,19 @@ int lbks_batch_forces(lbks_system* sys, int system, double* forces, size_t cap);
  * (EINVAL otherwise).  Synchronous. */
 int lbks_move_atoms(lbks_system* sys, const double* xyz);
 
+/* Born-Oppenheimer molecular dynamics of a single-system handle (the nuclei
+ * moved on the SCF ground-state surface, Sec. 3.1): velocity Verlet,
+ *   R <- R + dt v + dt^2 F / (2 m),  SCF at R (warm start),  v <- v + dt (F + F') / (2 m),
+ * with the Hellmann-Feynman forces of lbks_forces.  Atomic units: dt in
+ * hbar/Ha, masses in electron masses (n_atoms doubles), velocities in
+ * bohr hbar^-1 Ha (3 n_atoms, in: initial, out: final).  energies (may be
+ * NULL): (n_steps + 1) x 2 doubles, E_total of the electrons and nuclei and
+ * the nuclear kinetic energy at each step (step 0: the start).  xyz_traj (may
+ * be NULL): (n_steps + 1) x 3 n_atoms positions.  Every step's SCF must
+ * converge (LBKS_ENOTCONV otherwise, the arrays filled up to that step). */
+int lbks_md(lbks_system* sys, int n_steps, double dt, const double* masses, double* velocities, void* stream,
+            double* energies, double* xyz_traj);
+
 /* Born-Oppenheimer geometry relaxation of a single-system handle: SCF, forces,
  * then quasi-Newton moves R <- R + alpha H F (H: BFGS estimate of the inverse
  * Hessian, starting from step * I; no nucleus moved more than 0.2 bohr per

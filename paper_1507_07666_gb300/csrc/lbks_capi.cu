@@ -1108,6 +1108,52 @@ int lbks_move_atoms(lbks_system* s, const double* xyz) {
     return evaluate(s, st, 1);  // potential of the current orbitals at the new nuclei, unmixed
 }
 
+int lbks_md(lbks_system* s, int n_steps, double dt, const double* masses, double* velocities, void* stream,
+            double* energies, double* xyz_traj) {
+    if (!s || n_steps < 0 || !(dt > 0.0) || !masses || !velocities) return fail(LBKS_EINVAL, "bad argument");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: one geometry per handle");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    const int na = (int)s->Z[0].size();
+    for (int a = 0; a < na; ++a)
+        if (!(masses[a] > 0.0)) return fail(LBKS_EINVAL, "mass %d must be positive", a);
+    std::vector<double> R = s->xyz[0], F(3 * na), Fn(3 * na);
+    lbks_result res;
+    auto record = [&](int k) {
+        double ek = 0.0;
+        for (int a = 0; a < na; ++a)
+            for (int c = 0; c < 3; ++c) ek += 0.5 * masses[a] * velocities[3 * a + c] * velocities[3 * a + c];
+        if (energies) {
+            energies[2 * k] = res.E_total;
+            energies[2 * k + 1] = ek;
+        }
+        if (xyz_traj) std::copy(R.begin(), R.end(), xyz_traj + (size_t)k * 3 * na);
+    };
+    int rc = lbks_scf(s, stream, &res);
+    if (rc != LBKS_OK) return rc;
+    rc = lbks_forces(s, F.data(), F.size());
+    if (rc != LBKS_OK) return rc;
+    record(0);
+    for (int k = 1; k <= n_steps; ++k) {  // velocity Verlet
+        for (int a = 0; a < na; ++a)
+            for (int c = 0; c < 3; ++c) {
+                const int i = 3 * a + c;
+                R[i] += dt * velocities[i] + 0.5 * dt * dt * F[i] / masses[a];
+            }
+        rc = lbks_move_atoms(s, R.data());
+        if (rc == LBKS_OK) rc = lbks_scf(s, stream, &res);
+        if (rc == LBKS_OK) rc = lbks_forces(s, Fn.data(), Fn.size());
+        if (rc != LBKS_OK) return rc;
+        for (int a = 0; a < na; ++a)
+            for (int c = 0; c < 3; ++c) {
+                const int i = 3 * a + c;
+                velocities[i] += 0.5 * dt * (F[i] + Fn[i]) / masses[a];
+            }
+        F = Fn;
+        record(k);
+    }
+    return LBKS_OK;
+}
+
 int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step, const int* fixed, void* stream,
                         lbks_result* out, double* xyz_out, int* steps_out) {
     if (!s || max_steps < 0 || !(fmax > 0.0) || !(step > 0.0)) return fail(LBKS_EINVAL, "bad argument");

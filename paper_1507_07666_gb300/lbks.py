@@ -93,6 +93,7 @@ _SIGS = {
     "lbks_forces": (_i, [_vp, _dp, _sz]),
     "lbks_batch_forces": (_i, [_vp, _i, _dp, _sz]),
     "lbks_move_atoms": (_i, [_vp, _dp]),
+    "lbks_md": (_i, [_vp, _i, _d, _dp, _dp, _vp, _dp, _dp]),
     "lbks_relax_geometry": (_i, [_vp, _i, _d, _d, ctypes.POINTER(_i), _vp, ctypes.POINTER(lbks_result), _dp,
                                  ctypes.POINTER(_i)]),
     "lbks_get_density": (_i, [_vp, _dp, _sz]),
@@ -253,6 +254,17 @@ def lbks_batch_forces(handle, system, n_atoms):
 def lbks_move_atoms(handle, xyz):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
     _check(_lib.lbks_move_atoms(handle, xyz.ctypes.data_as(_dp)))
+
+
+def lbks_md(handle, n_steps, dt, masses, velocities, stream=None):
+    """Returns (velocities after, energies [n_steps + 1, 2], positions [n_steps + 1, n_atoms, 3])."""
+    masses = np.ascontiguousarray(masses, dtype=np.float64).ravel()
+    v = np.ascontiguousarray(velocities, dtype=np.float64).reshape(-1, 3).copy()
+    e = np.empty((n_steps + 1, 2), dtype=np.float64)
+    traj = np.empty((n_steps + 1, len(masses), 3), dtype=np.float64)
+    _check(_lib.lbks_md(handle, n_steps, dt, masses.ctypes.data_as(_dp), v.ctypes.data_as(_dp), _stream(stream),
+                        e.ctypes.data_as(_dp), traj.ctypes.data_as(_dp)))
+    return v, e, traj
 
 
 def lbks_relax_geometry(handle, n_atoms, max_steps, fmax, step, stream=None, n_orb=MAX_ORB, allow_notconv=False,
@@ -554,6 +566,9 @@ class System:
 
     def move_atoms(self, xyz):
         lbks_move_atoms(self.handle, xyz)
+
+    def md(self, n_steps, dt, masses, velocities, stream=None):
+        return lbks_md(self.handle, n_steps, dt, masses, velocities, stream)
 
     def relax_geometry(self, max_steps=50, fmax=1e-3, step=0.5, stream=None, allow_notconv=False, fixed=None):
         return lbks_relax_geometry(self.handle, self.n_atoms, max_steps, fmax, step, stream, self.n_orb,

@@ -87,3 +87,24 @@ def test_hf_force_matches_the_scf_energy_difference_for_h2():
     assert abs(F[1, 0] - fd) <= 3e-3 * abs(fd), (F[1, 0], fd)
     np.testing.assert_allclose(F[0], -F[1], atol=1e-6)  # the two nuclei, mirror images
     assert np.abs(F[:, 1:]).max() < 1e-6
+
+
+def test_velocity_verlet_follows_the_harmonic_oscillator():
+    """F = -k x: the closed form x(t) = x0 cos(w t), w = sqrt(k/m), to
+    O(dt^2); the energy stays within O(dt^2) of its start; reversing the
+    final velocity retraces the path (time reversibility)."""
+    from oracle import md
+
+    k, m, x0, dt, n = 2.0, 3.0, 0.7, 0.01, 2000
+    w = np.sqrt(k / m)
+
+    def force(R):
+        return -k * R, 0.5 * k * float((R * R).sum())
+
+    R, v, e = md.velocity_verlet(force, np.array([[x0, 0.0, 0.0]]), np.zeros((1, 3)), [m], dt, n)
+    t = dt * np.arange(n + 1)
+    np.testing.assert_allclose(R[:, 0, 0], x0 * np.cos(w * t), atol=2e-4)
+    tot = e.sum(axis=1)
+    assert np.abs(tot - tot[0]).max() < 1e-4 * tot[0]
+    Rb, _, _ = md.velocity_verlet(force, R[-1], -v[-1], [m], dt, n)
+    np.testing.assert_allclose(Rb[-1], R[0], atol=1e-9)
