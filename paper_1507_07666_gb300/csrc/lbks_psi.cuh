@@ -187,13 +187,46 @@ __global__ void __launch_bounds__(kThreads, 3) k_relax_psi_wide(Grid g, Coef c, 
 constexpr int kTX = 32, kTY = 8, kTZ = 4;
 constexpr int kBX = kTX + 2, kBY = kTY + 2, kBZ = kTZ + 2, kBox = kBX * kBY * kBZ;
 
-template <typename T, int NO, bool BATCHED>
+// Box row layout.  Scalar staging: kBX values from x0 - 1.  Vector staging
+// (VEC: nx a multiple of 16 / sizeof(T), 16-byte aligned psi and Vc): the
+// tile's kTX values sit 16-byte aligned at column vpad<T>, the halo values
+// beside them, rows of kTX + 2 vpad<T> values; interior pieces are copied with
+// 16-byte loads and stores.
+template <typename T>
+__host__ __device__ constexpr int vpad() { return 16 / (int)sizeof(T); }
+template <typename T, bool VEC>
+__host__ __device__ constexpr int box_pitch() { return VEC ? kTX + 2 * vpad<T>() : kBX; }
+template <typename T, bool VEC>
+__host__ __device__ constexpr int box_size() { return box_pitch<T, VEC>() * kBY * kBZ; }
+
+// 16 bytes of T from global (read-only) to shared memory.
+template <typename T>
+__device__ __forceinline__ void copy16(T* dst, const T* src) {
+    *reinterpret_cast<float4*>(dst) = __ldg(reinterpret_cast<const float4*>(src));
+}
+// 16 / sizeof(T) values of Vc (FP64) as T.
+template <typename T>
+__device__ __forceinline__ void copy16_v(T* dst, const double* src) {
+    if constexpr (sizeof(T) == 8) {
+        *reinterpret_cast<double2*>(dst) = __ldg(reinterpret_cast<const double2*>(src));
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(src));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(src + 2));
+        *reinterpret_cast<float4*>(dst) = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void zero16(T* dst) { *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f); }
+
+template <typename T, int NO, bool BATCHED, bool VEC>
 __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
                                                                                          Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
     constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
+    constexpr int PX = box_pitch<T, VEC>(), BOX = box_size<T, VEC>();
+    constexpr int XO = VEC ? vpad<T>() : 1;  // column of the tile's first x
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* box = reinterpret_cast<T*>(smem_raw);  // [NO + 1][kBox]: psi_0 .. psi_{NO-1}, then Vc
+    T* box = reinterpret_cast<T*>(smem_raw);  // [NO + 1][BOX]: psi_0 .. psi_{NO-1}, then Vc
     if (BATCHED && inactive(g)) return;
     const uint32_t N = g.N;
     const size_t y = BATCHED ? sys_id() : 0;
@@ -222,34 +255,65 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
     const int ntiles = ntx * nty * ntz;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int bxi = tile % ntx, byi = (tile / ntx) % nty, bzi = tile / (ntx * nty);
-        const int x0 = bxi * kTX - 1, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;  // box origin (halo included)
+        const int xs = bxi * kTX, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;  // tile x start; box y, z origin
         __syncthreads();  // the previous tile's box is no longer read
-        for (int i = threadIdx.x; i < kBox; i += kThreads) {
-            const int bx = i % kBX, by = (i / kBX) % kBY, bz = i / (kBX * kBY);
-            const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
-            const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
-            const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+        if constexpr (VEC) {
+            constexpr int E = vpad<T>(), CH = kTX / E, ITEMS = CH + 2;  // 16-byte pieces and the two halo values
+            for (int i = threadIdx.x; i < kBY * kBZ * ITEMS; i += kThreads) {
+                const int row = i / ITEMS, k = i - row * ITEMS;
+                const int by = row % kBY, bz = row / kBY;
+                const int gy = y0 + by, gz = z0 + bz;
+                const bool rin = gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+                T* r = box + row * PX;
+                if (k < CH) {
+                    const int gx = xs + k * E;  // a whole piece is in or out: nx is a multiple of E
+                    const bool in = rin && gx < g.nx;
+                    const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
 #pragma unroll
-            for (int j = 0; j < NO; ++j) box[j * kBox + i] = in ? __ldg(pin + (size_t)j * N + gs) : T(0);
-            box[NO * kBox + i] = in ? (T)__ldg(Vc + gs) : T(0);
+                    for (int j = 0; j < NO; ++j) {
+                        if (in) copy16(r + j * BOX + XO + k * E, pin + (size_t)j * N + gs);
+                        else zero16(r + j * BOX + XO + k * E);
+                    }
+                    if (in) copy16_v(r + NO * BOX + XO + k * E, Vc + gs);
+                    else zero16(r + NO * BOX + XO + k * E);
+                } else {
+                    const int gx = k == CH ? xs - 1 : xs + kTX;
+                    const int col = k == CH ? XO - 1 : XO + kTX;
+                    const bool in = rin && gx >= 0 && gx < g.nx;
+                    const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+                    for (int j = 0; j < NO; ++j) r[j * BOX + col] = in ? __ldg(pin + (size_t)j * N + gs) : T(0);
+                    r[NO * BOX + col] = in ? (T)__ldg(Vc + gs) : T(0);
+                }
+            }
+        } else {
+            for (int i = threadIdx.x; i < BOX; i += kThreads) {
+                const int bx = i % PX, by = (i / PX) % kBY, bz = i / (PX * kBY);
+                const int gx = xs - 1 + bx, gy = y0 + by, gz = z0 + bz;
+                const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+                const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+                for (int j = 0; j < NO; ++j) box[j * BOX + i] = in ? __ldg(pin + (size_t)j * N + gs) : T(0);
+                box[NO * BOX + i] = in ? (T)__ldg(Vc + gs) : T(0);
+            }
         }
         __syncthreads();
-        const int gx = x0 + 1 + tx, gy = y0 + 1 + ty;
+        const int gx = xs + tx, gy = y0 + 1 + ty;
 #pragma unroll 1
         for (int dz = 0; dz < kTZ; ++dz) {
             const int gz = z0 + 1 + dz;
             const bool live = gx < g.nx && gy < g.ny && gz < g.nz;
-            const int b = ((dz + 1) * kBY + (ty + 1)) * kBX + (tx + 1);  // the site in the box
+            const int b = ((dz + 1) * kBY + (ty + 1)) * PX + (tx + XO);  // the site in the box
             T ps[NO], kx[NO];
 #pragma unroll
             for (int j = 0; j < NO; ++j) ps[j] = kx[j] = T(0);
 #pragma unroll
             for (int p = 0; p < 19; ++p) {
-                const int src = b - (vel(p, 0) + vel(p, 1) * kBX + vel(p, 2) * kBX * kBY);
-                const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[NO * kBox + src];
+                const int src = b - (vel(p, 0) + vel(p, 1) * PX + vel(p, 2) * PX * kBY);
+                const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[NO * BOX + src];
 #pragma unroll
                 for (int j = 0; j < NO; ++j) {
-                    const T v = box[j * kBox + src];
+                    const T v = box[j * BOX + src];
                     ps[j] += a * v;
                     kx[j] += xi[vclass(p)] * v;
                 }
@@ -281,11 +345,11 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
 }
 
-template <typename T, int NO, bool BATCHED>
-cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                                  cudaStream_t st) {
-    auto kern = k_relax_psi_tile<T, NO, BATCHED>;
-    const size_t smem = (size_t)(NO + 1) * kBox * sizeof(T);
+template <typename T, int NO, bool BATCHED, bool VEC>
+cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                    cudaStream_t st) {
+    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC>;
+    const size_t smem = (size_t)(NO + 1) * box_size<T, VEC>() * sizeof(T);
     // opted in whatever the size: static and dynamic shared memory together may exceed 48 KB
     static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
@@ -297,6 +361,16 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
     kern<<<dim3((unsigned)std::min<size_t>(tiles, (size_t)per), (unsigned)B), kThreads, smem, st>>>(g, c, io, sc);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// Vector staging where rows are whole 16-byte pieces and the arrays aligned.
+template <typename T, int NO, bool BATCHED>
+cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                  cudaStream_t st) {
+    auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
+    if (g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V))
+        return launch_relax_psi_tile_v<T, NO, BATCHED, true>(g, c, io, sc, B, st);
+    return launch_relax_psi_tile_v<T, NO, BATCHED, false>(g, c, io, sc, B, st);
 }
 
 // More than kMaxOrb orbitals, staged in shared memory: a block takes one
