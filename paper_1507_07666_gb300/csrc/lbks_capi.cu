@@ -1185,7 +1185,7 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     rc = free_forces(F);
     if (rc != LBKS_OK) return rc;
     double E = res.E_total, alpha = 1.0;
-    int steps = 0, accepted = 0;
+    int steps = 0;
     bool at_R = true, done = false;
     // inverse Hessian estimate (BFGS), starting from step * identity
     const int n3 = 3 * na;
@@ -1255,7 +1255,6 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
             res = tr;
             alpha = std::min(1.0, alpha * 2.0);
             at_R = true;
-            ++accepted;
         } else {  // undo, and halve the step along the same direction next time
             alpha *= 0.5;
             at_R = false;
@@ -1276,7 +1275,6 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     if (out) *out = res;
     if (xyz_out) std::copy(R.begin(), R.end(), xyz_out);
     if (steps_out) *steps_out = steps;
-    (void)accepted;
     if (!done) return fail(LBKS_ENOTCONV, "largest force %.3e Ha/bohr after %d steps", fmax_of(F), steps);
     return LBKS_OK;
 }

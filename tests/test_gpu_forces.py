@@ -173,4 +173,8 @@ def test_force_and_move_errors():
         s.move_atoms(xyz + np.array([0.0, 0.0, 50.0]))
     with pytest.raises(lbks.LbksError):
         lbks.lbks_relax_geometry(s.handle, 2, 10, -1.0, 0.5)
+    with pytest.raises(lbks.LbksError):  # a non-positive mass
+        s.md(2, 10.0, [1836.0, 0.0], np.zeros((2, 3)))
+    with pytest.raises(lbks.LbksError):  # a non-positive time step
+        s.md(2, 0.0, [1836.0, 1836.0], np.zeros((2, 3)))
     s.close()
