@@ -378,10 +378,12 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
 // system * groups + group), stages the group's psi and W field and Vc with a
 // one-site halo, and writes psi'; the overlap follows in its own kernel.
 // Dynamic shared memory: (2 kPsiGroup + 1) box values of T.
-template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_relax_psi_wide_tile(Grid g, Coef c, RelaxIO io, int NO) {
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(kThreads, 3) k_relax_psi_wide_tile(Grid g, Coef c, RelaxIO io, int NO) {
+    constexpr int PX = box_pitch<T, VEC>(), BOX = box_size<T, VEC>();
+    constexpr int XO = VEC ? vpad<T>() : 1;  // column of the tile's first x
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* box = reinterpret_cast<T*>(smem_raw);  // [kPsiGroup psi][kPsiGroup u][Vc], kBox each
+    T* box = reinterpret_cast<T*>(smem_raw);  // [kPsiGroup psi][kPsiGroup u][Vc], BOX each
     const int groups = (NO + kPsiGroup - 1) / kPsiGroup;
     const int y = (int)blockIdx.y / groups, jg = (int)blockIdx.y - y * groups;
     if (g.active && !g.active[y]) return;
@@ -399,39 +401,77 @@ __global__ void __launch_bounds__(kThreads, 2) k_relax_psi_wide_tile(Grid g, Coe
     const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY;
     const int tile = blockIdx.x;
     const int bxi = tile % ntx, byi = (tile / ntx) % nty, bzi = tile / (ntx * nty);
-    const int x0 = bxi * kTX - 1, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;
-    for (int i = threadIdx.x; i < kBox; i += kThreads) {
-        const int bx = i % kBX, by = (i / kBX) % kBY, bz = i / (kBX * kBY);
-        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
-        const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
-        const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+    const int xs = bxi * kTX, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;
+    // the array staged in box slot a (0 .. 2 kPsiGroup - 1), or null for zeros
+    auto source = [&](int a) -> const T* {
+        if (a < kPsiGroup) return a < J ? pin + (size_t)a * N : nullptr;
+        const int j = a - kPsiGroup, jj = j0 + j;  // the W field exists for orbitals >= 1
+        return (j < J && ubase && jj > 0) ? ubase + (size_t)(jj - 1) * N : nullptr;
+    };
+    if constexpr (VEC) {
+        constexpr int E = vpad<T>(), CH = kTX / E, ITEMS = CH + 2;  // 16-byte pieces and the two halo values
+        for (int i = threadIdx.x; i < kBY * kBZ * ITEMS; i += kThreads) {
+            const int row = i / ITEMS, k = i - row * ITEMS;
+            const int by = row % kBY, bz = row / kBY;
+            const int gy = y0 + by, gz = z0 + bz;
+            const bool rin = gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+            T* r = box + row * PX;
+            if (k < CH) {
+                const int gx = xs + k * E;  // a whole piece is in or out: nx is a multiple of E
+                const bool in = rin && gx < g.nx;
+                const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
 #pragma unroll
-        for (int j = 0; j < kPsiGroup; ++j) {
-            const bool has = in && j < J;
-            box[j * kBox + i] = has ? __ldg(pin + (size_t)j * N + gs) : T(0);
-            const int jj = j0 + j;  // the W field exists for orbitals >= 1
-            box[(kPsiGroup + j) * kBox + i] =
-                (has && ubase && jj > 0) ? __ldg(ubase + (size_t)(jj - 1) * N + gs) : T(0);
+                for (int a = 0; a < 2 * kPsiGroup; ++a) {
+                    const T* src = source(a);
+                    if (in && src) copy16(r + a * BOX + XO + k * E, src + gs);
+                    else zero16(r + a * BOX + XO + k * E);
+                }
+                if (in) copy16_v(r + 2 * kPsiGroup * BOX + XO + k * E, Vc + gs);
+                else zero16(r + 2 * kPsiGroup * BOX + XO + k * E);
+            } else {
+                const int gx = k == CH ? xs - 1 : xs + kTX;
+                const int col = k == CH ? XO - 1 : XO + kTX;
+                const bool in = rin && gx >= 0 && gx < g.nx;
+                const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+                for (int a = 0; a < 2 * kPsiGroup; ++a) {
+                    const T* src = source(a);
+                    r[a * BOX + col] = (in && src) ? __ldg(src + gs) : T(0);
+                }
+                r[2 * kPsiGroup * BOX + col] = in ? (T)__ldg(Vc + gs) : T(0);
+            }
         }
-        box[2 * kPsiGroup * kBox + i] = in ? (T)__ldg(Vc + gs) : T(0);
+    } else {
+        for (int i = threadIdx.x; i < BOX; i += kThreads) {
+            const int bx = i % PX, by = (i / PX) % kBY, bz = i / (PX * kBY);
+            const int gx = xs - 1 + bx, gy = y0 + by, gz = z0 + bz;
+            const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+            const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
+#pragma unroll
+            for (int a = 0; a < 2 * kPsiGroup; ++a) {
+                const T* src = source(a);
+                box[a * BOX + i] = (in && src) ? __ldg(src + gs) : T(0);
+            }
+            box[2 * kPsiGroup * BOX + i] = in ? (T)__ldg(Vc + gs) : T(0);
+        }
     }
     __syncthreads();
-    const int gx = x0 + 1 + tx, gy = y0 + 1 + ty;
+    const int gx = xs + tx, gy = y0 + 1 + ty;
 #pragma unroll 1
     for (int dz = 0; dz < kTZ; ++dz) {
         const int gz = z0 + 1 + dz;
         if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
-        const int b = ((dz + 1) * kBY + (ty + 1)) * kBX + (tx + 1);
+        const int b = ((dz + 1) * kBY + (ty + 1)) * PX + (tx + XO);
         T ps[kPsiGroup];
 #pragma unroll
         for (int j = 0; j < kPsiGroup; ++j) ps[j] = T(0);
 #pragma unroll
         for (int p = 0; p < 19; ++p) {
-            const int src = b - (vel(p, 0) + vel(p, 1) * kBX + vel(p, 2) * kBX * kBY);
-            const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[2 * kPsiGroup * kBox + src];
+            const int src = b - (vel(p, 0) + vel(p, 1) * PX + vel(p, 2) * PX * kBY);
+            const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[2 * kPsiGroup * BOX + src];
 #pragma unroll
             for (int j = 0; j < kPsiGroup; ++j)
-                ps[j] += a * box[j * kBox + src] + xi[vclass(p)] * box[(kPsiGroup + j) * kBox + src];
+                ps[j] += a * box[j * BOX + src] + xi[vclass(p)] * box[(kPsiGroup + j) * BOX + src];
         }
         const size_t s = ((size_t)gz * g.ny + gy) * g.nx + gx;
         const size_t o0 = (size_t)y * NO + j0;
@@ -467,14 +507,16 @@ cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO
         const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
         if (groups * B > 65535) return cudaErrorInvalidConfiguration;
         if (tiled) {
-            const size_t smem = (size_t)(2 * kPsiGroup + 1) * kBox * sizeof(T);
-            static const cudaError_t attr =
-                cudaFuncSetAttribute(k_relax_psi_wide_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (attr != cudaSuccess) return attr;
+            // scalar staging: the 16-byte layout's padded rows (9 x 9.6 KB of FP32 boxes)
+            // leave two blocks per SM instead of three, which measured slower
+            auto kern = k_relax_psi_wide_tile<T, false>;
+            const size_t smem = (size_t)(2 * kPsiGroup + 1) * box_size<T, false>() * sizeof(T);
+            static const cudaError_t attr_s =
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (attr_s != cudaSuccess) return attr_s;
             const size_t tiles =
                 (size_t)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
-            k_relax_psi_wide_tile<T><<<dim3((unsigned)tiles, (unsigned)(groups * B)), kThreads, smem, st>>>(g, c, io,
-                                                                                                        NO);
+            kern<<<dim3((unsigned)tiles, (unsigned)(groups * B)), kThreads, smem, st>>>(g, c, io, NO);
             count_launches(1);
             return cudaGetLastError();
         }
