@@ -665,9 +665,16 @@ struct Ops {
     template <int MAXO>
     static cudaError_t wfield_wide_m(int NO, const Grid& g, double omega, const void* psi, const double* lam,
                                      void* u, int B, cudaStream_t st) {
-        auto kern = k_w_field_wide<T, MAXO>;
-        static const int nb = blocks_per_sm(kern);
-        kern<<<batch_grid(g.N, nb * num_sms(), B), kThreads, 0, st>>>(g, omega, (const T*)psi, lam, (T*)u, NO);
+        if constexpr (sizeof(T) == 4 && MAXO >= 32 && MAXO <= 48) {  // FP32: two sites per thread, packed FMAs (spill-free here)
+            auto kern = k_w_field_wide2<MAXO>;
+            static const int nb = blocks_per_sm(kern);
+            kern<<<batch_grid((g.N + 1) / 2, nb * num_sms(), B), kThreads, 0, st>>>(g, omega, (const float*)psi, lam,
+                                                                                    (float*)u, NO);
+        } else {
+            auto kern = k_w_field_wide<T, MAXO>;
+            static const int nb = blocks_per_sm(kern);
+            kern<<<batch_grid(g.N, nb * num_sms(), B), kThreads, 0, st>>>(g, omega, (const T*)psi, lam, (T*)u, NO);
+        }
         count_launches(1);
         return cudaGetLastError();
     }

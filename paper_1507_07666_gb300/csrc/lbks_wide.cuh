@@ -172,6 +172,55 @@ __global__ void __launch_bounds__(kThreads) k_w_field_wide(const Grid g, double 
     }
 }
 
+// FP32 form of k_w_field_wide with two sites per thread (s and s + kThreads
+// of a 2 kThreads-site chunk): the two sites' values of an orbital form one
+// float2, so each 16-byte broadcast load of -omega Lambda serves both sites
+// and each packed FMA (fma.rn.f32x2, __ffma2_rn) does both: half the shared
+// loads and half the FMA instructions per site.
+template <int MAXO>
+__global__ void __launch_bounds__(kThreads, 2) k_w_field_wide2(const Grid g, double omega,
+                                                              const float* __restrict__ psi,
+                                                              const double* __restrict__ lam, float* __restrict__ u,
+                                                              int NO) {
+    static_assert(MAXO % 4 == 0, "row pitch must keep 16-byte alignment");
+    if (inactive(g)) return;
+    __shared__ __align__(16) float L[MAXO * MAXO];
+    const size_t n = g.N, y = sys_id();
+    psi += y * NO * n;
+    lam += y * NO * NO;
+    u += y * (NO - 1) * n;
+    for (int i = threadIdx.x; i < MAXO * MAXO; i += kThreads) {
+        const int j = i / MAXO, k = i % MAXO;
+        L[i] = (j < NO && k < j) ? (float)(-omega * lam[j * NO + k]) : 0.f;
+    }
+    __syncthreads();
+    const size_t chunk = 2 * (size_t)kThreads;
+    for (size_t base = blockIdx.x * chunk; base < n; base += (size_t)gridDim.x * chunk) {
+        const size_t s0 = base + threadIdx.x, s1 = s0 + kThreads;
+        const bool h0 = s0 < n, h1 = s1 < n;
+        float2 ps[MAXO];
+#pragma unroll
+        for (int k = 0; k < MAXO; ++k) {
+            ps[k].x = (k < NO && h0) ? __ldcs(psi + (size_t)k * n + s0) : 0.f;
+            ps[k].y = (k < NO && h1) ? __ldcs(psi + (size_t)k * n + s1) : 0.f;
+        }
+#pragma unroll
+        for (int j = 1; j < MAXO; ++j) {
+            if (j >= NO) break;
+            float2 w = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kb = 0; kb < j; kb += 4) {
+                float l[4];
+                lds16(&L[j * MAXO + kb], l);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) w = __ffma2_rn(make_float2(l[e], l[e]), ps[kb + e], w);
+            }
+            if (h0) __stcs(u + (size_t)(j - 1) * n + s0, w.x);
+            if (h1) __stcs(u + (size_t)(j - 1) * n + s1, w.y);
+        }
+    }
+}
+
 // In-place orthonormalisation f_jp <- sum_k Linv_jk f_kp, psi likewise:
 // per site, one velocity at a time, the NO values staged per thread in
 // shared memory.  Dynamic shared memory: (NO * kThreads + NO * NO) * sizeof(T).

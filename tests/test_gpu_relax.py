@@ -32,6 +32,9 @@ CASES = [
     ((66, 7, 5), 2, 1.2, 10),
     ((10, 9, 11), 8, 0.8, 11),
     ((12, 10, 9), 64, 1.0, 12),  # the largest orbital count the library takes
+    # 25-48 orbitals: the W field two sites per thread (an odd site count leaves a lone last site)
+    ((13, 7, 9), 33, 0.9, 13),
+    ((14, 9, 8), 40, 1.0, 14),
 ]
 VARIANTS = [1, 2, 3, 4]  # lbks_set_relax_variant: one site, two sites, next orbital prefetched, staged by cp.async
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
