@@ -469,23 +469,49 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix(Grid g, Coef c, cons
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
         const Site t = decode(g, s);
         const double vr = V[s];
-        double a[NO], hp[NO];
+        if constexpr (sizeof(T) == 4) {
+            // FP32 orbitals: (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1;
+            // a missing neighbour counts as psi(r)), each difference of two nearby FP32 values
+            // exact; the weighted sums and products in FP32, the sums over sites in FP64
+            float af[NO], hf[NO];
+            const float xf[3] = {(float)c.xi[0], (float)c.xi[1], (float)c.xi[2]};
+            const float invf = (float)inv, vf = (float)vr;
 #pragma unroll
-        for (int j = 0; j < NO; ++j) {
-            const T* pj = psi + (size_t)j * N;
-            double kx = 0.0;
+            for (int j = 0; j < NO; ++j) {
+                const T* pj = psi + (size_t)j * N;
+                const float aj = (float)pj[s];
+                float d = 0.f;
 #pragma unroll
-            for (int p = 0; p < 19; ++p)
-                if (has_source(t, p)) kx += c.xi[vclass(p)] * (double)pj[source_index(g, s, p)];
-            a[j] = (double)pj[s];
-            const double tp = (a[j] - kx) * inv;
-            acc[NO * NO + j] += a[j] * tp;
-            hp[j] = tp + vr * a[j];
+                for (int p = 1; p < 19; ++p)
+                    d += xf[vclass(p)] * (has_source(t, p) ? aj - (float)pj[source_index(g, s, p)] : aj);
+                const float tp = d * invf;
+                af[j] = aj;
+                hf[j] = tp + vf * aj;
+                acc[NO * NO + j] += (double)(aj * tp);
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j)
+#pragma unroll
+                for (int k = 0; k < NO; ++k) acc[j * NO + k] += (double)(af[j] * hf[k]);
+        } else {
+            double a[NO], hp[NO];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+                const T* pj = psi + (size_t)j * N;
+                double kx = 0.0;
+#pragma unroll
+                for (int p = 0; p < 19; ++p)
+                    if (has_source(t, p)) kx += c.xi[vclass(p)] * (double)pj[source_index(g, s, p)];
+                a[j] = (double)pj[s];
+                const double tp = (a[j] - kx) * inv;
+                acc[NO * NO + j] += a[j] * tp;
+                hp[j] = tp + vr * a[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j)
+#pragma unroll
+                for (int k = 0; k < NO; ++k) acc[j * NO + k] += a[j] * hp[k];
         }
-#pragma unroll
-        for (int j = 0; j < NO; ++j)
-#pragma unroll
-            for (int k = 0; k < NO; ++k) acc[j * NO + k] += a[j] * hp[k];
     }
     double* partial = sys_partial(sc);
     block_sum_store<K>(acc, partial + (size_t)blockIdx.x * K);
