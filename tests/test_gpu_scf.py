@@ -1,7 +1,7 @@
 """GPU parity of the full self-consistent solve against the oracle, through
 the C ABI (lbks_create_system / lbks_set_geometry / lbks_scf / lbks_energy).
 
-Tolerances (the benchmark spec's): |Delta E_total| <= 1e-5 Ha, Ritz eigenvalues
+Tolerances: |Delta E_total| <= 1e-5 Ha, Ritz eigenvalues
 <= 1e-5 Ha, relative density L2 <= 1e-5.  The FP64 path reproduces the
 oracle's trajectory to round-off; FP32 populations stay within the same
 tolerances."""
