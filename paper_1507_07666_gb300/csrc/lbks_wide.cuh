@@ -380,12 +380,14 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix_wide(Grid g, Coef c,
             if (s < N) {
                 const Site t = decode(g, s);
                 const T* pj = psi + (size_t)j * N;
-                T kx = T(0);
-#pragma unroll
-                for (int p = 0; p < 19; ++p)
-                    if (has_source(t, p)) kx += (T)c.xi[vclass(p)] * pj[source_index(g, s, p)];
                 a = pj[s];
-                tp = (a - kx) * inv;
+                // (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1; a missing
+                // neighbour counts as psi(r)): differences of nearby values are exact in T
+                T d = T(0);
+#pragma unroll
+                for (int p = 1; p < 19; ++p)
+                    d += (T)c.xi[vclass(p)] * (has_source(t, p) ? a - pj[source_index(g, s, p)] : a);
+                tp = d * inv;
                 hp = tp + (T)V[s] * a;
             }
             A[i] = a;
