@@ -97,7 +97,7 @@ typedef struct lbks_params {
                             dt = theta h^2 (2 - omega) / omega (Sec. 3, D relation) */
     int n_inner;         /* relaxation steps per self-consistent cycle, >= 2 [50] */
     double mix;          /* linear potential mixing V <- mix V_out + (1-mix) V [0.5] */
-    double e_tol;        /* stop when |E_c - E_{c-1}| < e_tol Hartree [1e-6] */
+    double e_tol;        /* stop rule on the total energy (below), Hartree, > 0 [1e-6] */
     int max_cycles;      /* [200] */
     int precision;       /* enum lbks_precision [LBKS_FP64] */
     double softening;    /* nuclear softening a (bohr); <= 0 means a = h [0] */
@@ -110,7 +110,29 @@ typedef struct lbks_params {
                             (bfloat16 rounding would otherwise bound the accuracy); <= 0 never [1e-4] */
     int storage;         /* enum lbks_storage [LBKS_STORE_POPULATIONS]; LBKS_STORE_PSI needs omega = 1
                             and LBKS_FP64 or LBKS_FP32 */
+    double eig_tol;      /* stop rule on the eigenvalues (largest change), Hartree; <= 0: not watched [2e-6] */
+    double rho_tol;      /* stop rule on the density (relative L2 change); <= 0: not watched [2e-6] */
+    uint64_t seed;       /* start orbitals: 0 the fixed offsets of lbks_set_geometry, else seeded offsets
+                            (SplitMix64) [0]; the converged state does not depend on it */
 } lbks_params;
+
+/* Stop rule of lbks_scf and lbks_batch_scf (the paper stops once the orbital
+ * energies no longer change, Sec. 4; the bound is this library's reading).
+ * Per cycle c three changes are watched: d_E = |E_c - E_(c-1)|, d_eig =
+ * max_j |eps_j,c - eps_j,(c-1)| and d_rho = ||rho_c - rho_(c-1)|| / ||rho_c||.
+ * Each is extended by its geometric tail d q / (1 - q), q the larger of the
+ * last two contraction ratios d_c / d_(c-1), d_(c-1) / d_(c-2), capped at 0.98
+ * (a change that does not shrink counts as shrinking at 0.98).  A system has
+ * converged once, for each quantity with a positive tolerance (e_tol,
+ * eig_tol, rho_tol), both its change and its tail are within the tolerance,
+ * or its change is below the rounding floor 8 u s: u the unit roundoff of
+ * the orbital values (2^-53 for LBKS_FP64, 2^-24 otherwise), s = |E|,
+ * max_j |eps_j| and 1 for the three quantities (single-precision orbitals keep
+ * the changes from falling below a few u s); at least three cycles run.  The tail estimates the distance left to the
+ * fixed point: a change alone does not bound it when a cycle contracts the
+ * error slowly (the Gram-Schmidt source of Eq. KSLB separates occupied
+ * orbitals of close eigenvalues slowly, and that rotation leaks into the
+ * density). */
 
 void lbks_params_default(lbks_params* p);
 
@@ -128,7 +150,10 @@ uint64_t lbks_kernel_launches(void);
 /* ------------------------------------------------------------------ systems */
 typedef struct lbks_system lbks_system;
 
-/* Allocates all device state of one system on the current device: two
+/* A system is the paper's problem statement (Sec. 2: nuclei and electrons ->
+ * Kohn-Sham orbitals, density and energies) on one grid: n_orb doubly occupied
+ * orbitals, each carrying the D3Q19 populations of Eq. KSLB (Sec. 3).
+ * Allocates all device state of one system on the current device: two
  * population buffers of n_orb*19*N elements, orbitals, W field, potentials,
  * CG vectors and reduction scratch.  Up to 8 orbitals the overlap products
  * are fused into the stream-collide kernel; above, a separate tiled Gram
@@ -160,11 +185,22 @@ typedef struct lbks_result {
     int converged;
     int poisson_iters;                /* CG iterations, all cycles */
     double wall_s;
+    double d_eig;                     /* max_j |eps_j,c - eps_j,(c-1)| of the last cycle */
+    double d_rho;                     /* ||rho_c - rho_(c-1)|| / ||rho_c|| of the last cycle */
+    double err_E, err_eig, err_rho;   /* geometric tails of the three changes (see the stop rule);
+                                         INFINITY before three cycles */
 } lbks_result;
 
-/* Runs the self-consistent loop from the current state until |dE| < e_tol
+/* The self-consistent loop of the Born-Oppenheimer scenario (Sec. 3.1: nuclei
+ * fixed, orbitals relaxed by Eq. KSLB while the density, the Hartree and the
+ * exchange-correlation potentials are rebuilt from them; Sec. 4 stops once
+ * the orbital energies settle).  Each cycle runs n_inner - 1 relaxation
+ * steps at fixed potential, one step that orthonormalises the orbitals
+ * (Cholesky), then rebuilds density, potentials and energies and mixes the
+ * potential.  Runs from the current state until the stop rule above holds
  * or max_cycles (ENOTCONV, result filled).  Blocking; all GPU work is queued
- * on `stream`. */
+ * on `stream`.  ENOTCONV also when the overlap is not positive definite or
+ * an energy is not finite; ECUDA on a CUDA failure. */
 int lbks_scf(lbks_system* sys, void* stream, lbks_result* out);
 
 /* Runs exactly n cycles (no convergence test); result as lbks_scf (one
@@ -209,7 +245,15 @@ int lbks_set_relax_variant(int mode);
  * handle). */
 int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
 
-/* Energy terms of the last evaluation (after lbks_set_geometry or a cycle). */
+/* Energy terms of the last evaluation (after lbks_set_geometry or a cycle).
+ * Sec. 2 states that the ground-state energy is a functional of the density
+ * (Kohn-Sham formulation) but prints no expression; the standard Kohn-Sham
+ * one is taken, with the terms of H_KS (Sec. 2): T_s + E_ext + E_H + E_xc
+ * plus the nucleus-nucleus repulsion E_nn, T_s = 2 sum_j <psi_j|T_h|psi_j>,
+ * T_h = (1 - K_xi) / (theta h^2) the kinetic operator of the equilibrium
+ * stencil (Sec. 3).  The eigenvalues are the orbital energies E_j of Eq. KSE,
+ * taken as Ritz values of the occupied subspace (the quantity Sec. 4's stop
+ * rule watches).  Host copy; synchronous. */
 int lbks_energy(const lbks_system* sys, lbks_energy_terms* out);
 
 /* Hellmann-Feynman forces on the nuclei (Born-Oppenheimer, Sec. 3.1 with the

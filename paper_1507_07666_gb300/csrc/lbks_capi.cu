@@ -190,10 +190,71 @@ void jacobi_eigenvalues(int n, std::vector<double> a, double* out) {
 bool valid_params(const lbks_params* p) {
     return p && p->omega > 0.0 && p->omega < 2.0 && p->theta > 0.0 && p->n_inner >= 2 && p->mix > 0.0 &&
            p->mix <= 1.0 && p->e_tol > 0.0 && p->max_cycles >= 1 && ops_for(p->precision) &&
-           p->poisson_rtol > 0.0 && p->poisson_max_iter >= 1 &&
+           p->poisson_rtol > 0.0 && p->poisson_max_iter >= 1 && !std::isnan(p->eig_tol) &&
+           !std::isnan(p->rho_tol) &&
            (p->storage == LBKS_STORE_POPULATIONS ||
             (p->storage == LBKS_STORE_PSI && p->omega == 1.0 && p->precision != LBKS_BF16));
 }
+
+// SplitMix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): advances the state, returns the next output.
+uint64_t splitmix64(uint64_t& state) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Offsets (bohr) of the Gaussian start centres from their nuclei, n_orb x 3.
+// seed 0: 0.25 (sin(1 + 2.1 j), sin(2 + 3.3 j), sin(3 + 4.7 j)); otherwise
+// 0.25 (2u - 1) per component, u the top 53 bits of successive SplitMix64
+// outputs from state = seed, drawn x, y, z for j = 0, 1, ...
+std::vector<double> start_offsets(int n_orb, uint64_t seed) {
+    std::vector<double> off(3 * (size_t)n_orb);
+    if (seed == 0) {
+        for (int j = 0; j < n_orb; ++j) {
+            off[3 * j] = 0.25 * std::sin(1.0 + 2.1 * j);
+            off[3 * j + 1] = 0.25 * std::sin(2.0 + 3.3 * j);
+            off[3 * j + 2] = 0.25 * std::sin(3.0 + 4.7 * j);
+        }
+        return off;
+    }
+    uint64_t state = seed;
+    for (size_t k = 0; k < off.size(); ++k) {
+        const double u = (double)(splitmix64(state) >> 11) * 0x1.0p-53;
+        off[k] = 0.25 * (2.0 * u - 1.0);
+    }
+    return off;
+}
+
+// Stop rule (include/lbks.h): the last three per-cycle changes of one
+// watched quantity, newest first.  A change below kFloorUlps u s (u the unit
+// roundoff of the orbital values, s the quantity's scale) is rounding noise.
+constexpr double kTailCap = 0.98;
+constexpr double kFloorUlps = 8.0;
+struct Changes {
+    double d[3] = {INFINITY, INFINITY, INFINITY};
+    int n = 0;
+    void push(double v) {
+        d[2] = d[1];
+        d[1] = d[0];
+        d[0] = v;
+        ++n;
+    }
+    // d0 q / (1 - q), q the larger of d0/d1 and d1/d2 capped at kTailCap
+    double tail() const {
+        if (n < 3) return INFINITY;
+        auto ratio = [](double a, double b) { return b > 0.0 ? a / b : (a > 0.0 ? INFINITY : 0.0); };
+        const double q = std::min(std::max(ratio(d[0], d[1]), ratio(d[1], d[2])), kTailCap);
+        return d[0] * q / (1.0 - q);
+    }
+    bool settled(double tol, double floor) const {
+        if (!(tol > 0.0)) return true;
+        if (n < 3) return false;
+        return d[0] <= floor || (d[0] <= tol && tail() <= tol);
+    }
+};
 
 }  // namespace
 }  // namespace lbks
@@ -243,6 +304,7 @@ struct lbks_system {
     std::vector<int> has_atoms;
     bool ready = false;  // orbitals and energies initialised
     std::vector<lbks_energy_terms> terms;
+    std::vector<double> drho;  // ||rho - rho_prev|| / ||rho|| of the last evaluation, per system
     int poisson_iters = 0;
 };
 
@@ -252,8 +314,9 @@ namespace {
 // energy integrals, energy matrix, multipoles).
 size_t small_per_sys(int no) { return 3 * (size_t)no * no + no + kE4Stride + emat_stride(no) + kMpStride; }
 constexpr int kPoissonChunk = 2;  // PCG iterations per graph launch between convergence checks
-// Doubles per system of the pinned readback area: energy integrals + matrix + status slot.
-size_t host_per_sys(int no) { return kE4Stride + emat_stride(no) + 2; }
+// Doubles per system of the pinned readback area: energy integrals, energy
+// matrix, the density change (two sums) and spare room.
+size_t host_per_sys(int no) { return kE4Stride + emat_stride(no) + 4; }
 
 PoissonBufs poisson_bufs(double* v, size_t n, CGState* cg, double* mp) {
     return PoissonBufs{v, v + n, v + 2 * n, v + 3 * n, v + 4 * n, v + 5 * n, cg, mp};
@@ -261,6 +324,8 @@ PoissonBufs poisson_bufs(double* v, size_t n, CGState* cg, double* mp) {
 
 double* host_e4(lbks_system* s, int i) { return s->host + (size_t)i * host_per_sys(s->n_orb); }
 double* host_emat(lbks_system* s, int i) { return host_e4(s, i) + kE4Stride; }
+// h^3 sum (rho - rho_prev)^2 and h^3 sum rho^2 of the last density (mp[10], mp[11])
+double* host_drho(lbks_system* s, int i) { return host_emat(s, i) + emat_stride(s->n_orb); }
 int* host_status(lbks_system* s) { return reinterpret_cast<int*>(s->host + (size_t)s->B * host_per_sys(s->n_orb)); }
 int* host_active(lbks_system* s) { return host_status(s) + s->B; }
 CGState* host_cg(lbks_system* s) {
@@ -343,6 +408,9 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_emat(s, i), s->emat + (size_t)i * emat_stride(no), sizeof(double) * (no * no + no),
                                 cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_drho(s, i), s->mp + (size_t)i * kMpStride + 10, sizeof(double) * 2,
+                                cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_status(s), s->status, sizeof(int) * B, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -382,6 +450,8 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
             for (int k = 0; k < no; ++k) H[j * no + k] = 0.5 * (hm[j * no + k] + hm[k * no + j]);
         }
         jacobi_eigenvalues(no, H, t.eigenvalues);
+        const double* dr = host_drho(s, i);
+        s->drho[i] = dr[1] > 0.0 ? std::sqrt(std::max(dr[0], 0.0) / dr[1]) : INFINITY;
     }
     return LBKS_OK;
 }
@@ -481,16 +551,19 @@ int polish(lbks_system* s, cudaStream_t st) {
 }
 
 // Relaxation cycles of all systems in lock step; a system stops (drops out
-// of every launch) once its |dE| < e_tol, unless `fixed`.
+// of every launch) once the stop rule holds for it (include/lbks.h), unless
+// `fixed` (exactly n cycles).
 int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* out) {
     if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
-    const int B = s->B;
+    const int B = s->B, no = s->n_orb;
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<double> prev(B), de(B, INFINITY), de1(B, INFINITY), de2(B, INFINITY);
-    std::vector<int> cycles(B, 0), converged(B, 0), p0(B, 0);
+    std::vector<double> prev(B), prev_eig((size_t)B * no);
+    std::vector<Changes> dE(B), dEig(B), dRho(B);
+    std::vector<int> cycles(B, 0), converged(B, 0);
     int* act = host_active(s);
     for (int i = 0; i < B; ++i) {
         prev[i] = s->terms[i].E_total;
+        for (int j = 0; j < no; ++j) prev_eig[(size_t)i * no + j] = s->terms[i].eigenvalues[j];
         act[i] = 1;
     }
     int rc = upload_active(s, st);
@@ -517,16 +590,30 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         for (int i = 0; i < B; ++i) {
             if (!act[i]) continue;
             ++cycles[i];
-            de2[i] = de1[i];
-            de1[i] = de[i];
-            de[i] = std::fabs(s->terms[i].E_total - prev[i]);
-            prev[i] = s->terms[i].E_total;
-            if (!std::isfinite(s->terms[i].E_total)) return fail(LBKS_ENOTCONV, "system %d: energy not finite", i);
+            const lbks_energy_terms& t = s->terms[i];
+            if (!std::isfinite(t.E_total)) return fail(LBKS_ENOTCONV, "system %d: energy not finite", i);
+            double de_eig = 0.0;
+            for (int j = 0; j < no; ++j) {
+                de_eig = std::max(de_eig, std::fabs(t.eigenvalues[j] - prev_eig[(size_t)i * no + j]));
+                prev_eig[(size_t)i * no + j] = t.eigenvalues[j];
+            }
+            dE[i].push(std::fabs(t.E_total - prev[i]));
+            dEig[i].push(de_eig);
+            dRho[i].push(s->drho[i]);
+            prev[i] = t.E_total;
             // ready for FP32 storage: below polish_tol, or stalled at the
             // bfloat16 noise floor (|dE| no longer halving over two cycles)
-            const bool stalled = de[i] < 100.0 * s->prm.polish_tol && de[i] > 0.5 * de2[i];
-            if (!(de[i] < s->prm.polish_tol || stalled)) ready = false;
-            if (!fixed && !wait_polish && de[i] < s->prm.e_tol) {
+            const double d0 = dE[i].d[0], d2 = dE[i].d[2];
+            const bool stalled = d0 < 100.0 * s->prm.polish_tol && d0 > 0.5 * d2;
+            if (!(d0 < s->prm.polish_tol || stalled)) ready = false;
+            // rounding floors: FP64 orbitals 2^-53, FP32 (and the BF16 handle's
+            // FP32 polish) 2^-24, scaled by |E|, max |eps_j| and 1
+            const double u = s->ops->psi_elem == sizeof(double) ? 0x1.0p-53 : 0x1.0p-24;
+            double eig_scale = 0.0;
+            for (int j = 0; j < no; ++j) eig_scale = std::max(eig_scale, std::fabs(t.eigenvalues[j]));
+            if (!fixed && !wait_polish && dE[i].settled(s->prm.e_tol, kFloorUlps * u * std::fabs(t.E_total)) &&
+                dEig[i].settled(s->prm.eig_tol, kFloorUlps * u * eig_scale) &&
+                dRho[i].settled(s->prm.rho_tol, kFloorUlps * u)) {
                 converged[i] = 1;
                 act[i] = 0;
             } else {
@@ -552,16 +639,20 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         lbks_result& r = out[i];
         memset(&r, 0, sizeof r);
         r.E_total = s->terms[i].E_total;
-        r.dE = de[i];
-        for (int j = 0; j < s->n_orb; ++j) r.eigenvalues[j] = s->terms[i].eigenvalues[j];
+        r.dE = dE[i].d[0];
+        for (int j = 0; j < no; ++j) r.eigenvalues[j] = s->terms[i].eigenvalues[j];
         r.n_electrons = s->terms[i].n_electrons;
         r.cycles = cycles[i];
         r.steps = cycles[i] * s->prm.n_inner;
         r.converged = converged[i];
         r.poisson_iters = s->poisson_iters - start_iters;
         r.wall_s = wall;
+        r.d_eig = dEig[i].d[0];
+        r.d_rho = dRho[i].d[0];
+        r.err_E = dE[i].tail();
+        r.err_eig = dEig[i].tail();
+        r.err_rho = dRho[i].tail();
     }
-    (void)p0;
     if (!all) return fail(LBKS_ENOTCONV, "not every system converged within %d cycles", limit);
     return LBKS_OK;
 }
@@ -725,12 +816,13 @@ int initialise(lbks_system* s) {
         std::vector<int> order(na);
         for (int a = 0; a < na; ++a) order[a] = a;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return Z[a] > Z[b]; });
+        const std::vector<double> off = start_offsets(s->n_orb, s->prm.seed);
         for (int j = 0; j < s->n_orb; ++j) {
             const int I = order[j % na], m = j / na;
             OrbitalStart& o = starts[(size_t)i * s->n_orb + j];
-            o.cx = xyz[3 * I] + 0.25 * std::sin(1.0 + 2.1 * j);
-            o.cy = xyz[3 * I + 1] + 0.25 * std::sin(2.0 + 3.3 * j);
-            o.cz = xyz[3 * I + 2] + 0.25 * std::sin(3.0 + 4.7 * j);
+            o.cx = xyz[3 * I] + off[3 * j];
+            o.cy = xyz[3 * I + 1] + off[3 * j + 1];
+            o.cz = xyz[3 * I + 2] + off[3 * j + 2];
             o.width = 1.2 * (1.0 + 0.35 * m);
         }
     }
@@ -838,6 +930,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     s->N = (size_t)nx * ny * nz;
     cudaGetDevice(&s->dev);
     s->terms.assign(B, lbks_energy_terms{});
+    s->drho.assign(B, INFINITY);
     s->xyz.assign(B, {});
     s->Z.assign(B, {});
     s->has_atoms.assign(B, 0);
@@ -885,6 +978,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     // then see the arrival counters or the active flags reset mid-solve.
     if (err == cudaSuccess) err = cudaMemsetAsync(s->sc.counter, 0, sizeof(unsigned) * B, s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->vh, 0, 8 * NB, s->st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->rho, 0, 8 * NB, s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->u, 0, ep * NB * std::max(1, n_orb - 1), s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->ints, 0, sizeof(int) * 3 * B, s->st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->st);
@@ -956,6 +1050,9 @@ void lbks_params_default(lbks_params* p) {
     p->poisson_max_iter = 20000;
     p->polish_tol = 1e-4;
     p->storage = LBKS_STORE_POPULATIONS;
+    p->eig_tol = 2e-6;
+    p->rho_tol = 2e-6;
+    p->seed = 0;
 }
 
 int lbks_last_error(char* buf, size_t cap) {

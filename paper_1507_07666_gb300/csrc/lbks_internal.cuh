@@ -173,7 +173,9 @@ struct PrecisionOps {
     cudaError_t (*init_orbitals)(int n_orb, const Grid&, double h, const OrbitalStart* starts, void* psi, int B,
                                  cudaStream_t);
     cudaError_t (*equilibrium)(int n_orb, const Grid&, const Coef&, const void* psi, void* f, int B, cudaStream_t);
-    // rho = 2 sum psi^2 and its multipoles mp[10] = {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz}
+    // rho = 2 sum psi^2 (overwriting the previous density) and its multipoles
+    // mp[0..9] = {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz}; mp[10] =
+    // h^3 sum (rho - rho_prev)^2 and mp[11] = h^3 sum rho^2 (the stop rule's density change)
     cudaError_t (*density)(int n_orb, const Grid&, double h, const void* psi, double* rho, double* mp,
                            const Scratch&, int B, cudaStream_t);
     // H[j][k] = <psi_j|T_h + V|psi_k>, kin[j] = <psi_j|T_h|psi_j>  (n_orb^2 + n_orb doubles per system)

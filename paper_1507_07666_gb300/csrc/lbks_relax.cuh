@@ -405,7 +405,8 @@ __global__ void __launch_bounds__(kThreads) k_equilibrium(const Grid g, Coef c, 
     }
 }
 
-// rho = 2 sum_j psi_j^2 and its moments about the box centre.
+// rho = 2 sum_j psi_j^2 (written over the previous density) and its moments
+// about the box centre; mp[10], mp[11] = h^3 sum (rho - rho_prev)^2, h^3 sum rho^2.
 template <typename T, int NO>
 __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T* __restrict__ psi,
                                                       double* __restrict__ rho, double* mp, Scratch sc) {
@@ -413,9 +414,9 @@ __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T*
     psi += (size_t)sys_id() * NO * g.N;
     rho += (size_t)sys_id() * g.N;
     mp += (size_t)sys_id() * kMpStride;
-    double acc[10];
+    double acc[12];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 12; ++k) acc[k] = 0.0;
     const uint32_t N = g.N;
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < N; s += gridDim.x * kThreads) {
         double r = 0.0;
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T*
             r += a * a;
         }
         r *= 2.0;
+        const double dr = r - rho[s];  // change from the previous evaluation (stop rule)
         rho[s] = r;
         const uint32_t q = g.divx.div(s);
         const int x = (int)(s - q * (uint32_t)g.nx);
@@ -436,17 +438,19 @@ __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T*
         acc[1] += r * rx; acc[2] += r * ry; acc[3] += r * rz;
         acc[4] += r * rx * rx; acc[5] += r * ry * ry; acc[6] += r * rz * rz;
         acc[7] += r * rx * ry; acc[8] += r * rx * rz; acc[9] += r * ry * rz;
+        acc[10] += dr * dr; acc[11] += r * r;
     }
     double* partial = sys_partial(sc);
-    block_sum_store<10>(acc, partial + (size_t)blockIdx.x * 10);
-    __shared__ double tot[10];
-    if (grid_total<10>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
+    block_sum_store<12>(acc, partial + (size_t)blockIdx.x * 12);
+    __shared__ double tot[12];
+    if (grid_total<12>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         const double h3 = h * h * h;
         const double tr = tot[4] + tot[5] + tot[6];
         mp[0] = h3 * tot[0];
         mp[1] = h3 * tot[1]; mp[2] = h3 * tot[2]; mp[3] = h3 * tot[3];
         mp[4] = h3 * (3.0 * tot[4] - tr); mp[5] = h3 * (3.0 * tot[5] - tr); mp[6] = h3 * (3.0 * tot[6] - tr);
         mp[7] = h3 * 3.0 * tot[7]; mp[8] = h3 * 3.0 * tot[8]; mp[9] = h3 * 3.0 * tot[9];
+        mp[10] = h3 * tot[10]; mp[11] = h3 * tot[11];
     }
 }
 

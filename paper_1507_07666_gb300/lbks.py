@@ -36,14 +36,17 @@ class lbks_params(ctypes.Structure):
                 ("mix", ctypes.c_double), ("e_tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("softening", ctypes.c_double),
                 ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
-                ("polish_tol", ctypes.c_double), ("storage", ctypes.c_int)]
+                ("polish_tol", ctypes.c_double), ("storage", ctypes.c_int), ("eig_tol", ctypes.c_double),
+                ("rho_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
 class lbks_result(ctypes.Structure):
     _fields_ = [("E_total", ctypes.c_double), ("dE", ctypes.c_double),
                 ("eigenvalues", ctypes.c_double * MAX_ORB), ("n_electrons", ctypes.c_double),
                 ("cycles", ctypes.c_int), ("steps", ctypes.c_int), ("converged", ctypes.c_int),
-                ("poisson_iters", ctypes.c_int), ("wall_s", ctypes.c_double)]
+                ("poisson_iters", ctypes.c_int), ("wall_s", ctypes.c_double), ("d_eig", ctypes.c_double),
+                ("d_rho", ctypes.c_double), ("err_E", ctypes.c_double), ("err_eig", ctypes.c_double),
+                ("err_rho", ctypes.c_double)]
 
 
 class lbks_energy_terms(ctypes.Structure):
@@ -214,7 +217,8 @@ def lbks_set_geometry(handle, xyz, Z):
 def _result_dict(r: lbks_result, n_orb: int) -> dict:
     return {"E_total": r.E_total, "dE": r.dE, "eigenvalues": np.array(r.eigenvalues[:n_orb]),
             "n_electrons": r.n_electrons, "cycles": r.cycles, "steps": r.steps,
-            "converged": bool(r.converged), "poisson_iters": r.poisson_iters, "wall_s": r.wall_s}
+            "converged": bool(r.converged), "poisson_iters": r.poisson_iters, "wall_s": r.wall_s,
+            "d_eig": r.d_eig, "d_rho": r.d_rho, "err_E": r.err_E, "err_eig": r.err_eig, "err_rho": r.err_rho}
 
 
 def lbks_scf(handle, stream=None, n_orb=MAX_ORB, allow_notconv=False) -> dict:

@@ -31,9 +31,12 @@ def test_helium_converges_with_invariants():
     assert res["converged"] and res["cycles"] < 30
     assert res["n_electrons"] == pytest.approx(2.0, abs=1e-12)
     assert _orthonormal(st.psi, w.h) < 1e-12
-    # energies fall towards the variational minimum
+    # energies fall towards the minimum; near the fixed point they may rise by
+    # ~1e-8 Ha: the scheme's fixed point is not exactly the minimum of the
+    # energy functional, since its potential source is smoothed by the chi_p
+    # stencil (sum_p chi_p shift_p differs from the identity at O(h^4))
     hist = np.array(res["history"])
-    assert (np.diff(hist) < 1e-9).all()
+    assert (np.diff(hist) < 2e-8).all()
     # the parts add up, the potential terms have the physical signs
     assert res["E_ext"] < 0 < res["E_H"] and res["E_xc"] < 0 < res["T_s"]
     assert res["eigenvalues"][0] < 0
@@ -76,3 +79,70 @@ def test_two_orbital_span_is_dominant_invariant_subspace():
     # the lowest orbital is the dominant eigenvector itself
     assert _angle(st.psi[0], U[:, o[0]].real) < 1e-9
     assert _orthonormal(st.psi, h) < 1e-12
+
+
+# ------------------------------------------------------------------ stop rule
+def test_tail_estimate_is_exact_for_a_geometric_sequence():
+    """For changes d_k = a q^k the remaining distance sum_{i>k} a q^i equals
+    d_k q / (1 - q): the rule's tail is exact there, and the cap applies
+    when the changes do not shrink."""
+    a, q = 3e-3, 0.87
+    d = [a * q ** k for k in range(6)]
+    remaining = a * q ** 6 / (1 - q)  # sum of all later changes
+    assert scf.tail_estimate(d[5], d[4], d[3]) == pytest.approx(remaining, rel=1e-12)
+    # growing or flat changes count as contracting at the cap
+    assert scf.tail_estimate(1e-6, 1e-6, 1e-6) == pytest.approx(1e-6 * scf.Q_CAP / (1 - scf.Q_CAP))
+    assert scf.tail_estimate(2e-6, 1e-6, 5e-7) == pytest.approx(2e-6 * scf.Q_CAP / (1 - scf.Q_CAP))
+    assert scf.tail_estimate(0.0, 1e-6, 2e-6) == 0.0
+    assert not scf.settled([1e-9, 1e-9], 1e-6)  # fewer than three cycles
+    assert scf.settled([4e-6, 2e-6, 1e-6], 1e-6)  # change 1e-6, tail 1e-6
+    assert not scf.settled([3e-6, 2e-6, 1e-6], 1e-6)  # q = 2/3: tail 2e-6
+    assert scf.settled([3e-6, 2e-6, 1e-6], 0.0)  # not watched
+
+
+def test_stopped_solve_lies_within_the_tolerance_of_the_fixed_point():
+    """Methane's occupied levels 2a1 and t2 lie 0.064 Ha apart here, so the
+    time-dependent Gram-Schmidt separates them slowly (a ratio near 0.8 per
+    30-step cycle) and the energy change drops below 1e-6 Ha while the
+    density still moves by ~1e-4 per cycle.  Stopped by the full rule, the
+    solve is within the tolerances of a run taken 60 cycles further; the
+    energy-only rule stops far short of it.  (Orbital storage: the same
+    steps, faster.)"""
+    mol, n, h, n_inner = W.methane(), (24, 24, 24), 0.45, 30
+    args = (n, h, mol.xyz, mol.Z, 5)
+    st, res = scf.scf(*args, n_inner=n_inner, max_cycles=400, storage="psi")
+    assert res["converged"]
+    assert res["err_eig"] <= 2e-6 and res["err_rho"] <= 2e-6
+    rho, eig, E = st.rho.copy(), res["eigenvalues"].copy(), res["E_total"]
+    st2, far = scf.scf(*args, n_inner=n_inner, fixed_cycles=60, state=st)
+    assert abs(E - far["E_total"]) <= 1e-6
+    assert np.abs(eig - far["eigenvalues"]).max() <= 4e-6
+    assert np.linalg.norm(rho - st2.rho) / np.linalg.norm(st2.rho) <= 4e-6
+    st3, early = scf.scf(*args, n_inner=n_inner, eig_tol=0.0, rho_tol=0.0, storage="psi")
+    assert early["cycles"] < 0.6 * res["cycles"]
+    assert np.linalg.norm(st3.rho - st2.rho) / np.linalg.norm(st2.rho) > 3e-5
+
+
+def test_seeded_start_offsets():
+    """seed 0 is the fixed start 0.25 sin(...); other seeds draw every
+    component uniformly in [-0.25, 0.25) and differ from each other."""
+    off0 = scf.start_offsets(4, 0)
+    for j in range(4):
+        assert off0[j, 0] == pytest.approx(0.25 * np.sin(1.0 + 2.1 * j), abs=1e-15)
+        assert off0[j, 2] == pytest.approx(0.25 * np.sin(3.0 + 4.7 * j), abs=1e-15)
+    a, b = scf.start_offsets(2000, 7), scf.start_offsets(2000, 8)
+    assert np.abs(a).max() <= 0.25 and not np.allclose(a, b)
+    # uniform on [-0.25, 0.25): mean 0 and variance 0.25^2 / 3 within 5 sigma of 6000 draws
+    assert abs(a.mean()) < 5 * 0.25 / np.sqrt(3 * a.size)
+    assert a.var() == pytest.approx(0.25 ** 2 / 3, rel=0.05)
+    np.testing.assert_array_equal(scf.start_offsets(3, 7), a[:3])
+
+
+def test_fixed_point_does_not_depend_on_the_seed():
+    mol, n, h = W.lih(3.0), (20, 18, 22), 0.35
+    _, a = scf.scf(n, h, mol.xyz, mol.Z, 2, n_inner=15, e_tol=1e-10, eig_tol=1e-8, rho_tol=1e-8, max_cycles=600)
+    _, b = scf.scf(n, h, mol.xyz, mol.Z, 2, n_inner=15, e_tol=1e-10, eig_tol=1e-8, rho_tol=1e-8, max_cycles=600,
+                   seed=11)
+    assert a["converged"] and b["converged"]
+    assert a["E_total"] == pytest.approx(b["E_total"], abs=1e-8)
+    np.testing.assert_allclose(a["eigenvalues"], b["eigenvalues"], atol=1e-7)

@@ -216,3 +216,23 @@ def random_state(n: Sequence[int], n_orb: int, seed: int, q: int = 19):
     u = rng.uniform(-0.2, 0.2, size=(n_orb, nz, ny, nx))
     u[0] = 0.0
     return f, v, sigma, lam, u
+
+
+# ------------------------------------------------ converged reference solves
+def converged_cases():
+    """Solves whose oracle fixed points are stored under tests/golden (written
+    by tests/golden/make_goldens.py): small grids the oracle converges in
+    minutes, a served mix of five molecules, and the 128^3 methane and 96^3
+    water (first geometry of the scan) bench workloads."""
+    scan0 = water_scan(64, 0)[0]
+    return {
+        "he_24": Workload("He 24^3 h=0.4", helium(), (24, 24, 24), 0.4, n_inner=20),
+        "h2_24": Workload("H2 24^3 h=0.4", h2(), (24, 24, 24), 0.4, n_inner=20),
+        "lih_28": Workload("LiH 28x28x32 h=0.35", lih(), (28, 28, 32), 0.35, n_inner=30),
+        "h2o_32": Workload("H2O 32^3 h=0.35", water(), (32, 32, 32), 0.35, n_inner=40),
+        "ch4_32": Workload("CH4 32^3 h=0.35", methane(), (32, 32, 32), 0.35, n_inner=40),
+        "dimer_36": Workload("(H2O)2 36x32x34 h=0.35", water_cluster(2, seed=3, box=11.0, min_oo=5.0, margin=2.5),
+                             (36, 32, 34), 0.35, n_inner=40),
+        "ch4_128": ch4_128(),
+        "h2o_96": water_96(scan0),
+    }
