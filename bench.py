@@ -1,18 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the lattice-kinetic Kohn-Sham solver on GB300.
 
-One step = one complete self-consistent solve of the workload (orbital start,
-relaxation cycles, Hartree, LDA, orthonormalisation, energies) to
-|dE| < 1e-6 Ha, through the C ABI.  The metric is orbital-site updates per
-second (GLUPS): relaxation steps x orbitals x grid sites / wall time of the
-solves.  Default workload: methane, 128^3 grid at h = 0.2 bohr, five doubly
-occupied orbitals, FP32 populations and collide with FP64 reductions.
+The metric is orbital-site updates per second (GLUPS): relaxation steps x
+orbitals x grid sites / wall time, through the C ABI.  Default workload: the
+8-water cluster, 256^3 grid at h = 0.2 bohr, 40 doubly occupied orbitals,
+FP32 populations and collide with FP64 overlaps, Cholesky, energies and
+Poisson (about 110 GB on the device); one bench step = one self-consistent
+cycle (100 relaxation steps, density, Hartree, LDA, orthonormalisation,
+energies), continuing from the previous one.  Workloads that fit a full
+solve per step (--workload ch4_128, h2o_96, he_24) run one complete solve
+per step to the stop rule of include/lbks.h.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lbks|reference]
 
 --impl reference times the FP64 numpy oracle (the method as the paper states
 it, plain CPU code) on the host cores, one relaxation step of the same
-workload per bench step.
+workload per bench step (the cluster: the same molecule on a 64^3 grid of
+the same box), one oracle process per core as far as host memory allows.
 
 Multi-GPU (torchrun): every rank solves its own replica (independent
 systems, no collective on the data path); value = all ranks' updates / the
@@ -44,6 +48,12 @@ L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
 KERNEL_SRC = os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_relax.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "stream_collide_ch4_128_fp32.json")
 KERNEL_END_MARK = b"// u_(j-1)(r) = -omega sum_{k<j} Lambda_jk psi_k(r)"
+# more than eight orbitals: the relaxation step is the wide stream-collide
+# kernel plus the tensor-core overlap; their DRAM bytes per orbital-site from
+# one ncu capture, valid while both kernels' sources are unchanged
+WIDE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_wide_h2o8_fp32.json")
+WIDE_SOURCES = (os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_wide.cuh"),
+                os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_gram_tc.cu"))
 
 WORKLOADS = {
     "ch4_128": W.ch4_128,
@@ -59,7 +69,7 @@ CYCLES = {"h2o8_256": W.cluster_256}
 # (batched and served workloads: one water geometry at 96^3)
 ORACLE_SAMPLE_OF = {"h2o8_256": W.cluster_sample, "water_scan_64": W.water_96, "serving_mix": W.water_96,
                     "h2o_relax_96": W.water_96}
-SERVING = {"serving_mix": 48}  # requests of the mixed stream (Poisson arrivals, mean 200/s, seed 0)
+SERVING = {"serving_mix": 200}  # requests of the mixed stream (Poisson arrivals, mean 200/s, seed 0)
 BATCHES = {
     # 64 seeded water geometries (O-H ~ U[1.6, 2.0] bohr, HOH ~ U[95, 115] deg), 96^3 grid, h = 0.2
     "water_scan_64": (64, 0),
@@ -79,8 +89,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lbks", "reference"], default="lbks")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CYCLES) + sorted(BATCHES) + sorted(SERVING)
-                    + sorted(RELAXATIONS), default="ch4_128")
+                    + sorted(RELAXATIONS), default="h2o8_256")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent solve slots")
+    ap.add_argument("--requests", type=int, default=0, help="serving: requests of the stream (0: the default)")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
     ap.add_argument("--storage", choices=["populations", "psi"], default="populations",
                     help="what a relaxation step keeps: the 19 populations per orbital-site (any omega), or, at "
@@ -95,7 +106,8 @@ def parse_args():
                     help="--kernel-only: which step to launch alone")
     ap.add_argument("--relax-variant", type=int, choices=[0, 1, 2, 3, 4], default=0,
                     help="stream-collide variant: 0 tuned per shape, 1 one site per thread, 2 site pairs, "
-                         "3 one site with the next orbital prefetched, 4 populations staged by cp.async")
+                         "3 one site with the next orbital prefetched, 4 populations copied by the tensor memory "
+                         "accelerator (omega = 1)")
     return ap.parse_args()
 
 
@@ -129,43 +141,84 @@ print(json.dumps({{"times": times, "updates_per_step": no * n[0] * n[1] * n[2]}}
 """
 
 
-def run_oracle_sample(workload: str, seconds: float, min_steps: int, max_steps: int):
+def oracle_workload(workload: str):
     fn = WORKLOADS[workload] if workload in WORKLOADS else ORACLE_SAMPLE_OF[workload]
-    code = ORACLE_SAMPLE.format(root=ROOT, wl=fn.__name__, seconds=seconds,
+    return fn
+
+
+def oracle_processes(workload: str) -> int:
+    """Concurrent single-thread oracle processes: one per host core, as far as
+    half of the available host memory holds them (about six population
+    arrays of the sampled workload each, plus 1 GB)."""
+    w = oracle_workload(workload)()
+    per = 6 * 19 * 8 * w.n_orb * w.sites + (1 << 30)
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    if avail is None:
+        avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    return max(1, min(os.cpu_count() or 1, int(0.5 * avail // per)))
+
+
+def run_oracle_samples(workload: str, seconds: float, min_steps: int, max_steps: int, procs: int = 1):
+    """Runs `procs` oracle processes at once (one thread each); returns their
+    step timings."""
+    code = ORACLE_SAMPLE.format(root=ROOT, wl=oracle_workload(workload).__name__, seconds=seconds,
                                 min_steps=min_steps, max_steps=max_steps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    out = []
+    for p in ps:
+        so, se = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed:\n" + se[-2000:])
+        out.append(json.loads(so.strip().splitlines()[-1]))
+    return out
+
+
+def oracle_rate(samples, skip=0):
+    """Whole-host rate of concurrent samples: all processes' timed updates
+    over the slowest process's timed seconds."""
+    steps = sum(len(s["times"]) - skip for s in samples)
+    t = max(sum(s["times"][skip:]) for s in samples)
+    return steps * samples[0]["updates_per_step"] / t / 1e9, steps, t
 
 
 def cpu_baseline(workload: str, seconds: float):
-    s = run_oracle_sample(workload, seconds, 2, 1000)
-    t = sum(s["times"])
-    return {"value": len(s["times"]) * s["updates_per_step"] / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(s['times'])} relaxation steps (Eq. KSLB, all orbitals) of the "
-                      f"{(WORKLOADS.get(workload) or ORACLE_SAMPLE_OF[workload])().name} workload from "
-                      f"its Gaussian start, FP64 numpy, one thread, {t:.1f} s"}
+    name = oracle_workload(workload)().name
+    one = run_oracle_samples(workload, seconds, 2, 1000)
+    v1, n1, t1 = oracle_rate(one)
+    procs = oracle_processes(workload)
+    many = run_oracle_samples(workload, seconds, 2, 1000, procs)
+    v, n, t = oracle_rate(many)
+    return {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{n} relaxation steps (Eq. KSLB, all orbitals) of the {name} workload from its Gaussian "
+                      f"start in {procs} concurrent FP64 numpy processes of one thread each, {t:.1f} s",
+            "one_core": {"value": v1, "cores": 1, "sample": f"{n1} steps, one process, {t1:.1f} s"}}
 
 
 def main_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w = (WORKLOADS[args.workload] if args.workload in WORKLOADS else ORACLE_SAMPLE_OF[args.workload])()
-    s = run_oracle_sample(args.workload, 0.0, args.warmup + args.steps, args.warmup + args.steps)
-    times = s["times"][args.warmup:]
-    t = sum(times)
-    value = len(times) * s["updates_per_step"] / t / 1e9
+    w = oracle_workload(args.workload)()
+    procs = oracle_processes(args.workload)
+    samples = run_oracle_samples(args.workload, 0.0, args.warmup + args.steps, args.warmup + args.steps, procs)
+    value, steps, t = oracle_rate(samples, skip=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times), "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name + " single solve", "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
-                   "step": "one oracle relaxation step of all orbitals"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{len(times)} timed relaxation steps of {w.name}, FP64 numpy, one thread"},
+        "config": {"workload": w.name, "grid": list(w.n), "h": w.h, "n_orb": w.n_orb,
+                   "step": f"one oracle relaxation step of all orbitals in each of {procs} concurrent processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{steps} timed relaxation steps of {w.name} in {procs} concurrent FP64 numpy "
+                                   "processes of one thread each"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -257,6 +310,28 @@ def recorded_traffic():
         sha = kernel_source_sha()
         if rec.get("kernel_src_sha256") == sha:
             return float(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def wide_sources_sha():
+    """sha256 over the sources of the wide relaxation step's two kernels."""
+    h = hashlib.sha256()
+    for path in WIDE_SOURCES:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
+
+
+def recorded_wide_traffic(units):
+    """DRAM bytes of one wide relaxation step (stream-collide + overlap) over
+    `units` orbital-sites, scaled from the committed ncu capture of a smaller
+    grid (traffic grows in proportion to the orbital-sites), if it was taken
+    on the current sources."""
+    try:
+        rec = json.load(open(WIDE_TRAFFIC_FILE))
+        if rec.get("sources_sha256") == wide_sources_sha():
+            return float(rec["dram_bytes_per_orbital_site"]) * units
     except (OSError, KeyError, ValueError):
         pass
     return None
@@ -415,9 +490,9 @@ def main_kernel_only(args):
     ms, units = time_stream_collide(torch, lbks, w, prec, stream, launches=args.launches)
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
     gbs = 38 * elem * units / (ms / 1e3) / 1e9
-    print(json.dumps({"kernel": {2: "k_stream_collide_pair", 4: "k_stream_collide_async"}.get(args.relax_variant,
-                                                                                            "k_stream_collide"),
-                      "variant": ("sites (untuned)", "sites", "pairs", "prefetch", "async")[args.relax_variant],
+    print(json.dumps({"kernel": {2: "k_stream_collide_pair", 4: "k_stream_collide_bulk"}.get(args.relax_variant,
+                                                                                           "k_stream_collide"),
+                      "variant": ("sites (untuned)", "sites", "pairs", "prefetch", "bulk")[args.relax_variant],
                       "grid": list(w.n), "n_orb": w.n_orb, "dtype": args.precision,
                       "ms_per_launch": ms, "algorithmic_GBps": gbs, "launches": args.launches}), flush=True)
     return 0
@@ -517,7 +592,20 @@ def _serve_arm(lbks, reqs, precision, slots, warm, storage=0):
     finally:
         lbks.lbks_server_destroy(srv)
     lat = sorted(out[rid][1]["latency_s"] for rid in ids)
-    return lat, makespan, [out[rid][0] for rid in ids]
+    run = sorted(out[rid][1]["run_s"] for rid in ids)
+    return lat, run, makespan, [out[rid][0] for rid in ids]
+
+
+def percentile(sorted_values, q):
+    """Nearest-rank percentile: the smallest value with at least a fraction q
+    of the sample at or below it."""
+    n = len(sorted_values)
+    return sorted_values[min(n - 1, max(0, math.ceil(q * n) - 1))]
+
+
+def latency_summary(values):
+    return {"p50": percentile(values, 0.5), "p90": percentile(values, 0.9), "p99": percentile(values, 0.99),
+            "max": values[-1], "n": len(values)}
 
 
 def main_serving(args):
@@ -527,22 +615,21 @@ def main_serving(args):
     from paper_1507_07666_gb300 import build as build_mod
     build_mod.build()
     from paper_1507_07666_gb300 import lbks
-    reqs = W.serving_stream(SERVING[args.workload], 200.0, 0)
+    reqs = W.serving_stream(args.requests or SERVING[args.workload], 200.0, 0)
     kinds = {}
     for t, w in reqs:
         kinds.setdefault(w.name, (t, w))
     warm = list(kinds.values())
-    pct = lambda lat, q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
     psi = args.storage == "psi"  # orbital storage: FP32 (it has no bfloat16 form)
-    lat, span, res = _serve_arm(lbks, reqs, lbks.FP32 if psi else lbks.BF16, args.slots, warm,
-                                lbks.STORE_PSI if psi else lbks.STORE_POPULATIONS)
-    lat64, span64, res64 = _serve_arm(lbks, reqs, lbks.FP64, 1, warm)
+    lat, run, span, res = _serve_arm(lbks, reqs, lbks.FP32 if psi else lbks.BF16, args.slots, warm,
+                                     lbks.STORE_PSI if psi else lbks.STORE_POPULATIONS)
+    lat64, run64, span64, res64 = _serve_arm(lbks, reqs, lbks.FP64, 1, warm)
     de = max(abs(a["E_total"] - b["E_total"]) for a, b in zip(res, res64))
     odd = [{"request": i, "kind": w.name, "h": round(w.h, 4), "converged": a["converged"], "status": a["status"],
             "cycles": a["cycles"], "E_total": a["E_total"], "E_total_fp64": b["E_total"],
             "fp64_converged": b["converged"]}
            for i, ((_, w), a, b) in enumerate(zip(reqs, res, res64))
-           if not a["converged"] or not b["converged"] or abs(a["E_total"] - b["E_total"]) > 1e-4]
+           if not a["converged"] or not b["converged"] or abs(a["E_total"] - b["E_total"]) > 1e-5]
     line = {
         "metric": "solves/s (served mixed stream)", "value": len(reqs) / span, "unit": "solves/s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * span, "higher_is_better": True, "scaling": "weak",
@@ -551,8 +638,12 @@ def main_serving(args):
                                "H2 48^3, He 48^3, LiH 64^3, H2O 96^3, CH4 128^3, h ~ U[0.2, 0.25], jitter 0.05 bohr",
                    "slots": args.slots,
                    "precision": "FP32, orbital storage (omega = 1)" if psi else "BF16 populations + FP32 polish"},
-        "latency_s": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "max": lat[-1]},
-        "plain_fp64_single_slot": {"solves_per_s": len(reqs) / span64, "p50": pct(lat64, 0.5), "p99": pct(lat64, 0.99)},
+        "latency_s": latency_summary(lat),
+        "run_s": latency_summary(run),
+        "latency_note": "latency = submit to result (queueing included: the whole stream arrives within about "
+                        f"{reqs[-1][0]:.2f} s); run_s = slot start to result",
+        "plain_fp64_single_slot": {"solves_per_s": len(reqs) / span64, "latency_s": latency_summary(lat64),
+                                   "run_s": latency_summary(run64)},
         "max_abs_dE_vs_fp64_Ha": de,
         "converged": sum(r["converged"] for r in res),
         "fp64_converged": sum(r["converged"] for r in res64),
@@ -739,7 +830,9 @@ def main_lbks(args):
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_launch / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if (wide or psi_mode) else recorded_traffic(),
+                "traffic": None if psi_mode else
+                (recorded_wide_traffic(units) if wide and prec == lbks.FP32 else
+                 None if wide else recorded_traffic()),
                 "kernel": kname,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms,
                 "peak_source": f"hbm_gbs of {peak_kind}"}

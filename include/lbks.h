@@ -118,21 +118,23 @@ typedef struct lbks_params {
 
 /* Stop rule of lbks_scf and lbks_batch_scf (the paper stops once the orbital
  * energies no longer change, Sec. 4; the bound is this library's reading).
- * Per cycle c three changes are watched: d_E = |E_c - E_(c-1)|, d_eig =
- * max_j |eps_j,c - eps_j,(c-1)| and d_rho = ||rho_c - rho_(c-1)|| / ||rho_c||.
- * Each is extended by its geometric tail d q / (1 - q), q the larger of the
- * last two contraction ratios d_c / d_(c-1), d_(c-1) / d_(c-2), capped at 0.98
- * (a change that does not shrink counts as shrinking at 0.98).  A system has
- * converged once, for each quantity with a positive tolerance (e_tol,
- * eig_tol, rho_tol), both its change and its tail are within the tolerance,
- * or its change is below the rounding floor 8 u s: u the unit roundoff of
- * the orbital values (2^-53 for LBKS_FP64, 2^-24 otherwise), s = |E|,
- * max_j |eps_j| and 1 for the three quantities (single-precision orbitals keep
- * the changes from falling below a few u s); at least three cycles run.  The tail estimates the distance left to the
- * fixed point: a change alone does not bound it when a cycle contracts the
- * error slowly (the Gram-Schmidt source of Eq. KSLB separates occupied
- * orbitals of close eigenvalues slowly, and that rotation leaks into the
- * density). */
+ * Cycles are grouped in blocks of 4.  At the end of block m three changes
+ * since the end of block m-1 are watched: D_E = |E_m - E_(m-1)|, D_eig =
+ * max_j |eps_j,m - eps_j,(m-1)| and D_rho = ||rho_m - rho_(m-1)|| / ||rho_m||.
+ * Each is extended by its geometric tail D r / (1 - r), r the larger of the
+ * last two ratios D_m / D_(m-1), D_(m-1) / D_(m-2), capped at 0.92 (0.98 per
+ * cycle: a change that does not shrink counts as shrinking at that rate).  A
+ * system has converged once, for each quantity with a positive tolerance
+ * (e_tol, eig_tol, rho_tol), both its change and its tail are within the
+ * tolerance, or its change is below the rounding floor 8 u s: u the unit
+ * roundoff of the orbital values (2^-53 for LBKS_FP64, 2^-24 otherwise), s =
+ * |E|, max_j |eps_j| and 1 for the three quantities; at least three blocks
+ * run.  The tail estimates the distance left to the fixed point: a change
+ * alone does not bound it when a cycle contracts the error slowly (the
+ * Gram-Schmidt source of Eq. KSLB separates occupied orbitals of close
+ * eigenvalues slowly, and that rotation leaks into the density); blocks let
+ * a slow drift stand out of single-precision rounding noise, which does not
+ * grow with the block length. */
 
 void lbks_params_default(lbks_params* p);
 
@@ -146,6 +148,23 @@ const char* lbks_version(void);
 /* Number of kernels this library has enqueued in this process (a CUDA-graph
  * replay counts each of its kernel nodes).  Bookkeeping only. */
 uint64_t lbks_kernel_launches(void);
+
+/* Bounded device waits.  The tensor-core overlap kernel (more than eight FP32
+ * orbitals) waits on mbarriers for its own tensor-core work; every such wait
+ * gives up after a number of polls (default 2^22, far beyond any normal
+ * completion).  A block whose wait gave up counts a timeout, writes NaN
+ * partial sums -- the overlap, and with it the solve, becomes non-finite and
+ * lbks_scf returns LBKS_ENOTCONV -- waits for its own tensor-core work
+ * (2^22 polls at most, whatever the limit), frees its tensor memory and
+ * returns, leaving the context usable.
+ * lbks_set_wait_limit sets the polls of these waits for launches enqueued
+ * afterwards (0: every wait gives up at once; a handle's captured cycle graph
+ * keeps the value it was captured with) and returns the previous value;
+ * process-wide, meant for tests of the failure path.  lbks_wait_timeouts
+ * returns the number of blocks whose wait gave up on the current device
+ * since the library was loaded (synchronous). */
+uint32_t lbks_set_wait_limit(uint32_t polls);
+uint64_t lbks_wait_timeouts(void);
 
 /* ------------------------------------------------------------------ systems */
 typedef struct lbks_system lbks_system;
@@ -185,10 +204,11 @@ typedef struct lbks_result {
     int converged;
     int poisson_iters;                /* CG iterations, all cycles */
     double wall_s;
-    double d_eig;                     /* max_j |eps_j,c - eps_j,(c-1)| of the last cycle */
-    double d_rho;                     /* ||rho_c - rho_(c-1)|| / ||rho_c|| of the last cycle */
-    double err_E, err_eig, err_rho;   /* geometric tails of the three changes (see the stop rule);
-                                         INFINITY before three cycles */
+    double d_eig;                     /* D_eig of the last block of the stop rule */
+    double d_rho;                     /* D_rho of the last block */
+    double err_E, err_eig, err_rho;   /* geometric tails of the three block changes (the stop
+                                         rule's estimates of the distance left); INFINITY before
+                                         three blocks */
 } lbks_result;
 
 /* The self-consistent loop of the Born-Oppenheimer scenario (Sec. 3.1: nuclei
@@ -222,9 +242,15 @@ typedef struct lbks_energy_terms {
  *      populations by warp shuffle (nx even and arrays 16-byte aligned, else 0);
  *   2  one site per thread, the next orbital's populations loaded before the
  *      current orbital collides (more loads in flight, fewer threads);
- *   3  one site per thread, the pulled populations of a 256-site tile staged
- *      in shared memory by cp.async several tiles ahead (N % 8 == 0 and
- *      16-byte aligned arrays, else 0).
+ *   3  omega = 1, FP32 or bfloat16 populations, any orbital count: the pulled
+ *      populations of each (256-site tile, orbital) copied into a ring of
+ *      shared-memory slots by the tensor memory accelerator (bulk copies, one
+ *      producer warp, mbarriers), consumer warps collide one site each, and
+ *      the overlap of the step is summed from the tile's orbitals in shared
+ *      memory (no separate overlap kernel; N a multiple of 8 and 16-byte
+ *      aligned arrays, else 0).
+ * More than 8 orbitals: 0 is the one-orbital-per-thread kernel followed by the
+ * tensor-core overlap; 1 and 2 are taken as 0.
  * In orbital storage (LBKS_STORE_PSI) the variants are 0: the stencil staged
  * in shared memory by tiles, 1: one site per thread from L1, 2: the stencil's
  * boxes copied into shared memory by the tensor memory accelerator, which also
@@ -440,8 +466,10 @@ int lbks_relax_step(int precision, int nx, int ny, int nz, int n_orb, double h,
  * calls share the one array, so calls that overlap on the GPU (different
  * streams, or different host threads without ordering) race and give wrong
  * overlaps: order them on one stream.  EINVAL for n_orb > 8 (the array's
- * limit) and for every argument lbks_relax_step rejects.  Arguments and
- * results are exactly those of lbks_relax_step. */
+ * limit) and for every argument lbks_relax_step rejects; all three
+ * precisions (LBKS_FP64, LBKS_FP32, LBKS_BF16) are accepted.  Arguments and
+ * results are exactly those of lbks_relax_step, and so is the stream-collide
+ * variant it runs (lbks_set_relax_variant). */
 int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, int n_orb, double h,
                             double omega, double theta, double dt,
                             const void* f_in_dev, const void* u_in_dev, const double* V_dev,
@@ -470,6 +498,18 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
                         const void* psi_in_dev, const double* lambda_in_dev, const double* Vc_dev,
                         const double* sigma_in_dev, void* psi_out_dev, double* S_out_dev,
                         double* lambda_out_dev, double* sigma_out_dev, void* stream);
+
+/* Energy matrix of n_orb orbitals in the potential V (the orbital energies of
+ * Eq. KSE as a Ritz problem; kinetic operator of the equilibrium stencil,
+ * Sec. 3): out[j*n_orb + k] = H_jk = h^3 sum_r psi_j (T_h + V) psi_k and
+ * out[n_orb^2 + j] = h^3 sum_r psi_j T_h psi_j, T_h psi = (psi - K_xi psi) /
+ * (theta h^2), K_xi psi(r) = sum_p xi_p psi(r - v_p), psi = 0 outside the box.
+ * psi: n_orb*N values (double for LBKS_FP64, float otherwise), orbital-major;
+ * V: N doubles; out: n_orb^2 + n_orb doubles.  The solver's own kernel (FP32
+ * orbitals: FP32 neighbour differences and products, FP64 sums over sites).
+ * Asynchronous on stream. */
+int lbks_energy_matrix(int precision, int nx, int ny, int nz, int n_orb, double h, double theta,
+                       const void* psi_dev, const double* V_dev, double* out_dev, void* stream);
 
 /* W field of the orthogonalisation source (Sec. 3, W_jp):
  * u_(j-1)(r) = -omega sum_{k<j} lambda_jk psi_k(r), j = 1..n_orb-1. */

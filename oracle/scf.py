@@ -23,18 +23,19 @@ cycles does not bound the distance to the fixed point when a cycle contracts
 the error slowly: the time-dependent Gram-Schmidt of Eq. KSLB separates two
 occupied orbitals at the rate of their eigenvalue ratio, and the part of the
 orthogonalisation source that the potential term does not carry leaks that
-slow rotation into the occupied span, hence into the density.  So three
-quantities are watched -- the total energy, the eigenvalues (largest change)
-and the density (relative L2 change) -- and for each the last change d_c is
-extended by its geometric tail d_c q / (1 - q), q the larger of the last two
-contraction ratios d_c / d_{c-1}, d_{c-1} / d_{c-2}, capped at Q_CAP (a
-sequence that does not contract counts as contracting at Q_CAP).  The loop
-stops once, for every quantity with a positive tolerance, both d_c and that
-tail are within the tolerance, or d_c is below the rounding floor
+slow rotation into the occupied span, hence into the density.  Cycles are
+grouped in blocks of STOP_BLOCK; at the end of each block three changes since
+the previous block end are watched -- the total energy, the eigenvalues
+(largest change) and the density (relative L2 change) -- and for each the
+last block change D_m is extended by its geometric tail D_m r / (1 - r), r
+the larger of the last two ratios D_m / D_{m-1}, D_{m-1} / D_{m-2}, capped at
+Q_CAP (a sequence that does not contract counts as contracting at Q_CAP).
+The loop stops once, for every quantity with a positive tolerance, both D_m
+and that tail are within the tolerance, or D_m is below the rounding floor
 FLOOR_ULPS u s (u the unit roundoff of the orbital values, 2^-53 here; s =
-|E|, max_j |eps_j| and 1 for the three quantities); at least three cycles
-run.  The floor matters only for single-precision orbitals, whose rounding
-keeps the per-cycle changes from falling below a few u s.
+|E|, max_j |eps_j| and 1 for the three quantities); at least three blocks
+run.  Blocks let a slow drift stand out of the rounding noise of
+single-precision orbitals, which does not grow with the block length.
 """
 from __future__ import annotations
 
@@ -60,7 +61,8 @@ def external_potential(n, h, xyz, Z, a):
     return v
 
 
-Q_CAP = 0.98
+STOP_BLOCK = 4
+Q_CAP = 0.92  # per block of four cycles: 0.98 per cycle
 FLOOR_ULPS = 8.0
 UNIT_ROUNDOFF = 2.0 ** -53
 
@@ -227,27 +229,31 @@ def scf(n, h, xyz, Z, n_orb, n_inner=50, e_tol=1e-6, max_cycles=200, mix=0.5,
     st = state if state is not None else State(n, h, xyz, Z, n_orb, theta, omega, softening, poisson_rtol, seed,
                                                storage)
     history = [st.terms["E_total"]]
-    d_e, d_eig, d_rho = [], [], []
+    d_e, d_eig, d_rho = [], [], []  # block changes
+    ref_E, ref_eig, ref_rho = st.terms["E_total"], st.terms["eigenvalues"].copy(), st.rho.copy()
     converged = False
     cycles = 0
+    de = math.inf
     limit = fixed_cycles if fixed_cycles is not None else max_cycles
     for c in range(limit):
-        prev_eig, prev_rho = st.terms["eigenvalues"].copy(), st.rho.copy()
-        d_e.append(st.cycle(n_inner))
-        d_eig.append(float(np.abs(st.terms["eigenvalues"] - prev_eig).max()))
-        d_rho.append(float(np.linalg.norm(st.rho - prev_rho) / np.linalg.norm(st.rho)))
+        de = st.cycle(n_inner)
         cycles += 1
         history.append(st.terms["E_total"])
-        eig = st.terms["eigenvalues"]
-        if (fixed_cycles is None and settled(d_e, e_tol, abs(st.terms["E_total"]))
-                and settled(d_eig, eig_tol, float(np.abs(eig).max())) and settled(d_rho, rho_tol)):
-            converged = True
-            break
+        if cycles % STOP_BLOCK == 0:
+            E, eig = st.terms["E_total"], st.terms["eigenvalues"]
+            d_e.append(abs(E - ref_E))
+            d_eig.append(float(np.abs(eig - ref_eig).max()))
+            d_rho.append(float(np.linalg.norm(st.rho - ref_rho) / np.linalg.norm(st.rho)))
+            ref_E, ref_eig, ref_rho = E, eig.copy(), st.rho.copy()
+            if (fixed_cycles is None and settled(d_e, e_tol, abs(E))
+                    and settled(d_eig, eig_tol, float(np.abs(eig).max())) and settled(d_rho, rho_tol)):
+                converged = True
+                break
         st.mix(mix)
     tails = [tail_estimate(*d[-1:-4:-1]) if len(d) >= 3 else math.inf for d in (d_e, d_eig, d_rho)]
     res = dict(st.terms)
     res.update({"cycles": cycles, "steps": st.steps, "converged": converged,
-                "dE": d_e[-1] if d_e else math.inf, "d_eig": d_eig[-1] if d_eig else math.inf,
+                "dE": de, "d_eig": d_eig[-1] if d_eig else math.inf,
                 "d_rho": d_rho[-1] if d_rho else math.inf, "err_E": tails[0], "err_eig": tails[1],
                 "err_rho": tails[2], "history": history})
     return st, res

@@ -228,10 +228,12 @@ std::vector<double> start_offsets(int n_orb, uint64_t seed) {
     return off;
 }
 
-// Stop rule (include/lbks.h): the last three per-cycle changes of one
-// watched quantity, newest first.  A change below kFloorUlps u s (u the unit
-// roundoff of the orbital values, s the quantity's scale) is rounding noise.
-constexpr double kTailCap = 0.98;
+// Stop rule (include/lbks.h): the changes of one watched quantity over the
+// last three blocks of kStopBlock cycles, newest first.  A change below
+// kFloorUlps u s (u the unit roundoff of the orbital values, s the quantity's
+// scale) is rounding noise.
+constexpr int kStopBlock = 4;
+constexpr double kTailCap = 0.92;  // per block: a contraction of 0.98 per cycle
 constexpr double kFloorUlps = 8.0;
 struct Changes {
     double d[3] = {INFINITY, INFINITY, INFINITY};
@@ -282,6 +284,7 @@ struct lbks_system {
     void* u = nullptr;
     void* psi = nullptr;
     double *vin = nullptr, *vout = nullptr, *vext = nullptr, *vh = nullptr, *rho = nullptr;
+    double* rho_ref = nullptr;  // density at the end of the last block of the stop rule
     double* pvec = nullptr;  // b, r, p, ap, z, tmp (B*N each), then the multigrid levels
     CGState* cg = nullptr;
     MGHierarchy mg;
@@ -393,7 +396,7 @@ int hartree_solve(lbks_system* s, cudaStream_t st) {
 // current orthonormal orbitals of every active system.
 int evaluate(lbks_system* s, cudaStream_t st, int first) {
     const int B = s->B;
-    cudaError_t e = s->ops->density(s->n_orb, s->g, s->h, s->psi, s->rho, s->mp, s->sc, B, st);
+    cudaError_t e = s->ops->density(s->n_orb, s->g, s->h, s->psi, s->rho, s->rho_ref, s->mp, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "density");
     int rc = hartree_solve(s, st);
     if (rc != LBKS_OK) return rc;
@@ -550,6 +553,13 @@ int polish(lbks_system* s, cudaStream_t st) {
     return LBKS_OK;
 }
 
+// Keeps the current density as the reference of the stop rule's next block
+// (the density kernel measures the change against it).
+int mark_block(lbks_system* s, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(s->rho_ref, s->rho, sizeof(double) * s->N * s->B, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "reference density");
+}
+
 // Relaxation cycles of all systems in lock step; a system stops (drops out
 // of every launch) once the stop rule holds for it (include/lbks.h), unless
 // `fixed` (exactly n cycles).
@@ -557,16 +567,19 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
     if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
     const int B = s->B, no = s->n_orb;
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<double> prev(B), prev_eig((size_t)B * no);
+    // per cycle: the energy (BF16 polish switch, lbks_result.dE); per block of
+    // kStopBlock cycles: energy, eigenvalues and density (the stop rule)
+    std::vector<double> prev(B), ref_E(B), ref_eig((size_t)B * no), de1(B, INFINITY), de2(B, INFINITY);
     std::vector<Changes> dE(B), dEig(B), dRho(B);
     std::vector<int> cycles(B, 0), converged(B, 0);
     int* act = host_active(s);
     for (int i = 0; i < B; ++i) {
-        prev[i] = s->terms[i].E_total;
-        for (int j = 0; j < no; ++j) prev_eig[(size_t)i * no + j] = s->terms[i].eigenvalues[j];
+        prev[i] = ref_E[i] = s->terms[i].E_total;
+        for (int j = 0; j < no; ++j) ref_eig[(size_t)i * no + j] = s->terms[i].eigenvalues[j];
         act[i] = 1;
     }
     int rc = upload_active(s, st);
+    if (rc == LBKS_OK) rc = mark_block(s, st);  // the current density starts the first block
     if (rc != LBKS_OK) return rc;
     const int limit = fixed ? n : s->prm.max_cycles;
     const int start_iters = s->poisson_iters;
@@ -587,25 +600,32 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         const bool wait_polish = s->f_wide[0] && !fixed && (!s->polished || cycles_polished < 2);
         int remaining = 0;
         bool ready = true;
+        const bool block_end = (c + 1) % kStopBlock == 0;
         for (int i = 0; i < B; ++i) {
             if (!act[i]) continue;
             ++cycles[i];
             const lbks_energy_terms& t = s->terms[i];
             if (!std::isfinite(t.E_total)) return fail(LBKS_ENOTCONV, "system %d: energy not finite", i);
+            // per cycle: ready for FP32 storage below polish_tol, or stalled at
+            // the bfloat16 noise floor (|dE| no longer halving over two cycles)
+            de2[i] = de1[i];
+            de1[i] = std::fabs(t.E_total - prev[i]);
+            prev[i] = t.E_total;
+            const bool stalled = de1[i] < 100.0 * s->prm.polish_tol && de1[i] > 0.5 * de2[i];
+            if (!(de1[i] < s->prm.polish_tol || stalled)) ready = false;
+            if (!block_end) {
+                ++remaining;
+                continue;
+            }
             double de_eig = 0.0;
             for (int j = 0; j < no; ++j) {
-                de_eig = std::max(de_eig, std::fabs(t.eigenvalues[j] - prev_eig[(size_t)i * no + j]));
-                prev_eig[(size_t)i * no + j] = t.eigenvalues[j];
+                de_eig = std::max(de_eig, std::fabs(t.eigenvalues[j] - ref_eig[(size_t)i * no + j]));
+                ref_eig[(size_t)i * no + j] = t.eigenvalues[j];
             }
-            dE[i].push(std::fabs(t.E_total - prev[i]));
+            dE[i].push(std::fabs(t.E_total - ref_E[i]));
             dEig[i].push(de_eig);
             dRho[i].push(s->drho[i]);
-            prev[i] = t.E_total;
-            // ready for FP32 storage: below polish_tol, or stalled at the
-            // bfloat16 noise floor (|dE| no longer halving over two cycles)
-            const double d0 = dE[i].d[0], d2 = dE[i].d[2];
-            const bool stalled = d0 < 100.0 * s->prm.polish_tol && d0 > 0.5 * d2;
-            if (!(d0 < s->prm.polish_tol || stalled)) ready = false;
+            ref_E[i] = t.E_total;
             // rounding floors: FP64 orbitals 2^-53, FP32 (and the BF16 handle's
             // FP32 polish) 2^-24, scaled by |E|, max |eps_j| and 1
             const double u = s->ops->psi_elem == sizeof(double) ? 0x1.0p-53 : 0x1.0p-24;
@@ -619,6 +639,10 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
             } else {
                 ++remaining;
             }
+        }
+        if (block_end) {
+            rc = mark_block(s, st);
+            if (rc != LBKS_OK) return rc;
         }
         if (s->polished) ++cycles_polished;
         if (!remaining) break;
@@ -639,7 +663,7 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         lbks_result& r = out[i];
         memset(&r, 0, sizeof r);
         r.E_total = s->terms[i].E_total;
-        r.dE = dE[i].d[0];
+        r.dE = de1[i];
         for (int j = 0; j < no; ++j) r.eigenvalues[j] = s->terms[i].eigenvalues[j];
         r.n_electrons = s->terms[i].n_electrons;
         r.cycles = cycles[i];
@@ -676,11 +700,12 @@ TuneKey tune_key(int precision, int n_orb, double omega, int nx, int ny, int nz,
 // the shape, else one site per thread.
 int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) {
     const int mode = g_variant_mode.load();
-    if (n_orb > kMaxOrb) return kRelaxSites;
-    if (mode > 0) return mode - 1;
+    // more than kMaxOrb orbitals: the one-orbital-per-thread kernel or the bulk-copy one
+    if (mode > 0) return n_orb > kMaxOrb && mode - 1 != kRelaxBulk ? kRelaxSites : mode - 1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(tune_key(precision, n_orb, omega, nx, ny, nz, 1));
-    return it == g_tuned.end() ? kRelaxSites : it->second;
+    if (it == g_tuned.end()) return kRelaxSites;
+    return n_orb > kMaxOrb && it->second != kRelaxBulk ? kRelaxSites : it->second;
 }
 
 // Times both variants on the handle's own buffers before they hold state
@@ -693,15 +718,19 @@ int tune_relax(lbks_system* s) {
                         psi_tma_applies(s->nx, s->f[1], s->vprev, s->ops->psi_elem);
     if (mode > 0) {
         s->variant = mode - 1;
-        if (s->psi_storage && (s->variant == kRelaxAsync || (s->variant == kPsiKernelTma && !tma_ok)))
+        if (s->psi_storage && (s->variant == kRelaxBulk || (s->variant == kPsiKernelTma && !tma_ok)))
             s->variant = kPsiKernelTiled;
-        if (!s->psi_storage && s->n_orb > kMaxOrb) s->variant = kRelaxSites;
+        if (!s->psi_storage && s->n_orb > kMaxOrb && s->variant != kRelaxBulk) s->variant = kRelaxSites;
         return LBKS_OK;
     }
-    // more than kMaxOrb orbitals: one population kernel; in orbital storage the
-    // tiled step with its W-field pass is timed against the TMA step
+    // the bulk-copy kernel: omega = 1, FP32 or bfloat16 populations, N a multiple of 8
+    // (the launch checks alignment too and falls back to the one-site kernel)
+    const bool bulk_may = !s->psi_storage && s->prm.omega == 1.0 && s->prm.precision != LBKS_FP64 && s->N % 8 == 0;
+    // more than kMaxOrb orbitals: the one-orbital-per-thread population kernel
+    // against the bulk-copy kernel; in orbital storage the tiled step with its
+    // W-field pass against the TMA step
     const bool wide = s->n_orb > kMaxOrb;
-    if (wide && !tma_ok) {
+    if (wide && (s->psi_storage ? !tma_ok : !bulk_may)) {
         s->variant = kRelaxSites;
         return LBKS_OK;
     }
@@ -747,7 +776,7 @@ int tune_relax(lbks_system* s) {
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
     // variants that differ from the first kernel on this shape
     bool tried[kRelaxVariants] = {true, !wide && (s->psi_storage || s->nx % 2 == 0),
-                                  s->psi_storage ? tma_ok : s->n_orb > 1, !s->psi_storage && s->N % 8 == 0};
+                                  s->psi_storage ? tma_ok : (!wide && s->n_orb > 1), bulk_may};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
         e = step(v);  // warm-up
@@ -853,8 +882,11 @@ int initialise(lbks_system* s) {
     s->poisson_iters = 0;
     s->ready = true;
     int rc = evaluate(s, st, 1);
-    if (rc != LBKS_OK) s->ready = false;
-    return rc;
+    if (rc != LBKS_OK) {
+        s->ready = false;
+        return rc;
+    }
+    return mark_block(s, st);
 }
 
 int check_atoms(const lbks_system* s, int n_atoms, const double* xyz, const double* Z) {
@@ -883,7 +915,8 @@ void free_system(lbks_system* s) {
     if (s->poisson_graph) cudaGraphExecDestroy(s->poisson_graph);
     if (s->psi_storage) s->psi = nullptr;  // an alias of f[cur]
     void* ptrs[] = {s->u,   s->psi,   s->vin,    s->vout,          s->vext,          s->vh, s->rho, s->pvec,
-                    s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter, s->vprev};
+                    s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter, s->vprev,
+                    s->rho_ref};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (s->host) cudaFreeHost(s->host);
@@ -898,7 +931,7 @@ size_t bytes_of(const lbks_params* p, int nx, int ny, int nz, int n_orb, int B) 
     const bool psi = p->storage == LBKS_STORE_PSI;  // f[] hold psi, no separate psi array, one more field
     const size_t per = (psi ? ep * N * (size_t)n_orb * 2 : e * N * (size_t)n_orb * 19 * 2) +
                        ep * N * ((size_t)std::max(1, n_orb - 1) + (psi ? 0 : n_orb)) +
-                       sizeof(double) * N * (psi ? 12 : 11) + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
+                       sizeof(double) * N * (psi ? 13 : 12) + sizeof(double) * mg_coarse_doubles(nx, ny, nz) +
                        sizeof(double) * ((size_t)num_sms() * 8 * scratch_vals(n_orb) + small_per_sys(n_orb) +
                                          7 * kMaxAtoms) +
                        ((p->precision == LBKS_BF16 && p->polish_tol > 0.0) ? sizeof(float) * N * n_orb * 19 * 2 : 0);
@@ -955,6 +988,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     A((void**)&s->vext, 8 * NB);
     A((void**)&s->vh, 8 * NB);
     A((void**)&s->rho, 8 * NB);
+    A((void**)&s->rho_ref, 8 * NB);
     A((void**)&s->pvec, 8 * (6 * NB + B * mg_coarse_doubles(nx, ny, nz)));
     A((void**)&s->cg, sizeof(CGState) * B);
     A((void**)&s->small, sizeof(double) * (small_per_sys(n_orb) + 7 * kMaxAtoms) * B);
@@ -979,6 +1013,7 @@ int create(const lbks_params* p, int nx, int ny, int nz, double h, int n_orb, in
     if (err == cudaSuccess) err = cudaMemsetAsync(s->sc.counter, 0, sizeof(unsigned) * B, s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->vh, 0, 8 * NB, s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->rho, 0, 8 * NB, s->st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(s->rho_ref, 0, 8 * NB, s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->u, 0, ep * NB * std::max(1, n_orb - 1), s->st);
     if (err == cudaSuccess) err = cudaMemsetAsync(s->ints, 0, sizeof(int) * 3 * B, s->st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s->st);
@@ -1067,6 +1102,10 @@ int lbks_last_error(char* buf, size_t cap) {
 const char* lbks_version(void) { return "lbks 0.2 (sm_103a)"; }
 
 uint64_t lbks_kernel_launches(void) { return g_launches.load(); }
+
+uint32_t lbks_set_wait_limit(uint32_t polls) { return set_gram_tc_wait_limit(polls); }
+
+uint64_t lbks_wait_timeouts(void) { return gram_tc_timeouts(); }
 
 size_t lbks_system_bytes(const lbks_params* p, int nx, int ny, int nz, int n_orb) {
     if (!valid_params(p) || nx < 2 || ny < 2 || nz < 2 || n_orb < 1 || n_orb > kMaxOrbWide) return 0;
@@ -1214,7 +1253,7 @@ int lbks_md(lbks_system* s, int n_steps, double dt, const double* masses, double
     for (int a = 0; a < na; ++a)
         if (!(masses[a] > 0.0)) return fail(LBKS_EINVAL, "mass %d must be positive", a);
     std::vector<double> R = s->xyz[0], F(3 * na), Fn(3 * na);
-    lbks_result res;
+    lbks_result res{};
     auto record = [&](int k) {
         double ek = 0.0;
         for (int a = 0; a < na; ++a)
@@ -1448,7 +1487,7 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     const int mode = g_variant_mode.load();
     const bool tma_ok = psi_tma_applies(nx, psi_in, Vc, ops->psi_elem);
     int kernel = mode > 0 ? mode - 1 : (tma_ok ? kPsiKernelTma : kPsiKernelTiled);
-    if ((kernel == kPsiKernelTma && !tma_ok) || kernel == kRelaxAsync) kernel = kPsiKernelTiled;
+    if ((kernel == kPsiKernelTma && !tma_ok) || kernel == kRelaxBulk) kernel = kPsiKernelTiled;
     // the W field goes through workspace scratch unless the kernel forms it
     const bool wide = n_orb > kMaxOrb && lambda_in && kernel != kPsiKernelTma;
     Workspace* w = nullptr;
@@ -1479,6 +1518,23 @@ int lbks_overlap(int precision, size_t n_sites, int n_orb, double h, const void*
                                          (cudaStream_t)stream)
                         : ops->gram(n_orb, g, h, psi, S, w->sc, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_overlap");
+}
+
+int lbks_energy_matrix(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, const void* psi,
+                       const double* V, double* out, void* stream) {
+    const PrecisionOps* ops = ops_for(precision);
+    if (!ops) return fail(LBKS_EINVAL, "unknown precision %d", precision);
+    if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= (1ull << 31))
+        return fail(LBKS_EINVAL, "bad grid %d x %d x %d", nx, ny, nz);
+    if (n_orb < 1 || n_orb > kMaxOrbWide) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrbWide);
+    if (!psi || !V || !out) return fail(LBKS_EINVAL, "null device pointer");
+    if (!(h > 0.0) || !(theta > 0.0)) return fail(LBKS_EINVAL, "bad h or theta");
+    Workspace* w = nullptr;
+    int rc = workspace(stream, 0, &w);
+    if (rc != LBKS_OK) return rc;
+    cudaError_t e = ops->energy_matrix(n_orb, make_grid(nx, ny, nz), make_coef(1.0, theta, theta * h * h, h), psi, V,
+                                       out, w->sc, 1, (cudaStream_t)stream);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_energy_matrix");
 }
 
 int lbks_w_field(int precision, size_t n_sites, int n_orb, double omega, const void* psi, const double* lambda,

@@ -1,8 +1,8 @@
 // Overlap (Gram) matrix of more than eight FP32 orbitals on the fifth-
 // generation tensor cores: S = h^3 Psi Psi^T, the N_O x N_O x N contraction
 // behind the normalisation sigma_j = 1/||psi_j|| and the couplings
-// Lambda_jk = S_jk / S_kk of each relaxation step (Sec. 2, the normalised
-// update) and behind the Cholesky orthonormalisation that ends a cycle.
+// Lambda_jk = S_jk / S_kk of each relaxation step (Sec. 3, the normalised
+// update and Eq. W) and behind the Cholesky orthonormalisation that ends a cycle.
 //
 // Precision.  Every FP32 orbital value x is split into bf16 parts
 // hi = rn(x), lo = rn(x - hi).  A shared-memory tile of 64 sites holds hi in
@@ -18,15 +18,17 @@
 // tile into registers while they split the current one into a 128-byte-
 // swizzled K-major tile (two stages); one thread issues the four K = 16 MMAs
 // of a tile and commits them to the stage's mbarrier.  Every wait on an
-// mbarrier is bounded: on expiry the block records a timeout, writes NaN
-// partial sums (so the solve fails with a non-finite energy), waits (bounded)
-// for its own MMAs, frees its TMEM and returns.
+// mbarrier is bounded (lbks_set_wait_limit polls, default 2^22): on expiry the
+// block records a timeout, writes NaN partial sums (so the solve fails with a
+// non-finite energy), waits (2^22 polls at most) for its own MMAs, frees its
+// TMEM and returns.
 #include "lbks_internal.cuh"
 #include "lbks_reduce.cuh"
 
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 
 namespace lbks {
 namespace {
@@ -49,6 +51,10 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int kTmemColumnsPerSm = 512;
 
 __device__ unsigned g_tc_timeouts;
+// Polls of the main mbarrier waits, read at each launch (a test can lower it
+// to make the waits give up; the wait for the block's own MMAs after a
+// failure keeps kWaitLimit).
+std::atomic<uint32_t> g_wait_limit{kWaitLimit};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -75,8 +81,8 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + (((k >> 3) ^ (r & 7)) << 4) + (k & 7) * 2);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -147,7 +153,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <bool LAM, bool BULK, int MAXO>
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
-              double* sigma, Scratch sc) {
+              double* sigma, Scratch sc, uint32_t wait_limit) {
     if (inactive(g)) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const int s = it % kTcStages;
         const uint32_t bar = smem_u32(&mbar[s]);
         // the MMAs of tile it - kTcStages read this stage
-        late = late || (it >= kTcStages && !mbar_wait(bar, (uint32_t)((it / kTcStages) + 1) & 1u));
+        late = late || (it >= kTcStages && !mbar_wait(bar, (uint32_t)((it / kTcStages) + 1) & 1u, wait_limit));
         unsigned char* st = smem + s * kTcTileBytes;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         last_parity = (uint32_t)(it / kTcStages) & 1u;
         if (++in_chunk == drain_tiles || last_tile) {
             in_chunk = 0;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity));
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity, wait_limit));
             tc_fence_after();
             if (ok && lane_base < R) {  // the two warp groups drain alternate 16-column blocks
                 const int row = lane_base + (tid & 31);
@@ -338,7 +344,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
     if (failed) {
         if (tid == 0) atomicAdd(&g_tc_timeouts, 1u);
-        if (last_bar) mbar_wait(last_bar, last_parity);  // own MMAs in flight, bounded
+        // own MMAs in flight: the last commit tracks every earlier MMA of this
+        // thread; always the full bound, whatever limit the main waits had
+        if (last_bar) mbar_wait(last_bar, last_parity, kWaitLimit);
     }
     if (BULK) cp_async_wait<0>();  // no copy may land after the block's shared memory is gone
     tc_fence_before();
@@ -407,7 +415,7 @@ static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* 
     const size_t tiles = (g.N + kTcSites - 1) / kTcSites;
     const int per = std::max(1, std::min(sc.max_blocks, occ * num_sms() / std::max(B, 1)));
     const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)per)), (unsigned)B);
-    kern<<<grid, kTcThreads, smem, st>>>(g, h, psi, NO, drain_tiles, S, lam, sigma, sc);
+    kern<<<grid, kTcThreads, smem, st>>>(g, h, psi, NO, drain_tiles, S, lam, sigma, sc, g_wait_limit.load());
     count_launches(1);
     return cudaGetLastError();
 }
@@ -429,6 +437,9 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
     LBKS_TC(kMaxOrbWide)
 #undef LBKS_TC
 }
+
+uint32_t set_gram_tc_wait_limit(uint32_t polls) { return g_wait_limit.exchange(polls); }
+uint32_t device_wait_limit() { return g_wait_limit.load(); }
 
 unsigned gram_tc_timeouts() {
     unsigned v = 0;

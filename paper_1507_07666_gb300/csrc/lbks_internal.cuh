@@ -91,6 +91,11 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
 // Blocks of the tensor-core Gram kernel whose bounded mbarrier waits expired
 // (device counter since the library was loaded; 0 unless the hardware stalled).
 unsigned gram_tc_timeouts();
+// Polls of the tensor-core Gram kernel's mbarrier waits for later launches;
+// returns the previous value.
+uint32_t set_gram_tc_wait_limit(uint32_t polls);
+// The current limit (polls) for the main mbarrier waits of later launches.
+uint32_t device_wait_limit();
 
 // Launch bookkeeping.
 void count_launches(uint64_t n);
@@ -105,7 +110,8 @@ int num_sms();
 constexpr int kRelaxSites = 0;
 constexpr int kRelaxPairs = 1;
 constexpr int kRelaxPrefetch = 2;
-constexpr int kRelaxAsync = 3;  // populations staged in shared memory by cp.async (lbks_async.cuh)
+constexpr int kRelaxBulk = 3;  // omega = 1: populations copied into shared memory by the tensor memory
+                               // accelerator, overlap fused (lbks_bulk.cuh)
 constexpr int kRelaxVariants = 4;
 constexpr int kRelaxVariantMask = 3;
 // In orbital storage the same ids pick the stencil kernel: staged in shared
@@ -173,11 +179,11 @@ struct PrecisionOps {
     cudaError_t (*init_orbitals)(int n_orb, const Grid&, double h, const OrbitalStart* starts, void* psi, int B,
                                  cudaStream_t);
     cudaError_t (*equilibrium)(int n_orb, const Grid&, const Coef&, const void* psi, void* f, int B, cudaStream_t);
-    // rho = 2 sum psi^2 (overwriting the previous density) and its multipoles
-    // mp[0..9] = {q, p_x, p_y, p_z, Q_xx, Q_yy, Q_zz, Q_xy, Q_xz, Q_yz}; mp[10] =
-    // h^3 sum (rho - rho_prev)^2 and mp[11] = h^3 sum rho^2 (the stop rule's density change)
-    cudaError_t (*density)(int n_orb, const Grid&, double h, const void* psi, double* rho, double* mp,
-                           const Scratch&, int B, cudaStream_t);
+    // rho = 2 sum psi^2 and its multipoles mp[0..9] = {q, p_x, p_y, p_z, Q_xx,
+    // Q_yy, Q_zz, Q_xy, Q_xz, Q_yz}; mp[10] = h^3 sum (rho - rho_ref)^2 and
+    // mp[11] = h^3 sum rho^2 (the stop rule's density change; rho_ref may alias rho)
+    cudaError_t (*density)(int n_orb, const Grid&, double h, const void* psi, double* rho, const double* rho_ref,
+                           double* mp, const Scratch&, int B, cudaStream_t);
     // H[j][k] = <psi_j|T_h + V|psi_k>, kin[j] = <psi_j|T_h|psi_j>  (n_orb^2 + n_orb doubles per system)
     cudaError_t (*energy_matrix)(int n_orb, const Grid&, const Coef&, const void* psi, const double* V,
                                  double* out, const Scratch&, int B, cudaStream_t);

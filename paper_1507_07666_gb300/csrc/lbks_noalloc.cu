@@ -55,7 +55,10 @@ extern "C" int lbks_relax_step_noalloc(int precision, int nx, int ny, int nz, in
                                        double theta, double dt, const void* f_in, const void* u_in,
                                        const double* V, const double* sigma_in, void* f_out, void* psi_out,
                                        double* S_out, double* lambda_out, double* sigma_out, void* stream) {
-    const PrecisionOps* ops = precision == LBKS_FP64 ? &ops_f64() : precision == LBKS_FP32 ? &ops_f32() : nullptr;
+    const PrecisionOps* ops = precision == LBKS_FP64   ? &ops_f64()
+                              : precision == LBKS_FP32 ? &ops_f32()
+                              : precision == LBKS_BF16 ? &ops_bf16()
+                                                       : nullptr;
     int rc = LBKS_OK;
     if (!ops) rc = fail(LBKS_EINVAL, "unknown precision");
     else if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= (1ull << 31))

@@ -405,14 +405,17 @@ __global__ void __launch_bounds__(kThreads) k_equilibrium(const Grid g, Coef c, 
     }
 }
 
-// rho = 2 sum_j psi_j^2 (written over the previous density) and its moments
-// about the box centre; mp[10], mp[11] = h^3 sum (rho - rho_prev)^2, h^3 sum rho^2.
+// rho = 2 sum_j psi_j^2 and its moments about the box centre; mp[10], mp[11] =
+// h^3 sum (rho - rho_ref)^2, h^3 sum rho^2 (rho_ref may alias rho: each
+// site reads its reference before writing).
 template <typename T, int NO>
 __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T* __restrict__ psi,
-                                                      double* __restrict__ rho, double* mp, Scratch sc) {
+                                                      double* __restrict__ rho, const double* rho_ref, double* mp,
+                                                      Scratch sc) {
     if (inactive(g)) return;
     psi += (size_t)sys_id() * NO * g.N;
     rho += (size_t)sys_id() * g.N;
+    rho_ref += (size_t)sys_id() * g.N;
     mp += (size_t)sys_id() * kMpStride;
     double acc[12];
 #pragma unroll
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_density(Grid g, double h, const T*
             r += a * a;
         }
         r *= 2.0;
-        const double dr = r - rho[s];  // change from the previous evaluation (stop rule)
+        const double dr = r - rho_ref[s];  // change from the reference density (stop rule)
         rho[s] = r;
         const uint32_t q = g.divx.div(s);
         const int x = (int)(s - q * (uint32_t)g.nx);
@@ -474,9 +477,12 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix(Grid g, Coef c, cons
         const Site t = decode(g, s);
         const double vr = V[s];
         if constexpr (sizeof(T) == 4) {
-            // FP32 orbitals: (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1;
-            // a missing neighbour counts as psi(r)), each difference of two nearby FP32 values
-            // exact; the weighted sums and products in FP32, the sums over sites in FP64
+            // FP32 orbitals: (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1).
+            // A neighbour outside the box is psi = 0, so its term is xi_p psi(r).  A difference
+            // is exact in FP32 when the two values are within a factor of two of each other
+            // (Sterbenz's lemma), else it carries one rounding of the larger value (near nodes
+            // and sign changes).  The weighted sums and products in FP32, the sums over sites
+            // in FP64.
             float af[NO], hf[NO];
             const float xf[3] = {(float)c.xi[0], (float)c.xi[1], (float)c.xi[2]};
             const float invf = (float)inv, vf = (float)vr;
@@ -591,9 +597,11 @@ cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, c
 template <typename TS, typename T>
 cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
                                   const Scratch& sc, int B, cudaStream_t st);
+// The bulk-copy stream-collide (lbks_bulk.cuh) for any orbital count, its
+// overlap fused (exact: FP64 products); FP32 and bfloat16 populations.
 template <typename TS, typename T>
-cudaError_t launch_relax_async(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
-                               const Scratch& sc, int B, cudaStream_t st);
+cudaError_t launch_relax_bulk(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                              bool exact, cudaStream_t st);
 // Orbital-storage relaxation at omega = 1 (lbks_psi.cuh; io.f_in / f_out hold
 // psi, io.V the potential of the collision that produced psi), compiled in
 // lbks_relax_<precision>_psi.cu.
@@ -603,10 +611,13 @@ template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                              int kernel, cudaStream_t st);
 
-// The staged (cp.async) kernel copies 16-byte pieces of whole index ranges.
-inline bool async_applies(const Grid& g, const RelaxIO& io, size_t elem) {
+// The bulk copies need 16-byte pieces of whole index ranges: N a multiple of
+// the elements per 16 bytes of the populations and of the W field, 16-byte
+// aligned arrays, and omega = 1 (three distinct post-collision values).
+inline bool bulk_applies(const Grid& g, const Coef& c, const RelaxIO& io, size_t elem) {
     auto al = [](const void* p) { return p == nullptr || reinterpret_cast<uintptr_t>(p) % 16 == 0; };
-    return g.N % (16 / elem) == 0 && g.N % 4 == 0 && al(io.f_in) && al(io.u_in);
+    return c.omega == 1.0 && g.N % (16 / elem) == 0 && g.N % 4 == 0 && al(io.f_in) && al(io.f_out) &&
+           al(io.u_in) && al(io.psi_out) && al(io.V);
 }
 
 template <typename TS, typename T>
@@ -617,8 +628,9 @@ struct Ops {
         const int v = variant & kRelaxVariantMask;
         if (v == kRelaxPairs && pairs_apply(g, io)) return launch_relax_pairs<TS, T>(NO, OM1, g, c, io, sc, B, st);
         if (v == kRelaxPrefetch && NO > 1) return launch_relax_prefetch<TS, T>(NO, OM1, g, c, io, sc, B, st);
-        if (v == kRelaxAsync && async_applies(g, io, sizeof(TS)))
-            return launch_relax_async<TS, T>(NO, OM1, g, c, io, sc, B, st);
+        if constexpr (sizeof(T) == 4)
+            if (v == kRelaxBulk && bulk_applies(g, c, io, sizeof(TS)))
+                return launch_relax_bulk<TS, T>(NO, g, c, io, sc, B, (variant & kRelaxExactOverlap) != 0, st);
         return B > 1 ? launch_stream_collide<TS, T, NO, OM1, true, false>(g, c, io, sc, B, st)
                      : launch_stream_collide<TS, T, NO, OM1, false, false>(g, c, io, sc, B, st);
     }
@@ -671,12 +683,12 @@ struct Ops {
         return cudaGetLastError();
     }
     template <int NO>
-    static cudaError_t density_n(const Grid& g, double h, const void* psi, double* rho, double* mp,
-                                 const Scratch& sc, int B, cudaStream_t st) {
+    static cudaError_t density_n(const Grid& g, double h, const void* psi, double* rho, const double* rho_ref,
+                                 double* mp, const Scratch& sc, int B, cudaStream_t st) {
         auto kern = k_density<T, NO>;
-        if (sc.max_vals < 10 || sc.systems < B) return cudaErrorInvalidValue;
+        if (sc.max_vals < 12 || sc.systems < B) return cudaErrorInvalidValue;
         kern<<<batch_grid(g.N, blocks_per_sm(kern) * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(
-            g, h, (const T*)psi, rho, mp, sc);
+            g, h, (const T*)psi, rho, rho_ref, mp, sc);
         count_launches(1);
         return cudaGetLastError();
     }
@@ -723,6 +735,9 @@ struct Ops {
     }
     static cudaError_t relax_wide(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                   int variant, cudaStream_t st) {
+        if constexpr (sizeof(T) == 4)
+            if ((variant & kRelaxVariantMask) == kRelaxBulk && bulk_applies(g, c, io, sizeof(TS)))
+                return launch_relax_bulk<TS, T>(NO, g, c, io, sc, B, (variant & kRelaxExactOverlap) != 0, st);
         auto kern = c.omega == 1.0 ? k_stream_collide_wide<TS, T, true> : k_stream_collide_wide<TS, T, false>;
         if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
         kern<<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
@@ -842,11 +857,11 @@ struct Ops {
 #undef WIDE
 #undef CALL
     }
-    static cudaError_t density(int n_orb, const Grid& g, double h, const void* psi, double* rho, double* mp,
-                               const Scratch& sc, int B, cudaStream_t st) {
-#define CALL(NO) density_n<NO>(g, h, psi, rho, mp, sc, B, st)
+    static cudaError_t density(int n_orb, const Grid& g, double h, const void* psi, double* rho,
+                               const double* rho_ref, double* mp, const Scratch& sc, int B, cudaStream_t st) {
+#define CALL(NO) density_n<NO>(g, h, psi, rho, rho_ref, mp, sc, B, st)
 #define WIDE (k_density_wide<T><<<batch_grid(g.N, num_sms() * 4, B, sc.max_blocks), kThreads, 0, st>>>(    \
-                  g, h, (const T*)psi, rho, mp, sc, n_orb),                                              \
+                  g, h, (const T*)psi, rho, rho_ref, mp, sc, n_orb),                                     \
               count_launches(1), cudaGetLastError())
         LBKS_SWITCH_NO(CALL)
 #undef WIDE

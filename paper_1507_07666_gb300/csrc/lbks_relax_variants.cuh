@@ -1,10 +1,10 @@
-// Definitions of the two-site and the prefetching stream-collide launchers
+// Definitions of the two-site, the prefetching and the bulk-copy stream-collide launchers
 // (declared in lbks_relax.cuh); each lbks_relax_<precision>_<variant>.cu
 // includes this and instantiates one of them for its precision.
 #pragma once
 
 #include "lbks_relax.cuh"
-#include "lbks_async.cuh"
+#include "lbks_bulk.cuh"
 
 namespace lbks {
 
@@ -41,18 +41,10 @@ struct PrefetchLaunch {
     }
 };
 
-template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
-struct AsyncLaunch {
-    static cudaError_t run(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                           cudaStream_t st) {
-        return launch_stream_collide_async<TS, T, NO, OM1, BATCHED>(g, c, io, sc, B, st);
-    }
-};
-
 template <typename TS, typename T>
-cudaError_t launch_relax_async(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
-                               const Scratch& sc, int B, cudaStream_t st) {
-    return dispatch_variant<TS, T, AsyncLaunch>(NO, om1, g, c, io, sc, B, st);
+cudaError_t launch_relax_bulk(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                              bool exact, cudaStream_t st) {
+    return launch_stream_collide_bulk<TS, T>(NO, g, c, io, sc, B, exact, device_wait_limit(), st);
 }
 
 template <typename TS, typename T>

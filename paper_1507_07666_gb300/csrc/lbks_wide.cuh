@@ -296,10 +296,12 @@ __global__ void __launch_bounds__(kThreads) k_equilibrium_wide(const Grid g, Coe
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_density_wide(Grid g, double h, const T* __restrict__ psi,
-                                                           double* __restrict__ rho, double* mp, Scratch sc, int NO) {
+                                                           double* __restrict__ rho, const double* rho_ref,
+                                                           double* mp, Scratch sc, int NO) {
     if (inactive(g)) return;
     psi += (size_t)sys_id() * NO * g.N;
     rho += (size_t)sys_id() * g.N;
+    rho_ref += (size_t)sys_id() * g.N;
     mp += (size_t)sys_id() * kMpStride;
     double acc[12];
 #pragma unroll
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_density_wide(Grid g, double h, con
             r += a * a;
         }
         r *= 2.0;
-        const double dr = r - rho[s];  // change from the previous evaluation (stop rule)
+        const double dr = r - rho_ref[s];  // change from the reference density (stop rule)
         rho[s] = r;
         const uint32_t q = g.divx.div(s);
         const int x = (int)(s - q * (uint32_t)g.nx);
@@ -384,8 +386,10 @@ __global__ void __launch_bounds__(kThreads) k_energy_matrix_wide(Grid g, Coef c,
                 const Site t = decode(g, s);
                 const T* pj = psi + (size_t)j * N;
                 a = pj[s];
-                // (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1; a missing
-                // neighbour counts as psi(r)): differences of nearby values are exact in T
+                // (1 - K_xi) psi = sum_p xi_p (psi(r) - psi(r - v_p)) (sum_p xi_p = 1); a neighbour
+                // outside the box is psi = 0, so its term is xi_p psi(r).  A difference is exact
+                // in T when the two values are within a factor of two of each other (Sterbenz's
+                // lemma), else it carries one rounding of the larger value.
                 T d = T(0);
 #pragma unroll
                 for (int p = 1; p < 19; ++p)

@@ -79,6 +79,8 @@ _SIGS = {
     "lbks_last_error": (_i, [ctypes.c_char_p, _sz]),
     "lbks_version": (ctypes.c_char_p, []),
     "lbks_kernel_launches": (ctypes.c_uint64, []),
+    "lbks_set_wait_limit": (ctypes.c_uint32, [ctypes.c_uint32]),
+    "lbks_wait_timeouts": (ctypes.c_uint64, []),
     "lbks_create_system": (_i, [ctypes.POINTER(lbks_params), _i, _i, _i, _d, _i, ctypes.POINTER(_vp)]),
     "lbks_destroy_system": (_i, [_vp]),
     "lbks_system_bytes": (_sz, [ctypes.POINTER(lbks_params), _i, _i, _i, _i]),
@@ -115,6 +117,7 @@ _SIGS = {
     "lbks_relax_step_noalloc": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      _vp, _vp]),
     "lbks_w_field": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
+    "lbks_energy_matrix": (_i, [_i, _i, _i, _i, _i, _d, _d, _vp, _vp, _vp, _vp]),
     "lbks_overlap": (_i, [_i, _sz, _i, _d, _vp, _vp, _i, _vp]),
     "lbks_set_relax_variant": (_i, [_i]),
     "lbks_get_relax_variant": (_i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
@@ -192,6 +195,14 @@ def lbks_version() -> str:
 
 def lbks_kernel_launches() -> int:
     return int(_lib.lbks_kernel_launches())
+
+
+def lbks_set_wait_limit(polls: int) -> int:
+    return int(_lib.lbks_set_wait_limit(int(polls)))
+
+
+def lbks_wait_timeouts() -> int:
+    return int(_lib.lbks_wait_timeouts())
 
 
 def lbks_system_bytes(params, nx, ny, nz, n_orb) -> int:
@@ -348,13 +359,19 @@ def lbks_w_field(precision, n_sites, n_orb, omega, psi, lam, u_out, stream=None)
                              _ptr(u_out, P, optional=True), _stream(stream)))
 
 
+def lbks_energy_matrix(precision, nx, ny, nz, n_orb, h, theta, psi, V, out, stream=None):
+    import torch
+    _check(_lib.lbks_energy_matrix(precision, nx, ny, nz, n_orb, h, theta, _ptr(psi, _psitype(precision)),
+                                   _ptr(V, torch.float64), _ptr(out, torch.float64), _stream(stream)))
+
+
 def lbks_overlap(precision, n_sites, n_orb, h, psi, S, tensor_cores=False, stream=None):
     import torch
     _check(_lib.lbks_overlap(precision, n_sites, n_orb, h, _ptr(psi, _psitype(precision)), _ptr(S, torch.float64),
                              int(bool(tensor_cores)), _stream(stream)))
 
 
-RELAX_VARIANTS = ("sites", "pairs", "prefetch", "async")
+RELAX_VARIANTS = ("sites", "pairs", "prefetch", "bulk")
 
 
 def lbks_set_relax_variant(mode: int) -> int:

@@ -45,3 +45,28 @@ def test_traffic_record_matches_the_kernel_source():
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "stream_collide_ch4_128_fp32.json")))
     assert rec["kernel_src_sha256"] == bench.kernel_source_sha()
     assert bench.recorded_traffic() == float(rec["dram_bytes_per_launch"])
+
+
+def test_nearest_rank_percentiles():
+    v = sorted(float(i) for i in range(1, 201))  # 1 .. 200
+    assert bench.percentile(v, 0.5) == 100.0
+    assert bench.percentile(v, 0.99) == 198.0  # the 198th of 200: not the maximum
+    assert bench.percentile(v, 1.0) == 200.0
+    s = bench.latency_summary(v)
+    assert s["n"] == 200 and s["max"] == 200.0 and s["p90"] == 180.0
+    assert bench.percentile([3.0], 0.99) == 3.0
+
+
+def test_concurrent_oracle_rate():
+    """Whole-host rate: every process's timed updates over the slowest
+    process's timed seconds (warm-up steps skipped)."""
+    a = {"times": [9.0, 1.0, 1.0], "updates_per_step": 1e9}
+    b = {"times": [9.0, 2.0, 2.0], "updates_per_step": 1e9}
+    value, steps, t = bench.oracle_rate([a, b], skip=1)
+    assert steps == 4 and t == 4.0 and value == 1.0  # 4e9 updates / 4 s = 1 GLUPS
+
+
+def test_wide_traffic_record_matches_the_kernel_sources():
+    rec = json.load(open(bench.WIDE_TRAFFIC_FILE))
+    assert rec["sources_sha256"] == bench.wide_sources_sha()
+    assert bench.recorded_wide_traffic(1000) == 1000 * float(rec["dram_bytes_per_orbital_site"])

@@ -22,11 +22,12 @@ def test_batched_water_scan_matches_single_solves():
     torch, lbks = require_gpu()
     n, h = (28, 26, 30), 0.4
     mols = _waters(3, 1)
-    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=25)
+    # water at h = 0.4 has two occupied levels 0.01 Ha apart: long cycles converge in fewer of them
+    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=100, max_cycles=400)
     b.set_geometries([(m.xyz, m.Z) for m in mols])
     res = b.scf()
     for i, m in enumerate(mols):
-        s = lbks.System(n, h, 5, precision=0, n_inner=25)
+        s = lbks.System(n, h, 5, precision=0, n_inner=100, max_cycles=400)
         s.set_geometry(m.xyz, m.Z)
         ref = s.scf()
         assert res[i]["converged"] and res[i]["cycles"] == ref["cycles"]

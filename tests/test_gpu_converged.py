@@ -32,7 +32,7 @@ pytestmark = pytest.mark.gpu
 
 E_TOL, EIG_TOL, RHO_TOL = 1e-5, 1e-5, 1e-5
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
-SMALL = ["he_24", "h2_24", "lih_28", "h2o_32", "ch4_32", "dimer_36"]
+SMALL = ["he_24", "h2_24", "lih_28", "h2o_38", "ch4_32", "dimer_36"]
 MODES = {"fp64": (0, 0), "fp32": (1, 0), "bf16_polish": (2, 0), "fp32_psi": (1, 1)}
 
 
@@ -93,7 +93,7 @@ def test_bench_workload_solve_matches_oracle_fixed_point(case):
     check(res, rho, golden(case), f"{case} fp32")
 
 
-SERVED = ["he_24", "h2_24", "lih_28", "h2o_32", "ch4_32"]
+SERVED = ["he_24", "h2_24", "lih_28", "h2o_38", "ch4_32"]
 
 
 @pytest.mark.parametrize("mode", ["bf16_polish", "fp32_psi"])

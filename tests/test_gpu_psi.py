@@ -143,7 +143,7 @@ def test_psi_and_population_storage_converge_alike():
     mol, n, h = W.water(1.8, 104.0), (30, 26, 28), 0.4
     out = []
     for storage in (lbks.STORE_POPULATIONS, lbks.STORE_PSI):
-        s = lbks.System(n, h, 5, precision=0, n_inner=20, storage=storage)
+        s = lbks.System(n, h, 5, precision=0, n_inner=100, max_cycles=400, storage=storage)
         s.set_geometry(mol.xyz, mol.Z)
         out.append(s.scf())
         s.close()
@@ -157,11 +157,11 @@ def test_psi_storage_batch_matches_single():
     torch, lbks = require_gpu()
     n, h = (28, 26, 30), 0.4
     mols = W.water_scan(3, 2)
-    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=20, storage=lbks.STORE_PSI)
+    b = lbks.Batch(n, h, 5, len(mols), precision=0, n_inner=100, max_cycles=400, storage=lbks.STORE_PSI)
     b.set_geometries([(m.xyz, m.Z) for m in mols])
     res = b.scf()
     for i, m in enumerate(mols):
-        s = lbks.System(n, h, 5, precision=0, n_inner=20, storage=lbks.STORE_PSI)
+        s = lbks.System(n, h, 5, precision=0, n_inner=100, max_cycles=400, storage=lbks.STORE_PSI)
         s.set_geometry(m.xyz, m.Z)
         ref = s.scf()
         assert res[i]["converged"] and res[i]["cycles"] == ref["cycles"]

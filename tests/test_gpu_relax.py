@@ -35,8 +35,11 @@ CASES = [
     # 25-48 orbitals: the W field two sites per thread (an odd site count leaves a lone last site)
     ((13, 7, 9), 33, 0.9, 13),
     ((14, 9, 8), 40, 1.0, 14),
+    # many 256-site tiles, a partial last tile (the bulk-copy kernel's work units)
+    ((64, 48, 40), 5, 1.0, 15),
+    ((40, 36, 33), 40, 1.0, 16),
 ]
-VARIANTS = [1, 2, 3, 4]  # lbks_set_relax_variant: one site, two sites, next orbital prefetched, staged by cp.async
+VARIANTS = [1, 2, 3, 4]  # lbks_set_relax_variant: one site, two sites, next orbital prefetched, bulk copies (omega = 1)
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
 # bfloat16 storage: orbitals and overlaps are float sums of the stored (rounded)
 # inputs; the stored outputs carry bfloat16's 2^-9 relative rounding
@@ -79,7 +82,7 @@ def relax_variant(request):
     lbks.lbks_set_relax_variant(prev)
 
 
-@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "async"], indirect=True)
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "bulk"], indirect=True)
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("n,n_orb,omega,seed", CASES)
 def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed, relax_variant):
@@ -100,7 +103,7 @@ def test_relax_step_matches_oracle(prec, n, n_orb, omega, seed, relax_variant):
     assert rel_err(fg, ref["fstar"]) < tol
 
 
-@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "async"], indirect=True)
+@pytest.mark.parametrize("relax_variant", VARIANTS, ids=["sites", "pairs", "prefetch", "bulk"], indirect=True)
 @pytest.mark.parametrize("n,n_orb,omega,seed", [((33, 20, 17), 5, 1.0, 2), ((7, 9, 11), 3, 0.8, 1),
                                                  ((34, 20, 17), 5, 1.0, 2), ((66, 7, 5), 2, 1.2, 10)])
 def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed, relax_variant):

@@ -175,7 +175,7 @@ def test_water_dimer_ten_orbitals_trajectory(prec):
     s.close()
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4], ids=["sites", "pairs", "prefetch", "async"])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4], ids=["sites", "pairs", "prefetch", "bulk"])
 def test_stream_collide_variants_give_the_oracle_trajectory(mode):
     """Both stream-collide kernels (one site or two x-neighbouring sites per
     thread), forced, follow the oracle's SCF trajectory; the tuner (mode 0)
