@@ -315,11 +315,23 @@ def recorded_traffic():
     return None
 
 
+WIDE_SEGMENTS = (
+    # the wide stream-collide kernel, up to the next kernel of its header
+    (b"__global__ void __launch_bounds__(kThreads, 4) k_stream_collide_wide", b"// S = h^3 Psi Psi^T over the packed"),
+    # the tensor-core overlap kernel and its device helpers, up to its launcher
+    (b"", b"template <bool LAM, bool BULK, int MAXO>\nstatic cudaError_t gram_tc_launch"),
+)
+
+
 def wide_sources_sha():
-    """sha256 over the sources of the wide relaxation step's two kernels."""
+    """sha256 over the source text of the wide relaxation step's two kernels
+    (each file's segment from its start mark to its end mark)."""
     h = hashlib.sha256()
-    for path in WIDE_SOURCES:
-        h.update(open(path, "rb").read())
+    for path, (start, end) in zip(WIDE_SOURCES, WIDE_SEGMENTS):
+        text = open(path, "rb").read()
+        i = text.find(start) if start else 0
+        k = text.find(end, max(i, 0))
+        h.update(text[i:k] if i >= 0 and k > i else text)
     return h.hexdigest()
 
 
@@ -339,12 +351,12 @@ def recorded_wide_traffic(units):
 
 def psi_step_kernels(w, pe, index):
     """Kernels of one orbital-storage step for kernel index (0 tiled, 1 direct,
-    2 TMA) and its algorithmic HBM bytes per site: psi in and out and the
-    collision potential once; more than eight orbitals add the overlap
-    kernel's read of psi' and, without the TMA kernel, the W-field kernel's
-    read of psi, its write of u and the step's read of u."""
+    2 TMA, 3 z-marching) and its algorithmic HBM bytes per site: psi in and
+    out and the collision potential once; more than eight orbitals add the
+    overlap kernel's read of psi' and, without the TMA kernel, the W-field
+    kernel's read of psi, its write of u and the step's read of u."""
     no, wide = w.n_orb, w.n_orb > 8
-    name = ("k_relax_psi_tile", "k_relax_psi", "k_relax_psi_tma")[index]
+    name = ("k_relax_psi_tile", "k_relax_psi", "k_relax_psi_tma", "k_relax_psi_zm")[index]
     if wide and index != 2:
         name = "k_w_field_wide + " + name.replace("k_relax_psi", "k_relax_psi_wide")
     words = 2 * no + ((no if index == 2 else 4 * no - 2) if wide else 0)
@@ -357,7 +369,7 @@ def psi_kernel_index(w, pe, mode):
     """The kernel lbks_relax_step_psi runs under lbks_set_relax_variant(mode)."""
     tma_ok = w.n[0] % (16 // pe) == 0
     k = mode - 1 if mode > 0 else (2 if tma_ok else 0)
-    return 0 if k == 3 or (k == 2 and not tma_ok) else k
+    return 0 if (k == 3 and w.n_orb > 8) or (k == 2 and not tma_ok) else k
 
 
 def time_relax_psi(torch, lbks, w, prec, stream, launches=20, mode=None):
@@ -535,8 +547,8 @@ def main_batch(args):
     elapsed_ms = ev0.elapsed_time(ev1)
     tuned = lbks.lbks_get_relax_variant(b.handle)
     if args.storage == "psi":  # orbital storage names its kernels differently
-        tuned = {"variant": ("tiled", "direct", "tma", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
-                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"]}
+        tuned = {"variant": ("tiled", "direct", "tma", "zmarch")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
+                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"], "ms_zmarch": tuned["ms_bulk"]}
     updates = sum(r["steps"] for res in results for r in res) * w.n_orb * w.sites
     last = results[-1]
     elem = {lbks.FP32: 4, lbks.FP64: 8, lbks.BF16: 2}[prec]
@@ -567,7 +579,9 @@ def main_batch(args):
 def _serve_arm(lbks, reqs, precision, slots, warm, storage=0):
     """Replays the arrival stream against a server; returns per-request
     latencies (s), the makespan and the results."""
-    srv = lbks.lbks_server_create(lbks.lbks_params_default(precision=precision, storage=storage), 0, slots)
+    # the stop rule of include/lbks.h; water's two close occupied levels need up to a few hundred cycles
+    srv = lbks.lbks_server_create(lbks.lbks_params_default(precision=precision, storage=storage, max_cycles=600), 0,
+                                  slots)
     try:
         for _, w in warm:  # first use of each shape: allocation and graph capture
             rid = lbks.lbks_submit(srv, w.n, w.h, w.molecule.xyz, w.molecule.Z, n_inner=w.n_inner)
@@ -805,8 +819,8 @@ def main_lbks(args):
     tuned = lbks.lbks_get_relax_variant(sysm.handle)
     tuned_index = tuned["index"]
     if psi_mode:  # orbital storage names its kernels differently
-        tuned = {"variant": ("tiled", "direct", "tma", "tiled")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
-                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"]}
+        tuned = {"variant": ("tiled", "direct", "tma", "zmarch")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
+                 "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"], "ms_zmarch": tuned["ms_bulk"]}
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration

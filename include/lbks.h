@@ -255,8 +255,11 @@ typedef struct lbks_energy_terms {
  * in shared memory by tiles, 1: one site per thread from L1, 2: the stencil's
  * boxes copied into shared memory by the tensor memory accelerator, which also
  * forms the W source at any orbital count (nx a multiple of 16 / the orbital
- * value's bytes and 16-byte aligned arrays, else 0; 3 is taken as 0).  More
- * than 8 orbitals in orbital storage: 2 where it applies, else 0.
+ * value's bytes and 16-byte aligned arrays, else 0), 3: up to 8 orbitals, a
+ * 32 x 8 column of sites marching along z with a ring of four planes in
+ * shared memory, the next plane's loads in flight while a plane is summed
+ * (more orbitals: 0).  More than 8 orbitals in orbital storage: 2 where it
+ * applies, else 0.
  * mode 0 (default), tuned: the first lbks_set_geometry of each shape
  * (precision, orbitals, omega == 1 or not, grid, systems) times every
  * variant on the handle's buffers (a few launches, before they hold state)

@@ -202,54 +202,53 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
                 const int64_t lt = min64(kBulkTile, (int64_t)N - s0);
                 const TS* fj = fin + (size_t)j * 19 * N;
                 const uint32_t slot = bulk_smem_u32(slots + (size_t)stage * Sh::slot_bytes);
-                int64_t lo[19], hi[19];
-                uint32_t bytes = 0;
+                const bool with_u = ubase != nullptr && j > 0;
+                // a range [lo, hi) of the array, its 16-byte-rounded start a, clamped to the array
+                auto pop_range = [&](int p, int64_t& a, int64_t& lo, int64_t& hi) {
+                    const int64_t off = vel(p, 0) + vel(p, 1) * (int64_t)g.nx + vel(p, 2) * nxy;
+                    a = floor_div(s0 - off, CE) * CE;
+                    lo = max64(a, 0);
+                    hi = min64(floor_div(s0 - off + lt + CE - 1, CE) * CE, (int64_t)N);
+                };
+                auto u_range = [&](int r, int64_t& a, int64_t& lo, int64_t& hi) {
+                    const int64_t off = urow_vy(r) * (int64_t)g.nx + urow_vz(r) * nxy;
+                    a = floor_div(s0 - off - 1, CEU) * CEU;
+                    lo = max64(a, 0);
+                    hi = min64(floor_div(s0 - off + lt + 1 + CEU - 1, CEU) * CEU, (int64_t)N);
+                };
+                uint32_t bytes = j == 0 ? (uint32_t)(lt * (int64_t)sizeof(double)) : 0u;
 #pragma unroll
                 for (int p = 0; p < 19; ++p) {
-                    const int64_t off = vel(p, 0) + vel(p, 1) * (int64_t)g.nx + vel(p, 2) * nxy;
-                    const int64_t a = floor_div(s0 - off, CE) * CE;
-                    const int64_t b = floor_div(s0 - off + lt + CE - 1, CE) * CE;
-                    lo[p] = max64(a, 0);
-                    hi[p] = min64(b, (int64_t)N);
-                    if (hi[p] > lo[p]) bytes += (uint32_t)((hi[p] - lo[p]) * (int64_t)sizeof(TS));
-                    lo[p] -= a;  // slot offset of the first copied element
-                    hi[p] -= a;
+                    int64_t a, lo, hi;
+                    pop_range(p, a, lo, hi);
+                    if (hi > lo) bytes += (uint32_t)((hi - lo) * (int64_t)sizeof(TS));
                 }
-                // W field of orbital j (row j - 1): nine row ranges with an x halo of one
-                const bool with_u = ubase != nullptr && j > 0;
-                int64_t ulo[9], uhi[9];
+                if (with_u) {
 #pragma unroll
-                for (int r = 0; r < 9; ++r) {
-                    const int64_t off = urow_vy(r) * (int64_t)g.nx + urow_vz(r) * nxy;
-                    const int64_t a = floor_div(s0 - off - 1, CEU) * CEU;
-                    const int64_t b = floor_div(s0 - off + lt + 1 + CEU - 1, CEU) * CEU;
-                    ulo[r] = max64(a, 0);
-                    uhi[r] = min64(b, (int64_t)N);
-                    if (with_u && uhi[r] > ulo[r]) bytes += (uint32_t)((uhi[r] - ulo[r]) * (int64_t)sizeof(T));
-                    ulo[r] -= a;
-                    uhi[r] -= a;
+                    for (int r = 0; r < 9; ++r) {
+                        int64_t a, lo, hi;
+                        u_range(r, a, lo, hi);
+                        if (hi > lo) bytes += (uint32_t)((hi - lo) * (int64_t)sizeof(T));
+                    }
                 }
-                if (j == 0) bytes += (uint32_t)(lt * (int64_t)sizeof(double));
                 bulk_mbar_expect(full0 + 8 * stage, bytes);
 #pragma unroll
                 for (int p = 0; p < 19; ++p) {
-                    if (hi[p] <= lo[p]) continue;
-                    const int64_t off = vel(p, 0) + vel(p, 1) * (int64_t)g.nx + vel(p, 2) * nxy;
-                    const int64_t a = floor_div(s0 - off, CE) * CE;
-                    bulk_load(slot + (uint32_t)((p * ROW + lo[p]) * (int64_t)sizeof(TS)),
-                              fj + (size_t)p * N + (size_t)(a + lo[p]), (uint32_t)((hi[p] - lo[p]) * sizeof(TS)),
-                              full0 + 8 * stage);
+                    int64_t a, lo, hi;
+                    pop_range(p, a, lo, hi);
+                    if (hi > lo)
+                        bulk_load(slot + (uint32_t)((p * ROW + (lo - a)) * (int64_t)sizeof(TS)), fj + (size_t)p * N + lo,
+                                  (uint32_t)((hi - lo) * (int64_t)sizeof(TS)), full0 + 8 * stage);
                 }
                 if (with_u) {
                     const T* uj = ubase + (size_t)(j - 1) * N;
 #pragma unroll
                     for (int r = 0; r < 9; ++r) {
-                        if (uhi[r] <= ulo[r]) continue;
-                        const int64_t off = urow_vy(r) * (int64_t)g.nx + urow_vz(r) * nxy;
-                        const int64_t a = floor_div(s0 - off - 1, CEU) * CEU;
-                        bulk_load(slot + (uint32_t)(Sh::pop_bytes + (r * ROWU + ulo[r]) * (int64_t)sizeof(T)),
-                                  uj + (size_t)(a + ulo[r]), (uint32_t)((uhi[r] - ulo[r]) * sizeof(T)),
-                                  full0 + 8 * stage);
+                        int64_t a, lo, hi;
+                        u_range(r, a, lo, hi);
+                        if (hi > lo)
+                            bulk_load(slot + (uint32_t)(Sh::pop_bytes + (r * ROWU + (lo - a)) * (int64_t)sizeof(T)),
+                                      uj + lo, (uint32_t)((hi - lo) * (int64_t)sizeof(T)), full0 + 8 * stage);
                     }
                 }
                 if (j == 0)
@@ -266,8 +265,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
         const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
         const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
         const T dt = (T)c.dt;
-        int idx[19];   // slot index of this thread's population source of velocity p
-        int uidx[19];  // slot index (in its W-field row) of the same source
+        // Tile starts are multiples of kBulkTile, so the slot index of the source
+        // r - v_p is tid + rem_p with rem_p = (-off_p) mod CE, and in the W-field
+        // row of (vy, vz) it is tid + 1 - vx + ((-off_row - 1) mod CEU): per-velocity
+        // constants of the grid, formed where they are used.
+        const int nxm = g.nx & (CE - 1), nxym = (int)(nxy & (CE - 1));
+        const int nxu = g.nx & (CEU - 1), nxyu = (int)(nxy & (CEU - 1));
         T vr = T(0);
         for (int tl = 0; tl < my_tiles; ++tl) {
             const int64_t s0 = (int64_t)(blockIdx.x + (uint32_t)tl * gridDim.x) * kBulkTile;
@@ -277,16 +280,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
             const Site t = decode(g, s);
             uint32_t mask = 0;
 #pragma unroll
-            for (int p = 0; p < 19; ++p) {
-                const int64_t off = vel(p, 0) + vel(p, 1) * (int64_t)g.nx + vel(p, 2) * nxy;
-                const int64_t a = floor_div(s0 - off, CE) * CE;
-                idx[p] = (int)((int64_t)s - off - a);
-                const int r = urow_of(p);
-                const int64_t offr = urow_vy(r) * (int64_t)g.nx + urow_vz(r) * nxy;
-                const int64_t au = floor_div(s0 - offr - 1, CEU) * CEU;
-                uidx[p] = r * ROWU + (int)((int64_t)s - off - au);
+            for (int p = 0; p < 19; ++p)
                 if (live && has_source(t, p)) mask |= 1u << p;
-            }
             T* prow = psit + (size_t)(psi_bufs > 1 ? (tl & 1) : 0) * NO * kBulkTile;
             for (int j = 0; j < NO; ++j) {
                 const int u = tl * NO + j, stage = u % S;
@@ -297,14 +292,19 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
                     const unsigned char* slot = slots + (size_t)stage * Sh::slot_bytes;
                     const TS* sf = reinterpret_cast<const TS*>(slot);
 #pragma unroll
-                    for (int p = 0; p < 19; ++p)
-                        if ((mask >> p) & 1u) ps += to_compute<T>(sf[p * ROW + idx[p]]);
+                    for (int p = 0; p < 19; ++p) {
+                        const int rem = (-vel(p, 0) - vel(p, 1) * nxm - vel(p, 2) * nxym) & (CE - 1);
+                        if ((mask >> p) & 1u) ps += to_compute<T>(sf[p * ROW + tid + rem]);
+                    }
                     if (ubase && j > 0) {
                         const T* su = reinterpret_cast<const T*>(slot + Sh::pop_bytes);
                         T w = T(0);
 #pragma unroll
-                        for (int p = 0; p < 19; ++p)
-                            if ((mask >> p) & 1u) w += xi[vclass(p)] * su[uidx[p]];
+                        for (int p = 0; p < 19; ++p) {
+                            const int r = urow_of(p);
+                            const int rem = (-urow_vy(r) * nxu - urow_vz(r) * nxyu - 1) & (CEU - 1);
+                            if ((mask >> p) & 1u) w += xi[vclass(p)] * su[r * ROWU + tid + 1 - vel(p, 0) + rem];
+                        }
                         ps += w;
                     }
                     if (j == 0)

@@ -718,7 +718,8 @@ int tune_relax(lbks_system* s) {
                         psi_tma_applies(s->nx, s->f[1], s->vprev, s->ops->psi_elem);
     if (mode > 0) {
         s->variant = mode - 1;
-        if (s->psi_storage && (s->variant == kRelaxBulk || (s->variant == kPsiKernelTma && !tma_ok)))
+        if (s->psi_storage && ((s->variant == kPsiKernelZ && s->n_orb > kMaxOrb) ||
+                               (s->variant == kPsiKernelTma && !tma_ok)))
             s->variant = kPsiKernelTiled;
         if (!s->psi_storage && s->n_orb > kMaxOrb && s->variant != kRelaxBulk) s->variant = kRelaxSites;
         return LBKS_OK;
@@ -776,7 +777,8 @@ int tune_relax(lbks_system* s) {
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
     // variants that differ from the first kernel on this shape
     bool tried[kRelaxVariants] = {true, !wide && (s->psi_storage || s->nx % 2 == 0),
-                                  s->psi_storage ? tma_ok : (!wide && s->n_orb > 1), bulk_may};
+                                  s->psi_storage ? tma_ok : (!wide && s->n_orb > 1),
+                                  s->psi_storage ? !wide : bulk_may};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
         e = step(v);  // warm-up
@@ -1487,7 +1489,7 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     const int mode = g_variant_mode.load();
     const bool tma_ok = psi_tma_applies(nx, psi_in, Vc, ops->psi_elem);
     int kernel = mode > 0 ? mode - 1 : (tma_ok ? kPsiKernelTma : kPsiKernelTiled);
-    if ((kernel == kPsiKernelTma && !tma_ok) || kernel == kRelaxBulk) kernel = kPsiKernelTiled;
+    if ((kernel == kPsiKernelTma && !tma_ok) || (kernel == kPsiKernelZ && n_orb > kMaxOrb)) kernel = kPsiKernelTiled;
     // the W field goes through workspace scratch unless the kernel forms it
     const bool wide = n_orb > kMaxOrb && lambda_in && kernel != kPsiKernelTma;
     Workspace* w = nullptr;

@@ -121,6 +121,7 @@ constexpr int kRelaxVariantMask = 3;
 constexpr int kPsiKernelTiled = kRelaxSites;
 constexpr int kPsiKernelDirect = kRelaxPairs;
 constexpr int kPsiKernelTma = kRelaxPrefetch;
+constexpr int kPsiKernelZ = kRelaxBulk;  // up to kMaxOrb orbitals: marching along z, a ring of planes
 // The TMA kernel's tensor maps need rows of whole 16-byte units (nx a
 // multiple of 16 / elem, elem the bytes of an orbital value) and 16-byte
 // aligned orbitals and potential.
@@ -226,9 +227,9 @@ struct PoissonBufs {
     double* mp;  // multipoles of rho (10 doubles)
 };
 constexpr int kMaxLevels = 10;
-struct MGLevel {
+struct MGLevel {  // single-precision arrays of the preconditioner (level 0 included)
     Grid g;
-    double *x = nullptr, *b = nullptr, *r = nullptr;
+    float *x = nullptr, *b = nullptr, *r = nullptr;
 };
 struct MGHierarchy {
     int nlev = 0;
@@ -236,7 +237,7 @@ struct MGHierarchy {
 };
 // lbks_poisson.cu
 int mg_levels(int nx, int ny, int nz);
-size_t mg_coarse_doubles(int nx, int ny, int nz);  // x, b, r of every level below the finest, one system
+size_t mg_coarse_doubles(int nx, int ny, int nz);  // doubles that hold x, b, r (FP32) of every level, one system
 // Carves `coarse` (B * mg_coarse_doubles) into the levels; level arrays hold
 // the B systems consecutively.
 MGHierarchy make_hierarchy(const Grid& fine, double* coarse, int B);

@@ -1,7 +1,13 @@
 // Hartree potential: the 7-point lattice Poisson problem
 //   (A v)(r) = 6 v(r) - sum of the six face neighbours = 4 pi h^2 rho(r) + ghost values
-// solved by conjugate gradients preconditioned with one geometric multigrid
-// V-cycle (FP64 throughout, scalars resident on the device).
+// solved by conjugate gradients in FP64 preconditioned with one geometric
+// multigrid V-cycle in FP32 (scalars resident on the device).  GB300 issues
+// FP64 at a small fraction of its FP32 rate, and the smoothing sweeps are
+// ALU-bound in FP64; the preconditioner needs no more than single precision,
+// since the FP64 iteration computes the residual and the solution.  Its
+// rounding makes the preconditioner vary slightly between applications, so
+// the direction update takes the flexible (Polak-Ribiere) form
+// beta = <z_new, r_new - r_old> / <z_old, r_old> = -alpha <z_new, A p_old> / <z_old, r_old>.
 //
 // Multigrid hierarchy: coarse point I of a level sits on fine index 2I+1 of
 // the level above (m = n/2 points per axis); coarsening stops when an axis
@@ -10,8 +16,8 @@
 // rediscretised 2^l (6 - sum of neighbours), the Galerkin product's
 // long-wavelength limit.  Smoothing is red-black Gauss-Seidel, red then
 // black before the coarse correction and black then red after it, with the
-// coarsest level solved by a fixed number of such sweeps: the V-cycle is a
-// fixed symmetric positive definite operator, as conjugate gradients needs.
+// coarsest level solved by a fixed number of such sweeps: in exact
+// arithmetic the V-cycle is a fixed symmetric positive definite operator.
 #include "lbks_internal.cuh"
 #include "lbks_reduce.cuh"
 
@@ -45,10 +51,11 @@ __device__ __forceinline__ void decode3(const Grid& g, uint32_t s, int& x, int& 
 }
 
 // 6 v(s) - sum of in-grid face neighbours
-__device__ __forceinline__ double stencil(const Grid& g, const double* __restrict__ v, uint32_t s, int x, int y,
-                                          int z, double self) {
+template <typename V>
+__device__ __forceinline__ V stencil(const Grid& g, const V* __restrict__ v, uint32_t s, int x, int y, int z,
+                                     V self) {
     const int sy = g.nx, sz = g.nx * g.ny;
-    double t = 6.0 * self;
+    V t = V(6) * self;
     if (x > 0) t -= v[s - 1];
     if (x < g.nx - 1) t -= v[s + 1];
     if (y > 0) t -= v[s - sy];
@@ -80,24 +87,24 @@ __device__ __forceinline__ double multipole_value(const double* mp, double X, do
 // ------------------------------------------------------------ multigrid kernels
 // One colour of red-black Gauss-Seidel on A_l = scale (6 - sum nb):
 // x = (b + scale * sum nb x) / (6 scale) at sites with (x+y+z) % 2 == colour.
-__global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, double scale, int colour, double* __restrict__ x,
-                                                        const double* __restrict__ b, const CGState* cg) {
+__global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, float scale, int colour, float* __restrict__ x,
+                                                        const float* __restrict__ b, const CGState* cg) {
     if (inactive(g) || cg[blockIdx.y].done) return;
     x += (size_t)blockIdx.y * g.N;
     b += (size_t)blockIdx.y * g.N;
-    const double inv = 1.0 / (6.0 * scale);
+    const float inv = 1.0f / (6.0f * scale);
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         int ix, iy, iz;
         decode3(g, s, ix, iy, iz);
         if (((ix + iy + iz) & 1) != colour) continue;
-        const double nb = 6.0 * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+        const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
         x[s] = (b[s] + scale * nb) * inv;
     }
 }
 
 // r = b - A_l x
-__global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, double scale, const double* __restrict__ x,
-                                                          const double* __restrict__ b, double* __restrict__ r,
+__global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, float scale, const float* __restrict__ x,
+                                                          const float* __restrict__ b, float* __restrict__ r,
                                                           const CGState* cg) {
     if (inactive(g) || cg[blockIdx.y].done) return;
     x += (size_t)blockIdx.y * g.N;
@@ -112,8 +119,8 @@ __global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, double scale, 
 
 // b_c(I) = sum over the 27 fine neighbours of fine point 2I+1 with weights
 // prod_axis (1 at the centre, 1/2 beside it)  (= P^T r)
-__global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, const double* __restrict__ rf,
-                                                          double* __restrict__ bc, const CGState* cg) {
+__global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, const float* __restrict__ rf,
+                                                          float* __restrict__ bc, const CGState* cg) {
     if (inactive(gf) || cg[blockIdx.y].done) return;
     rf += (size_t)blockIdx.y * gf.N;
     bc += (size_t)blockIdx.y * gc.N;
@@ -121,20 +128,20 @@ __global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, cons
         int I, J, K;
         decode3(gc, s, I, J, K);
         const int fx = 2 * I + 1, fy = 2 * J + 1, fz = 2 * K + 1;
-        double acc = 0.0;
+        float acc = 0.0f;
         for (int dz = -1; dz <= 1; ++dz) {
             const int z = fz + dz;
             if (z < 0 || z >= gf.nz) continue;
-            const double wz = dz ? 0.5 : 1.0;
+            const float wz = dz ? 0.5f : 1.0f;
             for (int dy = -1; dy <= 1; ++dy) {
                 const int y = fy + dy;
                 if (y < 0 || y >= gf.ny) continue;
-                const double wy = dy ? 0.5 : 1.0;
+                const float wy = dy ? 0.5f : 1.0f;
                 const size_t row = ((size_t)z * gf.ny + y) * gf.nx;
                 for (int dx = -1; dx <= 1; ++dx) {
                     const int x = fx + dx;
                     if (x < 0 || x >= gf.nx) continue;
-                    acc += wz * wy * (dx ? 0.5 : 1.0) * rf[row + x];
+                    acc += wz * wy * (dx ? 0.5f : 1.0f) * rf[row + x];
                 }
             }
         }
@@ -143,22 +150,22 @@ __global__ void __launch_bounds__(kThreads) k_mg_restrict(Grid gf, Grid gc, cons
 }
 
 // Coarse indices and weights of fine index i along an axis of m coarse points.
-__device__ __forceinline__ int interp_axis(int i, int m, int* c, double* w) {
+__device__ __forceinline__ int interp_axis(int i, int m, int* c, float* w) {
     if (i & 1) {
         c[0] = (i - 1) >> 1;
-        w[0] = 1.0;
+        w[0] = 1.0f;
         return c[0] < m ? 1 : 0;
     }
     int k = 0;
     const int lo = (i >> 1) - 1, hi = i >> 1;
-    if (lo >= 0 && lo < m) { c[k] = lo; w[k] = 0.5; ++k; }
-    if (hi >= 0 && hi < m) { c[k] = hi; w[k] = 0.5; ++k; }
+    if (lo >= 0 && lo < m) { c[k] = lo; w[k] = 0.5f; ++k; }
+    if (hi >= 0 && hi < m) { c[k] = hi; w[k] = 0.5f; ++k; }
     return k;
 }
 
 // x_f += P x_c (trilinear, zero ghosts)
-__global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const double* __restrict__ xc,
-                                                         double* __restrict__ xf, const CGState* cg) {
+__global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const float* __restrict__ xc,
+                                                         float* __restrict__ xf, const CGState* cg) {
     if (inactive(gf) || cg[blockIdx.y].done) return;
     xc += (size_t)blockIdx.y * gc.N;
     xf += (size_t)blockIdx.y * gf.N;
@@ -166,10 +173,10 @@ __global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const
         int x, y, z;
         decode3(gf, s, x, y, z);
         int cx[2], cy[2], cz[2];
-        double wx[2], wy[2], wz[2];
+        float wx[2], wy[2], wz[2];
         const int nxw = interp_axis(x, gc.nx, cx, wx), nyw = interp_axis(y, gc.ny, cy, wy),
                   nzw = interp_axis(z, gc.nz, cz, wz);
-        double acc = 0.0;
+        float acc = 0.0f;
         for (int a = 0; a < nzw; ++a)
             for (int b = 0; b < nyw; ++b) {
                 const size_t row = ((size_t)cz[a] * gc.ny + cy[b]) * gc.nx;
@@ -181,13 +188,13 @@ __global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const
 
 // Coarsest level in one CTA: x = 0, then kCoarse red/black sweeps and
 // kCoarse black/red sweeps, a barrier between colours.
-__global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, double scale, double* __restrict__ x,
-                                                              const double* __restrict__ b, const CGState* cg) {
+__global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, float scale, float* __restrict__ x,
+                                                              const float* __restrict__ b, const CGState* cg) {
     if (inactive(g) || cg[blockIdx.y].done) return;
     x += (size_t)blockIdx.y * g.N;
     b += (size_t)blockIdx.y * g.N;
-    const double inv = 1.0 / (6.0 * scale);
-    for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) x[s] = 0.0;
+    const float inv = 1.0f / (6.0f * scale);
+    for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) x[s] = 0.0f;
     __syncthreads();
     for (int half = 0; half < 4 * kCoarse; ++half) {
         const int k = half >> 1;  // sweep number
@@ -197,18 +204,184 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, double sca
             int ix, iy, iz;
             decode3(g, s, ix, iy, iz);
             if (((ix + iy + iz) & 1) != colour) continue;
-            const double nb = 6.0 * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+            const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
             x[s] = (b[s] + scale * nb) * inv;
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mg_zero(Grid g, double* __restrict__ x, const CGState* cg) {
+// ----------------------------------------------- coarse levels inside one CTA
+// Levels of at most kTailSites sites (and all coarser ones) run their part of
+// the V-cycle -- zero, pre-smoothing, residual, restriction down to the
+// coarsest solve, then prolongation and post-smoothing back up -- in one CTA
+// per system, a barrier between passes, on copies in shared memory (x, b and
+// r of every such level: at most 3 x 4 x 585 bytes, since each level has at
+// most an eighth of the sites of the one above).  The first of them takes
+// its right-hand side from global memory and returns its correction there.
+// The passes are those of the one-level kernels above, site by site in the
+// same arithmetic; red-black Gauss-Seidel updates of one colour read only the
+// other colour, so the results do not depend on how sites map to threads.
+constexpr int kTailThreads = 1024;
+// 8^3: on larger levels the passes of one CTA outlast the launches they save
+constexpr uint32_t kTailSites = 512;
+
+__device__ __forceinline__ void cta_smooth(const Grid& g, float scale, int colour, float* __restrict__ x,
+                                           const float* __restrict__ b) {
+    const float inv = 1.0f / (6.0f * scale);
+    for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) {
+        int ix, iy, iz;
+        decode3(g, s, ix, iy, iz);
+        if (((ix + iy + iz) & 1) != colour) continue;
+        const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+        x[s] = (b[s] + scale * nb) * inv;
+    }
+    __syncthreads();
+}
+
+// Shared-memory values the tail needs from level lc down.
+size_t tail_values(const MGHierarchy& H, int lc) {
+    size_t n = 0;
+    for (int l = lc; l < H.nlev; ++l) n += 3 * (size_t)H.lev[l].g.N;
+    return n;
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_mg_tail(MGHierarchy H, int lc, float* __restrict__ xg,
+                                                          const float* __restrict__ bg, const CGState* cg) {
+    if (inactive(H.lev[0].g) || cg[blockIdx.y].done) return;
+    extern __shared__ __align__(16) float tsh[];
+    const int L = H.nlev;
+    const size_t y = blockIdx.y;
+    // level l's x, b and r in shared memory, levels lc .. L - 1 one after the other
+    float* xs[kMaxLevels];
+    float* bs[kMaxLevels];
+    float* rs[kMaxLevels];
+    {
+        float* q = tsh;
+        for (int l = lc; l < L; ++l) {
+            const uint32_t n = H.lev[l].g.N;
+            xs[l] = q;
+            bs[l] = q + n;
+            rs[l] = q + 2 * n;
+            q += 3 * (size_t)n;
+        }
+    }
+    {
+        const uint32_t n = H.lev[lc].g.N;
+        const float* b = bg + y * n;
+        for (uint32_t s = threadIdx.x; s < n; s += blockDim.x) bs[lc][s] = b[s];
+    }
+    for (int l = lc; l < L; ++l) {
+        const Grid& g = H.lev[l].g;
+        const float sc = (float)(1 << l);
+        float* x = xs[l];
+        const float* b = bs[l];
+        for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) x[s] = 0.0f;
+        __syncthreads();
+        if (l == L - 1) {  // coarsest: kCoarse red/black sweeps, then kCoarse black/red
+            for (int k = 0; k < kCoarse; ++k) {
+                cta_smooth(g, sc, 0, x, b);
+                cta_smooth(g, sc, 1, x, b);
+            }
+            for (int k = 0; k < kCoarse; ++k) {
+                cta_smooth(g, sc, 1, x, b);
+                cta_smooth(g, sc, 0, x, b);
+            }
+            break;
+        }
+        for (int k = 0; k < kPre; ++k) {
+            cta_smooth(g, sc, 0, x, b);
+            cta_smooth(g, sc, 1, x, b);
+        }
+        float* r = rs[l];
+        for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) {
+            int ix, iy, iz;
+            decode3(g, s, ix, iy, iz);
+            r[s] = b[s] - sc * stencil(g, x, s, ix, iy, iz, x[s]);
+        }
+        __syncthreads();
+        const Grid& gc = H.lev[l + 1].g;
+        float* bc = bs[l + 1];
+        for (uint32_t s = threadIdx.x; s < gc.N; s += blockDim.x) {
+            int I, J, K;
+            decode3(gc, s, I, J, K);
+            const int fx = 2 * I + 1, fy = 2 * J + 1, fz = 2 * K + 1;
+            float acc = 0.0f;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int z = fz + dz;
+                if (z < 0 || z >= g.nz) continue;
+                const float wz = dz ? 0.5f : 1.0f;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int yy = fy + dy;
+                    if (yy < 0 || yy >= g.ny) continue;
+                    const float wy = dy ? 0.5f : 1.0f;
+                    const size_t row = ((size_t)z * g.ny + yy) * g.nx;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int xx = fx + dx;
+                        if (xx < 0 || xx >= g.nx) continue;
+                        acc += wz * wy * (dx ? 0.5f : 1.0f) * r[row + xx];
+                    }
+                }
+            }
+            bc[s] = acc;
+        }
+        __syncthreads();
+    }
+    for (int l = L - 2; l >= lc; --l) {
+        const Grid& g = H.lev[l].g;
+        const Grid& gc = H.lev[l + 1].g;
+        const float sc = (float)(1 << l);
+        float* x = xs[l];
+        const float* xc = xs[l + 1];
+        for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) {
+            int ix, iy, iz;
+            decode3(g, s, ix, iy, iz);
+            int cx[2], cy[2], cz[2];
+            float wx[2], wy[2], wz[2];
+            const int nxw = interp_axis(ix, gc.nx, cx, wx), nyw = interp_axis(iy, gc.ny, cy, wy),
+                      nzw = interp_axis(iz, gc.nz, cz, wz);
+            float acc = 0.0f;
+            for (int a = 0; a < nzw; ++a)
+                for (int bb = 0; bb < nyw; ++bb) {
+                    const size_t row = ((size_t)cz[a] * gc.ny + cy[bb]) * gc.nx;
+                    for (int cc = 0; cc < nxw; ++cc) acc += wz[a] * wy[bb] * wx[cc] * xc[row + cx[cc]];
+                }
+            x[s] += acc;
+        }
+        __syncthreads();
+        for (int k = 0; k < kPre; ++k) {
+            cta_smooth(g, sc, 1, x, bs[l]);
+            cta_smooth(g, sc, 0, x, bs[l]);
+        }
+    }
+    {
+        const uint32_t n = H.lev[lc].g.N;
+        float* x = xg + y * n;
+        for (uint32_t s = threadIdx.x; s < n; s += blockDim.x) x[s] = xs[lc][s];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mg_zero(Grid g, float* __restrict__ x, const CGState* cg) {
     if (inactive(g) || cg[blockIdx.y].done) return;
     const size_t n = g.N;
     x += (size_t)blockIdx.y * n;
-    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) x[s] = 0.0;
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) x[s] = 0.0f;
+}
+
+// Level 0 of the preconditioner: b = (float) r on entry, z = (double) x on exit.
+__global__ void __launch_bounds__(kThreads) k_mg_narrow(Grid g, const double* __restrict__ r, float* __restrict__ b,
+                                                        const CGState* cg) {
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    const size_t n = g.N, o = (size_t)blockIdx.y * n;
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads)
+        b[o + s] = (float)r[o + s];
+}
+__global__ void __launch_bounds__(kThreads) k_mg_widen(Grid g, const float* __restrict__ x, double* __restrict__ z,
+                                                       const CGState* cg) {
+    if (inactive(g) || cg[blockIdx.y].done) return;
+    const size_t n = g.N, o = (size_t)blockIdx.y * n;
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads)
+        z[o + s] = (double)x[o + s];
 }
 
 // --------------------------------------------------------------------- PCG kernels
@@ -255,20 +428,24 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
     }
 }
 
-// rz = r . z; beta = rz / rz_old (0 on the first iteration)
+// rz = r . z; beta = -alpha (A p_old . z) / rz_old (the flexible form; 0 on
+// the first iteration, where ap is not read)
 __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scratch sc) {
     if (inactive(g)) return;
     pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
-    double acc[1] = {0.0};
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads)
+    const bool first = pb.cg->iters == 0;
+    double acc[2] = {0.0, 0.0};
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
         acc[0] += pb.r[s] * pb.z[s];
+        if (!first) acc[1] += pb.ap[s] * pb.z[s];
+    }
     double* partial = sys_partial(sc);
-    block_sum_store<1>(acc, partial + (size_t)blockIdx.x);
-    __shared__ double tot[1];
-    if (grid_total<1>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
+    block_sum_store<2>(acc, partial + (size_t)blockIdx.x * 2);
+    __shared__ double tot[2];
+    if (grid_total<2>(partial, sys_counter(sc), tot) && threadIdx.x == 0) {
         CGState* cg = pb.cg;
-        cg->beta = cg->rz > 0.0 ? tot[0] / cg->rz : 0.0;
+        cg->beta = (!first && cg->rz > 0.0) ? -cg->alpha * tot[1] / cg->rz : 0.0;
         cg->rz = tot[0];
     }
 }
@@ -339,16 +516,33 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
 
 cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* tmp0, const CGState* cg, int ge,
                    int Bs, cudaStream_t st, uint64_t* nl) {
-    // level 0 works on (x = z0, b = r0, r = tmp0); levels >= 1 on their own arrays
-    auto X = [&](int l) { return l == 0 ? z0 : H.lev[l].x; };
-    auto B = [&](int l) -> const double* { return l == 0 ? r0 : H.lev[l].b; };
-    auto R = [&](int l) { return l == 0 ? tmp0 : H.lev[l].r; };
+    // every level on its own single-precision arrays; level 0's b is r narrowed,
+    // its x widened into z at the end
+    (void)tmp0;
+    auto X = [&](int l) { return H.lev[l].x; };
+    auto B = [&](int l) -> const float* { return H.lev[l].b; };
+    auto R = [&](int l) { return H.lev[l].r; };
     auto grid = [&](size_t n) { return dim3(grid_for(n, std::max(1, ge / Bs)), Bs); };
     const int L = H.nlev;
+    k_mg_narrow<<<grid(H.lev[0].g.N), kThreads, 0, st>>>(H.lev[0].g, r0, H.lev[0].b, cg);
+    ++*nl;
+    // first level small enough for the one-CTA tail (levels below it run there)
+    int lc = L;
+    for (int l = 0; l < L; ++l)
+        if (H.lev[l].g.N <= kTailSites) {
+            lc = l;
+            break;
+        }
     for (int l = 0; l < L; ++l) {
         const Grid& g = H.lev[l].g;
-        const double sc = (double)(1 << l);
+        const float sc = (float)(1 << l);
         const dim3 gl = grid(g.N);
+        if (l == lc) {
+            const size_t smem = sizeof(float) * tail_values(H, lc);  // at most 3 x 4 x 585 bytes
+            k_mg_tail<<<dim3(1, Bs), kTailThreads, smem, st>>>(H, lc, X(l), B(l), cg);
+            ++*nl;
+            break;
+        }
         if (l == L - 1 && g.N <= kCoarseSites) {
             k_mg_coarse_solve<<<dim3(1, Bs), kThreads, 0, st>>>(g, sc, X(l), B(l), cg);
             ++*nl;
@@ -377,9 +571,10 @@ cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* t
         k_mg_restrict<<<grid(gc.N), kThreads, 0, st>>>(g, gc, R(l), H.lev[l + 1].b, cg);
         *nl += 2 * kPre + 3;
     }
-    for (int l = L - 2; l >= 0; --l) {
+    for (int l = std::min(L, lc) - 1; l >= 0; --l) {
+        if (l == L - 1) continue;  // coarsest level: nothing to prolong from
         const Grid& g = H.lev[l].g;
-        const double sc = (double)(1 << l);
+        const float sc = (float)(1 << l);
         const dim3 gl = grid(g.N);
         k_mg_prolong<<<gl, kThreads, 0, st>>>(g, H.lev[l + 1].g, X(l + 1), X(l), cg);
         for (int k = 0; k < kPre; ++k) {
@@ -388,6 +583,8 @@ cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* t
         }
         *nl += 1 + 2 * kPre;
     }
+    k_mg_widen<<<grid(H.lev[0].g.N), kThreads, 0, st>>>(H.lev[0].g, H.lev[0].x, z0, cg);
+    ++*nl;
     return cudaGetLastError();
 }
 
@@ -404,34 +601,38 @@ int mg_levels(int nx, int ny, int nz) {
     return l;
 }
 
+// Floats of x, b, r of every level (the finest included), padded per level to
+// four floats (16-byte aligned arrays), as doubles.
 size_t mg_coarse_doubles(int nx, int ny, int nz) {
-    size_t total = 0;
+    size_t floats = 0;
     const int L = mg_levels(nx, ny, nz);
-    for (int l = 1; l < L; ++l) {
+    for (int l = 0; l < L; ++l) {
+        floats += 3 * (((size_t)nx * ny * nz + 3) & ~(size_t)3);
         nx /= 2;
         ny /= 2;
         nz /= 2;
-        total += 3 * (size_t)nx * ny * nz;
     }
-    return total;
+    return (floats + 1) / 2;
 }
 
 MGHierarchy make_hierarchy(const Grid& fine, double* coarse, int B) {
     MGHierarchy H;
     H.nlev = mg_levels(fine.nx, fine.ny, fine.nz);
-    H.lev[0].g = fine;
+    float* q = reinterpret_cast<float*>(coarse);
     int nx = fine.nx, ny = fine.ny, nz = fine.nz;
-    for (int l = 1; l < H.nlev; ++l) {
-        nx /= 2;
-        ny /= 2;
-        nz /= 2;
-        H.lev[l].g = make_grid(nx, ny, nz);
+    for (int l = 0; l < H.nlev; ++l) {
+        if (l > 0) {
+            nx /= 2;
+            ny /= 2;
+            nz /= 2;
+        }
+        H.lev[l].g = l == 0 ? fine : make_grid(nx, ny, nz);
         H.lev[l].g.active = fine.active;
-        const size_t n = (size_t)nx * ny * nz * B;
-        H.lev[l].x = coarse;
-        H.lev[l].b = coarse + n;
-        H.lev[l].r = coarse + 2 * n;
-        coarse += 3 * n;
+        const size_t n = (((size_t)nx * ny * nz + 3) & ~(size_t)3) * B;
+        H.lev[l].x = q;
+        H.lev[l].b = q + n;
+        H.lev[l].r = q + 2 * n;
+        q += 3 * n;
     }
     return H;
 }

@@ -481,6 +481,159 @@ __global__ void __launch_bounds__(kThreads, 3) k_relax_psi_wide_tile(Grid g, Coe
     }
 }
 
+// The same step marching along z: a block owns a 32 x 8 column of sites and
+// a run of zc planes, and keeps the planes z - 1, z, z + 1 of every orbital's
+// psi and of Vc (one-site x and y halo, zero outside the grid) in a ring of
+// four shared-memory planes.  While it sums the stencil of plane z it has
+// the loads of plane z + 2 in flight in registers, and stores them into the
+// ring slot that plane z - 2 held; one barrier per plane.  Every plane is
+// loaded once per run (zc + 2 planes for zc outputs) instead of three times
+// per 4-plane tile, and no thread waits for a whole box before it computes.
+// Up to kMaxOrb orbitals; W source, overlap partials, Lambda and sigma as in
+// k_relax_psi_tile.  Dynamic shared memory: 4 (NO + 1) 34 x 10 values of T.
+constexpr int kZmW = kTX + 2, kZmH = kTY + 2, kZmPlane = kZmW * kZmH;
+
+template <typename T, int NO, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi_zm(Grid g, Coef c, RelaxIO io,
+                                                                                       Scratch sc, int zc) {
+    constexpr int NP = NO * (NO + 1) / 2;
+    constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
+    constexpr int PT = (NO + 1) * kZmPlane;         // values of one plane of the ring (psi_0 .. psi_{NO-1}, Vc)
+    constexpr int K = (PT + kThreads - 1) / kThreads;  // of them loaded by each thread
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);  // [4][PT]
+    if (BATCHED && inactive(g)) return;
+    const uint32_t N = g.N;
+    const size_t y = BATCHED ? sys_id() : 0;
+    const T* __restrict__ pin = static_cast<const T*>(io.f_in) + y * NO * N;
+    T* __restrict__ pout = static_cast<T*>(io.f_out) + y * NO * N;
+    const double* __restrict__ Vc = io.V + y * N;
+    T sig[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) sig[j] = (T)io.sigma_in[y * NO + j];
+    const T dt = (T)c.dt;
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    T wl[NL];
+    const bool with_w = NO > 1 && io.lambda_in != nullptr;
+#pragma unroll
+    for (int j = 1; j < NO; ++j)
+#pragma unroll
+        for (int k = 0; k < j; ++k)
+            wl[tri(j - 1, k)] = with_w ? (T)(-c.omega * io.lambda_in[y * NO * NO + j * NO + k]) : T(0);
+    T acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = T(0);
+
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY, nzc = (g.nz + zc - 1) / zc;
+    const int items = ntx * nty * nzc;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int bxi = item % ntx, byi = (item / ntx) % nty, bzi = item / (ntx * nty);
+        const int x0 = bxi * kTX, y0 = byi * kTY, zs = bzi * zc, ze = min(zs + zc, g.nz);
+        // value i of plane z of the ring (zero outside the grid)
+        auto fetch = [&](int z, int i) -> T {
+            const int a = i / kZmPlane, e = i - a * kZmPlane;
+            const int gx = x0 - 1 + e % kZmW, gy = y0 - 1 + e / kZmW;
+            if (z < 0 || z >= g.nz || gx < 0 || gx >= g.nx || gy < 0 || gy >= g.ny) return T(0);
+            const size_t gs = ((size_t)z * g.ny + gy) * g.nx + gx;
+            return a < NO ? __ldg(pin + (size_t)a * N + gs) : (T)__ldg(Vc + gs);
+        };
+        auto slot = [&](int z) { return ring + (size_t)((z - zs + 1) & 3) * PT; };
+        __syncthreads();  // the previous run's ring is no longer read
+        for (int z = zs - 1; z <= zs + 1; ++z) {
+            T* r = slot(z);
+            for (int i = threadIdx.x; i < PT; i += kThreads) r[i] = fetch(z, i);
+        }
+        __syncthreads();
+        const int gx = x0 + tx, gy = y0 + ty;
+        const bool col = gx < g.nx && gy < g.ny;
+        const int b = (ty + 1) * kZmW + (tx + 1);  // the site in a plane
+#pragma unroll 1
+        for (int z = zs; z < ze; ++z) {
+            // plane z + 2 (needed while z + 1 < ze) in flight during this plane's sums
+            T pre[K];
+            const bool next = z + 2 <= ze;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int i = (int)threadIdx.x + k * kThreads;
+                pre[k] = (next && i < PT) ? fetch(z + 2, i) : T(0);
+            }
+            const T* pm = slot(z - 1);
+            const T* p0 = slot(z);
+            const T* pp = slot(z + 1);
+            T ps[NO], kx[NO];
+#pragma unroll
+            for (int j = 0; j < NO; ++j) ps[j] = kx[j] = T(0);
+#pragma unroll
+            for (int p = 0; p < 19; ++p) {
+                const T* pl = vel(p, 2) > 0 ? pm : vel(p, 2) < 0 ? pp : p0;  // source plane z - vz
+                const int src = b - (vel(p, 0) + vel(p, 1) * kZmW);
+                const T a = xi[vclass(p)] - dt * chi[vclass(p)] * pl[NO * kZmPlane + src];
+#pragma unroll
+                for (int j = 0; j < NO; ++j) {
+                    const T v = pl[j * kZmPlane + src];
+                    ps[j] += a * v;
+                    kx[j] += xi[vclass(p)] * v;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j) {
+#pragma unroll
+                for (int k = 0; k < j; ++k) ps[j] += wl[tri(j - 1, k)] * kx[k];
+                ps[j] = col ? ps[j] * sig[j] : T(0);
+            }
+            if (col) {
+                const size_t s = ((size_t)z * g.ny + gy) * g.nx + gx;
+#pragma unroll
+                for (int j = 0; j < NO; ++j) pout[(size_t)j * N + s] = ps[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NO; ++j)
+#pragma unroll
+                for (int i = 0; i <= j; ++i) acc[tri(j, i)] += ps[j] * ps[i];
+            if (next) {
+                T* r = slot(z + 2);
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int i = (int)threadIdx.x + k * kThreads;
+                    if (i < PT) r[i] = pre[k];
+                }
+            }
+            __syncthreads();
+        }
+    }
+    double v[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) v[k] = (double)acc[k];
+    double* partial = sc.partial + y * sc.max_blocks * sc.max_vals;
+    block_sum_store<NP>(v, partial + (size_t)blockIdx.x * NP);
+    __shared__ double tot[NP];
+    if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0)
+        store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
+}
+
+// One run per block where the overlap scratch allows (the hardware balances
+// the blocks): runs of at least 8 planes, as many runs as the scratch's
+// blocks per system hold.
+template <typename T, int NO, bool BATCHED>
+cudaError_t launch_relax_psi_zm(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                cudaStream_t st) {
+    auto kern = k_relax_psi_zm<T, NO, BATCHED>;
+    const size_t smem = (size_t)4 * (NO + 1) * kZmPlane * sizeof(T);
+    static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    const int columns = ((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY);
+    const int runs = std::max(1, sc.max_blocks / columns);  // runs along z the scratch allows per column
+    const int zc = std::max(8, (g.nz + runs - 1) / runs);
+    const size_t items = (size_t)columns * ((g.nz + zc - 1) / zc);
+    kern<<<dim3((unsigned)std::min<size_t>(items, (size_t)sc.max_blocks), (unsigned)B), kThreads, smem, st>>>(g, c, io,
+                                                                                                          sc, zc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_n(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                cudaStream_t st) {
@@ -502,7 +655,8 @@ template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                              int kernel, cudaStream_t st) {
     if (kernel == kPsiKernelTma) return launch_relax_psi_tma<T>(NO, g, c, io, sc, B, st);
-    const bool tiled = kernel == kPsiKernelTiled;
+    const bool tiled = kernel == kPsiKernelTiled || (kernel == kPsiKernelZ && NO > kMaxOrb);
+    const bool zmarch = kernel == kPsiKernelZ && NO <= kMaxOrb;
     if (NO > kMaxOrb) {
         const size_t groups = (NO + kPsiGroup - 1) / kPsiGroup;
         if (groups * B > 65535) return cudaErrorInvalidConfiguration;
@@ -529,6 +683,9 @@ cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO
     switch (NO) {
 #define LBKS_CASE(n)                                                                                  \
     case n:                                                                                           \
+        if (zmarch)                                                                                   \
+            return b ? launch_relax_psi_zm<T, n, true>(g, c, io, sc, B, st)                           \
+                     : launch_relax_psi_zm<T, n, false>(g, c, io, sc, B, st);                         \
         if (tiled)                                                                                    \
             return b ? launch_relax_psi_tile<T, n, true>(g, c, io, sc, B, st)                         \
                      : launch_relax_psi_tile<T, n, false>(g, c, io, sc, B, st);                       \

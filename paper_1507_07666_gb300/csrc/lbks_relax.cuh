@@ -882,7 +882,9 @@ struct Ops {
         // variant kPsiKernelTiled: the shared-memory tiled stencil; kPsiKernelDirect: one site per thread
         // from L1; kPsiKernelTma: boxes copied by the tensor memory accelerator (anything else: tiled)
         const int v = variant & kRelaxVariantMask;
-        cudaError_t e = launch_relax_psi<T>(n_orb, g, c, io, sc, B, v == kPsiKernelDirect || v == kPsiKernelTma ? v : kPsiKernelTiled, st);
+        cudaError_t e = launch_relax_psi<T>(
+            n_orb, g, c, io, sc, B, v == kPsiKernelDirect || v == kPsiKernelTma || v == kPsiKernelZ ? v : kPsiKernelTiled,
+            st);
         if (e != cudaSuccess || n_orb <= kMaxOrb) return e;  // up to kMaxOrb: overlap fused
         return gram_wide<true>(n_orb, g, c.h, io.f_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
                                (variant & kRelaxExactOverlap) != 0);

@@ -36,8 +36,9 @@ def test_orbital_storage_bytes_per_site():
 
 def test_kernel_for_each_forced_mode():
     w, ragged = _w(5, 128), _w(5, 130)  # 128: whole 16-byte rows in FP32; 130: not (FP64: yes)
-    assert [bench.psi_kernel_index(w, 4, m) for m in range(5)] == [2, 0, 1, 2, 0]
-    assert [bench.psi_kernel_index(ragged, 4, m) for m in range(5)] == [0, 0, 1, 0, 0]
+    assert [bench.psi_kernel_index(w, 4, m) for m in range(5)] == [2, 0, 1, 2, 3]
+    assert [bench.psi_kernel_index(ragged, 4, m) for m in range(5)] == [0, 0, 1, 0, 3]
+    assert bench.psi_kernel_index(_w(40, 128), 4, 4) == 0  # more than eight orbitals: tiled
     assert bench.psi_kernel_index(ragged, 8, 0) == 2
 
 

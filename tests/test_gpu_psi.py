@@ -35,12 +35,16 @@ def _populations(A, u, Vc, theta, dt):
     # with ragged ends, two planes, grids smaller than a box, each orbital bucket
     ((36, 11, 13), 5, 8), ((44, 9, 7), 12, 9), ((4, 3, 5), 3, 10), ((64, 17, 6), 40, 11),
     ((40, 8, 3), 8, 12), ((8, 2, 2), 1, 13), ((32, 9, 2), 2, 14), ((12, 20, 4), 33, 15),
+    # many z runs of the z-marching kernel
+    ((34, 17, 70), 5, 16),
 ])
 @pytest.mark.parametrize("with_w", [True, False], ids=["W", "noW"])
-@pytest.mark.parametrize("mode", [1, 2, 3], ids=["tiled", "direct", "tma"])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4], ids=["tiled", "direct", "tma", "zmarch"])
 def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
     """mode 3 forces the TMA kernel where its tensor maps apply (nx a multiple
-    of 16 / the value's bytes), the tiled one elsewhere."""
+    of 16 / the value's bytes), the tiled one elsewhere; mode 4 the z-marching
+    kernel up to eight orbitals (grids of one, two or many z runs, ragged x and
+    y tiles), the tiled one above."""
     torch, lbks = require_gpu()
     prev = lbks.lbks_set_relax_variant(mode)  # forced: tiled, one site per thread, or TMA
     try:
@@ -97,7 +101,7 @@ def test_psi_step_rejects_bad_arguments():
         lbks.System((8, 8, 8), 0.4, 1, storage=lbks.STORE_PSI, precision=lbks.BF16)
 
 
-SCF_MODE = {"ch4": 0, "ch4_direct": 2, "ch4_tma": 3, "water_dimer": 0, "water_dimer_tiled": 1}
+SCF_MODE = {"ch4": 0, "ch4_direct": 2, "ch4_tma": 3, "ch4_zmarch": 4, "water_dimer": 0, "water_dimer_tiled": 1}
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
@@ -107,7 +111,8 @@ def test_psi_storage_scf_follows_the_oracle(prec, case):
     potential term (the start is f = xi psi), every cycle's first step with
     the previous cycle's collision potential.  ch4: the tuned kernel;
     ch4_direct: one site per thread forced; ch4_tma: the TMA kernel forced on
-    a grid whose rows it takes; water_dimer (ten orbitals): the default, the
+    a grid whose rows it takes; ch4_zmarch: the z-marching kernel forced;
+    water_dimer (ten orbitals): the default, the
     TMA kernel with the W source formed in the step; water_dimer_tiled: the
     tiled kernel with the W field."""
     torch, lbks = require_gpu()
@@ -175,10 +180,10 @@ def test_psi_storage_batch_matches_single():
 ])
 def test_psi_kernel_choice(prec, nx, n_orb):
     """The tuner times the orbital-storage kernels that apply to the shape and
-    keeps the fastest: up to eight orbitals tiled, one site per thread and TMA
-    (where its tensor maps apply: nx a multiple of 16 / the value's bytes);
-    more than eight the tiled step with its W-field pass against the TMA step,
-    which forms the W source itself."""
+    keeps the fastest: up to eight orbitals tiled, one site per thread, TMA
+    (where its tensor maps apply: nx a multiple of 16 / the value's bytes) and
+    z-marching; more than eight the tiled step with its W-field pass against
+    the TMA step, which forms the W source itself."""
     torch, lbks = require_gpu()
     prev = lbks.lbks_set_relax_variant(0)
     try:
@@ -196,8 +201,9 @@ def test_psi_kernel_choice(prec, nx, n_orb):
     if n_orb > 8 and not tma_ok:  # nothing to choose: the tiled step
         assert got["index"] == 0
     else:
-        ms = {k: got["ms_" + names[k]] for k in range(3)}
-        timed = [k for k in range(3) if ms[k] >= 0]
+        ms = {k: got["ms_" + names[k]] for k in range(4)}
+        timed = [k for k in range(4) if ms[k] >= 0]
         assert (2 in timed) == tma_ok and 0 in timed and (1 in timed) == (n_orb <= 8)
+        assert (3 in timed) == (n_orb <= 8)
         assert got["index"] == min(timed, key=lambda k: ms[k])
     s.close()
