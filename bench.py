@@ -39,6 +39,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import workloads as W  # noqa: E402
 
 METRIC = "GLUPS (orbital-site updates/s)"
@@ -80,6 +82,11 @@ BATCHES = {
 # a nucleus sits between grid points by tenths of a hartree, and a free
 # relaxation slides the O onto a grid point instead of relaxing the bonds)
 RELAXATIONS = {"h2o_relax_96": (W.water_96, 2.0, 95.0, 2e-3, [1, 0, 0])}
+# concurrent dynamics (Eq. KSLBCD): from the ground state at a stretched
+# geometry, one bench step = CD_BLOCKS blocks of CD_NPOT real-time steps, each
+# block ending with the potential rebuilt and the nuclei moved
+DYNAMICS = {"ch4_cd_128": W.ch4_cd_128}
+CD_BLOCKS, CD_NPOT = 10, 10
 
 
 def parse_args():
@@ -89,7 +96,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lbks", "reference"], default="lbks")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(CYCLES) + sorted(BATCHES) + sorted(SERVING)
-                    + sorted(RELAXATIONS), default="h2o8_256")
+                    + sorted(RELAXATIONS) + sorted(DYNAMICS), default="h2o8_256")
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent solve slots")
     ap.add_argument("--requests", type=int, default=0, help="serving: requests of the stream (0: the default)")
     ap.add_argument("--precision", choices=["fp32", "fp64", "bf16"], default="fp32")
@@ -745,6 +752,139 @@ def main_relax(args):
     return 0
 
 
+ORACLE_CD_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import cd, lattice, lb, scf
+w = W.{wl}()
+n, h, no = w.n, w.h, w.n_orb
+dt = lattice.time_step(w.theta, 1.0, h)
+psi = lb.orthonormalize(scf.initial_orbitals(n, h, w.molecule.xyz, w.molecule.Z, no), h).astype(complex)
+V = scf.external_potential(n, h, w.molecule.xyz, w.molecule.Z, h)
+prev, cur = psi, psi
+times = []
+t_end = time.perf_counter() + {seconds}
+while len(times) < 2 or time.perf_counter() < t_end:
+    t0 = time.perf_counter()
+    prev, cur = cur, cd.cd_step(prev, cur, V, w.theta, dt, h, 0.5 * dt)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "updates_per_step": no * n[0] * n[1] * n[2]}}))
+"""
+
+
+def time_cd_step(torch, lbks, w, prec, launches=20):
+    """Average duration of one concurrent-dynamics step (k_cd_step, the launch
+    configuration of the run) on random levels of the workload's shape, CUDA
+    events on the launching stream, L2 flushed before every launch."""
+    P = torch.float64 if prec == lbks.FP64 else torch.float32
+    nx, ny, nz = w.n
+    no = w.n_orb
+    dt = w.theta * w.h * w.h
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a = torch.rand((no, 2, nz, ny, nx), dtype=P, device="cuda")
+        b = torch.rand_like(a)
+        c = torch.empty_like(a)
+        V = torch.rand((nz, ny, nx), dtype=torch.float64, device="cuda")
+        S = torch.zeros((no, no, 2), dtype=torch.float64, device="cuda")
+        L = torch.zeros_like(S)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        lbks.lbks_cd_overlap(prec, nx * ny * nz, no, w.h, b, S, L, stream=stream)
+        total = 0.0
+        for it in range(3 + launches):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lbks.lbks_cd_step(prec, nx, ny, nz, no, w.h, w.theta, 0.5 * dt, a, b, V, L, None, c, S, L, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            if it >= 3:
+                total += e0.elapsed_time(e1)
+    return total / launches, no * nx * ny * nz
+
+
+def main_dynamics(args):
+    """Concurrent dynamics of methane from a stretched geometry: the SCF
+    ground state there (untimed), then bench steps of CD_BLOCKS x CD_NPOT
+    real-time steps with the potential rebuilt and the nuclei moved after
+    every CD_NPOT steps.  value: orbital-site updates of the real-time steps
+    per second of the whole run (rebuilds, forces and moves included)."""
+    import torch
+    from paper_1507_07666_gb300 import build as build_mod
+    build_mod.build()
+    from paper_1507_07666_gb300 import lbks
+    w = DYNAMICS[args.workload]()
+    prec = {"fp32": lbks.FP32, "fp64": lbks.FP64, "bf16": lbks.FP32}[args.precision]
+    sysm = lbks.System(w.n, w.h, w.n_orb, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
+                       storage=lbks.STORE_PSI)
+    sysm.set_geometry(w.molecule.xyz, w.molecule.Z)
+    gs = sysm.scf()
+    M = W.masses(w.molecule)
+    e_start, n_el = sysm.cd_start(n_pot=CD_NPOT)
+    vel = np.zeros((len(M), 3))
+    energies = []
+    for _ in range(args.warmup):
+        vel, e, _ = sysm.cd_run(CD_BLOCKS, masses=M, velocities=vel)
+        energies.append(e)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = lbks.lbks_kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vel, e, traj = sysm.cd_run(CD_BLOCKS, masses=M, velocities=vel)
+        energies.append(e)
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    clk = clocks.stop()
+    launches = lbks.lbks_kernel_launches() - l0
+    st = sysm.cd_state()
+    e_all = np.concatenate(energies)
+    total = e_all[:, 0] + e_all[:, 1]
+    R = traj[-1]
+    r_ch = float(np.mean(np.linalg.norm(R[1:] - R[0], axis=1)))
+    sysm.close()
+    updates = args.steps * CD_BLOCKS * CD_NPOT * w.n_orb * w.sites
+    ms, units = time_cd_step(torch, lbks, w, prec)
+    pe = 8 if prec == lbks.FP64 else 4
+    per_site = 6 * pe + 8.0 / w.n_orb  # prev and cur read, next written (complex), V once per site
+    peak, peak_kind = measured_hbm_peak()
+    achieved = per_site * units / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": updates / elapsed / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == lbks.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": f"concurrent dynamics (Eq. KSLBCD, Ehrenfest nuclei) of {w.name} from its ground "
+                               f"state, {CD_BLOCKS} blocks x {CD_NPOT} steps per bench step, tau = theta h^2 / 2",
+                   "grid": list(w.n), "n_orb": w.n_orb,
+                   "l2": "levels larger than L2 (3 complex levels %.2f GB)" % (3 * 2 * pe * w.n_orb * w.sites / 1e9),
+                   "timing": "wall clock around synchronous lbks_cd_run calls (device synchronised on both sides)"},
+        "dynamics": {"ground_state_E": gs["E_total"], "ground_state_cycles": gs["cycles"], "E_start": e_start,
+                     "n_electrons": n_el, "time_au": st["time"], "steps": st["steps"],
+                     "max_abs_drift_E_total_plus_E_kin_Ha": float(np.abs(total - total[0]).max()),
+                     "E_kin_nuclei_end": float(e_all[-1, 1]), "mean_r_CH_end": r_ch},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_cd_step", "bytes_per_launch": per_site * units,
+                     "ms_per_launch": ms, "peak_source": f"hbm_gbs of {peak_kind}"},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        code = ORACLE_CD_SAMPLE.format(root=ROOT, wl=DYNAMICS[args.workload].__name__, seconds=args.cpu_seconds)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        if r.returncode == 0:
+            smp = json.loads(r.stdout.strip().splitlines()[-1])
+            v, nsteps, t = oracle_rate([smp])
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"{nsteps} oracle steps (oracle.cd.cd_step) of {w.name}, one FP64 "
+                                              f"numpy process, {t:.1f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main_lbks(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -908,6 +1048,8 @@ def main():
         return main_serving(args)
     if args.workload in RELAXATIONS:
         return main_relax(args)
+    if args.workload in DYNAMICS:
+        return main_dynamics(args)
     return main_lbks(args)
 
 

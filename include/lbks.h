@@ -335,6 +335,89 @@ int lbks_md(lbks_system* sys, int n_steps, double dt, const double* masses, doub
 int lbks_relax_geometry(lbks_system* sys, int max_steps, double fmax, double step, const int* fixed,
                         void* stream, lbks_result* out, double* xyz_out, int* steps_out);
 
+/* ---------------------------------------------------------------------------
+ * Concurrent dynamics (Sec. 3, "Concurrent Dynamics", Eq. KSLBCD): electrons
+ * and nuclei moved together.  The paper prints the two-step, time-centred
+ * update f(r + v h; t + h) = f(r - v h; t - h) + 2h (U + iV + iW) with
+ * U_jp = kappa w_p q_p E_j phi_j, but no kinetic term, no rule for kappa and
+ * no start.  It is read here as the real-time counterpart of the omega = 1
+ * ground-state step (Wick rotation of Sec. 3's first equation), with the
+ * complex orbitals phi_j as state and its own step tau:
+ *   phi_j(t + tau) = phi_j(t - tau) + 2i (tau/dt) D_j(phi(t)) + 2 tau kappa E_j (K_q phi_j)(t),
+ *   D_j(r) = sum_p [xi_p a_j - dt chi_p V phi_j](r - v_p) - phi_j(r),   zero outside the box,
+ *   a_j = phi_j - sum_{k<j} Lambda_jk phi_k,  Lambda_jk = <phi_k|phi_j> / <phi_k|phi_k>,
+ *   K_q phi(r) = sum_p w_p q_p phi(r - v_p),  dt = theta h^2.
+ * D_j = -dt H phi_j (+ the W source) with H = (1 - K_xi)/dt + K_chi V; an
+ * eigenvector of H with eigenvalue eps rotates at Omega, sin(Omega tau) =
+ * eps tau, and the scheme is stable while tau |eps| < 1 over the spectrum of
+ * H (tau = dt / 2 by default).  Every n_pot steps the nuclei make a
+ * velocity-Verlet step of n_pot tau under the Hellmann-Feynman forces of
+ * rho = 2 sum_j |phi_j|^2 (Ehrenfest form), and V = V_ext + V_H + v_xc is
+ * rebuilt from rho (no mixing).  Up to 8 orbitals; omega = 1 handles.
+ * A level is [j][part][z][y][x]: part 0 real, 1 imaginary values of orbital j,
+ * in the compute type (double for LBKS_FP64, float otherwise).  Lambda and
+ * S are [j][k][2] doubles (real, imaginary). */
+typedef struct lbks_cd_params {
+    double tau;   /* real-time step (hbar/Ha), at most theta h^2; 0: theta h^2 / 2 */
+    double kappa; /* gain of the U source (dimensionless); 0: no U source */
+    int n_pot;    /* electron steps per potential rebuild and nuclear move; 0: 10 */
+} lbks_cd_params;
+
+/* Starts the dynamics of a single-system handle from its current orbitals
+ * (normally an SCF ground state): level 0 = the orbitals (imaginary parts
+ * zero), the potential rebuilt from them, the forces, and the second level by
+ * Taylor expansion to second order, phi(tau) = phi + i s D(phi) -
+ * s^2 D0(D0(phi)) / 2 + tau kappa E K_q phi (s = tau/dt, D0 without the W
+ * source).  E_target: n_orb orbital energies (Ha) of the U source, or NULL
+ * with kappa = 0.  energy (may be NULL): E_total and the electron count of the
+ * start.  The handle's potential is replaced (a later lbks_scf restarts from
+ * it).  Allocates the three levels on first use (6 n_orb N values).
+ * Synchronous on the handle's stream. */
+int lbks_cd_start(lbks_system* sys, const lbks_cd_params* p, const double* E_target, void* stream, double* energy);
+
+/* n_blocks blocks of n_pot steps.  masses: n_atoms nuclear masses (electron
+ * masses) and velocities: 3 n_atoms (bohr Ha/hbar; in: initial, out: final),
+ * or masses NULL for fixed nuclei.  energies (may be NULL): n_blocks x 3
+ * doubles after each block: E_total of the orbitals at the nuclei, the
+ * nuclear kinetic energy and the electron count.  xyz_traj (may be NULL):
+ * n_blocks x 3 n_atoms positions.  EINVAL if a nucleus leaves the box.
+ * Synchronous. */
+int lbks_cd_run(lbks_system* sys, int n_blocks, const double* masses, double* velocities, void* stream,
+                double* energies, double* xyz_traj);
+
+/* Host copy of a level (0: the older, 1: the current): 2 n_orb N doubles,
+ * layout [j][part][z][y][x]. */
+int lbks_cd_get_orbitals(const lbks_system* sys, int level, double* host, size_t cap);
+
+/* Time since the start (hbar/Ha), steps taken (the start counts one) and the
+ * forces at the current level (3 n_atoms doubles, may be NULL). */
+int lbks_cd_get_state(const lbks_system* sys, double* time, int64_t* steps, double* forces, size_t cap);
+
+/* One step of the dynamics on device arrays (the update above):
+ * phi_next = phi_prev + 2i (tau/dt) D(phi) + u_j K_q phi_j with u_coef[j] =
+ * 2 tau kappa E_j (device, n_orb doubles, or NULL: no U source).  phi_prev
+ * may be NULL (taken as zero).  lambda: Lambda of phi (device, n_orb^2 x 2
+ * doubles, strictly lower part used) or NULL: no W source.  S_next (may be
+ * NULL): the overlap S[i][j] = <phi_next_i|phi_next_j> = h^3 sum conj(phi_i) phi_j;
+ * lambda_next (with S_next, may be NULL): Lambda of phi_next.  phi_next must
+ * not alias phi or phi_prev.  precision LBKS_FP64 or LBKS_FP32.  Up to 8
+ * orbitals.  Asynchronous on stream. */
+int lbks_cd_step(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double tau,
+                 const void* phi_prev_dev, const void* phi_dev, const double* V_dev, const double* lambda_dev,
+                 const double* u_coef_dev, void* phi_next_dev, double* S_next_dev, double* lambda_next_dev,
+                 void* stream);
+
+/* Kernel of later dynamics steps: -1 (default) the staged kernel (every
+ * orbital's box with a one-site halo in shared memory) where the box leaves
+ * two blocks per SM, else one site per thread from L1; 0 one site per thread;
+ * 1 staged where it applies.  Returns the previous mode, or -2 for a bad mode
+ * (lbks_last_error says why). */
+int lbks_set_cd_kernel(int mode);
+
+/* Overlap S and (lambda may be NULL) Lambda of one level of n_sites sites. */
+int lbks_cd_overlap(int precision, size_t n_sites, int n_orb, double h, const void* phi_dev, double* S_dev,
+                    double* lambda_dev, void* stream);
+
 /* Host copies (synchronous) of the last evaluation's density rho (N doubles),
  * orthonormal orbitals (n_orb*N doubles) and potentials (N doubles each).
  * EINVAL if cap (elements) is too small. */

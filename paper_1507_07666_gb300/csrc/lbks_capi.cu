@@ -309,6 +309,18 @@ struct lbks_system {
     std::vector<lbks_energy_terms> terms;
     std::vector<double> drho;  // ||rho - rho_prev|| / ||rho|| of the last evaluation, per system
     int poisson_iters = 0;
+    // concurrent dynamics (lbks_cd_start / lbks_cd_run): three complex levels
+    // [j][part][N] of the compute type, rotated step by step
+    void* cd_lev[3] = {nullptr, nullptr, nullptr};
+    int cd_prev = 0, cd_cur = 1;
+    double* cd_small = nullptr;  // Lambda x 2, S, U coefficients x 2, energy matrix of 2 n_orb rows
+    int cd_lam = 0;              // which Lambda buffer belongs to the current level
+    Scratch cd_sc;               // reductions of up to 2 n_orb rows
+    bool cd_ready = false, cd_u = false;
+    double cd_tau = 0.0, cd_time = 0.0;
+    int cd_npot = 10;
+    int64_t cd_steps = 0;
+    std::vector<double> cd_F;  // forces at the current level (host, 3 n_atoms)
 };
 
 namespace {
@@ -920,6 +932,11 @@ void free_system(lbks_system* s) {
                     s->cg,  s->small, s->ints,   s->starts,        s->sc.partial,    s->sc.counter, s->vprev,
                     s->rho_ref};
     for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (void* p : s->cd_lev)
+        if (p) cudaFree(p);
+    void* cdp[] = {s->cd_small, s->cd_sc.partial, s->cd_sc.counter};
+    for (void* p : cdp)
         if (p) cudaFree(p);
     if (s->host) cudaFreeHost(s->host);
     if (s->st) cudaStreamDestroy(s->st);
@@ -1608,6 +1625,370 @@ int lbks_lda(size_t n_sites, const double* rho, double* eps, double* v, void* st
     if (n_sites == 0) return LBKS_OK;
     cudaError_t e = launch_lda(n_sites, rho, eps, v, (cudaStream_t)stream);
     return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_lda");
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------- concurrent dynamics
+namespace {
+std::atomic<int> g_cd_kernel{-1};
+}  // namespace
+
+int lbks::cd_kernel_mode() { return g_cd_kernel.load(); }
+
+namespace {
+
+CdCoef make_cd_coef(double theta, double h) {
+    const Coef c = make_coef(1.0, theta, theta * h * h, h);
+    CdCoef d;
+    d.dt = c.dt;
+    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    for (int k = 0; k < 3; ++k) {
+        d.xi[k] = c.xi[k];
+        d.chi[k] = c.chi[k];
+        d.wq[k] = w[k] * (k - 1.0) * 4.5;  // w_p q_p, q_p = (v^2 - 3 c_s^2) / (2 c_s^4)
+    }
+    return d;
+}
+
+cudaError_t cd_step_launch(int precision, int NO, const Grid& g, const CdCoef& c, const CdIO& io, const Scratch& sc,
+                           int B, cudaStream_t st) {
+    return precision == LBKS_FP64 ? launch_cd_step<double>(NO, g, c, io, sc, B, st)
+                                  : launch_cd_step<float>(NO, g, c, io, sc, B, st);
+}
+
+cudaError_t cd_overlap_launch(int precision, int NO, const Grid& g, const void* phi, double h, double* S, double* lam,
+                              const Scratch& sc, int B, cudaStream_t st) {
+    return precision == LBKS_FP64 ? launch_cd_overlap<double>(NO, g, phi, h, S, lam, sc, B, st)
+                                  : launch_cd_overlap<float>(NO, g, phi, h, S, lam, sc, B, st);
+}
+
+// Device small arrays of the dynamics: Lambda (two buffers), S, the U
+// coefficients (step and start) and the energy matrix of 2 n_orb rows.
+size_t cd_small_doubles(int no) { return 3 * (size_t)no * no * 2 + 2 * (size_t)no + emat_stride(2 * no); }
+double* cd_lam(lbks_system* s, int k) { return s->cd_small + (size_t)k * s->n_orb * s->n_orb * 2; }
+double* cd_S(lbks_system* s) { return cd_lam(s, 2); }
+double* cd_ucoef(lbks_system* s, int half) { return cd_S(s) + (size_t)s->n_orb * s->n_orb * 2 + half * s->n_orb; }
+double* cd_emat(lbks_system* s) { return cd_ucoef(s, 0) + 2 * s->n_orb; }
+
+// Density of the current level (its 2 n_orb planes as real rows), Hartree,
+// potential (unmixed, into V_in and V_out), energies at the current nuclei
+// and the Hellmann-Feynman forces; E_total and the electron count out.
+int cd_rebuild(lbks_system* s, cudaStream_t st, double* e_total, double* n_el) {
+    const int no2 = 2 * s->n_orb;
+    const void* phi = s->cd_lev[s->cd_cur];
+    cudaError_t e = s->ops->density(no2, s->g, s->h, phi, s->rho, s->rho, s->mp, s->cd_sc, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "density (dynamics)");
+    int rc = hartree_solve(s, st);
+    if (rc != LBKS_OK) return rc;
+    e = launch_potential(s->g, s->h, s->rho, s->vext, s->vh, s->vout, s->vin, 1, 1.0, s->e4, s->sc, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "potential (dynamics)");
+    e = s->ops->energy_matrix(no2, s->g, s->c, phi, s->vout, cd_emat(s), s->cd_sc, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy matrix (dynamics)");
+    std::vector<double> kin(no2);
+    e = cudaMemcpyAsync(host_e4(s, 0), s->e4, sizeof(double) * kE4Stride, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "energy readback (dynamics)");
+    const double* h4 = host_e4(s, 0);
+    const double e_ext = h4[0], e_h = 0.5 * h4[1], e_xc = h4[2];
+    *n_el = h4[3];
+    e = cudaMemcpy(kin.data(), cd_emat(s) + (size_t)no2 * no2, sizeof(double) * no2, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "kinetic readback (dynamics)");
+    double ts = 0.0;
+    for (double k : kin) ts += k;
+    const std::vector<double>& xyz = s->xyz[0];
+    const std::vector<double>& Z = s->Z[0];
+    double enn = 0.0;
+    for (size_t a = 0; a < Z.size(); ++a)
+        for (size_t b = 0; b < a; ++b) {
+            const double dx = xyz[3 * a] - xyz[3 * b], dy = xyz[3 * a + 1] - xyz[3 * b + 1],
+                         dz = xyz[3 * a + 2] - xyz[3 * b + 2];
+            enn += Z[a] * Z[b] / std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    *e_total = 2.0 * ts + e_ext + e_h + e_xc + enn;
+    s->cd_F.assign(3 * Z.size(), 0.0);
+    return lbks_forces(s, s->cd_F.data(), s->cd_F.size());
+}
+
+// One step: next = prev + 2i (tau/dt) D(cur) + u K_q cur, then the levels rotate.
+int cd_advance(lbks_system* s, cudaStream_t st) {
+    const int nxt = 3 - s->cd_prev - s->cd_cur;
+    const bool w = s->n_orb > 1;
+    CdIO io{};
+    io.prev = s->cd_lev[s->cd_prev];
+    io.cur = s->cd_lev[s->cd_cur];
+    io.out = s->cd_lev[nxt];
+    io.V = s->vin;
+    io.lam = w ? cd_lam(s, s->cd_lam) : nullptr;
+    io.ucoef = s->cd_u ? cd_ucoef(s, 0) : nullptr;
+    io.S_out = w ? cd_S(s) : nullptr;
+    io.lam_out = w ? cd_lam(s, 1 - s->cd_lam) : nullptr;
+    io.alpha = 1.0;
+    io.c_re = 0.0;
+    io.c_im = 2.0 * s->cd_tau / (s->prm.theta * s->h * s->h);
+    io.h = s->h;
+    cudaError_t e = cd_step_launch(s->prm.precision == LBKS_FP64 ? LBKS_FP64 : LBKS_FP32, s->n_orb, s->g,
+                                   make_cd_coef(s->prm.theta, s->h), io, s->sc, 1, st);
+    if (e != cudaSuccess) return cuda_fail(e, "concurrent-dynamics step");
+    s->cd_prev = s->cd_cur;
+    s->cd_cur = nxt;
+    if (w) s->cd_lam = 1 - s->cd_lam;
+    ++s->cd_steps;
+    s->cd_time += s->cd_tau;
+    return LBKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbks_set_cd_kernel(int mode) {
+    if (mode < -1 || mode > 1) {
+        fail(LBKS_EINVAL, "mode must be -1, 0 or 1");
+        return -2;
+    }
+    return g_cd_kernel.exchange(mode);
+}
+
+int lbks_cd_start(lbks_system* s, const lbks_cd_params* p, const double* E_target, void* stream, double* energy) {
+    if (!s || !p) return fail(LBKS_EINVAL, "null argument");
+    if (s->B != 1) return fail(LBKS_EINVAL, "batched handle: one system per dynamics");
+    if (!s->ready) return fail(LBKS_EINVAL, "geometry has not been set");
+    if (s->n_orb > kMaxOrb) return fail(LBKS_EINVAL, "concurrent dynamics takes up to %d orbitals", kMaxOrb);
+    if (s->prm.omega != 1.0) return fail(LBKS_EINVAL, "concurrent dynamics is built on the omega = 1 step");
+    const double dt = s->prm.theta * s->h * s->h;
+    const double tau = p->tau > 0.0 ? p->tau : 0.5 * dt;
+    if (!(tau <= dt) || !std::isfinite(p->kappa)) return fail(LBKS_EINVAL, "tau must be in (0, theta h^2]");
+    if (p->n_pot < 0) return fail(LBKS_EINVAL, "n_pot must be >= 0");
+    if (p->kappa != 0.0 && !E_target) return fail(LBKS_EINVAL, "kappa != 0 needs E_target");
+    cudaStream_t st = s->st;
+    (void)stream;
+    const int no = s->n_orb;
+    const size_t N = s->N, ep = s->ops->psi_elem, level = ep * N * 2 * no;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+        if (!s->cd_lev[k]) e = cudaMalloc(&s->cd_lev[k], level);
+    if (e == cudaSuccess && !s->cd_small) e = cudaMalloc((void**)&s->cd_small, sizeof(double) * cd_small_doubles(no));
+    if (e == cudaSuccess && !s->cd_sc.partial) {
+        s->cd_sc.max_blocks = num_sms() * 8;
+        s->cd_sc.max_vals = scratch_vals(2 * no);
+        s->cd_sc.systems = 1;
+        e = cudaMalloc(&s->cd_sc.partial, sizeof(double) * (size_t)s->cd_sc.max_blocks * s->cd_sc.max_vals);
+        if (e == cudaSuccess) e = cudaMalloc(&s->cd_sc.counter, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->cd_sc.counter, 0, sizeof(unsigned), st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "concurrent-dynamics allocation");
+    s->cd_tau = tau;
+    s->cd_npot = p->n_pot > 0 ? p->n_pot : 10;
+    s->cd_u = p->kappa != 0.0;
+    std::vector<double> uc(2 * no, 0.0);
+    for (int j = 0; j < no && s->cd_u; ++j) {
+        uc[j] = 2.0 * tau * p->kappa * E_target[j];
+        uc[no + j] = tau * p->kappa * E_target[j];
+    }
+    e = cudaMemcpyAsync(cd_ucoef(s, 0), uc.data(), sizeof(double) * 2 * no, cudaMemcpyHostToDevice, st);
+    // level 0: the handle's orthonormal orbitals, imaginary parts zero
+    void* L0 = s->cd_lev[0];
+    for (int j = 0; j < no && e == cudaSuccess; ++j) {
+        char* dst = static_cast<char*>(L0) + (size_t)2 * j * N * ep;
+        e = cudaMemcpyAsync(dst, static_cast<const char*>(s->psi) + (size_t)j * N * ep, N * ep,
+                            cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dst + N * ep, 0, N * ep, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "concurrent-dynamics start");
+    s->cd_prev = 1;
+    s->cd_cur = 0;
+    host_active(s)[0] = 1;
+    int rc = upload_active(s, st);
+    if (rc != LBKS_OK) return rc;
+    double e_tot = 0.0, n_el = 0.0;
+    rc = cd_rebuild(s, st, &e_tot, &n_el);
+    if (rc != LBKS_OK) return rc;
+    // second level (Taylor, second order): phi1 = phi0 + i s D(phi0) - s^2 D0(D0(phi0)) / 2 + tau kappa E K_q phi0
+    const int prec = s->prm.precision == LBKS_FP64 ? LBKS_FP64 : LBKS_FP32;
+    const CdCoef cc = make_cd_coef(s->prm.theta, s->h);
+    const double sr = tau / dt;
+    const bool w = no > 1;
+    if (w) e = cd_overlap_launch(prec, no, s->g, L0, s->h, cd_S(s), cd_lam(s, 0), s->sc, 1, st);
+    CdIO io{};
+    io.V = s->vin;
+    io.h = s->h;
+    // X = D0(phi0) into level 2, Y = D0(X) into level 1
+    io.cur = L0;
+    io.out = s->cd_lev[2];
+    io.c_re = 1.0;
+    if (e == cudaSuccess) e = cd_step_launch(prec, no, s->g, cc, io, s->sc, 1, st);
+    io.cur = s->cd_lev[2];
+    io.out = s->cd_lev[1];
+    if (e == cudaSuccess) e = cd_step_launch(prec, no, s->g, cc, io, s->sc, 1, st);
+    // phi1 = phi0 + i s D(phi0) - s^2 Y / 2 + (u/2) K_q phi0 into level 2, with its overlap
+    io.prev = L0;
+    io.alpha = 1.0;
+    io.extra = s->cd_lev[1];
+    io.beta = -0.5 * sr * sr;
+    io.cur = L0;
+    io.out = s->cd_lev[2];
+    io.c_re = 0.0;
+    io.c_im = sr;
+    io.lam = w ? cd_lam(s, 0) : nullptr;
+    io.ucoef = s->cd_u ? cd_ucoef(s, 1) : nullptr;
+    io.S_out = w ? cd_S(s) : nullptr;
+    io.lam_out = w ? cd_lam(s, 1) : nullptr;
+    if (e == cudaSuccess) e = cd_step_launch(prec, no, s->g, cc, io, s->sc, 1, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "concurrent-dynamics start");
+    s->cd_prev = 0;
+    s->cd_cur = 2;
+    s->cd_lam = 1;
+    s->cd_steps = 1;
+    s->cd_time = tau;
+    s->cd_ready = true;
+    if (energy) {
+        energy[0] = e_tot;
+        energy[1] = n_el;
+    }
+    return LBKS_OK;
+}
+
+int lbks_cd_run(lbks_system* s, int n_blocks, const double* masses, double* velocities, void* stream,
+                double* energies, double* xyz_traj) {
+    if (!s || n_blocks < 0) return fail(LBKS_EINVAL, "bad argument");
+    if (!s->cd_ready) return fail(LBKS_EINVAL, "lbks_cd_start has not run on this handle");
+    const int na = (int)s->Z[0].size();
+    if (masses) {
+        if (!velocities) return fail(LBKS_EINVAL, "moving nuclei need velocities");
+        for (int a = 0; a < na; ++a)
+            if (!(masses[a] > 0.0)) return fail(LBKS_EINVAL, "mass %d must be positive", a);
+    }
+    (void)stream;
+    cudaStream_t st = s->st;
+    std::vector<double> R = s->xyz[0];
+    auto kinetic = [&]() {
+        double ek = 0.0;
+        for (int a = 0; a < na && masses; ++a)
+            for (int c = 0; c < 3; ++c) ek += 0.5 * masses[a] * velocities[3 * a + c] * velocities[3 * a + c];
+        return ek;
+    };
+    for (int b = 0; b < n_blocks; ++b) {
+        for (int k = 0; k < s->cd_npot; ++k) {
+            int rc = cd_advance(s, st);
+            if (rc != LBKS_OK) return rc;
+        }
+        const double tb = s->cd_npot * s->cd_tau;
+        const std::vector<double> F = s->cd_F;
+        if (masses) {  // velocity Verlet, first half: positions
+            for (int a = 0; a < na; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    const int i = 3 * a + c;
+                    R[i] += tb * velocities[i] + 0.5 * tb * tb * F[i] / masses[a];
+                }
+            int rc = check_atoms(s, na, R.data(), s->Z[0].data());
+            if (rc != LBKS_OK) return rc;
+            s->xyz[0] = R;
+            std::vector<double> atoms;
+            std::vector<int> counts;
+            pack_atoms(s, atoms, counts);
+            cudaError_t e =
+                cudaMemcpyAsync(s->atoms, atoms.data(), sizeof(double) * atoms.size(), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = launch_vext(s->g, s->h, s->counts, s->atoms, s->a, s->vext, 1, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host atom array is a temporary
+            if (e != cudaSuccess) return cuda_fail(e, "lbks_cd_run: move nuclei");
+        }
+        double e_tot = 0.0, n_el = 0.0;
+        int rc = cd_rebuild(s, st, &e_tot, &n_el);
+        if (rc != LBKS_OK) return rc;
+        if (masses)  // second half: velocities with the new forces
+            for (int a = 0; a < na; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    const int i = 3 * a + c;
+                    velocities[i] += 0.5 * tb * (F[i] + s->cd_F[i]) / masses[a];
+                }
+        if (energies) {
+            energies[3 * b] = e_tot;
+            energies[3 * b + 1] = kinetic();
+            energies[3 * b + 2] = n_el;
+        }
+        if (xyz_traj) std::copy(R.begin(), R.end(), xyz_traj + (size_t)b * 3 * na);
+    }
+    return LBKS_OK;
+}
+
+int lbks_cd_get_orbitals(const lbks_system* s, int level, double* host, size_t cap) {
+    if (!s || !host) return fail(LBKS_EINVAL, "null argument");
+    if (!s->cd_ready) return fail(LBKS_EINVAL, "lbks_cd_start has not run on this handle");
+    if (level != 0 && level != 1) return fail(LBKS_EINVAL, "level must be 0 (older) or 1 (current)");
+    const size_t n = (size_t)2 * s->n_orb * s->N;
+    if (cap < n) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, n);
+    const void* src = s->cd_lev[level == 0 ? s->cd_prev : s->cd_cur];
+    cudaError_t e;
+    if (s->ops->psi_elem == 8) {
+        e = cudaMemcpy(host, src, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    } else {
+        std::vector<float> tmp(n);
+        e = cudaMemcpy(tmp.data(), src, sizeof(float) * n, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < n && e == cudaSuccess; ++i) host[i] = tmp[i];
+    }
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_cd_get_orbitals");
+}
+
+int lbks_cd_get_state(const lbks_system* s, double* time, int64_t* steps, double* forces, size_t cap) {
+    if (!s) return fail(LBKS_EINVAL, "null argument");
+    if (!s->cd_ready) return fail(LBKS_EINVAL, "lbks_cd_start has not run on this handle");
+    if (time) *time = s->cd_time;
+    if (steps) *steps = s->cd_steps;
+    if (forces) {
+        if (cap < s->cd_F.size()) return fail(LBKS_EINVAL, "capacity %zu < %zu", cap, s->cd_F.size());
+        std::copy(s->cd_F.begin(), s->cd_F.end(), forces);
+    }
+    return LBKS_OK;
+}
+
+int lbks_cd_step(int precision, int nx, int ny, int nz, int n_orb, double h, double theta, double tau,
+                 const void* phi_prev, const void* phi, const double* V, const double* lambda, const double* u_coef,
+                 void* phi_next, double* S_next, double* lambda_next, void* stream) {
+    if (precision != LBKS_FP64 && precision != LBKS_FP32)
+        return fail(LBKS_EINVAL, "concurrent dynamics needs LBKS_FP64 or LBKS_FP32");
+    if (nx < 2 || ny < 2 || nz < 2 || (size_t)nx * ny * nz >= (1ull << 31))
+        return fail(LBKS_EINVAL, "bad grid %d x %d x %d", nx, ny, nz);
+    if (n_orb < 1 || n_orb > kMaxOrb) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrb);
+    if (!phi || !V || !phi_next) return fail(LBKS_EINVAL, "null device pointer");
+    if (phi == phi_next || phi_prev == phi_next) return fail(LBKS_EINVAL, "phi_next must not alias its inputs");
+    if (!(h > 0.0) || !(theta > 0.0) || !(tau > 0.0)) return fail(LBKS_EINVAL, "bad h, theta or tau");
+    if (lambda_next && !S_next) return fail(LBKS_EINVAL, "lambda_next needs S_next");
+    Workspace* w = nullptr;
+    int rc = workspace(stream, 0, &w);
+    if (rc != LBKS_OK) return rc;
+    CdIO io{};
+    io.prev = phi_prev;
+    io.alpha = 1.0;
+    io.cur = phi;
+    io.out = phi_next;
+    io.V = V;
+    io.lam = n_orb > 1 ? lambda : nullptr;
+    io.ucoef = u_coef;
+    io.S_out = S_next;
+    io.lam_out = lambda_next;
+    io.c_re = 0.0;
+    io.c_im = 2.0 * tau / (theta * h * h);
+    io.h = h;
+    cudaError_t e = cd_step_launch(precision, n_orb, make_grid(nx, ny, nz), make_cd_coef(theta, h), io, w->sc, 1,
+                                   (cudaStream_t)stream);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_cd_step");
+}
+
+int lbks_cd_overlap(int precision, size_t n_sites, int n_orb, double h, const void* phi, double* S, double* lambda,
+                    void* stream) {
+    if (precision != LBKS_FP64 && precision != LBKS_FP32)
+        return fail(LBKS_EINVAL, "concurrent dynamics needs LBKS_FP64 or LBKS_FP32");
+    if (n_orb < 1 || n_orb > kMaxOrb) return fail(LBKS_EINVAL, "n_orb must be in [1, %d]", kMaxOrb);
+    if (!phi || !S) return fail(LBKS_EINVAL, "null device pointer");
+    if (n_sites == 0 || n_sites >= (1ull << 31)) return fail(LBKS_EINVAL, "bad n_sites");
+    Workspace* w = nullptr;
+    int rc = workspace(stream, 0, &w);
+    if (rc != LBKS_OK) return rc;
+    cudaError_t e = cd_overlap_launch(precision, n_orb, make_grid((int)n_sites, 1, 1), phi, h, S, lambda, w->sc, 1,
+                                      (cudaStream_t)stream);
+    return e == cudaSuccess ? LBKS_OK : cuda_fail(e, "lbks_cd_overlap");
 }
 
 }  // extern "C"

@@ -1,0 +1,9 @@
+// FP64 instantiation of the concurrent-dynamics step.
+#include "lbks_cd.cuh"
+
+namespace lbks {
+template cudaError_t launch_cd_step<double>(int, const Grid&, const CdCoef&, const CdIO&, const Scratch&, int,
+                                            cudaStream_t);
+template cudaError_t launch_cd_overlap<double>(int, const Grid&, const void*, double, double*, double*,
+                                               const Scratch&, int, cudaStream_t);
+}  // namespace lbks

@@ -217,6 +217,38 @@ cudaError_t launch_potential(const Grid&, double h, const double* rho, const dou
                              const double* vh, double* vout, double* vin, int first, double mix,
                              double* e4, const Scratch&, int B, cudaStream_t);
 
+// ------------------------------------------------------ concurrent dynamics
+// lbks_cd_f64.cu, lbks_cd_f32.cu (up to kMaxOrb complex orbitals).  A level
+// is [system][j][part][z][y][x], part 0 real and 1 imaginary.
+struct CdIO {
+    const void* prev;    // may be null (alpha = 0)
+    const void* extra;   // may be null (beta = 0)
+    const void* cur;
+    void* out;
+    const double* V;      // [system][N]
+    const double* lam;    // [system][NO][NO][2] of cur, or null: no W source
+    const double* ucoef;  // [system][NO], or null: no U source
+    double* S_out;        // [system][NO][NO][2] of out, or null: no overlap
+    double* lam_out;      // [system][NO][NO][2] of out (with S_out), may be null
+    double alpha, beta, c_re, c_im, h;
+};
+// Lattice weights per velocity class: xi_p, chi_p and the U source's w_p q_p.
+struct CdCoef {
+    double dt;  // the ground-state step theta h^2 of the pulled populations
+    double xi[3], chi[3], wq[3];
+};
+// out_j = alpha prev_j + beta extra_j + c D_j(cur) + u_j (K_q cur_j), with the
+// overlap (and Lambda) of out when io.S_out is set.
+template <typename T>
+cudaError_t launch_cd_step(int NO, const Grid&, const CdCoef&, const CdIO&, const Scratch&, int B, cudaStream_t);
+// Kernel of the step: -1 the staged one wherever its box leaves two blocks per
+// SM (else one site per thread), 0 one site per thread, 1 staged where it applies.
+int cd_kernel_mode();
+// Overlap S[i][j] = <phi_i|phi_j> and Lambda of one level.
+template <typename T>
+cudaError_t launch_cd_overlap(int NO, const Grid&, const void* phi, double h, double* S, double* lam,
+                              const Scratch&, int B, cudaStream_t);
+
 struct CGState {  // device-resident scalars of the preconditioned CG
     double bb, rr, rz, pap, alpha, beta, relres;
     int iters, done;

@@ -72,6 +72,10 @@ class lbks_server_stats(ctypes.Structure):
                 ("completed", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
 
 
+class lbks_cd_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("kappa", ctypes.c_double), ("n_pot", ctypes.c_int)]
+
+
 _vp, _d, _i, _sz = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
 _dp = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
@@ -125,6 +129,13 @@ _SIGS = {
     "lbks_orth_apply": (_i, [_i, _sz, _i, _vp, _vp, _vp, _vp]),
     "lbks_hartree": (_i, [_i, _i, _i, _d, _vp, _vp, _d, _i, ctypes.POINTER(_i), _dp, _vp]),
     "lbks_lda": (_i, [_sz, _vp, _vp, _vp, _vp]),
+    "lbks_cd_start": (_i, [_vp, ctypes.POINTER(lbks_cd_params), _dp, _vp, _dp]),
+    "lbks_cd_run": (_i, [_vp, _i, _dp, _dp, _vp, _dp, _dp]),
+    "lbks_cd_get_orbitals": (_i, [_vp, _i, _dp, _sz]),
+    "lbks_cd_get_state": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_int64), _dp, _sz]),
+    "lbks_cd_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "lbks_cd_overlap": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
+    "lbks_set_cd_kernel": (_i, [_i]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -280,6 +291,74 @@ def lbks_md(handle, n_steps, dt, masses, velocities, stream=None):
     _check(_lib.lbks_md(handle, n_steps, dt, masses.ctypes.data_as(_dp), v.ctypes.data_as(_dp), _stream(stream),
                         e.ctypes.data_as(_dp), traj.ctypes.data_as(_dp)))
     return v, e, traj
+
+
+def lbks_cd_start(handle, tau=0.0, kappa=0.0, n_pot=0, E_target=None, stream=None):
+    """Starts the concurrent dynamics from the handle's orbitals; returns
+    (E_total, n_electrons) of the start."""
+    p = lbks_cd_params(tau, kappa, n_pot)
+    E = None if E_target is None else np.ascontiguousarray(E_target, dtype=np.float64)
+    out = np.empty(2, dtype=np.float64)
+    _check(_lib.lbks_cd_start(handle, ctypes.byref(p), None if E is None else E.ctypes.data_as(_dp),
+                              _stream(stream), out.ctypes.data_as(_dp)))
+    return float(out[0]), float(out[1])
+
+
+def lbks_cd_run(handle, n_blocks, n_atoms, masses=None, velocities=None, stream=None):
+    """Returns (velocities after or None, energies [n_blocks, 3] = (E_total,
+    E_kin nuclei, n_electrons), positions [n_blocks, n_atoms, 3])."""
+    m = None if masses is None else np.ascontiguousarray(masses, dtype=np.float64).ravel()
+    v = None
+    if velocities is not None:
+        v = np.ascontiguousarray(velocities, dtype=np.float64).reshape(-1, 3).copy()
+    elif m is not None:
+        v = np.zeros((n_atoms, 3))
+    e = np.empty((max(n_blocks, 1), 3), dtype=np.float64)
+    traj = np.empty((max(n_blocks, 1), n_atoms, 3), dtype=np.float64)
+    _check(_lib.lbks_cd_run(handle, n_blocks, None if m is None else m.ctypes.data_as(_dp),
+                            None if v is None else v.ctypes.data_as(_dp), _stream(stream), e.ctypes.data_as(_dp),
+                            traj.ctypes.data_as(_dp)))
+    return v, e[:n_blocks], traj[:n_blocks]
+
+
+def lbks_cd_get_orbitals(handle, level, n_orb, shape):
+    """Complex orbitals [n_orb, nz, ny, nx] of level 0 (older) or 1 (current)."""
+    out = np.empty((n_orb, 2) + tuple(shape), dtype=np.float64)
+    _check(_lib.lbks_cd_get_orbitals(handle, level, out.ctypes.data_as(_dp), out.size))
+    return out[:, 0] + 1j * out[:, 1]
+
+
+def lbks_cd_get_state(handle, n_atoms):
+    t, steps = ctypes.c_double(), ctypes.c_int64()
+    F = np.empty((n_atoms, 3), dtype=np.float64)
+    _check(_lib.lbks_cd_get_state(handle, ctypes.byref(t), ctypes.byref(steps), F.ctypes.data_as(_dp), F.size))
+    return {"time": t.value, "steps": steps.value, "forces": F}
+
+
+def lbks_cd_step(precision, nx, ny, nz, n_orb, h, theta, tau, phi_prev, phi, V, lam, u_coef, phi_next, S_next=None,
+                 lam_next=None, stream=None):
+    """phi tensors: [n_orb, 2, nz, ny, nx] of the compute type (real, imaginary planes)."""
+    import torch
+    P = _psitype(precision)
+    _check(_lib.lbks_cd_step(precision, nx, ny, nz, n_orb, h, theta, tau, _ptr(phi_prev, P, optional=True),
+                             _ptr(phi, P), _ptr(V, torch.float64), _ptr(lam, torch.float64, optional=True),
+                             _ptr(u_coef, torch.float64, optional=True), _ptr(phi_next, P),
+                             _ptr(S_next, torch.float64, optional=True), _ptr(lam_next, torch.float64, optional=True),
+                             _stream(stream)))
+
+
+def lbks_set_cd_kernel(mode):
+    """-1 automatic, 0 one site per thread, 1 staged; returns the previous mode."""
+    code = _lib.lbks_set_cd_kernel(mode)
+    if code < -1:
+        raise LbksError(EINVAL, last_error())
+    return code
+
+
+def lbks_cd_overlap(precision, n_sites, n_orb, h, phi, S, lam=None, stream=None):
+    import torch
+    _check(_lib.lbks_cd_overlap(precision, n_sites, n_orb, h, _ptr(phi, _psitype(precision)), _ptr(S, torch.float64),
+                                _ptr(lam, torch.float64, optional=True), _stream(stream)))
 
 
 def lbks_relax_geometry(handle, n_atoms, max_steps, fmax, step, stream=None, n_orb=MAX_ORB, allow_notconv=False,
@@ -590,6 +669,18 @@ class System:
 
     def md(self, n_steps, dt, masses, velocities, stream=None):
         return lbks_md(self.handle, n_steps, dt, masses, velocities, stream)
+
+    def cd_start(self, tau=0.0, kappa=0.0, n_pot=0, E_target=None, stream=None):
+        return lbks_cd_start(self.handle, tau, kappa, n_pot, E_target, stream)
+
+    def cd_run(self, n_blocks, masses=None, velocities=None, stream=None):
+        return lbks_cd_run(self.handle, n_blocks, self.n_atoms, masses, velocities, stream)
+
+    def cd_orbitals(self, level=1):
+        return lbks_cd_get_orbitals(self.handle, level, self.n_orb, self.grid_shape)
+
+    def cd_state(self):
+        return lbks_cd_get_state(self.handle, self.n_atoms)
 
     def relax_geometry(self, max_steps=50, fmax=1e-3, step=0.5, stream=None, allow_notconv=False, fixed=None):
         return lbks_relax_geometry(self.handle, self.n_atoms, max_steps, fmax, step, stream, self.n_orb,

@@ -171,6 +171,21 @@ def ch4_128() -> Workload:
     return Workload("CH4 128^3 h=0.2", methane(), (128, 128, 128), 0.2, n_inner=100, e_tol=1e-6)
 
 
+def ch4_cd_128() -> Workload:
+    """Methane with its C-H bonds stretched to 2.25 bohr (a breathing-mode
+    start), 128^3 grid at h = 0.2 bohr: the start of the concurrent dynamics."""
+    return Workload("CH4 (r_CH 2.25) 128^3 h=0.2", methane(2.25), (128, 128, 128), 0.2, n_inner=100, e_tol=1e-6)
+
+
+# nuclear masses in electron masses (1 u = 1822.888 m_e; H 1.008 u, He 4.0026 u, C 12.011 u, O 15.999 u)
+MASS_ME = {"H": 1.008 * 1822.888, "He": 4.0026 * 1822.888, "Li": 6.94 * 1822.888, "C": 12.011 * 1822.888,
+           "O": 15.999 * 1822.888}
+
+
+def masses(mol: Molecule) -> np.ndarray:
+    return np.array([MASS_ME[s] for s in mol.symbols])
+
+
 def ch4_small(n: int = 40, h: float = 0.4) -> Workload:
     """Reduced methane case that the oracle finishes in tens of seconds."""
     return Workload(f"CH4 {n}^3 h={h}", methane(), (n, n, n), h, n_inner=40, e_tol=1e-6)
