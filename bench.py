@@ -56,6 +56,10 @@ KERNEL_END_MARK = b"// u_(j-1)(r) = -omega sum_{k<j} Lambda_jk psi_k(r)"
 WIDE_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_wide_h2o8_fp32.json")
 WIDE_SOURCES = (os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_wide.cuh"),
                 os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_gram_tc.cu"))
+# the same step with the two-site stream-collide kernel (tuned variant index 1)
+WIDE_PAIR_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_wide_pair_h2o8_fp32.json")
+WIDE_PAIR_SOURCES = (os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_pair.cuh"),
+                     os.path.join(ROOT, "paper_1507_07666_gb300", "csrc", "lbks_gram_tc.cu"))
 
 WORKLOADS = {
     "ch4_128": W.ch4_128,
@@ -330,28 +334,37 @@ WIDE_SEGMENTS = (
 )
 
 
-def wide_sources_sha():
+WIDE_PAIR_SEGMENTS = (
+    (b"", b""),  # the whole two-site kernel header (its helpers, both two-site kernels)
+    WIDE_SEGMENTS[1],
+)
+
+
+def wide_sources_sha(variant=0):
     """sha256 over the source text of the wide relaxation step's two kernels
-    (each file's segment from its start mark to its end mark)."""
+    (each file's segment from its start mark to its end mark); variant 0:
+    one site per thread, 1: two sites per thread."""
     h = hashlib.sha256()
-    for path, (start, end) in zip(WIDE_SOURCES, WIDE_SEGMENTS):
+    sources, segments = (WIDE_SOURCES, WIDE_SEGMENTS) if variant == 0 else (WIDE_PAIR_SOURCES, WIDE_PAIR_SEGMENTS)
+    for path, (start, end) in zip(sources, segments):
         text = open(path, "rb").read()
         i = text.find(start) if start else 0
-        k = text.find(end, max(i, 0))
+        k = text.find(end, max(i, 0)) if end else len(text)
         h.update(text[i:k] if i >= 0 and k > i else text)
     return h.hexdigest()
 
 
-def recorded_wide_traffic(units):
+def recorded_wide_traffic(units, variant=0):
     """DRAM bytes of one wide relaxation step (stream-collide + overlap) over
     `units` orbital-sites, scaled from the committed ncu capture of a smaller
     grid (traffic grows in proportion to the orbital-sites), if it was taken
-    on the current sources."""
+    on the current sources of the variant's kernels."""
+    path = {0: WIDE_TRAFFIC_FILE, 1: WIDE_PAIR_TRAFFIC_FILE}.get(variant)
     try:
-        rec = json.load(open(WIDE_TRAFFIC_FILE))
-        if rec.get("sources_sha256") == wide_sources_sha():
+        rec = json.load(open(path))
+        if rec.get("sources_sha256") == wide_sources_sha(variant):
             return float(rec["dram_bytes_per_orbital_site"]) * units
-    except (OSError, KeyError, ValueError):
+    except (OSError, KeyError, ValueError, TypeError):
         pass
     return None
 
@@ -980,13 +993,17 @@ def main_lbks(args):
         # more than eight orbitals: the timed step is two kernels, stream-collide
         # and the overlap (Gram) kernel that reads the orbitals it wrote back
         bytes_per_launch = (38 * elem + (2 * psi_elem if wide else 0)) * units
-        kname = ("k_stream_collide_wide + %s (one relaxation step)" % gram_name) if wide else "k_stream_collide"
+        sc_name = {1: "k_stream_collide_pair", 3: "k_stream_collide_bulk"}.get(tuned_index, "k_stream_collide")
+        if wide:
+            sc_name = {1: "k_stream_collide_wide_pair", 3: "k_stream_collide_bulk"}.get(tuned_index,
+                                                                                        "k_stream_collide_wide")
+        kname = ("%s + %s (one relaxation step)" % (sc_name, gram_name)) if wide else sc_name
     peak, peak_kind = measured_hbm_peak()
     achieved = bytes_per_launch / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if psi_mode else
-                (recorded_wide_traffic(units) if wide and prec == lbks.FP32 else
-                 None if wide else recorded_traffic()),
+                (recorded_wide_traffic(units, tuned_index) if wide and prec == lbks.FP32 else
+                 None if wide or tuned_index != 0 else recorded_traffic()),
                 "kernel": kname,
                 "bytes_per_launch": bytes_per_launch, "ms_per_launch": ms,
                 "peak_source": f"hbm_gbs of {peak_kind}"}

@@ -712,12 +712,13 @@ TuneKey tune_key(int precision, int n_orb, double omega, int nx, int ny, int nz,
 // the shape, else one site per thread.
 int variant_for(int precision, int n_orb, double omega, int nx, int ny, int nz) {
     const int mode = g_variant_mode.load();
-    // more than kMaxOrb orbitals: the one-orbital-per-thread kernel or the bulk-copy one
-    if (mode > 0) return n_orb > kMaxOrb && mode - 1 != kRelaxBulk ? kRelaxSites : mode - 1;
+    // more than kMaxOrb orbitals: one orbital per thread at one or two sites, or the bulk-copy kernel
+    auto wide_ok = [&](int v) { return n_orb <= kMaxOrb || v == kRelaxBulk || v == kRelaxPairs ? v : kRelaxSites; };
+    if (mode > 0) return wide_ok(mode - 1);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(tune_key(precision, n_orb, omega, nx, ny, nz, 1));
     if (it == g_tuned.end()) return kRelaxSites;
-    return n_orb > kMaxOrb && it->second != kRelaxBulk ? kRelaxSites : it->second;
+    return wide_ok(it->second);
 }
 
 // Times both variants on the handle's own buffers before they hold state
@@ -733,17 +734,18 @@ int tune_relax(lbks_system* s) {
         if (s->psi_storage && ((s->variant == kPsiKernelZ && s->n_orb > kMaxOrb) ||
                                (s->variant == kPsiKernelTma && !tma_ok)))
             s->variant = kPsiKernelTiled;
-        if (!s->psi_storage && s->n_orb > kMaxOrb && s->variant != kRelaxBulk) s->variant = kRelaxSites;
+        if (!s->psi_storage && s->n_orb > kMaxOrb && s->variant != kRelaxBulk && s->variant != kRelaxPairs)
+            s->variant = kRelaxSites;
         return LBKS_OK;
     }
     // the bulk-copy kernel: omega = 1, FP32 or bfloat16 populations, N a multiple of 8
     // (the launch checks alignment too and falls back to the one-site kernel)
     const bool bulk_may = !s->psi_storage && s->prm.omega == 1.0 && s->prm.precision != LBKS_FP64 && s->N % 8 == 0;
     // more than kMaxOrb orbitals: the one-orbital-per-thread population kernel
-    // against the bulk-copy kernel; in orbital storage the tiled step with its
-    // W-field pass against the TMA step
+    // at one and at two sites per thread against the bulk-copy kernel; in
+    // orbital storage the tiled step with its W-field pass against the TMA step
     const bool wide = s->n_orb > kMaxOrb;
-    if (wide && (s->psi_storage ? !tma_ok : !bulk_may)) {
+    if (wide && (s->psi_storage ? !tma_ok : (!bulk_may && s->nx % 2 != 0))) {
         s->variant = kRelaxSites;
         return LBKS_OK;
     }
@@ -788,7 +790,7 @@ int tune_relax(lbks_system* s) {
     constexpr int kReps = 3;
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
     // variants that differ from the first kernel on this shape
-    bool tried[kRelaxVariants] = {true, !wide && (s->psi_storage || s->nx % 2 == 0),
+    bool tried[kRelaxVariants] = {true, s->psi_storage ? !wide : s->nx % 2 == 0,
                                   s->psi_storage ? tma_ok : (!wide && s->n_orb > 1),
                                   s->psi_storage ? !wide : bulk_may};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {

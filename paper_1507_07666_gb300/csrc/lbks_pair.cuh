@@ -71,6 +71,100 @@ __device__ __forceinline__ void pull_pair(const E* __restrict__ src, uint32_t ro
     }
 }
 
+// Velocities with x-component of the sign of sx (9, 5 and 5 for 0, +1, -1).
+__host__ __device__ constexpr int vx_count(int sx) {
+    int n = 0;
+    for (int p = 0; p < 19; ++p) n += (vel(p, 0) > 0 ? 1 : vel(p, 0) < 0 ? -1 : 0) == sx ? 1 : 0;
+    return n;
+}
+
+// pull_pair in two phases, so that all loads of a site pair are in flight
+// before the first shuffle waits on one: load_pair issues the aligned pair
+// load and, on the lanes at the warp's edges, the element beyond it;
+// shift_pair then forms the two arriving values.
+static_assert(vx_count(0) == 9 && vx_count(1) == 5 && vx_count(-1) == 5, "D3Q19 x-components");
+
+template <typename E, int VX>
+struct PairLoad {
+    typename Pack2<E>::type q;
+    E edge;
+};
+template <typename E, int VX>
+__device__ __forceinline__ PairLoad<E, VX> load_pair(const E* __restrict__ src, uint32_t row, bool ok, bool v0,
+                                                     bool v1, int lane) {
+    using P = Pack2<E>;
+    PairLoad<E, VX> r;
+    r.q = ok ? __ldg(reinterpret_cast<const typename P::type*>(src + row)) : P::zero();
+    r.edge = E(0);
+    if (VX > 0 && lane == 0 && ok && v0) r.edge = __ldg(src + row - 1);
+    if (VX < 0 && lane == 31 && ok && v1) r.edge = __ldg(src + row + 2);
+    return r;
+}
+template <typename E, typename T, int VX>
+__device__ __forceinline__ void shift_pair(const PairLoad<E, VX>& r, bool v0, bool v1, int lane, T& g0, T& g1) {
+    using P = Pack2<E>;
+    const T a = (T)P::lo(r.q), b = (T)P::hi(r.q);
+    if (VX == 0) {
+        g0 = a;
+        g1 = b;
+    } else if (VX > 0) {
+        T left = __shfl_up_sync(0xffffffffu, b, 1);
+        if (lane == 0) left = to_compute<T>(r.edge);
+        g0 = v0 ? left : T(0);
+        g1 = a;
+    } else {
+        T right = __shfl_down_sync(0xffffffffu, a, 1);
+        if (lane == 31) right = to_compute<T>(r.edge);
+        g0 = b;
+        g1 = v1 ? right : T(0);
+    }
+}
+
+// Sums of the populations of array base f (element E, one array of N per
+// velocity; stride N between velocities, or 0 for the W field, whose single
+// array is pulled along every velocity with weight xi_p) arriving at the two
+// sites of the pair, every load issued before the first shuffle.  W
+// (with the W field): adds xi_p w_p; KEEP: also stores each velocity's pair in
+// g0/g1 (for the (1 - omega) term).
+template <typename E, typename T, bool KEEP, int NG>
+__device__ __forceinline__ void gather_pair(const E* __restrict__ f, size_t stride, const T (&wt)[3], bool weighted,
+                                            const Grid& g, const Site& t, uint32_t s0, bool live, bool x0l, bool x1r,
+                                            int lane, T& ps0, T& ps1, T (&g0)[NG], T (&g1)[NG]) {
+    const int nxy = g.nx * g.ny;
+    PairLoad<E, 0> l0[vx_count(0)];
+    PairLoad<E, 1> lp[vx_count(1)];
+    PairLoad<E, -1> lm[vx_count(-1)];
+    int a = 0, b = 0, c = 0;
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        const int vy = vel(p, 1), vz = vel(p, 2);
+        const bool ok = live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
+        const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
+        const E* src = f + (size_t)p * stride;
+        if (vel(p, 0) == 0) l0[a++] = load_pair<E, 0>(src, row, ok, true, true, lane);
+        else if (vel(p, 0) > 0) lp[b++] = load_pair<E, 1>(src, row, ok, x0l, true, lane);
+        else lm[c++] = load_pair<E, -1>(src, row, ok, true, x1r, lane);
+    }
+    a = b = c = 0;
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        T a0, a1;
+        if (vel(p, 0) == 0) shift_pair<E, T, 0>(l0[a++], true, true, lane, a0, a1);
+        else if (vel(p, 0) > 0) shift_pair<E, T, 1>(lp[b++], x0l, true, lane, a0, a1);
+        else shift_pair<E, T, -1>(lm[c++], true, x1r, lane, a0, a1);
+        if (weighted) {
+            a0 *= wt[vclass(p)];
+            a1 *= wt[vclass(p)];
+        }
+        ps0 += a0;
+        ps1 += a1;
+        if constexpr (KEEP) {
+            g0[p] += a0;
+            g1[p] += a1;
+        }
+    }
+}
+
 // Resident 256-thread blocks per SM the register allocator must allow: two
 // sites per thread hold twice the populations of the one-site kernel, so two
 // blocks (1024 sites per SM in flight, as the one-site kernel's four).
@@ -126,38 +220,16 @@ __global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>())
             const TS* fj = fin + (y * NO + j) * 19 * N;
             const T* uj = (j > 0 && uin != nullptr) ? uin + (y * (NO > 1 ? NO - 1 : 1) + j - 1) * N : nullptr;
             TS* oj = fout + (y * NO + j) * 19 * N;
-            T g0[19], g1[19];
+            constexpr int NG = OM1 ? 1 : 19;  // omega = 1: only the sums enter the collision
+            T g0[NG], g1[NG];
 #pragma unroll
-            for (int p = 0; p < 19; ++p) {
-                const int vy = vel(p, 1), vz = vel(p, 2);
-                const bool rowok = live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
-                const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
-                const TS* src = fj + (size_t)p * N;
-                if (vel(p, 0) == 0) pull_pair<TS, T, 0>(src, row, rowok, true, true, lane, g0[p], g1[p]);
-                else if (vel(p, 0) > 0) pull_pair<TS, T, 1>(src, row, rowok, x0_has_left, true, lane, g0[p], g1[p]);
-                else pull_pair<TS, T, -1>(src, row, rowok, true, x1_has_right, lane, g0[p], g1[p]);
-            }
-            if (uj) {  // warp-uniform
-#pragma unroll
-                for (int p = 0; p < 19; ++p) {
-                    const int vy = vel(p, 1), vz = vel(p, 2);
-                    const bool rowok =
-                        live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
-                    const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
-                    T w0, w1;
-                    if (vel(p, 0) == 0) pull_pair<T, T, 0>(uj, row, rowok, true, true, lane, w0, w1);
-                    else if (vel(p, 0) > 0) pull_pair<T, T, 1>(uj, row, rowok, x0_has_left, true, lane, w0, w1);
-                    else pull_pair<T, T, -1>(uj, row, rowok, true, x1_has_right, lane, w0, w1);
-                    g0[p] += xi[vclass(p)] * w0;
-                    g1[p] += xi[vclass(p)] * w1;
-                }
-            }
+            for (int p = 0; p < NG; ++p) g0[p] = g1[p] = T(0);
             T ps0 = T(0), ps1 = T(0);
-#pragma unroll
-            for (int p = 0; p < 19; ++p) {
-                ps0 += g0[p];
-                ps1 += g1[p];
-            }
+            gather_pair<TS, T, !OM1, NG>(fj, N, xi, false, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0, ps1,
+                                         g0, g1);
+            if (uj)  // warp-uniform: the W field, weight xi_p
+                gather_pair<T, T, !OM1, NG>(uj, 0, xi, true, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0,
+                                            ps1, g0, g1);
             ps0 *= sig[j];
             ps1 *= sig[j];
             const T A0 = om * ps0, B0 = dt * vr0 * ps0, A1 = om * ps1, B1 = dt * vr1 * ps1;
@@ -167,7 +239,11 @@ __global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>())
                 for (int p = 0; p < 19; ++p) {
                     const int k = vclass(p);
                     const T e0 = xi[k] * A0 - chi[k] * B0, e1 = xi[k] * A1 - chi[k] * B1;
-                    const T o0 = OM1 ? e0 : c1 * g0[p] + e0, o1 = OM1 ? e1 : c1 * g1[p] + e1;
+                    T o0 = e0, o1 = e1;
+                    if constexpr (!OM1) {
+                        o0 += c1 * g0[p];
+                        o1 += c1 * g1[p];
+                    }
                     __stcs(reinterpret_cast<typename PS::type*>(oj + (size_t)p * N + s0), PS::make(o0, o1));
                 }
                 *reinterpret_cast<typename PT::type*>(psio + (y * NO + j) * N + s0) = PT::make(ps0, ps1);
@@ -189,6 +265,69 @@ __global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>())
     __shared__ double tot[NP];
     if (grid_total<NP>(partial, sc.counter + y, tot) && threadIdx.x == 0)
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
+}
+
+// More than kMaxOrb orbitals: the same two-site update with one orbital per
+// thread (blockIdx.y = system * NO + orbital), the psi epilogue only (the
+// overlap runs as its own kernel, as after k_stream_collide_wide).  Every
+// population of both sites arrives in one two-element load; the stores are
+// two-element streaming stores.
+template <typename TS, typename T, bool OM1>
+__global__ void __launch_bounds__(kThreads, OM1 ? 4 : 3) k_stream_collide_wide_pair(Grid g, Coef c, RelaxIO io, int NO) {
+    using PS = Pack2<TS>;
+    using PT = Pack2<T>;
+    const int y = (int)blockIdx.y / NO, j = (int)blockIdx.y - y * NO;
+    if (g.active && !g.active[y]) return;  // block-uniform
+    const uint32_t N = g.N, NH = N >> 1;
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    const bool live = i < NH;
+    const uint32_t s0 = live ? 2 * i : 0;
+    const int lane = threadIdx.x & 31;
+    const size_t oj = (size_t)y * NO + j;
+    const TS* __restrict__ fj = static_cast<const TS*>(io.f_in) + oj * 19 * N;
+    const T* __restrict__ uj =
+        (j > 0 && io.u_in != nullptr) ? static_cast<const T*>(io.u_in) + ((size_t)y * (NO - 1) + j - 1) * N : nullptr;
+    TS* __restrict__ out = static_cast<TS*>(io.f_out) + oj * 19 * N;
+    const T om = (T)c.omega, dt = (T)c.dt, om1 = (T)(1.0 - c.omega);
+    const T xi[3] = {(T)c.xi[0], (T)c.xi[1], (T)c.xi[2]};
+    const T chi[3] = {(T)c.chi[0], (T)c.chi[1], (T)c.chi[2]};
+    const Site t = decode(g, s0);
+    const bool x0_has_left = t.xm, x1_has_right = t.x + 2 < g.nx;
+    // at omega = 1 only the sums of the arriving populations enter the
+    // collision; otherwise every population is kept for the (1 - omega) term
+    constexpr int NG = OM1 ? 1 : 19;
+    T g0[NG], g1[NG];
+#pragma unroll
+    for (int p = 0; p < NG; ++p) g0[p] = g1[p] = T(0);
+    T ps0 = T(0), ps1 = T(0);
+    gather_pair<TS, T, !OM1, NG>(fj, N, xi, false, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0, ps1, g0, g1);
+    if (uj)  // block-uniform: the W field, weight xi_p
+        gather_pair<T, T, !OM1, NG>(uj, 0, xi, true, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0, ps1, g0,
+                                    g1);
+    if (!live) return;  // no shuffles below
+    T vr0, vr1;
+    {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(io.V + (size_t)y * N + s0));
+        vr0 = (T)v.x;
+        vr1 = (T)v.y;
+    }
+    const T sig = (T)io.sigma_in[oj];
+    ps0 *= sig;
+    ps1 *= sig;
+    const T A0 = om * ps0, B0 = dt * vr0 * ps0, A1 = om * ps1, B1 = dt * vr1 * ps1;
+    const T c1 = om1 * sig;
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        const int k = vclass(p);
+        const T e0 = xi[k] * A0 - chi[k] * B0, e1 = xi[k] * A1 - chi[k] * B1;
+        T o0 = e0, o1 = e1;
+        if constexpr (!OM1) {
+            o0 += c1 * g0[p];
+            o1 += c1 * g1[p];
+        }
+        __stcs(reinterpret_cast<typename PS::type*>(out + (size_t)p * N + s0), PS::make(o0, o1));
+    }
+    *reinterpret_cast<typename PT::type*>(static_cast<T*>(io.psi_out) + oj * N + s0) = PT::make(ps0, ps1);
 }
 
 }  // namespace lbks

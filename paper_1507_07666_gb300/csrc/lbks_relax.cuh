@@ -738,9 +738,15 @@ struct Ops {
         if constexpr (sizeof(T) == 4)
             if ((variant & kRelaxVariantMask) == kRelaxBulk && bulk_applies(g, c, io, sizeof(TS)))
                 return launch_relax_bulk<TS, T>(NO, g, c, io, sc, B, (variant & kRelaxExactOverlap) != 0, st);
-        auto kern = c.omega == 1.0 ? k_stream_collide_wide<TS, T, true> : k_stream_collide_wide<TS, T, false>;
         if ((size_t)NO * B > 65535) return cudaErrorInvalidConfiguration;
-        kern<<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
+        if ((variant & kRelaxVariantMask) == kRelaxPairs && pairs_apply(g, io)) {
+            auto kern =
+                c.omega == 1.0 ? k_stream_collide_wide_pair<TS, T, true> : k_stream_collide_wide_pair<TS, T, false>;
+            kern<<<dim3((g.N / 2 + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
+        } else {
+            auto kern = c.omega == 1.0 ? k_stream_collide_wide<TS, T, true> : k_stream_collide_wide<TS, T, false>;
+            kern<<<dim3((g.N + kThreads - 1) / kThreads, (unsigned)(NO * B)), kThreads, 0, st>>>(g, c, io, NO);
+        }
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

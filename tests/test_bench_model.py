@@ -71,3 +71,11 @@ def test_wide_traffic_record_matches_the_kernel_sources():
     rec = json.load(open(bench.WIDE_TRAFFIC_FILE))
     assert rec["sources_sha256"] == bench.wide_sources_sha()
     assert bench.recorded_wide_traffic(1000) == 1000 * float(rec["dram_bytes_per_orbital_site"])
+
+
+def test_wide_pair_traffic_record_matches_the_kernel_sources():
+    rec = json.load(open(bench.WIDE_PAIR_TRAFFIC_FILE))
+    assert rec["variant"] == "pairs"
+    assert rec["sources_sha256"] == bench.wide_sources_sha(1)
+    assert bench.recorded_wide_traffic(1000, 1) == 1000 * float(rec["dram_bytes_per_orbital_site"])
+    assert bench.recorded_wide_traffic(1000, 2) is None  # no record for the prefetch variant

@@ -38,6 +38,8 @@ CASES = [
     # many 256-site tiles, a partial last tile (the bulk-copy kernel's work units)
     ((64, 48, 40), 5, 1.0, 15),
     ((40, 36, 33), 40, 1.0, 16),
+    # more than eight orbitals at two sites per thread with the (1 - omega) term
+    ((22, 9, 10), 12, 0.9, 17),
 ]
 VARIANTS = [1, 2, 3, 4]  # lbks_set_relax_variant: one site, two sites, next orbital prefetched, bulk copies (omega = 1)
 TOL = {0: 1e-12, 1: 2e-5}  # precision -> max relative error
