@@ -165,6 +165,155 @@ __device__ __forceinline__ void gather_pair(const E* __restrict__ f, size_t stri
     }
 }
 
+// W consecutive elements of one array in one aligned load (W = 2, or 4 for
+// float and bfloat16), unpacked to the compute type T and packed from it.
+template <typename E, int W>
+struct VecW;
+template <>
+struct VecW<float, 2> {
+    using type = float2;
+    template <typename T>
+    __device__ static void get(float2 v, T (&a)[2]) { a[0] = (T)v.x; a[1] = (T)v.y; }
+    __device__ static float2 put(const float (&a)[2]) { return make_float2(a[0], a[1]); }
+    __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+};
+template <>
+struct VecW<float, 4> {
+    using type = float4;
+    template <typename T>
+    __device__ static void get(float4 v, T (&a)[4]) { a[0] = (T)v.x; a[1] = (T)v.y; a[2] = (T)v.z; a[3] = (T)v.w; }
+    __device__ static float4 put(const float (&a)[4]) { return make_float4(a[0], a[1], a[2], a[3]); }
+    __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct VecW<double, 2> {
+    using type = double2;
+    template <typename T>
+    __device__ static void get(double2 v, T (&a)[2]) { a[0] = (T)v.x; a[1] = (T)v.y; }
+    __device__ static double2 put(const double (&a)[2]) { return make_double2(a[0], a[1]); }
+    __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+};
+template <>
+struct VecW<__nv_bfloat16, 2> {
+    using type = __nv_bfloat162;
+    template <typename T>
+    __device__ static void get(__nv_bfloat162 v, T (&a)[2]) { a[0] = __low2float(v); a[1] = __high2float(v); }
+    __device__ static __nv_bfloat162 put(const float (&a)[2]) { return __floats2bfloat162_rn(a[0], a[1]); }
+    __device__ static __nv_bfloat162 zero() { return __floats2bfloat162_rn(0.f, 0.f); }
+};
+template <>
+struct VecW<__nv_bfloat16, 4> {  // four bfloat16 in 8 bytes
+    using type = uint2;
+    template <typename T>
+    __device__ static void get(uint2 v, T (&a)[4]) {
+        const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&v.x);
+        const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&v.y);
+        a[0] = __low2float(lo);
+        a[1] = __high2float(lo);
+        a[2] = __low2float(hi);
+        a[3] = __high2float(hi);
+    }
+    __device__ static uint2 put(const float (&a)[4]) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(a[0], a[1]), hi = __floats2bfloat162_rn(a[2], a[3]);
+        return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+    }
+    __device__ static uint2 zero() { return make_uint2(0u, 0u); }
+};
+
+// One velocity's aligned W-element load and, on the warp's edge lanes, the
+// element beyond it that an x-shift needs (see pull_pair).
+template <typename E, int W, int VX>
+struct RowLoad {
+    typename VecW<E, W>::type q;
+    E edge;
+};
+template <typename E, int W, int VX>
+__device__ __forceinline__ RowLoad<E, W, VX> load_row(const E* __restrict__ src, uint32_t row, bool ok, bool v0,
+                                                      bool vlast, int lane) {
+    using P = VecW<E, W>;
+    RowLoad<E, W, VX> r;
+    r.q = ok ? __ldg(reinterpret_cast<const typename P::type*>(src + row)) : P::zero();
+    r.edge = E(0);
+    if (VX > 0 && lane == 0 && ok && v0) r.edge = __ldg(src + row - 1);
+    if (VX < 0 && lane == 31 && ok && vlast) r.edge = __ldg(src + row + W);
+    return r;
+}
+// The W values arriving along the velocity: x-component +1 takes the element
+// left of the group from the lane to the left, -1 the element right of it
+// from the lane to the right; v0 / vlast: the first / last site has that source.
+template <typename E, typename T, int W, int VX>
+__device__ __forceinline__ void shift_row(const RowLoad<E, W, VX>& r, bool v0, bool vlast, int lane, T (&gs)[W]) {
+    T a[W];
+    VecW<E, W>::get(r.q, a);
+    if (VX == 0) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) gs[k] = a[k];
+    } else if (VX > 0) {
+        T left = __shfl_up_sync(0xffffffffu, a[W - 1], 1);
+        if (lane == 0) left = to_compute<T>(r.edge);
+        gs[0] = v0 ? left : T(0);
+#pragma unroll
+        for (int k = 1; k < W; ++k) gs[k] = a[k - 1];
+    } else {
+        T right = __shfl_down_sync(0xffffffffu, a[0], 1);
+        if (lane == 31) right = to_compute<T>(r.edge);
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) gs[k] = a[k + 1];
+        gs[W - 1] = vlast ? right : T(0);
+    }
+}
+
+// Sums of the populations arriving at the W sites of a group: f holds one
+// array of N per velocity (stride N), or, for the W field, one array pulled
+// along every velocity (stride 0) with weight xi_p (weighted).  Every load is
+// issued before the first shuffle.  KEEP: also adds each velocity's values to
+// gk[p][k] (for the (1 - omega) term).
+template <typename E, typename T, int W, bool KEEP, int NG>
+__device__ __forceinline__ void gather_row(const E* __restrict__ f, size_t stride, const T (&wt)[3], bool weighted,
+                                           const Grid& g, const Site& t, uint32_t s0, bool live, bool v0, bool vlast,
+                                           int lane, T (&ps)[W], T (&gk)[NG][W]) {
+    const int nxy = g.nx * g.ny;
+    RowLoad<E, W, 0> l0[vx_count(0)];
+    RowLoad<E, W, 1> lp[vx_count(1)];
+    RowLoad<E, W, -1> lm[vx_count(-1)];
+    int a = 0, b = 0, c = 0;
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        const int vy = vel(p, 1), vz = vel(p, 2);
+        const bool ok = live && (vy == 0 || (vy > 0 ? t.ym : t.yp)) && (vz == 0 || (vz > 0 ? t.zm : t.zp));
+        const uint32_t row = (uint32_t)((int)s0 - vy * g.nx - vz * nxy);
+        const E* src = f + (size_t)p * stride;
+        if (vel(p, 0) == 0) l0[a++] = load_row<E, W, 0>(src, row, ok, true, true, lane);
+        else if (vel(p, 0) > 0) lp[b++] = load_row<E, W, 1>(src, row, ok, v0, true, lane);
+        else lm[c++] = load_row<E, W, -1>(src, row, ok, true, vlast, lane);
+    }
+    a = b = c = 0;
+#pragma unroll
+    for (int p = 0; p < 19; ++p) {
+        T v[W];
+        if (vel(p, 0) == 0) shift_row<E, T, W, 0>(l0[a++], true, true, lane, v);
+        else if (vel(p, 0) > 0) shift_row<E, T, W, 1>(lp[b++], v0, true, lane, v);
+        else shift_row<E, T, W, -1>(lm[c++], true, vlast, lane, v);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const T x = weighted ? wt[vclass(p)] * v[k] : v[k];
+            ps[k] += x;
+            if constexpr (KEEP) gk[p][k] += x;
+        }
+    }
+}
+
+// Sites per thread of the row kernel: four for bfloat16 populations (8-byte
+// loads) where the rows take whole groups of four, else two (a tuning knob
+// for float populations, set by measurement).
+#ifndef LBKS_ROW_WIDTH_F32
+#define LBKS_ROW_WIDTH_F32 2
+#endif
+template <typename TS>
+constexpr int row_width_max() {
+    return sizeof(TS) == 2 ? 4 : sizeof(TS) == 4 ? LBKS_ROW_WIDTH_F32 : 2;
+}
+
 // Resident 256-thread blocks per SM the register allocator must allow: two
 // sites per thread hold twice the populations of the one-site kernel, so two
 // blocks (1024 sites per SM in flight, as the one-site kernel's four).
@@ -173,21 +322,21 @@ constexpr int pair_min_blocks() {
     return 2;
 }
 
-template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
+// Stream-collide of W x-neighbouring sites per thread (the update of
+// k_stream_collide): every population of the group in one aligned load.
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED, int W>
 __global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>()))
     k_stream_collide_pair(Grid g, Coef c, RelaxIO io, Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
-    using PS = Pack2<TS>;
-    using PT = Pack2<T>;
+    using PS = VecW<TS, W>;
     if (BATCHED && inactive(g)) return;
-    const uint32_t N = g.N, NH = N >> 1;
+    const uint32_t N = g.N, NG_ = N / W;
     const size_t y = BATCHED ? sys_id() : 0;
     const TS* __restrict__ fin = static_cast<const TS*>(io.f_in);
     const T* __restrict__ uin = static_cast<const T*>(io.u_in);
     TS* __restrict__ fout = static_cast<TS*>(io.f_out);
     T* __restrict__ psio = static_cast<T*>(io.psi_out);
     const int lane = threadIdx.x & 31;
-    const int nxy = g.nx * g.ny;
 
     T sig[NO];
 #pragma unroll
@@ -201,60 +350,76 @@ __global__ void __launch_bounds__(kThreads, (pair_min_blocks<TS, NO, BATCHED>())
     for (int k = 0; k < NP; ++k) acc[k] = T(0);
 
     // block-uniform trip count: every lane of a warp takes part in the shuffles
-    for (uint32_t i0 = blockIdx.x * kThreads; i0 < NH; i0 += gridDim.x * kThreads) {
+    for (uint32_t i0 = blockIdx.x * kThreads; i0 < NG_; i0 += gridDim.x * kThreads) {
         const uint32_t i = i0 + threadIdx.x;
-        const bool live = i < NH;
-        const uint32_t s0 = live ? 2 * i : 0;
+        const bool live = i < NG_;
+        const uint32_t s0 = live ? W * i : 0;
         const Site t = decode(g, s0);
-        const bool x0_has_left = t.xm;                        // site 0 pulls from x - 1
-        const bool x1_has_right = t.x + 2 < g.nx;             // site 1 pulls from x + 1
-        T vr0 = T(0), vr1 = T(0);
+        const bool v0 = t.xm;                  // the first site pulls from x - 1
+        const bool vlast = t.x + W < g.nx;     // the last site pulls from x + 1
+        T vr[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) vr[k] = T(0);
         if (live) {
-            const double2 v = __ldg(reinterpret_cast<const double2*>(io.V + y * N + s0));
-            vr0 = (T)v.x;
-            vr1 = (T)v.y;
+#pragma unroll
+            for (int k = 0; k < W; k += 2) {
+                const double2 v = __ldg(reinterpret_cast<const double2*>(io.V + y * N + s0 + k));
+                vr[k] = (T)v.x;
+                vr[k + 1] = (T)v.y;
+            }
         }
-        T psi0[NO], psi1[NO];
+        T pso[NO][W];
 #pragma unroll
         for (int j = 0; j < NO; ++j) {
             const TS* fj = fin + (y * NO + j) * 19 * N;
             const T* uj = (j > 0 && uin != nullptr) ? uin + (y * (NO > 1 ? NO - 1 : 1) + j - 1) * N : nullptr;
             TS* oj = fout + (y * NO + j) * 19 * N;
             constexpr int NG = OM1 ? 1 : 19;  // omega = 1: only the sums enter the collision
-            T g0[NG], g1[NG];
+            T gk[NG][W];
 #pragma unroll
-            for (int p = 0; p < NG; ++p) g0[p] = g1[p] = T(0);
-            T ps0 = T(0), ps1 = T(0);
-            gather_pair<TS, T, !OM1, NG>(fj, N, xi, false, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0, ps1,
-                                         g0, g1);
+            for (int p = 0; p < NG; ++p)
+#pragma unroll
+                for (int k = 0; k < W; ++k) gk[p][k] = T(0);
+            T ps[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) ps[k] = T(0);
+            gather_row<TS, T, W, !OM1, NG>(fj, N, xi, false, g, t, s0, live, v0, vlast, lane, ps, gk);
             if (uj)  // warp-uniform: the W field, weight xi_p
-                gather_pair<T, T, !OM1, NG>(uj, 0, xi, true, g, t, s0, live, x0_has_left, x1_has_right, lane, ps0,
-                                            ps1, g0, g1);
-            ps0 *= sig[j];
-            ps1 *= sig[j];
-            const T A0 = om * ps0, B0 = dt * vr0 * ps0, A1 = om * ps1, B1 = dt * vr1 * ps1;
+                gather_row<T, T, W, !OM1, NG>(uj, 0, xi, true, g, t, s0, live, v0, vlast, lane, ps, gk);
+            T A[W], Bv[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                ps[k] *= sig[j];
+                A[k] = om * ps[k];
+                Bv[k] = dt * vr[k] * ps[k];
+            }
             const T c1 = om1 * sig[j];
             if (live) {
 #pragma unroll
                 for (int p = 0; p < 19; ++p) {
-                    const int k = vclass(p);
-                    const T e0 = xi[k] * A0 - chi[k] * B0, e1 = xi[k] * A1 - chi[k] * B1;
-                    T o0 = e0, o1 = e1;
-                    if constexpr (!OM1) {
-                        o0 += c1 * g0[p];
-                        o1 += c1 * g1[p];
+                    const int q = vclass(p);
+                    T e[W];  // T is double for double populations, float for float and bfloat16 ones
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        e[k] = xi[q] * A[k] - chi[q] * Bv[k];
+                        if constexpr (!OM1) e[k] += c1 * gk[p][k];
                     }
-                    __stcs(reinterpret_cast<typename PS::type*>(oj + (size_t)p * N + s0), PS::make(o0, o1));
+                    __stcs(reinterpret_cast<typename PS::type*>(oj + (size_t)p * N + s0), PS::put(e));
                 }
-                *reinterpret_cast<typename PT::type*>(psio + (y * NO + j) * N + s0) = PT::make(ps0, ps1);
+                *reinterpret_cast<typename VecW<T, W>::type*>(psio + (y * NO + j) * N + s0) = VecW<T, W>::put(ps);
             }
-            psi0[j] = live ? ps0 : T(0);
-            psi1[j] = live ? ps1 : T(0);
+#pragma unroll
+            for (int k = 0; k < W; ++k) pso[j][k] = live ? ps[k] : T(0);
         }
 #pragma unroll
         for (int j = 0; j < NO; ++j)
 #pragma unroll
-            for (int k = 0; k <= j; ++k) acc[tri(j, k)] += psi0[j] * psi0[k] + psi1[j] * psi1[k];
+            for (int m = 0; m <= j; ++m) {
+                T sum = T(0);
+#pragma unroll
+                for (int k = 0; k < W; ++k) sum += pso[j][k] * pso[m][k];
+                acc[tri(j, m)] += sum;
+            }
     }
 
     double v[NP];

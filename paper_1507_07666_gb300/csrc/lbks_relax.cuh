@@ -577,15 +577,26 @@ cudaError_t launch_stream_collide(const Grid& g, const Coef& c, const RelaxIO& i
     count_launches(1);
     return cudaGetLastError();
 }
+template <typename TS, typename T, int NO, bool OM1, bool BATCHED, int W>
+cudaError_t launch_stream_collide_row(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                      cudaStream_t st) {
+    auto kern = k_stream_collide_pair<TS, T, NO, OM1, BATCHED, W>;
+    static const int nb = blocks_per_sm(kern);
+    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
+    kern<<<batch_grid(g.N / W, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
+    count_launches(1);
+    return cudaGetLastError();
+}
+// W sites per thread: four where the populations are bfloat16 and the rows
+// take whole groups of four (the arrays are 16-byte aligned, pairs_apply),
+// else two.
 template <typename TS, typename T, int NO, bool OM1, bool BATCHED>
 cudaError_t launch_stream_collide_pair(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                        cudaStream_t st) {
-    auto kern = k_stream_collide_pair<TS, T, NO, OM1, BATCHED>;
-    static const int nb = blocks_per_sm(kern);
-    if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
-    kern<<<batch_grid(g.N / 2, nb * num_sms(), B, sc.max_blocks), kThreads, 0, st>>>(g, c, io, sc);
-    count_launches(1);
-    return cudaGetLastError();
+    constexpr int W4 = row_width_max<TS>();
+    if (W4 == 4 && g.nx % 4 == 0)
+        return launch_stream_collide_row<TS, T, NO, OM1, BATCHED, W4>(g, c, io, sc, B, st);
+    return launch_stream_collide_row<TS, T, NO, OM1, BATCHED, 2>(g, c, io, sc, B, st);
 }
 
 // The two-site and the prefetching variants for NO <= kMaxOrb orbitals, each
