@@ -335,7 +335,10 @@ WIDE_SEGMENTS = (
 
 
 WIDE_PAIR_SEGMENTS = (
-    (b"", b""),  # the whole two-site kernel header (its helpers, both two-site kernels)
+    # in the row-kernel header: the two-site helpers (pair types, the two-phase
+    # gather) and, from its comment to the end, the wide two-site kernel
+    ((b"template <typename TS>\nstruct Pack2;", b"// W consecutive elements of one array"),
+     (b"// More than kMaxOrb orbitals: the same two-site update", b"")),
     WIDE_SEGMENTS[1],
 )
 
@@ -346,11 +349,12 @@ def wide_sources_sha(variant=0):
     one site per thread, 1: two sites per thread."""
     h = hashlib.sha256()
     sources, segments = (WIDE_SOURCES, WIDE_SEGMENTS) if variant == 0 else (WIDE_PAIR_SOURCES, WIDE_PAIR_SEGMENTS)
-    for path, (start, end) in zip(sources, segments):
+    for path, spans in zip(sources, segments):
         text = open(path, "rb").read()
-        i = text.find(start) if start else 0
-        k = text.find(end, max(i, 0)) if end else len(text)
-        h.update(text[i:k] if i >= 0 and k > i else text)
+        for start, end in (spans if isinstance(spans[0], tuple) else (spans,)):
+            i = text.find(start) if start else 0
+            k = text.find(end, max(i, 0)) if end else len(text)
+            h.update(text[i:k] if i >= 0 and k > i else text)
     return h.hexdigest()
 
 
@@ -1031,7 +1035,8 @@ def main_lbks(args):
         "solves_per_s": world * args.steps / (elapsed_ms / 1e3),
         "solve": {"E_total": last["E_total"], "eigenvalues": [float(x) for x in last["eigenvalues"]],
                   "cycles": last["cycles"], "steps": last["steps"], "converged": last["converged"],
-                  "poisson_iters": last["poisson_iters"]},
+                  "poisson_iters": last["poisson_iters"], "poisson_s": last["poisson_s"],
+                  "poisson_share": last["poisson_s"] / last["wall_s"] if last["wall_s"] > 0 else None},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline,

@@ -209,6 +209,7 @@ typedef struct lbks_result {
     double err_E, err_eig, err_rho;   /* geometric tails of the three block changes (the stop
                                          rule's estimates of the distance left); INFINITY before
                                          three blocks */
+    double poisson_s;                 /* device time of the Hartree solves (CUDA events), all cycles */
 } lbks_result;
 
 /* The self-consistent loop of the Born-Oppenheimer scenario (Sec. 3.1: nuclei

@@ -309,6 +309,8 @@ struct lbks_system {
     std::vector<lbks_energy_terms> terms;
     std::vector<double> drho;  // ||rho - rho_prev|| / ||rho|| of the last evaluation, per system
     int poisson_iters = 0;
+    double poisson_ms = 0.0;                   // device time of the Hartree solves (CUDA events)
+    cudaEvent_t pev[2] = {nullptr, nullptr};
     // concurrent dynamics (lbks_cd_start / lbks_cd_run): three complex levels
     // [j][part][N] of the compute type, rotated step by step
     void* cd_lev[3] = {nullptr, nullptr, nullptr};
@@ -333,8 +335,8 @@ constexpr int kPoissonChunk = 2;  // PCG iterations per graph launch between con
 // matrix, the density change (two sums) and spare room.
 size_t host_per_sys(int no) { return kE4Stride + emat_stride(no) + 4; }
 
-PoissonBufs poisson_bufs(double* v, size_t n, CGState* cg, double* mp) {
-    return PoissonBufs{v, v + n, v + 2 * n, v + 3 * n, v + 4 * n, v + 5 * n, cg, mp};
+PoissonBufs poisson_bufs(double* v, size_t n, CGState* cg, double* mp, const MGHierarchy& H) {
+    return PoissonBufs{v, v + n, v + 2 * n, v + 3 * n, v + 4 * n, v + 5 * n, cg, mp, H.lev[0].b, H.lev[0].x};
 }
 
 double* host_e4(lbks_system* s, int i) { return s->host + (size_t)i * host_per_sys(s->n_orb); }
@@ -349,7 +351,7 @@ CGState* host_cg(lbks_system* s) {
 
 int poisson_graph(lbks_system* s) {
     if (s->poisson_graph) return LBKS_OK;
-    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp);
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp, s->mg);
     cudaGraph_t gr = nullptr;
     cudaError_t e = cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_fail(e, "begin capture");
@@ -373,10 +375,15 @@ int poisson_graph(lbks_system* s) {
 }
 
 int hartree_solve(lbks_system* s, cudaStream_t st) {
-    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp);
+    const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp, s->mg);
     int rc = poisson_graph(s);
     if (rc != LBKS_OK) return rc;
-    cudaError_t e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, s->B, st);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        if (!s->pev[k]) e = cudaEventCreate(&s->pev[k]);
+    if (e == cudaSuccess) e = cudaEventRecord(s->pev[0], st);
+    if (e == cudaSuccess)
+        e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, s->B, st);
     if (e != cudaSuccess) return cuda_fail(e, "poisson start");
     CGState* hcg = host_cg(s);
     const int* act = host_active(s);
@@ -401,6 +408,13 @@ int hartree_solve(lbks_system* s, cudaStream_t st) {
     for (int i = 0; i < s->B; ++i)
         if (act[i]) most = std::max(most, hcg[i].iters);
     s->poisson_iters += most;
+    // the loop above ended on a synchronised readback: the events are complete
+    float ms = 0.0f;
+    e = cudaEventRecord(s->pev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->pev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]);
+    if (e != cudaSuccess) return cuda_fail(e, "poisson timing");
+    s->poisson_ms += ms;
     return LBKS_OK;
 }
 
@@ -595,6 +609,7 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
     if (rc != LBKS_OK) return rc;
     const int limit = fixed ? n : s->prm.max_cycles;
     const int start_iters = s->poisson_iters;
+    const double start_poisson_ms = s->poisson_ms;
     int cycles_polished = 0;
     for (int c = 0; c < limit; ++c) {
         rc = cycle_graph(s, s->cur);
@@ -683,6 +698,7 @@ int run_cycles(lbks_system* s, int fixed, int n, cudaStream_t st, lbks_result* o
         r.converged = converged[i];
         r.poisson_iters = s->poisson_iters - start_iters;
         r.wall_s = wall;
+        r.poisson_s = 1e-3 * (s->poisson_ms - start_poisson_ms);
         r.d_eig = dEig[i].d[0];
         r.d_rho = dRho[i].d[0];
         r.err_E = dE[i].tail();
@@ -940,6 +956,8 @@ void free_system(lbks_system* s) {
     void* cdp[] = {s->cd_small, s->cd_sc.partial, s->cd_sc.counter};
     for (void* p : cdp)
         if (p) cudaFree(p);
+    for (cudaEvent_t ev : s->pev)
+        if (ev) cudaEventDestroy(ev);
     if (s->host) cudaFreeHost(s->host);
     if (s->st) cudaStreamDestroy(s->st);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -1319,13 +1337,14 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     const int na = (int)s->Z[0].size();
     lbks_result res;
     int total_cycles = 0, total_steps = 0, total_iters = 0;
-    double total_wall = 0.0;
+    double total_wall = 0.0, total_poisson = 0.0;
     auto solve = [&](lbks_result* r) {
         const int code = lbks_scf(s, stream, r);
         total_cycles += r->cycles;
         total_steps += r->steps;
         total_iters += r->poisson_iters;
         total_wall += r->wall_s;
+        total_poisson += r->poisson_s;
         return code;
     };
     int rc = solve(&res);
@@ -1429,6 +1448,7 @@ int lbks_relax_geometry(lbks_system* s, int max_steps, double fmax, double step,
     res.steps = total_steps;
     res.poisson_iters = total_iters;
     res.wall_s = total_wall;
+    res.poisson_s = total_poisson;
     if (out) *out = res;
     if (xyz_out) std::copy(R.begin(), R.end(), xyz_out);
     if (steps_out) *steps_out = steps;
@@ -1598,8 +1618,8 @@ int lbks_hartree(int nx, int ny, int nz, double h, const double* rho, double* v,
     int rc = workspace(stream, 6 * (size_t)g.N + mg_coarse_doubles(nx, ny, nz), &w);
     if (rc != LBKS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const PoissonBufs pb = poisson_bufs(w->pvec, g.N, w->cg, w->mp);
     const MGHierarchy H = make_hierarchy(g, w->pvec + 6 * (size_t)g.N, 1);
+    const PoissonBufs pb = poisson_bufs(w->pvec, g.N, w->cg, w->mp, H);
     cudaError_t e = launch_multipoles_from_rho(g, h, rho, w->mp, w->sc, 1, st);
     if (e == cudaSuccess) e = launch_poisson_start(g, h, rho, v, rtol, pb, w->sc, 1, st);
     if (e != cudaSuccess) return cuda_fail(e, "lbks_hartree");

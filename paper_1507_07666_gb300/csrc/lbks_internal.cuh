@@ -254,9 +254,11 @@ struct CGState {  // device-resident scalars of the preconditioned CG
     int iters, done;
 };
 struct PoissonBufs {
-    double *b, *r, *p, *ap, *z, *tmp;  // fine-grid vectors
+    double *b, *r, *p, *ap, *z, *tmp;  // fine-grid vectors (tmp: spare)
     CGState* cg;
     double* mp;  // multipoles of rho (10 doubles)
+    float* r32 = nullptr;  // the residual in single precision: the preconditioner's right-hand side
+    float* x32 = nullptr;  // the preconditioner's result (the finest level's x)
 };
 constexpr int kMaxLevels = 10;
 struct MGLevel {  // single-precision arrays of the preconditioner (level 0 included)

@@ -27,8 +27,16 @@ namespace lbks {
 
 namespace {
 
-constexpr int kPre = 2;       // red-black sweeps before the coarse correction (and after)
-constexpr int kCoarse = 24;   // sweeps each way on the coarsest level
+// Tuning knobs (set by measurement): red-black sweeps before the coarse
+// correction (and after it), and the largest level the one-CTA tail takes.
+#ifndef LBKS_MG_PRE
+#define LBKS_MG_PRE 2
+#endif
+#ifndef LBKS_MG_TAIL_SITES
+#define LBKS_MG_TAIL_SITES 4096
+#endif
+constexpr int kPre = LBKS_MG_PRE;
+constexpr int kCoarse = 4;    // sweeps each way on the coarsest level (the flexible CG takes an inexact solve)
 constexpr uint32_t kCoarseSites = 4096;  // coarsest levels up to this size are solved by one CTA
 
 int grid_for(size_t n, int cap_blocks) {
@@ -65,10 +73,26 @@ __device__ __forceinline__ V stencil(const Grid& g, const V* __restrict__ v, uin
     return t;
 }
 
+// Sum of the in-grid face neighbours of site s (the site's own value is not
+// read: a red-black half-sweep may find it stale).
+__device__ __forceinline__ float nb_sum(const Grid& g, const float* __restrict__ v, uint32_t s, int x, int y, int z) {
+    const int sy = g.nx, sz = g.nx * g.ny;
+    float t = 0.0f;
+    if (x > 0) t += v[s - 1];
+    if (x < g.nx - 1) t += v[s + 1];
+    if (y > 0) t += v[s - sy];
+    if (y < g.ny - 1) t += v[s + sy];
+    if (z > 0) t += v[s - sz];
+    if (z < g.nz - 1) t += v[s + sz];
+    return t;
+}
+
 // The system's slice of the PCG vectors and scalars.
 __device__ __forceinline__ PoissonBufs at_sys(PoissonBufs pb, size_t N) {
     const size_t o = (size_t)blockIdx.y * N;
     pb.b += o; pb.r += o; pb.p += o; pb.ap += o; pb.z += o; pb.tmp += o;
+    if (pb.r32) pb.r32 += o;
+    if (pb.x32) pb.x32 += o;
     pb.cg += blockIdx.y;
     pb.mp += (size_t)blockIdx.y * kMpStride;
     return pb;
@@ -87,21 +111,43 @@ __device__ __forceinline__ double multipole_value(const double* mp, double X, do
 // ------------------------------------------------------------ multigrid kernels
 // One colour of red-black Gauss-Seidel on A_l = scale (6 - sum nb):
 // x = (b + scale * sum nb x) / (6 scale) at sites with (x+y+z) % 2 == colour.
-__global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, float scale, int colour, float* __restrict__ x,
-                                                        const float* __restrict__ b, const CGState* cg) {
+// Slot k of a launch addresses the colour's site x = 2m + ((colour + y + z) & 1)
+// of row (y, z), m = k mod hx, hx = ceil(nx / 2) slots per row (divh divides by hx).
+// The update reads only the other colour; from_zero: the level starts at x = 0,
+// so the sweep is x = b / (6 scale) and no neighbour is read.
+__device__ __forceinline__ bool colour_site(const Grid& g, const FastDiv& divh, uint32_t k, int colour, int& ix,
+                                            int& iy, int& iz, uint32_t& s) {
+    const uint32_t q = divh.div(k);
+    const int m = (int)(k - q * divh.d);
+    const uint32_t zz = g.divy.div(q);
+    iy = (int)(q - zz * (uint32_t)g.ny);
+    iz = (int)zz;
+    ix = 2 * m + ((colour + iy + iz) & 1);
+    if (ix >= g.nx) return false;
+    s = ((uint32_t)iz * (uint32_t)g.ny + (uint32_t)iy) * (uint32_t)g.nx + (uint32_t)ix;
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mg_smooth(Grid g, FastDiv divh, float scale, int colour, int from_zero,
+                                                        float* __restrict__ x, const float* __restrict__ b,
+                                                        const CGState* cg) {
     if (inactive(g) || cg[blockIdx.y].done) return;
     x += (size_t)blockIdx.y * g.N;
     b += (size_t)blockIdx.y * g.N;
     const float inv = 1.0f / (6.0f * scale);
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
+    const uint32_t slots = divh.d * (uint32_t)g.ny * (uint32_t)g.nz;
+    for (uint32_t k = blockIdx.x * kThreads + threadIdx.x; k < slots; k += gridDim.x * kThreads) {
         int ix, iy, iz;
-        decode3(g, s, ix, iy, iz);
-        if (((ix + iy + iz) & 1) != colour) continue;
-        const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+        uint32_t s;
+        if (!colour_site(g, divh, k, colour, ix, iy, iz, s)) continue;
+        if (from_zero) {
+            x[s] = b[s] * inv;
+            continue;
+        }
+        const float nb = nb_sum(g, x, s, ix, iy, iz);
         x[s] = (b[s] + scale * nb) * inv;
     }
 }
-
 // r = b - A_l x
 __global__ void __launch_bounds__(kThreads) k_mg_residual(Grid g, float scale, const float* __restrict__ x,
                                                           const float* __restrict__ b, float* __restrict__ r,
@@ -163,7 +209,10 @@ __device__ __forceinline__ int interp_axis(int i, int m, int* c, float* w) {
     return k;
 }
 
-// x_f += P x_c (trilinear, zero ghosts)
+
+// x_f += P x_c (trilinear, zero ghosts).  (Fusing it into the first
+// post-smoothing half-sweep, each site taking its neighbours' prolongated
+// corrections, measured slower: six interpolations per site instead of one.)
 __global__ void __launch_bounds__(kThreads) k_mg_prolong(Grid gf, Grid gc, const float* __restrict__ xc,
                                                          float* __restrict__ xf, const CGState* cg) {
     if (inactive(gf) || cg[blockIdx.y].done) return;
@@ -204,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, float scal
             int ix, iy, iz;
             decode3(g, s, ix, iy, iz);
             if (((ix + iy + iz) & 1) != colour) continue;
-            const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+            const float nb = nb_sum(g, x, s, ix, iy, iz);
             x[s] = (b[s] + scale * nb) * inv;
         }
         __syncthreads();
@@ -216,24 +265,32 @@ __global__ void __launch_bounds__(kThreads) k_mg_coarse_solve(Grid g, float scal
 // the V-cycle -- zero, pre-smoothing, residual, restriction down to the
 // coarsest solve, then prolongation and post-smoothing back up -- in one CTA
 // per system, a barrier between passes, on copies in shared memory (x, b and
-// r of every such level: at most 3 x 4 x 585 bytes, since each level has at
+// r of every such level: at most 3 x 4 x 4689 bytes, since each level has at
 // most an eighth of the sites of the one above).  The first of them takes
 // its right-hand side from global memory and returns its correction there.
 // The passes are those of the one-level kernels above, site by site in the
 // same arithmetic; red-black Gauss-Seidel updates of one colour read only the
 // other colour, so the results do not depend on how sites map to threads.
-constexpr int kTailThreads = 1024;
-// 8^3: on larger levels the passes of one CTA outlast the launches they save
-constexpr uint32_t kTailSites = 512;
+constexpr int kTailThreads = 512;
+// 16^3: the single-precision passes of one CTA over a 16^3 level and the
+// coarser ones take less than the launches they replace
+constexpr uint32_t kTailSites = LBKS_MG_TAIL_SITES;
+// shared-memory values of the tail at most: x, b, r of a level of kTailSites
+// sites and of every coarser one (each at most an eighth of the one above)
+constexpr size_t kTailValuesMax = 3 * (kTailSites + kTailSites / 7 + 8);
 
 __device__ __forceinline__ void cta_smooth(const Grid& g, float scale, int colour, float* __restrict__ x,
                                            const float* __restrict__ b) {
     const float inv = 1.0f / (6.0f * scale);
-    for (uint32_t s = threadIdx.x; s < g.N; s += blockDim.x) {
-        int ix, iy, iz;
-        decode3(g, s, ix, iy, iz);
-        if (((ix + iy + iz) & 1) != colour) continue;
-        const float nb = 6.0f * x[s] - stencil(g, x, s, ix, iy, iz, x[s]);
+    const uint32_t hx = (uint32_t)(g.nx + 1) / 2, slots = hx * (uint32_t)g.ny * (uint32_t)g.nz;
+    for (uint32_t k = threadIdx.x; k < slots; k += blockDim.x) {  // the colour's sites only
+        const uint32_t q = k / hx;
+        const uint32_t zz = g.divy.div(q);
+        const int iy = (int)(q - zz * (uint32_t)g.ny), iz = (int)zz;
+        const int ix = 2 * (int)(k - q * hx) + ((colour + iy + iz) & 1);
+        if (ix >= g.nx) continue;
+        const uint32_t s = (zz * (uint32_t)g.ny + (uint32_t)iy) * (uint32_t)g.nx + (uint32_t)ix;
+        const float nb = nb_sum(g, x, s, ix, iy, iz);
         x[s] = (b[s] + scale * nb) * inv;
     }
     __syncthreads();
@@ -361,28 +418,7 @@ __global__ void __launch_bounds__(kTailThreads) k_mg_tail(MGHierarchy H, int lc,
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mg_zero(Grid g, float* __restrict__ x, const CGState* cg) {
-    if (inactive(g) || cg[blockIdx.y].done) return;
-    const size_t n = g.N;
-    x += (size_t)blockIdx.y * n;
-    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) x[s] = 0.0f;
-}
 
-// Level 0 of the preconditioner: b = (float) r on entry, z = (double) x on exit.
-__global__ void __launch_bounds__(kThreads) k_mg_narrow(Grid g, const double* __restrict__ r, float* __restrict__ b,
-                                                        const CGState* cg) {
-    if (inactive(g) || cg[blockIdx.y].done) return;
-    const size_t n = g.N, o = (size_t)blockIdx.y * n;
-    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads)
-        b[o + s] = (float)r[o + s];
-}
-__global__ void __launch_bounds__(kThreads) k_mg_widen(Grid g, const float* __restrict__ x, double* __restrict__ z,
-                                                       const CGState* cg) {
-    if (inactive(g) || cg[blockIdx.y].done) return;
-    const size_t n = g.N, o = (size_t)blockIdx.y * n;
-    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads)
-        z[o + s] = (double)x[o + s];
-}
 
 // --------------------------------------------------------------------- PCG kernels
 // b = 4 pi h^2 rho + ghost values; r = b - A x; |b|^2, |r|^2.
@@ -411,6 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
         pb.b[s] = b;
         const double r = b - stencil(g, x, s, ix, iy, iz, x[s]);
         pb.r[s] = r;
+        pb.r32[s] = (float)r;
         acc[0] += b * b;
         acc[1] += r * r;
     }
@@ -428,8 +465,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
     }
 }
 
-// rz = r . z; beta = -alpha (A p_old . z) / rz_old (the flexible form; 0 on
-// the first iteration, where ap is not read)
+// z = (double) x32 (the V-cycle's result); rz = r . z; beta = -alpha
+// (A p_old . z) / rz_old (the flexible form; 0 on the first iteration, where ap
+// is not read)
 __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scratch sc) {
     if (inactive(g)) return;
     pb = at_sys(pb, g.N);
@@ -437,8 +475,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scr
     const bool first = pb.cg->iters == 0;
     double acc[2] = {0.0, 0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
-        acc[0] += pb.r[s] * pb.z[s];
-        if (!first) acc[1] += pb.ap[s] * pb.z[s];
+        const double z = (double)pb.x32[s];  // the preconditioner's single-precision result, widened
+        pb.z[s] = z;
+        acc[0] += pb.r[s] * z;
+        if (!first) acc[1] += pb.ap[s] * z;
     }
     double* partial = sys_partial(sc);
     block_sum_store<2>(acc, partial + (size_t)blockIdx.x * 2);
@@ -451,7 +491,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_rz(Grid g, PoissonBufs pb, Scr
 }
 
 // p = z + beta p; p = z on the first iteration of a solve (p is not read
-// then: it holds whatever the memory held, and 0 * NaN is NaN)
+// then: it holds whatever the memory held, and 0 * NaN is NaN).  (Forming p
+// inside the A p kernel at the site and its six neighbours costs seven times
+// the FP64 arithmetic, which GB300 issues at a small fraction of its FP32
+// rate: measured slower than this separate pass.)
 __global__ void __launch_bounds__(kThreads) k_pcg_dir(Grid g, PoissonBufs pb) {
     if (inactive(g)) return;
     pb = at_sys(pb, g.N);
@@ -487,7 +530,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scr
     }
 }
 
-// x += alpha p; r -= alpha ap; convergence test on |r| / |b|
+// x += alpha p; r -= alpha ap (and its single-precision copy); convergence
+// test on |r| / |b|
 __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
                                                          Scratch sc) {
     if (inactive(g)) return;
@@ -495,11 +539,13 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
     if (pb.cg->done) return;
     x += (size_t)blockIdx.y * g.N;
     const double alpha = pb.cg->alpha;
+    const double* __restrict__ p = pb.p;
     double acc[1] = {0.0};
     for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < g.N; s += gridDim.x * kThreads) {
-        x[s] += alpha * pb.p[s];
+        x[s] += alpha * p[s];
         const double r = pb.r[s] - alpha * pb.ap[s];
         pb.r[s] = r;
+        pb.r32[s] = (float)r;  // the next V-cycle's right-hand side
         acc[0] += r * r;
     }
     double* partial = sys_partial(sc);
@@ -514,18 +560,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
     }
 }
 
-cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* tmp0, const CGState* cg, int ge,
-                   int Bs, cudaStream_t st, uint64_t* nl) {
-    // every level on its own single-precision arrays; level 0's b is r narrowed,
-    // its x widened into z at the end
-    (void)tmp0;
+// One V-cycle on every system's level arrays: the finest level's b is the
+// single-precision residual (written by the CG kernels) and its x the result.
+cudaError_t vcycle(const MGHierarchy& H, const CGState* cg, int ge, int Bs, cudaStream_t st, uint64_t* nl) {
     auto X = [&](int l) { return H.lev[l].x; };
     auto B = [&](int l) -> const float* { return H.lev[l].b; };
     auto R = [&](int l) { return H.lev[l].r; };
     auto grid = [&](size_t n) { return dim3(grid_for(n, std::max(1, ge / Bs)), Bs); };
     const int L = H.nlev;
-    k_mg_narrow<<<grid(H.lev[0].g.N), kThreads, 0, st>>>(H.lev[0].g, r0, H.lev[0].b, cg);
-    ++*nl;
     // first level small enough for the one-CTA tail (levels below it run there)
     int lc = L;
     for (int l = 0; l < L; ++l)
@@ -533,12 +575,21 @@ cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* t
             lc = l;
             break;
         }
+    auto half = [&](int l) {  // one colour's sites: ceil(nx / 2) slots per row
+        const Grid& g = H.lev[l].g;
+        const uint32_t hx = (uint32_t)(g.nx + 1) / 2;
+        return std::make_pair(FastDiv(hx), (size_t)hx * g.ny * g.nz);
+    };
     for (int l = 0; l < L; ++l) {
         const Grid& g = H.lev[l].g;
         const float sc = (float)(1 << l);
         const dim3 gl = grid(g.N);
         if (l == lc) {
-            const size_t smem = sizeof(float) * tail_values(H, lc);  // at most 3 x 4 x 585 bytes
+            const size_t smem = sizeof(float) * tail_values(H, lc);
+            static const cudaError_t attr = cudaFuncSetAttribute(
+                k_mg_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * kTailValuesMax));
+            if (attr != cudaSuccess) return attr;
+            if (smem > sizeof(float) * kTailValuesMax) return cudaErrorInvalidValue;
             k_mg_tail<<<dim3(1, Bs), kTailThreads, smem, st>>>(H, lc, X(l), B(l), cg);
             ++*nl;
             break;
@@ -548,43 +599,46 @@ cudaError_t vcycle(const MGHierarchy& H, const double* r0, double* z0, double* t
             ++*nl;
             break;
         }
-        k_mg_zero<<<gl, kThreads, 0, st>>>(g, X(l), cg);
-        ++*nl;
-        if (l == L - 1) {
-            for (int k = 0; k < kCoarse; ++k) {
-                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
-                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+        const auto hd = half(l);
+        const dim3 gh = grid(hd.second);
+        if (l == L - 1) {  // a coarsest level too large for one CTA: sweeps from zero
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 0, 1, X(l), B(l), cg);
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 1, 0, X(l), B(l), cg);
+            for (int k = 1; k < kCoarse; ++k) {
+                k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 0, 0, X(l), B(l), cg);
+                k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 1, 0, X(l), B(l), cg);
             }
             for (int k = 0; k < kCoarse; ++k) {
-                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
-                k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+                k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 1, 0, X(l), B(l), cg);
+                k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 0, 0, X(l), B(l), cg);
             }
             *nl += 4 * kCoarse;
             break;
         }
+        // pre-smoothing from x = 0: the first red half-sweep reads no neighbour
         for (int k = 0; k < kPre; ++k) {
-            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
-            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 0, k == 0 ? 1 : 0, X(l), B(l), cg);
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 1, 0, X(l), B(l), cg);
         }
         k_mg_residual<<<gl, kThreads, 0, st>>>(g, sc, X(l), B(l), R(l), cg);
         const Grid& gc = H.lev[l + 1].g;
         k_mg_restrict<<<grid(gc.N), kThreads, 0, st>>>(g, gc, R(l), H.lev[l + 1].b, cg);
-        *nl += 2 * kPre + 3;
+        *nl += 2 * kPre + 2;
     }
     for (int l = std::min(L, lc) - 1; l >= 0; --l) {
         if (l == L - 1) continue;  // coarsest level: nothing to prolong from
         const Grid& g = H.lev[l].g;
         const float sc = (float)(1 << l);
-        const dim3 gl = grid(g.N);
-        k_mg_prolong<<<gl, kThreads, 0, st>>>(g, H.lev[l + 1].g, X(l + 1), X(l), cg);
+        const auto hd = half(l);
+        const dim3 gh = grid(hd.second);
+        // correction, then post-smoothing black then red
+        k_mg_prolong<<<grid(g.N), kThreads, 0, st>>>(g, H.lev[l + 1].g, X(l + 1), X(l), cg);
         for (int k = 0; k < kPre; ++k) {
-            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 1, X(l), B(l), cg);
-            k_mg_smooth<<<gl, kThreads, 0, st>>>(g, sc, 0, X(l), B(l), cg);
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 1, 0, X(l), B(l), cg);
+            k_mg_smooth<<<gh, kThreads, 0, st>>>(g, hd.first, sc, 0, 0, X(l), B(l), cg);
         }
         *nl += 1 + 2 * kPre;
     }
-    k_mg_widen<<<grid(H.lev[0].g.N), kThreads, 0, st>>>(H.lev[0].g, H.lev[0].x, z0, cg);
-    ++*nl;
     return cudaGetLastError();
 }
 
@@ -655,7 +709,7 @@ cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int it
     const dim3 gel(grid_for(g.N, std::max(1, ge / B)), B);
     uint64_t nl = 0;
     for (int i = 0; i < iters; ++i) {
-        cudaError_t e = vcycle(H, pb.r, pb.z, pb.tmp, pb.cg, ge, B, st, &nl);
+        cudaError_t e = vcycle(H, pb.cg, ge, B, st, &nl);
         if (e != cudaSuccess) return e;
         k_pcg_rz<<<gr, kThreads, 0, st>>>(g, pb, sc);
         k_pcg_dir<<<gel, kThreads, 0, st>>>(g, pb);

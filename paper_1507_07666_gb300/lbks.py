@@ -46,7 +46,7 @@ class lbks_result(ctypes.Structure):
                 ("cycles", ctypes.c_int), ("steps", ctypes.c_int), ("converged", ctypes.c_int),
                 ("poisson_iters", ctypes.c_int), ("wall_s", ctypes.c_double), ("d_eig", ctypes.c_double),
                 ("d_rho", ctypes.c_double), ("err_E", ctypes.c_double), ("err_eig", ctypes.c_double),
-                ("err_rho", ctypes.c_double)]
+                ("err_rho", ctypes.c_double), ("poisson_s", ctypes.c_double)]
 
 
 class lbks_energy_terms(ctypes.Structure):
@@ -240,7 +240,8 @@ def _result_dict(r: lbks_result, n_orb: int) -> dict:
     return {"E_total": r.E_total, "dE": r.dE, "eigenvalues": np.array(r.eigenvalues[:n_orb]),
             "n_electrons": r.n_electrons, "cycles": r.cycles, "steps": r.steps,
             "converged": bool(r.converged), "poisson_iters": r.poisson_iters, "wall_s": r.wall_s,
-            "d_eig": r.d_eig, "d_rho": r.d_rho, "err_E": r.err_E, "err_eig": r.err_eig, "err_rho": r.err_rho}
+            "d_eig": r.d_eig, "d_rho": r.d_rho, "err_E": r.err_E, "err_eig": r.err_eig, "err_rho": r.err_rho,
+            "poisson_s": r.poisson_s}
 
 
 def lbks_scf(handle, stream=None, n_orb=MAX_ORB, allow_notconv=False) -> dict:
