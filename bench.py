@@ -107,6 +107,9 @@ def parse_args():
     ap.add_argument("--storage", choices=["populations", "psi"], default="populations",
                     help="what a relaxation step keeps: the 19 populations per orbital-site (any omega), or, at "
                          "omega = 1, the orbital alone (the same step as a 19-point stencil)")
+    ap.add_argument("--poisson-adapt", type=float, default=0.0,
+                    help="lbks_params.poisson_adapt: each cycle's Hartree solve stops at max(rtol, min(1e-4, "
+                         "value x the previous density change)); 0: the fixed tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel-only", action="store_true",
@@ -923,7 +926,8 @@ def main_lbks(args):
     psi_mode = args.storage == "psi"
     sysm = lbks.System(w.n, w.h, w.n_orb, precision=prec, n_inner=w.n_inner, e_tol=w.e_tol, theta=w.theta,
                        omega=w.omega, mix=w.mix, max_cycles=w.max_cycles,
-                       storage=lbks.STORE_PSI if psi_mode else lbks.STORE_POPULATIONS)
+                       storage=lbks.STORE_PSI if psi_mode else lbks.STORE_POPULATIONS,
+                       poisson_adapt=args.poisson_adapt)
     xyz, Z = w.molecule.xyz, w.molecule.Z
     N = w.sites
     stream = torch.cuda.Stream()
@@ -1028,6 +1032,7 @@ def main_lbks(args):
                                  lbks.BF16: "BF16 populations, FP32 collide, FP32 polish below |dE| 1e-4, "
                                             "FP64 overlaps/energies/Poisson"}[prec],
                    "n_inner": w.n_inner, "e_tol": w.e_tol, "storage": args.storage,
+                   "poisson_adapt": args.poisson_adapt,
                    "l2": ("orbital storage: a solve's working set (psi pair, W field, potentials, Poisson vectors) "
                           "exceeds L2; the kernel timing writes 256 MB before every timed launch") if psi_mode else
                          "inputs larger than L2 (populations %.2f GB)" % (2 * 19 * elem * units / 1e9),

@@ -114,6 +114,11 @@ typedef struct lbks_params {
     double rho_tol;      /* stop rule on the density (relative L2 change); <= 0: not watched [2e-6] */
     uint64_t seed;       /* start orbitals: 0 the fixed offsets of lbks_set_geometry, else seeded offsets
                             (SplitMix64) [0]; the converged state does not depend on it */
+    double poisson_adapt;/* > 0: each cycle's Hartree solve stops at the relative residual
+                            max(poisson_rtol, min(1e-4, poisson_adapt * D)), D the relative density
+                            change of the previous evaluation (an inexact solve while the density
+                            still moves; at the stop rule's D <= rho_tol it is poisson_adapt * rho_tol
+                            or tighter); 0: poisson_rtol always [0] */
 } lbks_params;
 
 /* Stop rule of lbks_scf and lbks_batch_scf (the paper stops once the orbital

@@ -191,6 +191,7 @@ bool valid_params(const lbks_params* p) {
     return p && p->omega > 0.0 && p->omega < 2.0 && p->theta > 0.0 && p->n_inner >= 2 && p->mix > 0.0 &&
            p->mix <= 1.0 && p->e_tol > 0.0 && p->max_cycles >= 1 && ops_for(p->precision) &&
            p->poisson_rtol > 0.0 && p->poisson_max_iter >= 1 && !std::isnan(p->eig_tol) &&
+           p->poisson_adapt >= 0.0 && std::isfinite(p->poisson_adapt) &&
            !std::isnan(p->rho_tol) &&
            (p->storage == LBKS_STORE_POPULATIONS ||
             (p->storage == LBKS_STORE_PSI && p->omega == 1.0 && p->precision != LBKS_BF16));
@@ -374,7 +375,19 @@ int poisson_graph(lbks_system* s) {
     return LBKS_OK;
 }
 
-int hartree_solve(lbks_system* s, cudaStream_t st) {
+// The cycle's Hartree tolerance: poisson_rtol, or with poisson_adapt > 0 the
+// inexact-solve bound of include/lbks.h from the previous evaluation's density
+// change (the largest over the running systems); `adapt` false: poisson_rtol.
+double hartree_rtol(const lbks_system* s, bool adapt) {
+    const double base = s->prm.poisson_rtol;
+    if (!adapt || s->prm.poisson_adapt <= 0.0) return base;
+    double d = 0.0;
+    for (int i = 0; i < s->B; ++i)
+        if (host_active(const_cast<lbks_system*>(s))[i]) d = std::max(d, s->drho[i]);
+    return std::max(base, std::min(1e-4, s->prm.poisson_adapt * d));
+}
+
+int hartree_solve(lbks_system* s, cudaStream_t st, bool adapt = false) {
     const PoissonBufs pb = poisson_bufs(s->pvec, s->N * s->B, s->cg, s->mp, s->mg);
     int rc = poisson_graph(s);
     if (rc != LBKS_OK) return rc;
@@ -383,7 +396,7 @@ int hartree_solve(lbks_system* s, cudaStream_t st) {
         if (!s->pev[k]) e = cudaEventCreate(&s->pev[k]);
     if (e == cudaSuccess) e = cudaEventRecord(s->pev[0], st);
     if (e == cudaSuccess)
-        e = launch_poisson_start(s->g, s->h, s->rho, s->vh, s->prm.poisson_rtol, pb, s->sc, s->B, st);
+        e = launch_poisson_start(s->g, s->h, s->rho, s->vh, hartree_rtol(s, adapt), pb, s->sc, s->B, st);
     if (e != cudaSuccess) return cuda_fail(e, "poisson start");
     CGState* hcg = host_cg(s);
     const int* act = host_active(s);
@@ -424,7 +437,7 @@ int evaluate(lbks_system* s, cudaStream_t st, int first) {
     const int B = s->B;
     cudaError_t e = s->ops->density(s->n_orb, s->g, s->h, s->psi, s->rho, s->rho_ref, s->mp, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "density");
-    int rc = hartree_solve(s, st);
+    int rc = hartree_solve(s, st, true);
     if (rc != LBKS_OK) return rc;
     e = launch_potential(s->g, s->h, s->rho, s->vext, s->vh, s->vout, s->vin, first, s->prm.mix, s->e4, s->sc, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "potential");
@@ -1121,6 +1134,7 @@ void lbks_params_default(lbks_params* p) {
     p->precision = LBKS_FP64;
     p->softening = 0.0;
     p->poisson_rtol = 1e-11;
+    p->poisson_adapt = 0.0;
     p->poisson_max_iter = 20000;
     p->polish_tol = 1e-4;
     p->storage = LBKS_STORE_POPULATIONS;

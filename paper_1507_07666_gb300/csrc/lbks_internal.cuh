@@ -251,6 +251,7 @@ cudaError_t launch_cd_overlap(int NO, const Grid&, const void* phi, double h, do
 
 struct CGState {  // device-resident scalars of the preconditioned CG
     double bb, rr, rz, pap, alpha, beta, relres;
+    double rtol;  // the solve's relative residual target (set by the start kernel)
     int iters, done;
 };
 struct PoissonBufs {
@@ -278,7 +279,8 @@ MGHierarchy make_hierarchy(const Grid& fine, double* coarse, int B);
 // Builds the right-hand side (4 pi h^2 rho + ghost values) and r = b - A x.
 cudaError_t launch_poisson_start(const Grid&, double h, const double* rho, double* x, double rtol,
                                  const PoissonBufs&, const Scratch&, int B, cudaStream_t);
-// `iters` preconditioned CG iterations (no-ops once converged).
+// `iters` preconditioned CG iterations (no-ops once converged), to the
+// tolerance the start kernel recorded (rtol is that of the start).
 cudaError_t launch_poisson_iterate(const Grid&, double* x, double rtol, int iters, const PoissonBufs&,
                                    const MGHierarchy&, const Scratch&, int B, cudaStream_t);
 cudaError_t launch_multipoles_from_rho(const Grid&, double h, const double* rho, double* mp,

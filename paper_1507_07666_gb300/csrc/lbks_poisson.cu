@@ -459,6 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_start(Grid g, double h, const 
         cg->bb = tot[0];
         cg->rr = tot[1];
         cg->rz = 0.0;
+        cg->rtol = rtol;
         cg->iters = 0;
         cg->relres = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
         cg->done = (tot[0] == 0.0 || sqrt(tot[1]) <= rtol * sqrt(tot[0])) ? 1 : 0;
@@ -532,8 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_ap(Grid g, PoissonBufs pb, Scr
 
 // x += alpha p; r -= alpha ap (and its single-precision copy); convergence
 // test on |r| / |b|
-__global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restrict__ x, double rtol, PoissonBufs pb,
-                                                         Scratch sc) {
+__global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restrict__ x, PoissonBufs pb, Scratch sc) {
     if (inactive(g)) return;
     pb = at_sys(pb, g.N);
     if (pb.cg->done) return;
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Grid g, double* __restr
         cg->rr = tot[0];
         cg->iters += 1;
         cg->relres = sqrt(tot[0] / cg->bb);
-        cg->done = (sqrt(tot[0]) <= rtol * sqrt(cg->bb)) ? 1 : 0;
+        cg->done = (sqrt(tot[0]) <= cg->rtol * sqrt(cg->bb)) ? 1 : 0;
     }
 }
 
@@ -702,6 +702,7 @@ cudaError_t launch_poisson_start(const Grid& g, double h, const double* rho, dou
 
 cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int iters, const PoissonBufs& pb,
                                    const MGHierarchy& H, const Scratch& sc, int B, cudaStream_t st) {
+    (void)rtol;  // the start kernel's tolerance, device-resident
     const int cap = red_cap(sc, 1, B);
     if (cap < 1) return cudaErrorInvalidValue;
     const dim3 gr(grid_for(g.N, cap), B);
@@ -714,7 +715,7 @@ cudaError_t launch_poisson_iterate(const Grid& g, double* x, double rtol, int it
         k_pcg_rz<<<gr, kThreads, 0, st>>>(g, pb, sc);
         k_pcg_dir<<<gel, kThreads, 0, st>>>(g, pb);
         k_pcg_ap<<<gr, kThreads, 0, st>>>(g, pb, sc);
-        k_pcg_update<<<gr, kThreads, 0, st>>>(g, x, rtol, pb, sc);
+        k_pcg_update<<<gr, kThreads, 0, st>>>(g, x, pb, sc);
         nl += 4;
     }
     count_launches(nl);

@@ -37,7 +37,7 @@ class lbks_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("softening", ctypes.c_double),
                 ("poisson_rtol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int),
                 ("polish_tol", ctypes.c_double), ("storage", ctypes.c_int), ("eig_tol", ctypes.c_double),
-                ("rho_tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("rho_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("poisson_adapt", ctypes.c_double)]
 
 
 class lbks_result(ctypes.Structure):
