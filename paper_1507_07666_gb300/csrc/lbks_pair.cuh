@@ -317,9 +317,12 @@ constexpr int row_width_max() {
 // Resident 256-thread blocks per SM the register allocator must allow: two
 // sites per thread hold twice the populations of the one-site kernel, so two
 // blocks (1024 sites per SM in flight, as the one-site kernel's four).
+#ifndef LBKS_PAIR_MIN_BLOCKS
+#define LBKS_PAIR_MIN_BLOCKS 2
+#endif
 template <typename TS, int NO, bool BATCHED>
 constexpr int pair_min_blocks() {
-    return 2;
+    return LBKS_PAIR_MIN_BLOCKS;
 }
 
 // Stream-collide of W x-neighbouring sites per thread (the update of

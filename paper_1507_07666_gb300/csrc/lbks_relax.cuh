@@ -789,8 +789,22 @@ struct Ops {
         if (NO <= 48) return wfield_wide_m<48>(NO, g, omega, psi, lam, u, B, st);
         return wfield_wide_m<kMaxOrbWide>(NO, g, omega, psi, lam, u, B, st);
     }
+    template <int MAXO>
+    static cudaError_t orth_wide_m(int NO, const Grid& g, const double* Linv, void* f, void* psi, int B,
+                                   cudaStream_t st) {
+        auto kern = k_orth_apply_wide_reg<TS, T, MAXO>;
+        static const int nb = blocks_per_sm(kern);
+        kern<<<batch_grid(g.N, nb * num_sms(), B), kThreads, 0, st>>>(g, Linv, (TS*)f, (T*)psi, NO);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     static cudaError_t orth_wide(int NO, const Grid& g, const double* Linv, void* f, void* psi, int B,
                                  cudaStream_t st) {
+        if (NO <= 16) return orth_wide_m<16>(NO, g, Linv, f, psi, B, st);
+        if (NO <= 24) return orth_wide_m<24>(NO, g, Linv, f, psi, B, st);
+        if (NO <= 32) return orth_wide_m<32>(NO, g, Linv, f, psi, B, st);
+        if (NO <= 40) return orth_wide_m<40>(NO, g, Linv, f, psi, B, st);
+        if (NO <= 48) return orth_wide_m<48>(NO, g, Linv, f, psi, B, st);
         const size_t smem = ((size_t)NO * kThreads + (size_t)NO * NO) * sizeof(T);
         cudaError_t e = with_smem(k_orth_apply_wide<TS, T>, smem);
         if (e != cudaSuccess) return e;

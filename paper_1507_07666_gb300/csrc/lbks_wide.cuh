@@ -224,6 +224,61 @@ __global__ void __launch_bounds__(kThreads, 2) k_w_field_wide2(const Grid g, dou
 // In-place orthonormalisation f_jp <- sum_k Linv_jk f_kp, psi likewise:
 // per site, one velocity at a time, the NO values staged per thread in
 // shared memory.  Dynamic shared memory: (NO * kThreads + NO * NO) * sizeof(T).
+// The same with each site's NO values of one population in registers (MAXO
+// a compile-time bound on NO) and L^-1 in shared memory read 16 bytes at a
+// time by every thread of the warp at once (broadcast): the triangular
+// product costs one shared-memory load per four (FP32) or two (FP64)
+// multiply-adds instead of two loads per multiply-add.  Rows are formed from
+// the top, so row j reads the original values k <= j, not yet overwritten.
+template <typename TS, typename T, int MAXO>
+__global__ void __launch_bounds__(kThreads) k_orth_apply_wide_reg(const Grid g, const double* __restrict__ Linv,
+                                                                  TS* __restrict__ f, T* __restrict__ psi, int NO) {
+    constexpr int V = 16 / sizeof(T);  // coefficients per shared-memory load
+    static_assert(MAXO % V == 0, "row pitch must keep 16-byte alignment");
+    if (inactive(g)) return;
+    __shared__ __align__(16) T L[MAXO * MAXO];
+    const size_t n = g.N, y = sys_id();
+    Linv += y * NO * NO;
+    if (f) f += y * NO * 19 * n;
+    if (psi) psi += y * NO * n;
+    for (int i = threadIdx.x; i < MAXO * MAXO; i += kThreads) {
+        const int j = i / MAXO, k = i % MAXO;
+        L[i] = (j < NO && k <= j) ? (T)Linv[j * NO + k] : T(0);
+    }
+    __syncthreads();
+    for (size_t s = blockIdx.x * (size_t)kThreads + threadIdx.x; s < n; s += (size_t)gridDim.x * kThreads) {
+        for (int p = (f ? 0 : 19); p <= 19; ++p) {
+            if (p == 19 && !psi) break;
+            T x[MAXO];
+#pragma unroll
+            for (int k = 0; k < MAXO; ++k)
+                x[k] = k >= NO ? T(0)
+                       : (p < 19) ? to_compute<T>(f[((size_t)k * 19 + p) * n + s])
+                                  : psi[(size_t)k * n + s];
+#pragma unroll
+            for (int j = MAXO - 1; j >= 0; --j) {
+                if (j >= NO) continue;
+                T w = T(0);
+#pragma unroll
+                for (int kb = 0; kb <= j; kb += V) {
+                    T l[V];
+                    lds16(&L[j * MAXO + kb], l);
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (kb + e <= j) w += l[e] * x[kb + e];
+                }
+                x[j] = w;
+            }
+#pragma unroll
+            for (int j = 0; j < MAXO; ++j) {
+                if (j >= NO) break;
+                if (p < 19) f[((size_t)j * 19 + p) * n + s] = to_store<TS>(x[j]);
+                else psi[(size_t)j * n + s] = x[j];
+            }
+        }
+    }
+}
+
 template <typename TS, typename T>
 __global__ void __launch_bounds__(kThreads) k_orth_apply_wide(const Grid g, const double* __restrict__ Linv,
                                                               TS* __restrict__ f, T* __restrict__ psi, int NO) {

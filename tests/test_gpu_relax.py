@@ -127,11 +127,13 @@ def test_bf16_storage_step_matches_oracle(n, n_orb, omega, seed, relax_variant):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("n,n_orb,seed", [((19, 13, 10), 4, 11), ((13, 11, 9), 11, 12)])
+@pytest.mark.parametrize("n,n_orb,seed", [((19, 13, 10), 4, 11), ((13, 11, 9), 11, 12), ((12, 9, 10), 40, 13),
+                                          ((9, 8, 7), 64, 14)])
 def test_orthonormalising_step_matches_oracle(prec, n, n_orb, seed):
     """Relax step, Cholesky of its overlap and L^{-1} applied to populations
     and orbitals reproduce the oracle's cycle-ending step (eight or fewer
-    orbitals: fused kernels; more: the tiled kernels)."""
+    orbitals: fused kernels; up to 48: values in registers; more: staged in
+    shared memory)."""
     torch, lbks = require_gpu()
     omega, theta, h = 1.0, 0.5, 0.25
     dt = lattice.time_step(theta, omega, h)
