@@ -280,6 +280,20 @@ int lbks_set_relax_variant(int mode);
  * handle). */
 int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
 
+/* Orbital storage, up to 8 orbitals: the tile shape of the staged stencil
+ * (the box of every orbital's psi and of Vc that a block sums from shared
+ * memory).  Shapes: 0 32 x 8 x 4 sites (the default), 1 32 x 8 x 8,
+ * 2 64 x 4 x 4, 3 32 x 8 x 2; shapes 1-3 need rows of whole 16-byte pieces
+ * and a box that fits a block's shared memory (else shape 0 runs).  The tuner times every shape on the first handle of a
+ * grid shape and keeps the fastest with the staged kernel (then compares the
+ * staged kernel with the others).  lbks_set_psi_tile(-1) restores that; 0..3
+ * forces the shape for later handles and lbks_relax_step_psi calls.  Returns
+ * the previous setting, or -2 for a bad shape (lbks_last_error says why).
+ * lbks_get_psi_tile: the handle's shape and the tuner's ms per step of each
+ * shape in ms[0..3] (may be NULL; negative: not timed). */
+int lbks_set_psi_tile(int shape);
+int lbks_get_psi_tile(const lbks_system* sys, int* shape, double* ms);
+
 /* Energy terms of the last evaluation (after lbks_set_geometry or a cycle).
  * Sec. 2 states that the ground-state energy is a functional of the density
  * (Kohn-Sham formulation) but prints no expression; the standard Kohn-Sham

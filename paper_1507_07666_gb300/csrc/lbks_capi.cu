@@ -302,6 +302,7 @@ struct lbks_system {
     cudaStream_t cap = nullptr;  // capture stream
     int variant = kRelaxSites;   // stream-collide variant (tuned per shape)
     double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0, -1.0};
+    double tune_shape_ms[kPsiShapes] = {-1.0, -1.0, -1.0, -1.0};  // orbital storage: the staged kernel per tile shape
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
     std::vector<std::vector<double>> xyz, Z;  // per system
@@ -506,7 +507,7 @@ cudaError_t enqueue_cycle_psi(lbks_system* s, cudaStream_t st, int start) {
     const int n = s->prm.n_inner, B = s->B;
     // up to kMaxOrb orbitals, and at any count with the TMA kernel, the step
     // forms the W source from Lambda itself; otherwise it pulls the W field u
-    const bool fused_w = s->n_orb <= kMaxOrb || s->variant == kPsiKernelTma;
+    const bool fused_w = s->n_orb <= kMaxOrb || (s->variant & kRelaxVariantMask) == kPsiKernelTma;
     for (int t = 0; t < n; ++t) {
         RelaxIO io{s->f[cur], (t == 0 || fused_w) ? nullptr : s->u, t == 0 ? s->vprev : s->vin, s->sigma,
                    s->f[1 - cur], s->f[1 - cur], s->S, s->lam, s->sigma, (t == 0 || !fused_w) ? nullptr : s->lam};
@@ -732,6 +733,9 @@ using TuneKey = std::tuple<int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
 std::atomic<int> g_variant_mode{0};  // 0 tuned, else 1 + the forced variant
+// Orbital storage, up to kMaxOrb orbitals: the staged kernel's tile shape,
+// -1 tuned per grid shape (step-level calls: the default shape), else forced.
+std::atomic<int> g_psi_shape{-1};
 
 TuneKey tune_key(int precision, int n_orb, double omega, int nx, int ny, int nz, int B) {
     return TuneKey(precision, n_orb, omega == 1.0 ? 1 : 0, nx, ny, nz, B);
@@ -758,6 +762,8 @@ int tune_relax(lbks_system* s) {
     // orbital storage: the TMA kernel where its tensor maps apply
     const bool tma_ok = s->psi_storage && psi_tma_applies(s->nx, s->f[0], s->vin, s->ops->psi_elem) &&
                         psi_tma_applies(s->nx, s->f[1], s->vprev, s->ops->psi_elem);
+    const int forced_shape = g_psi_shape.load();
+    const bool shaped = s->psi_storage && s->n_orb <= kMaxOrb;  // the staged kernel takes a tile shape
     if (mode > 0) {
         s->variant = mode - 1;
         if (s->psi_storage && ((s->variant == kPsiKernelZ && s->n_orb > kMaxOrb) ||
@@ -765,6 +771,7 @@ int tune_relax(lbks_system* s) {
             s->variant = kPsiKernelTiled;
         if (!s->psi_storage && s->n_orb > kMaxOrb && s->variant != kRelaxBulk && s->variant != kRelaxPairs)
             s->variant = kRelaxSites;
+        if (shaped && forced_shape > 0) s->variant |= forced_shape << kPsiShapeShift;
         return LBKS_OK;
     }
     // the bulk-copy kernel: omega = 1, FP32 or bfloat16 populations, N a multiple of 8
@@ -779,8 +786,8 @@ int tune_relax(lbks_system* s) {
         return LBKS_OK;
     }
     // orbital storage has its own kernels (0: tiled in shared memory, 1: one site per thread, 2: TMA)
-    const TuneKey key = tune_key(s->prm.precision + (s->psi_storage ? 16 : 0), s->n_orb, s->prm.omega, s->nx, s->ny,
-                                 s->nz, s->B);
+    const TuneKey key = tune_key(s->prm.precision + (s->psi_storage ? 16 : 0) + (forced_shape >= 0 ? 32 * (1 + forced_shape) : 0),
+                                 s->n_orb, s->prm.omega, s->nx, s->ny, s->nz, s->B);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -817,6 +824,30 @@ int tune_relax(lbks_system* s) {
         return relax(s->n_orb, s->g, s->c, sio, s->sc, s->B, v, st);
     };
     constexpr int kReps = 3;
+    auto timed = [&](int v, float* out) -> cudaError_t {
+        cudaError_t te = step(v);  // warm-up
+        if (te == cudaSuccess) te = cudaEventRecord(ev[0], st);
+        for (int r = 0; r < kReps && te == cudaSuccess; ++r) te = step(v);
+        if (te == cudaSuccess) te = cudaEventRecord(ev[1], st);
+        if (te == cudaSuccess) te = cudaEventSynchronize(ev[1]);
+        if (te == cudaSuccess) te = cudaEventElapsedTime(out, ev[0], ev[1]);
+        return te;
+    };
+    // orbital storage: the staged kernel's tile shape first (forced, or the fastest)
+    int shape = forced_shape >= 0 ? forced_shape : 0;
+    if (shaped && forced_shape < 0) {
+        float best = 0.f;
+        for (int k = 0; k < kPsiShapes && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = timed(kPsiKernelTiled | (k << kPsiShapeShift), &t);
+            s->tune_shape_ms[k] = t / kReps;
+            if (k == 0 || t < best) {
+                best = t;
+                shape = k;
+            }
+        }
+    }
+    const int tiled_v = shaped ? (kPsiKernelTiled | (shape << kPsiShapeShift)) : kPsiKernelTiled;
     float ms[kRelaxVariants] = {0.f, 0.f, 0.f, 0.f};
     // variants that differ from the first kernel on this shape
     bool tried[kRelaxVariants] = {true, s->psi_storage ? !wide : s->nx % 2 == 0,
@@ -824,21 +855,18 @@ int tune_relax(lbks_system* s) {
                                   s->psi_storage ? !wide : bulk_may};
     for (int v = 0; v < kRelaxVariants && e == cudaSuccess; ++v) {
         if (!tried[v]) continue;
-        e = step(v);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = step(v);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[v], ev[0], ev[1]);
+        e = timed(v == kPsiKernelTiled && s->psi_storage ? tiled_v : v, &ms[v]);
     }
     for (int k = 0; k < 3; ++k)
         if (ev[k]) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(e, "stream-collide tuning");
-    s->variant = kRelaxSites;
+    int best = kRelaxSites;
     for (int v = 0; v < kRelaxVariants; ++v) {
         s->tune_ms[v] = tried[v] ? ms[v] / kReps : -1.0;
-        if (tried[v] && ms[v] < ms[s->variant]) s->variant = v;
+        if (tried[v] && ms[v] < ms[best]) best = v;
     }
+    // the tuned shape rides along whichever kernel wins (the others ignore it)
+    s->variant = best | (shaped ? shape << kPsiShapeShift : 0);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned.emplace(key, s->variant);
     return LBKS_OK;
@@ -1110,6 +1138,22 @@ int lbks::relax_variant_for(int precision, int n_orb, double omega, int nx, int 
 
 extern "C" {
 
+int lbks_set_psi_tile(int shape) {
+    if (shape < -1 || shape >= kPsiShapes) {
+        fail(LBKS_EINVAL, "shape must be in [-1, %d]", kPsiShapes - 1);
+        return -2;
+    }
+    return g_psi_shape.exchange(shape);
+}
+
+int lbks_get_psi_tile(const lbks_system* s, int* shape, double* ms) {
+    if (!s || !shape) return fail(LBKS_EINVAL, "null argument");
+    *shape = (s->variant >> kPsiShapeShift) & 0xff;
+    if (ms)
+        for (int k = 0; k < kPsiShapes; ++k) ms[k] = s->tune_shape_ms[k];
+    return LBKS_OK;
+}
+
 int lbks_set_relax_variant(int mode) {
     if (mode < 0 || mode > kRelaxVariants) return -1;
     return g_variant_mode.exchange(mode);
@@ -1117,7 +1161,7 @@ int lbks_set_relax_variant(int mode) {
 
 int lbks_get_relax_variant(const lbks_system* s, int* variant, double* ms) {
     if (!s || !variant) return fail(LBKS_EINVAL, "null argument");
-    *variant = s->variant;
+    *variant = s->variant & kRelaxVariantMask;
     if (ms)
         for (int v = 0; v < kRelaxVariants; ++v) ms[v] = s->tune_ms[v];
     return LBKS_OK;
@@ -1543,6 +1587,8 @@ int lbks_relax_step_psi(int precision, int nx, int ny, int nz, int n_orb, double
     const bool tma_ok = psi_tma_applies(nx, psi_in, Vc, ops->psi_elem);
     int kernel = mode > 0 ? mode - 1 : (tma_ok ? kPsiKernelTma : kPsiKernelTiled);
     if ((kernel == kPsiKernelTma && !tma_ok) || (kernel == kPsiKernelZ && n_orb > kMaxOrb)) kernel = kPsiKernelTiled;
+    const int shape = g_psi_shape.load();
+    if (kernel == kPsiKernelTiled && n_orb <= kMaxOrb && shape > 0) kernel |= shape << kPsiShapeShift;
     // the W field goes through workspace scratch unless the kernel forms it
     const bool wide = n_orb > kMaxOrb && lambda_in && kernel != kPsiKernelTma;
     Workspace* w = nullptr;

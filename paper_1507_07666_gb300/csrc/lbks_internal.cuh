@@ -122,6 +122,10 @@ constexpr int kPsiKernelTiled = kRelaxSites;
 constexpr int kPsiKernelDirect = kRelaxPairs;
 constexpr int kPsiKernelTma = kRelaxPrefetch;
 constexpr int kPsiKernelZ = kRelaxBulk;  // up to kMaxOrb orbitals: marching along z, a ring of planes
+// The staged kernel (up to kMaxOrb orbitals) takes its tile shape from the
+// kernel id's bits from kPsiShapeShift on (0: the default 32 x 8 x 4).
+constexpr int kPsiShapeShift = 8;
+constexpr int kPsiShapes = 4;
 // The TMA kernel's tensor maps need rows of whole 16-byte units (nx a
 // multiple of 16 / elem, elem the bytes of an orbital value) and 16-byte
 // aligned orbitals and potential.

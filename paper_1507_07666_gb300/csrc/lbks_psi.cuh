@@ -199,6 +199,21 @@ __host__ __device__ constexpr int box_pitch() { return VEC ? kTX + 2 * vpad<T>()
 template <typename T, bool VEC>
 __host__ __device__ constexpr int box_size() { return box_pitch<T, VEC>() * kBY * kBZ; }
 
+// Tile shapes of the staged stencil up to kMaxOrb orbitals: TX x (kThreads / TX) x TZ
+// sites, each thread one (x, y) column of TZ sites; the tuner picks one per grid shape.
+template <int TX, int TZ>
+struct PsiTile {
+    static constexpr int TY = kThreads / TX, BY = TY + 2, BZ = TZ + 2;
+    template <typename T, bool VEC>
+    __host__ __device__ static constexpr int pitch() { return VEC ? TX + 2 * vpad<T>() : TX + 2; }
+    template <typename T, bool VEC>
+    __host__ __device__ static constexpr int size() { return pitch<T, VEC>() * BY * BZ; }
+};
+// The shapes (TX, TZ) the tuner tries; shape 0 is the default.
+constexpr int kPsiTileShapes = 4;
+constexpr int kPsiTileTX[kPsiTileShapes] = {32, 32, 64, 32};
+constexpr int kPsiTileTZ[kPsiTileShapes] = {4, 8, 4, 2};
+
 // 16 bytes of T from global (read-only) to shared memory.
 template <typename T>
 __device__ __forceinline__ void copy16(T* dst, const T* src) {
@@ -218,12 +233,14 @@ __device__ __forceinline__ void copy16_v(T* dst, const double* src) {
 template <typename T>
 __device__ __forceinline__ void zero16(T* dst) { *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f); }
 
-template <typename T, int NO, bool BATCHED, bool VEC>
+template <typename T, int NO, bool BATCHED, bool VEC, int TX = kTX, int TZ = kTZ>
 __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
                                                                                          Scratch sc) {
     constexpr int NP = NO * (NO + 1) / 2;
     constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
-    constexpr int PX = box_pitch<T, VEC>(), BOX = box_size<T, VEC>();
+    using TS_ = PsiTile<TX, TZ>;
+    constexpr int TY = TS_::TY, BY = TS_::BY, BZ = TS_::BZ;
+    constexpr int PX = TS_::template pitch<T, VEC>(), BOX = TS_::template size<T, VEC>();
     constexpr int XO = VEC ? vpad<T>() : 1;  // column of the tile's first x
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* box = reinterpret_cast<T*>(smem_raw);  // [NO + 1][BOX]: psi_0 .. psi_{NO-1}, then Vc
@@ -250,18 +267,18 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = T(0);
 
-    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-    const int ntx = (g.nx + kTX - 1) / kTX, nty = (g.ny + kTY - 1) / kTY, ntz = (g.nz + kTZ - 1) / kTZ;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY, ntz = (g.nz + TZ - 1) / TZ;
     const int ntiles = ntx * nty * ntz;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int bxi = tile % ntx, byi = (tile / ntx) % nty, bzi = tile / (ntx * nty);
-        const int xs = bxi * kTX, y0 = byi * kTY - 1, z0 = bzi * kTZ - 1;  // tile x start; box y, z origin
+        const int xs = bxi * TX, y0 = byi * TY - 1, z0 = bzi * TZ - 1;  // tile x start; box y, z origin
         __syncthreads();  // the previous tile's box is no longer read
         if constexpr (VEC) {
-            constexpr int E = vpad<T>(), CH = kTX / E, ITEMS = CH + 2;  // 16-byte pieces and the two halo values
-            for (int i = threadIdx.x; i < kBY * kBZ * ITEMS; i += kThreads) {
+            constexpr int E = vpad<T>(), CH = TX / E, ITEMS = CH + 2;  // 16-byte pieces and the two halo values
+            for (int i = threadIdx.x; i < BY * BZ * ITEMS; i += kThreads) {
                 const int row = i / ITEMS, k = i - row * ITEMS;
-                const int by = row % kBY, bz = row / kBY;
+                const int by = row % BY, bz = row / BY;
                 const int gy = y0 + by, gz = z0 + bz;
                 const bool rin = gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
                 T* r = box + row * PX;
@@ -277,8 +294,8 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
                     if (in) copy16_v(r + NO * BOX + XO + k * E, Vc + gs);
                     else zero16(r + NO * BOX + XO + k * E);
                 } else {
-                    const int gx = k == CH ? xs - 1 : xs + kTX;
-                    const int col = k == CH ? XO - 1 : XO + kTX;
+                    const int gx = k == CH ? xs - 1 : xs + TX;
+                    const int col = k == CH ? XO - 1 : XO + TX;
                     const bool in = rin && gx >= 0 && gx < g.nx;
                     const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
 #pragma unroll
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
             }
         } else {
             for (int i = threadIdx.x; i < BOX; i += kThreads) {
-                const int bx = i % PX, by = (i / PX) % kBY, bz = i / (PX * kBY);
+                const int bx = i % PX, by = (i / PX) % BY, bz = i / (PX * BY);
                 const int gx = xs - 1 + bx, gy = y0 + by, gz = z0 + bz;
                 const bool in = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
                 const size_t gs = in ? ((size_t)gz * g.ny + gy) * g.nx + gx : 0;
@@ -300,16 +317,16 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
         __syncthreads();
         const int gx = xs + tx, gy = y0 + 1 + ty;
 #pragma unroll 1
-        for (int dz = 0; dz < kTZ; ++dz) {
+        for (int dz = 0; dz < TZ; ++dz) {
             const int gz = z0 + 1 + dz;
             const bool live = gx < g.nx && gy < g.ny && gz < g.nz;
-            const int b = ((dz + 1) * kBY + (ty + 1)) * PX + (tx + XO);  // the site in the box
+            const int b = ((dz + 1) * BY + (ty + 1)) * PX + (tx + XO);  // the site in the box
             T ps[NO], kx[NO];
 #pragma unroll
             for (int j = 0; j < NO; ++j) ps[j] = kx[j] = T(0);
 #pragma unroll
             for (int p = 0; p < 19; ++p) {
-                const int src = b - (vel(p, 0) + vel(p, 1) * PX + vel(p, 2) * PX * kBY);
+                const int src = b - (vel(p, 0) + vel(p, 1) * PX + vel(p, 2) * PX * BY);
                 const T a = xi[vclass(p)] - dt * chi[vclass(p)] * box[NO * BOX + src];
 #pragma unroll
                 for (int j = 0; j < NO; ++j) {
@@ -345,18 +362,20 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
 }
 
-template <typename T, int NO, bool BATCHED, bool VEC>
+template <typename T, int NO, bool BATCHED, bool VEC, int TX, int TZ>
 cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                     cudaStream_t st) {
-    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC>;
-    const size_t smem = (size_t)(NO + 1) * box_size<T, VEC>() * sizeof(T);
+    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC, TX, TZ>;
+    using TS_ = PsiTile<TX, TZ>;
+    const size_t smem = (size_t)(NO + 1) * TS_::template size<T, VEC>() * sizeof(T);
     // opted in whatever the size: static and dynamic shared memory together may exceed 48 KB
     static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kThreads, smem) != cudaSuccess || nb < 1) nb = 1;
     if (sc.max_vals < NO * (NO + 1) / 2 || sc.systems < B) return cudaErrorInvalidValue;
-    const size_t tiles = (size_t)((g.nx + kTX - 1) / kTX) * ((g.ny + kTY - 1) / kTY) * ((g.nz + kTZ - 1) / kTZ);
+    const size_t tiles =
+        (size_t)((g.nx + TX - 1) / TX) * ((g.ny + TS_::TY - 1) / TS_::TY) * ((g.nz + TZ - 1) / TZ);
     const int per = std::max(1, std::min(sc.max_blocks, nb * num_sms() / std::max(B, 1)));
     kern<<<dim3((unsigned)std::min<size_t>(tiles, (size_t)per), (unsigned)B), kThreads, smem, st>>>(g, c, io, sc);
     count_launches(1);
@@ -364,13 +383,30 @@ cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO&
 }
 
 // Vector staging where rows are whole 16-byte pieces and the arrays aligned.
+// Shapes other than the default run with vector staging only; where it does
+// not apply (rows not of whole 16-byte pieces, unaligned arrays) the default
+// shape's scalar staging runs, and so does the default shape where another's
+// box would not fit in a block's shared memory (FP64, many orbitals).
+template <typename T, int NO, int TX, int TZ>
+constexpr bool psi_tile_fits() {
+    return (size_t)(NO + 1) * PsiTile<TX, TZ>::template size<T, true>() * sizeof(T) <= 227 * 1024;
+}
 template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
-                                  cudaStream_t st) {
+                                  int shape, cudaStream_t st) {
     auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
-    if (g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V))
-        return launch_relax_psi_tile_v<T, NO, BATCHED, true>(g, c, io, sc, B, st);
-    return launch_relax_psi_tile_v<T, NO, BATCHED, false>(g, c, io, sc, B, st);
+    if (!(g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V)))
+        return launch_relax_psi_tile_v<T, NO, BATCHED, false, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
+    if ((shape == 1 && !psi_tile_fits<T, NO, kPsiTileTX[1], kPsiTileTZ[1]>()) ||
+        (shape == 2 && !psi_tile_fits<T, NO, kPsiTileTX[2], kPsiTileTZ[2]>()) ||
+        (shape == 3 && !psi_tile_fits<T, NO, kPsiTileTX[3], kPsiTileTZ[3]>()))
+        shape = 0;
+    switch (shape) {
+        case 1: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[1], kPsiTileTZ[1]>(g, c, io, sc, B, st);
+        case 2: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[2], kPsiTileTZ[2]>(g, c, io, sc, B, st);
+        case 3: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[3], kPsiTileTZ[3]>(g, c, io, sc, B, st);
+        default: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
+    }
 }
 
 // More than kMaxOrb orbitals, staged in shared memory: a block takes one
@@ -654,6 +690,8 @@ namespace lbks {
 template <typename T>
 cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                              int kernel, cudaStream_t st) {
+    const int shape = (kernel >> kPsiShapeShift) & 0xff;  // the staged kernel's tile shape
+    kernel &= (1 << kPsiShapeShift) - 1;
     if (kernel == kPsiKernelTma) return launch_relax_psi_tma<T>(NO, g, c, io, sc, B, st);
     const bool tiled = kernel == kPsiKernelTiled || (kernel == kPsiKernelZ && NO > kMaxOrb);
     const bool zmarch = kernel == kPsiKernelZ && NO <= kMaxOrb;
@@ -687,8 +725,8 @@ cudaError_t launch_relax_psi(int NO, const Grid& g, const Coef& c, const RelaxIO
             return b ? launch_relax_psi_zm<T, n, true>(g, c, io, sc, B, st)                           \
                      : launch_relax_psi_zm<T, n, false>(g, c, io, sc, B, st);                         \
         if (tiled)                                                                                    \
-            return b ? launch_relax_psi_tile<T, n, true>(g, c, io, sc, B, st)                         \
-                     : launch_relax_psi_tile<T, n, false>(g, c, io, sc, B, st);                       \
+            return b ? launch_relax_psi_tile<T, n, true>(g, c, io, sc, B, shape, st)                  \
+                     : launch_relax_psi_tile<T, n, false>(g, c, io, sc, B, shape, st);                \
         return b ? launch_relax_psi_n<T, n, true>(g, c, io, sc, B, st) : launch_relax_psi_n<T, n, false>(g, c, io, sc, B, st);
         LBKS_CASE(1) LBKS_CASE(2) LBKS_CASE(3) LBKS_CASE(4) LBKS_CASE(5) LBKS_CASE(6) LBKS_CASE(7) LBKS_CASE(8)
 #undef LBKS_CASE

@@ -912,10 +912,12 @@ struct Ops {
                                  int B, int variant, cudaStream_t st) {
         // variant kPsiKernelTiled: the shared-memory tiled stencil; kPsiKernelDirect: one site per thread
         // from L1; kPsiKernelTma: boxes copied by the tensor memory accelerator (anything else: tiled)
+        // (the tiled kernel's tile shape rides in the bits from kPsiShapeShift on)
         const int v = variant & kRelaxVariantMask;
+        const int shape = variant & (0xff << kPsiShapeShift);
         cudaError_t e = launch_relax_psi<T>(
-            n_orb, g, c, io, sc, B, v == kPsiKernelDirect || v == kPsiKernelTma || v == kPsiKernelZ ? v : kPsiKernelTiled,
-            st);
+            n_orb, g, c, io, sc, B,
+            v == kPsiKernelDirect || v == kPsiKernelTma || v == kPsiKernelZ ? v : (kPsiKernelTiled | shape), st);
         if (e != cudaSuccess || n_orb <= kMaxOrb) return e;  // up to kMaxOrb: overlap fused
         return gram_wide<true>(n_orb, g, c.h, io.f_out, io.S_out, io.lambda_out, io.sigma_out, sc, B, st,
                                (variant & kRelaxExactOverlap) != 0);

@@ -136,6 +136,8 @@ _SIGS = {
     "lbks_cd_step": (_i, [_i, _i, _i, _i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "lbks_cd_overlap": (_i, [_i, _sz, _i, _d, _vp, _vp, _vp, _vp]),
     "lbks_set_cd_kernel": (_i, [_i]),
+    "lbks_set_psi_tile": (_i, [_i]),
+    "lbks_get_psi_tile": (_i, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -468,6 +470,23 @@ def lbks_get_relax_variant(handle) -> dict:
     out = {"variant": RELAX_VARIANTS[v.value], "index": v.value}
     out.update({f"ms_{name}": ms[k] for k, name in enumerate(RELAX_VARIANTS)})
     return out
+
+
+PSI_TILES = ((32, 8, 4), (32, 8, 8), (64, 4, 4), (32, 8, 2))  # staged orbital-storage stencil tile shapes
+
+
+def lbks_set_psi_tile(shape):
+    """-1: tuned per grid shape; 0..3: forced (PSI_TILES).  Returns the previous setting."""
+    code = _lib.lbks_set_psi_tile(shape)
+    if code < -1:
+        raise LbksError(EINVAL, last_error())
+    return code
+
+
+def lbks_get_psi_tile(handle) -> dict:
+    sh, ms = ctypes.c_int(), (ctypes.c_double * len(PSI_TILES))()
+    _check(_lib.lbks_get_psi_tile(handle, ctypes.byref(sh), ms))
+    return {"shape": sh.value, "tile": PSI_TILES[sh.value], "ms": [ms[k] for k in range(len(PSI_TILES))]}
 
 
 def lbks_cholesky_inverse(n, S, Linv, status, stream=None):

@@ -53,6 +53,42 @@ def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
         lbks.lbks_set_relax_variant(prev)
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("n,n_orb,seed", [((36, 11, 13), 5, 8), ((40, 8, 3), 8, 12), ((64, 17, 19), 3, 20),
+                                          ((68, 9, 10), 1, 21), ((8, 2, 2), 1, 13), ((33, 20, 17), 5, 1)])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3], ids=["32x8x4", "32x8x8", "64x4x4", "32x8x2"])
+def test_psi_step_tile_shapes_match_population_oracle(prec, n, n_orb, seed, shape):
+    """The staged stencil at every tile shape the tuner tries (ragged tiles in
+    x, y and z; an odd nx runs the default shape's scalar staging)."""
+    torch, lbks = require_gpu()
+    prev = lbks.lbks_set_relax_variant(1)
+    prev_shape = lbks.lbks_set_psi_tile(shape)
+    try:
+        _psi_step_case(torch, lbks, prec, n, n_orb, seed, True)
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+        lbks.lbks_set_psi_tile(prev_shape)
+
+
+def test_psi_tile_shape_is_tuned():
+    """The tuner times every tile shape of the staged stencil and keeps the
+    fastest; a bad shape is refused."""
+    torch, lbks = require_gpu()
+    prev = lbks.lbks_set_relax_variant(0)
+    try:
+        s = lbks.System((44, 26, 18), 0.4, 5, precision=1, storage=lbks.STORE_PSI)  # a shape no other test tunes
+        mol = W.methane()
+        s.set_geometry(mol.xyz, mol.Z)
+        got = lbks.lbks_get_psi_tile(s.handle)
+        s.close()
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+    assert all(t > 0 for t in got["ms"])
+    assert got["ms"][got["shape"]] == min(got["ms"])
+    with pytest.raises(lbks.LbksError):
+        lbks.lbks_set_psi_tile(4)
+
+
 def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w):
     theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, 1.0, h)
