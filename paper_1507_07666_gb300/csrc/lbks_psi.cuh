@@ -409,6 +409,43 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
     }
 }
 
+// Explicit instantiations of the staged kernels' launchers for one value
+// type (PREFIX extern: declared only, so that a unit that dispatches to them
+// leaves their compilation to the unit that instantiates them).
+#define LBKS_PSI_TILE_INST(PREFIX, T)                                                                            \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 1, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 2, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 3, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 4, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 5, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 6, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 7, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 8, false>(const Grid&, const Coef&, const RelaxIO&,    \
+                                                                   const Scratch&, int, int, cudaStream_t);      \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 1, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 2, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 3, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 4, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 5, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 6, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 7, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);       \
+    PREFIX template cudaError_t launch_relax_psi_tile<T, 8, true>(const Grid&, const Coef&, const RelaxIO&,     \
+                                                                  const Scratch&, int, int, cudaStream_t);
+
 // More than kMaxOrb orbitals, staged in shared memory: a block takes one
 // tile and one group of up to kPsiGroup orbitals of one system (blockIdx.y =
 // system * groups + group), stages the group's psi and W field and Vc with a

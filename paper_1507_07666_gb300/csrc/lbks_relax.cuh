@@ -602,9 +602,23 @@ cudaError_t launch_stream_collide_pair(const Grid& g, const Coef& c, const Relax
 // The two-site and the prefetching variants for NO <= kMaxOrb orbitals, each
 // compiled in a translation unit of its own (lbks_relax_<precision>_<variant>.cu)
 // so that the per-precision units stay small enough to build in parallel.
+// The row (two- or four-site) kernels are compiled in five translation units
+// per precision -- orbital counts 1-4, and 5, 6, 7, 8 one each -- so that no
+// unit holds more than a few of them.
+template <typename TS, typename T, int LO, int HI>
+cudaError_t launch_relax_pairs_range(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                                     const Scratch& sc, int B, cudaStream_t st);
 template <typename TS, typename T>
-cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
-                               const Scratch& sc, int B, cudaStream_t st);
+inline cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                                      const Scratch& sc, int B, cudaStream_t st) {
+    switch (NO) {
+        case 5: return launch_relax_pairs_range<TS, T, 5, 5>(NO, om1, g, c, io, sc, B, st);
+        case 6: return launch_relax_pairs_range<TS, T, 6, 6>(NO, om1, g, c, io, sc, B, st);
+        case 7: return launch_relax_pairs_range<TS, T, 7, 7>(NO, om1, g, c, io, sc, B, st);
+        case 8: return launch_relax_pairs_range<TS, T, 8, 8>(NO, om1, g, c, io, sc, B, st);
+        default: return launch_relax_pairs_range<TS, T, 1, 4>(NO, om1, g, c, io, sc, B, st);
+    }
+}
 template <typename TS, typename T>
 cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
                                   const Scratch& sc, int B, cudaStream_t st);

@@ -1,7 +1,7 @@
-// FP32 instantiation of the two-site stream-collide kernels.
+// FP32 instantiation of the row (two- or four-site) stream-collide kernels, 1-4 orbitals.
 #include "lbks_relax_variants.cuh"
 
 namespace lbks {
-template cudaError_t launch_relax_pairs<float, float>(int, bool, const Grid&, const Coef&, const RelaxIO&, const Scratch&, int,
-                                     cudaStream_t);
+template cudaError_t launch_relax_pairs_range<float, float, 1, 4>(int, bool, const Grid&, const Coef&,
+                                                                     const RelaxIO&, const Scratch&, int, cudaStream_t);
 }  // namespace lbks

@@ -1,0 +1,7 @@
+// FP32 instantiation of the row (two- or four-site) stream-collide kernels, 7 orbitals.
+#include "lbks_relax_variants.cuh"
+
+namespace lbks {
+template cudaError_t launch_relax_pairs_range<float, float, 7, 7>(int, bool, const Grid&, const Coef&,
+                                                                     const RelaxIO&, const Scratch&, int, cudaStream_t);
+}  // namespace lbks

@@ -47,10 +47,24 @@ cudaError_t launch_relax_bulk(int NO, const Grid& g, const Coef& c, const RelaxI
     return launch_stream_collide_bulk<TS, T>(NO, g, c, io, sc, B, exact, device_wait_limit(), st);
 }
 
-template <typename TS, typename T>
-cudaError_t launch_relax_pairs(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
-                               const Scratch& sc, int B, cudaStream_t st) {
-    return dispatch_variant<TS, T, PairLaunch>(NO, om1, g, c, io, sc, B, st);
+// Orbital counts LO..HI only.
+template <typename TS, typename T, int LO, int HI>
+cudaError_t launch_relax_pairs_range(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
+                                     const Scratch& sc, int B, cudaStream_t st) {
+    const bool b = B > 1;
+#define LBKS_CASE(N)                                                                                 \
+    case N:                                                                                          \
+        if constexpr (N >= LO && N <= HI)                                                            \
+            return om1 ? (b ? PairLaunch<TS, T, N, true, true>::run(g, c, io, sc, B, st)              \
+                            : PairLaunch<TS, T, N, true, false>::run(g, c, io, sc, B, st))            \
+                       : (b ? PairLaunch<TS, T, N, false, true>::run(g, c, io, sc, B, st)             \
+                            : PairLaunch<TS, T, N, false, false>::run(g, c, io, sc, B, st));          \
+        return cudaErrorInvalidValue;
+    switch (NO) {
+        LBKS_CASE(1) LBKS_CASE(2) LBKS_CASE(3) LBKS_CASE(4) LBKS_CASE(5) LBKS_CASE(6) LBKS_CASE(7) LBKS_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef LBKS_CASE
 }
 template <typename TS, typename T>
 cudaError_t launch_relax_prefetch(int NO, bool om1, const Grid& g, const Coef& c, const RelaxIO& io,
