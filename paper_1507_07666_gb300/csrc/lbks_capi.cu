@@ -302,7 +302,7 @@ struct lbks_system {
     cudaStream_t cap = nullptr;  // capture stream
     int variant = kRelaxSites;   // stream-collide variant (tuned per shape)
     double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0, -1.0};
-    double tune_shape_ms[kPsiShapes] = {-1.0, -1.0, -1.0, -1.0};  // orbital storage: the staged kernel per tile shape
+    double tune_shape_ms[kPsiShapes] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0};  // orbital storage: the staged kernel per tile shape
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
     std::vector<std::vector<double>> xyz, Z;  // per system
@@ -838,6 +838,7 @@ int tune_relax(lbks_system* s) {
     if (shaped && forced_shape < 0) {
         float best = 0.f;
         for (int k = 0; k < kPsiShapes && e == cudaSuccess; ++k) {
+            if (!psi_tile_runs((int)s->ops->psi_elem, s->n_orb, k)) continue;  // would run shape 0
             float t = 0.f;
             e = timed(kPsiKernelTiled | (k << kPsiShapeShift), &t);
             s->tune_shape_ms[k] = t / kReps;

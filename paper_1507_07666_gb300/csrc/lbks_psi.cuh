@@ -199,20 +199,19 @@ __host__ __device__ constexpr int box_pitch() { return VEC ? kTX + 2 * vpad<T>()
 template <typename T, bool VEC>
 __host__ __device__ constexpr int box_size() { return box_pitch<T, VEC>() * kBY * kBZ; }
 
-// Tile shapes of the staged stencil up to kMaxOrb orbitals: TX x (kThreads / TX) x TZ
-// sites, each thread one (x, y) column of TZ sites; the tuner picks one per grid shape.
-template <int TX, int TZ>
-struct PsiTile {
-    static constexpr int TY = kThreads / TX, BY = TY + 2, BZ = TZ + 2;
+// Tile shapes of the staged stencil up to kMaxOrb orbitals: TX x (kThreads XW / TX) x TZ
+// sites, each thread XW x-neighbouring (x, y) columns of TZ sites; the tuner picks one
+// per grid shape.
+template <int TX, int TZ, int XW = 1>
+struct PsiTile {  // XW: x-neighbouring sites per thread (TX / XW thread columns)
+    static constexpr int TY = kThreads * XW / TX, BY = TY + 2, BZ = TZ + 2;
     template <typename T, bool VEC>
     __host__ __device__ static constexpr int pitch() { return VEC ? TX + 2 * vpad<T>() : TX + 2; }
     template <typename T, bool VEC>
     __host__ __device__ static constexpr int size() { return pitch<T, VEC>() * BY * BZ; }
 };
-// The shapes (TX, TZ) the tuner tries; shape 0 is the default.
-constexpr int kPsiTileShapes = 4;
-constexpr int kPsiTileTX[kPsiTileShapes] = {32, 32, 64, 32};
-constexpr int kPsiTileTZ[kPsiTileShapes] = {4, 8, 4, 2};
+// The shapes (TX, TZ, XW) the tuner tries (kPsiTileTX, kPsiTileTZ, kPsiTileXW);
+// shape 0 is the default.
 
 // 16 bytes of T from global (read-only) to shared memory.
 template <typename T>
@@ -233,12 +232,20 @@ __device__ __forceinline__ void copy16_v(T* dst, const double* src) {
 template <typename T>
 __device__ __forceinline__ void zero16(T* dst) { *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f); }
 
-template <typename T, int NO, bool BATCHED, bool VEC, int TX = kTX, int TZ = kTZ>
-__global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
+// Two sites per thread take twice the accumulators and their larger boxes
+// leave at most two CTAs per SM anyway: at least two resident CTAs there.
+template <typename T, int NO, int XW>
+constexpr int psi_tile_min_blocks() {
+    return XW == 2 && psi_min_blocks<T, NO>() > 2 ? 2 : psi_min_blocks<T, NO>();
+}
+
+template <typename T, int NO, bool BATCHED, bool VEC, int TX = kTX, int TZ = kTZ, int XW = 1>
+__global__ void __launch_bounds__(kThreads, (psi_tile_min_blocks<T, NO, XW>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
                                                                                          Scratch sc) {
+    static_assert(XW == 1 || VEC, "two sites per thread read aligned pairs: vector staging only");
     constexpr int NP = NO * (NO + 1) / 2;
     constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
-    using TS_ = PsiTile<TX, TZ>;
+    using TS_ = PsiTile<TX, TZ, XW>;
     constexpr int TY = TS_::TY, BY = TS_::BY, BZ = TS_::BZ;
     constexpr int PX = TS_::template pitch<T, VEC>(), BOX = TS_::template size<T, VEC>();
     constexpr int XO = VEC ? vpad<T>() : 1;  // column of the tile's first x
@@ -267,7 +274,8 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = T(0);
 
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    constexpr int TC = TX / XW;  // thread columns of the tile
+    const int tx = threadIdx.x % TC, ty = threadIdx.x / TC;
     const int ntx = (g.nx + TX - 1) / TX, nty = (g.ny + TY - 1) / TY, ntz = (g.nz + TZ - 1) / TZ;
     const int ntiles = ntx * nty * ntz;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -315,6 +323,80 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
             }
         }
         __syncthreads();
+        if constexpr (XW == 2) {
+            // two x-neighbouring sites (x even): the arriving values of velocity p
+            // at both sites from aligned pairs of the box row -- x-component 0:
+            // the pair at the source; +1: the pair's left neighbour and its first
+            // element; -1: its second element and the right neighbour's first
+            using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+            auto ld2 = [&](int i) { return *reinterpret_cast<const T2*>(box + i); };
+            const int gx = xs + 2 * tx, gy = y0 + 1 + ty;
+#pragma unroll 1
+            for (int dz = 0; dz < TZ; ++dz) {
+                const int gz = z0 + 1 + dz;
+                const bool live = gx < g.nx && gy < g.ny && gz < g.nz;  // nx is even here: both sites or none
+                const int b = ((dz + 1) * BY + (ty + 1)) * PX + (2 * tx + XO);  // the first site in the box (even)
+                T ps0[NO], ps1[NO], kx0[NO], kx1[NO];
+#pragma unroll
+                for (int j = 0; j < NO; ++j) ps0[j] = ps1[j] = kx0[j] = kx1[j] = T(0);
+#pragma unroll
+                for (int p = 0; p < 19; ++p) {
+                    const int r = b - (vel(p, 1) * PX + vel(p, 2) * PX * BY);  // the source row at x-shift 0
+                    const int vx = vel(p, 0);
+                    auto pair = [&](int f, T& a0, T& a1) {
+                        if (vx == 0) {
+                            const T2 q = ld2(f * BOX + r);
+                            a0 = q.x;
+                            a1 = q.y;
+                        } else if (vx > 0) {
+                            a0 = ld2(f * BOX + r - 2).y;
+                            a1 = ld2(f * BOX + r).x;
+                        } else {
+                            a0 = ld2(f * BOX + r).y;
+                            a1 = ld2(f * BOX + r + 2).x;
+                        }
+                    };
+                    T v0, v1;
+                    pair(NO, v0, v1);
+                    const T a0 = xi[vclass(p)] - dt * chi[vclass(p)] * v0;
+                    const T a1 = xi[vclass(p)] - dt * chi[vclass(p)] * v1;
+#pragma unroll
+                    for (int j = 0; j < NO; ++j) {
+                        T u0, u1;
+                        pair(j, u0, u1);
+                        ps0[j] += a0 * u0;
+                        ps1[j] += a1 * u1;
+                        kx0[j] += xi[vclass(p)] * u0;
+                        kx1[j] += xi[vclass(p)] * u1;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NO; ++j) {
+#pragma unroll
+                    for (int k = 0; k < j; ++k) {
+                        ps0[j] += wl[tri(j - 1, k)] * kx0[k];
+                        ps1[j] += wl[tri(j - 1, k)] * kx1[k];
+                    }
+                    ps0[j] = live ? ps0[j] * sig[j] : T(0);
+                    ps1[j] = live ? ps1[j] * sig[j] : T(0);
+                }
+                if (live) {
+                    const size_t s = ((size_t)gz * g.ny + gy) * g.nx + gx;
+#pragma unroll
+                    for (int j = 0; j < NO; ++j) {
+                        T2 o;
+                        o.x = ps0[j];
+                        o.y = ps1[j];
+                        *reinterpret_cast<T2*>(pout + (size_t)j * N + s) = o;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NO; ++j)
+#pragma unroll
+                    for (int i = 0; i <= j; ++i) acc[tri(j, i)] += ps0[j] * ps0[i] + ps1[j] * ps1[i];
+            }
+            continue;
+        }
         const int gx = xs + tx, gy = y0 + 1 + ty;
 #pragma unroll 1
         for (int dz = 0; dz < TZ; ++dz) {
@@ -362,11 +444,11 @@ __global__ void __launch_bounds__(kThreads, (psi_min_blocks<T, NO>())) k_relax_p
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
 }
 
-template <typename T, int NO, bool BATCHED, bool VEC, int TX, int TZ>
+template <typename T, int NO, bool BATCHED, bool VEC, int TX, int TZ, int XW = 1>
 cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                     cudaStream_t st) {
-    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC, TX, TZ>;
-    using TS_ = PsiTile<TX, TZ>;
+    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC, TX, TZ, XW>;
+    using TS_ = PsiTile<TX, TZ, XW>;
     const size_t smem = (size_t)(NO + 1) * TS_::template size<T, VEC>() * sizeof(T);
     // opted in whatever the size: static and dynamic shared memory together may exceed 48 KB
     static const cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -386,10 +468,16 @@ cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO&
 // Shapes other than the default run with vector staging only; where it does
 // not apply (rows not of whole 16-byte pieces, unaligned arrays) the default
 // shape's scalar staging runs, and so does the default shape where another's
-// box would not fit in a block's shared memory (FP64, many orbitals).
-template <typename T, int NO, int TX, int TZ>
-constexpr bool psi_tile_fits() {
-    return (size_t)(NO + 1) * PsiTile<TX, TZ>::template size<T, true>() * sizeof(T) <= 227 * 1024;
+// box would not fit in a block's shared memory (FP64, many orbitals) or whose
+// two sites per thread would not fit the registers (psi_tile_runs).
+template <typename T, int NO, bool BATCHED, int K>
+cudaError_t launch_relax_psi_tile_k(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
+                                    cudaStream_t st) {
+    if constexpr (K > 0 && psi_tile_runs((int)sizeof(T), NO, K))
+        return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[K], kPsiTileTZ[K], kPsiTileXW[K]>(g, c, io, sc,
+                                                                                                         B, st);
+    else
+        return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
 }
 template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
@@ -397,15 +485,13 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
     auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
     if (!(g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V)))
         return launch_relax_psi_tile_v<T, NO, BATCHED, false, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
-    if ((shape == 1 && !psi_tile_fits<T, NO, kPsiTileTX[1], kPsiTileTZ[1]>()) ||
-        (shape == 2 && !psi_tile_fits<T, NO, kPsiTileTX[2], kPsiTileTZ[2]>()) ||
-        (shape == 3 && !psi_tile_fits<T, NO, kPsiTileTX[3], kPsiTileTZ[3]>()))
-        shape = 0;
     switch (shape) {
-        case 1: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[1], kPsiTileTZ[1]>(g, c, io, sc, B, st);
-        case 2: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[2], kPsiTileTZ[2]>(g, c, io, sc, B, st);
-        case 3: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[3], kPsiTileTZ[3]>(g, c, io, sc, B, st);
-        default: return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
+        case 1: return launch_relax_psi_tile_k<T, NO, BATCHED, 1>(g, c, io, sc, B, st);
+        case 2: return launch_relax_psi_tile_k<T, NO, BATCHED, 2>(g, c, io, sc, B, st);
+        case 3: return launch_relax_psi_tile_k<T, NO, BATCHED, 3>(g, c, io, sc, B, st);
+        case 4: return launch_relax_psi_tile_k<T, NO, BATCHED, 4>(g, c, io, sc, B, st);
+        case 5: return launch_relax_psi_tile_k<T, NO, BATCHED, 5>(g, c, io, sc, B, st);
+        default: return launch_relax_psi_tile_k<T, NO, BATCHED, 0>(g, c, io, sc, B, st);
     }
 }
 

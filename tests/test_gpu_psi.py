@@ -55,11 +55,15 @@ def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("n,n_orb,seed", [((36, 11, 13), 5, 8), ((40, 8, 3), 8, 12), ((64, 17, 19), 3, 20),
-                                          ((68, 9, 10), 1, 21), ((8, 2, 2), 1, 13), ((33, 20, 17), 5, 1)])
-@pytest.mark.parametrize("shape", [0, 1, 2, 3], ids=["32x8x4", "32x8x8", "64x4x4", "32x8x2"])
+                                          ((68, 9, 10), 1, 21), ((8, 2, 2), 1, 13), ((33, 20, 17), 5, 1),
+                                          ((132, 10, 5), 6, 22), ((4, 9, 9), 2, 23)])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5],
+                         ids=["32x8x4", "32x8x8", "64x4x4", "32x8x2", "64x8x4w2", "64x8x2w2"])
 def test_psi_step_tile_shapes_match_population_oracle(prec, n, n_orb, seed, shape):
     """The staged stencil at every tile shape the tuner tries (ragged tiles in
-    x, y and z; an odd nx runs the default shape's scalar staging)."""
+    x, y and z; an odd nx runs the default shape's scalar staging); shapes 4
+    and 5 sum two x-neighbouring sites per thread (FP32, FP64 up to three
+    orbitals)."""
     torch, lbks = require_gpu()
     prev = lbks.lbks_set_relax_variant(1)
     prev_shape = lbks.lbks_set_psi_tile(shape)
@@ -83,10 +87,10 @@ def test_psi_tile_shape_is_tuned():
         s.close()
     finally:
         lbks.lbks_set_relax_variant(prev)
-    assert all(t > 0 for t in got["ms"])
+    assert all(t > 0 for t in got["ms"])  # FP32, five orbitals: every shape runs as itself
     assert got["ms"][got["shape"]] == min(got["ms"])
     with pytest.raises(lbks.LbksError):
-        lbks.lbks_set_psi_tile(4)
+        lbks.lbks_set_psi_tile(len(lbks.PSI_TILES))
 
 
 def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w):
