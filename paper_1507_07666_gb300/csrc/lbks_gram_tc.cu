@@ -14,10 +14,12 @@
 // per-thread FP64 sums, so no FP32 sum runs over more than 512 sites.  Blocks
 // and the grid finish in FP64 (the last block of each system, fixed order).
 //
-// Pipeline.  128 threads (warp w owns TMEM lanes 32w..32w+31) load the next
-// tile into registers while they split the current one into a 128-byte-
+// Pipeline.  256 threads (320 for 33..40 orbitals, so that every thread
+// splits two 4-site groups of a tile) stream the next tiles into a cp.async
+// ring (or registers) while they split the current one into a 128-byte-
 // swizzled K-major tile (two stages); one thread issues the four K = 16 MMAs
-// of a tile and commits them to the stage's mbarrier.  Every wait on an
+// of a tile and commits them to the stage's mbarrier; warps 0..7 drain TMEM
+// (warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31).  Every wait on an
 // mbarrier is bounded (lbks_set_wait_limit polls, default 2^22): on expiry the
 // block records a timeout, writes NaN partial sums (so the solve fails with a
 // non-finite energy), waits (2^22 polls at most) for its own MMAs, frees its
@@ -33,17 +35,17 @@
 namespace lbks {
 namespace {
 
-constexpr int kTcThreads = 256;                              // 8 warps; warp w reads TMEM lanes 32 (w % 4) ..
+constexpr int kTcThreads = 256;                              // 8 warps (the default block)
 constexpr int kTcSites = 64;                                 // sites per tile: 64 bf16 = one 128-byte row
 constexpr int kTcRows = 128;                                 // MMA M
 constexpr int kTcStages = 2;
 constexpr int kTcTileBytes = kTcRows * kTcSites * 2;         // 16 KB
 // Per-thread work bounds for at most MAXO orbitals: 4-site groups of a tile,
 // and overlap pairs of the packed lower triangle.
-template <int MAXO>
+template <int MAXO, int TH>
 struct TcBounds {
-    static constexpr int quads = (MAXO * (kTcSites / 4) + kTcThreads - 1) / kTcThreads;
-    static constexpr int pairs = (MAXO * (MAXO + 1) / 2 + kTcThreads - 1) / kTcThreads;
+    static constexpr int quads = (MAXO * (kTcSites / 4) + TH - 1) / TH;
+    static constexpr int pairs = (MAXO * (MAXO + 1) / 2 + TH - 1) / TH;
 };
 constexpr int kDrainTiles = 8;
 constexpr int kInStages = 4;                                 // staged FP32 tiles in flight (bulk-copy path)
@@ -81,15 +83,18 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + (((k >> 3) ^ (r & 7)) << 4) + (k & 7) * 2);
 }
 
+// Each poll may suspend the thread until the phase completes, for at most
+// kPollSuspendNs (so that waiting warps issue few instructions).
+constexpr uint32_t kPollSuspendNs = 1000;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
     for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "n"(kPollSuspendNs)
             : "memory");
         if (done) return true;
     }
@@ -143,15 +148,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //
 // BULK (N % 4 == 0, 16-byte aligned orbitals): every thread streams its 16-byte
 // pieces of the tiles kInStages - 1 ahead into a staging ring with cp.async,
-// so the loads in flight do not depend on registers.  Otherwise every thread
+// so the loads in flight do not depend on registers; a thread's ring pieces
+// are its own (one block barrier per tile, before the MMAs).  Otherwise every thread
 // loads its values for the next tile into registers while it converts the
 // current one.
 //
 // Dynamic shared memory: 1 KB alignment slack, kTcStages bf16 tiles, the
 // staging ring (BULK), the (2N_O) x (2N_O + 1) FP32 fold buffer (reused for
 // the block totals).
-template <bool LAM, bool BULK, int MAXO>
-__global__ void __launch_bounds__(kTcThreads, 2)
+template <bool LAM, bool BULK, int MAXO, int TH>
+__global__ void __launch_bounds__(TH, 2)
     k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
               double* sigma, Scratch sc, uint32_t wait_limit) {
     if (inactive(g)) return;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __shared__ __align__(8) uint64_t mbar[kTcStages];
     __shared__ uint32_t tmem_sh;
 
-    constexpr int kTcQuads = TcBounds<MAXO>::quads, kTcMaxPairs = TcBounds<MAXO>::pairs;
+    constexpr int kTcQuads = TcBounds<MAXO, TH>::quads, kTcMaxPairs = TcBounds<MAXO, TH>::pairs;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int lane_base = (warp & 3) * 32, half = warp >> 2;  // TMEM lanes of this warp; column half it drains
     const uint32_t N = g.N;
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const uint32_t ntiles = (N + kTcSites - 1) / kTcSites;
     const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // >= 1: gridDim.x <= ntiles
 
-    for (int i = tid; i < kTcStages * kTcTileBytes / 16; i += kTcThreads)
+    for (int i = tid; i < kTcStages * kTcTileBytes / 16; i += TH)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         for (int s = 0; s < kTcStages; ++s)
@@ -200,6 +206,20 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     const uint32_t tiles_u32 = smem_u32(smem);
 
     const int nq = NO * (kTcSites / 4);
+    // This thread's 4-site groups of every tile (the same in each tile): the
+    // group's first site in the tile, its orbital's offset in psi, its
+    // byte offset in a staged FP32 tile and in the swizzled hi and lo rows.
+    uint32_t qk[kTcQuads], qring[kTcQuads], qhi[kTcQuads], qlo[kTcQuads];
+    size_t qrow[kTcQuads];
+#pragma unroll
+    for (int q = 0; q < kTcQuads; ++q) {
+        const int i = tid + q * TH, r = i >> 4, k = 4 * (i & 15);
+        qk[q] = (uint32_t)k;
+        qrow[q] = (size_t)r * N;
+        qring[q] = (uint32_t)(r * kTcSites + k) * 4u;
+        qhi[q] = tile_off(r, k);
+        qlo[q] = tile_off(NO + r, k);
+    }
     // Staged copy of local tile `it` into ring slot it % kInStages: this
     // thread's 16-byte pieces, one commit group per tile (empty past the end).
     auto issue = [&](int it) {
@@ -208,12 +228,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const uint32_t slot = smem_u32(ring + (it % kInStages) * stage_bytes);
 #pragma unroll
             for (int q = 0; q < kTcQuads; ++q) {
-                const int i = tid + q * kTcThreads;
-                if (i >= nq) continue;
-                const uint32_t site = base + 4 * (i & 15);
+                if (tid + q * TH >= nq) continue;
+                const uint32_t site = base + qk[q];
                 const bool in = site < N;  // N % 4 == 0: a piece is all in or all out
-                cp_async16(slot + (uint32_t)((i >> 4) * kTcSites + 4 * (i & 15)) * 4u,
-                           in ? psi + (size_t)(i >> 4) * N + site : psi, in ? 16u : 0u);
+                cp_async16(slot + qring[q], in ? psi + qrow[q] + site : psi, in ? 16u : 0u);
             }
         }
         cp_async_commit();
@@ -226,7 +244,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 #pragma unroll
     for (int q = 0; q < kTcMaxPairs; ++q) {
         acc[q] = 0.0;
-        const int k = tid + q * kTcThreads;
+        const int k = tid + q * TH;
         int a = 0, b = 0;
         if (k < NP) tri_pair(k, a, b);
         pr[q] = k < NP ? (a << 8) | b : -1;
@@ -238,10 +256,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
-            const int i = tid + q * kTcThreads;
-            if (i >= nq) continue;
-            const uint32_t site = base + 4 * (i & 15);
-            const float* p = psi + (size_t)(i >> 4) * N + site;
+            if (tid + q * TH >= nq) continue;
+            const uint32_t site = base + qk[q];
+            const float* p = psi + qrow[q] + site;
             v[q].x = site < N ? __ldg(p) : 0.f;
             v[q].y = site + 1 < N ? __ldg(p + 1) : 0.f;
             v[q].z = site + 2 < N ? __ldg(p + 2) : 0.f;
@@ -257,18 +274,19 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         const bool last_tile = it + 1 == my_tiles;
         bool late = false;
         if (BULK) {
-            cp_async_wait<kInStages - 2>();  // this thread's pieces of tile `it` have landed
-            __syncthreads();                 // everyone's; and slot (it - 1) % kInStages is free
+            // this thread's pieces of tile `it` have landed; every thread reads
+            // back only the pieces it copied itself, so no block barrier is
+            // needed, and slot (it - 1) % kInStages, which it refills now, was
+            // read into its registers in the previous iteration
+            cp_async_wait<kInStages - 2>();
             issue(it + kInStages - 1);
             const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
-            const float* stg = reinterpret_cast<const float*>(ring + (it % kInStages) * stage_bytes);
+            const unsigned char* stg = ring + (it % kInStages) * stage_bytes;
 #pragma unroll
             for (int q = 0; q < kTcQuads; ++q) {
-                const int i = tid + q * kTcThreads;
-                if (i >= nq) continue;
-                const uint32_t site = base + 4 * (i & 15);
-                cur[q] = site < N ? *reinterpret_cast<const float4*>(stg + (i >> 4) * kTcSites + 4 * (i & 15))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid + q * TH >= nq) continue;
+                cur[q] = base + qk[q] < N ? *reinterpret_cast<const float4*>(stg + qring[q])
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         } else if (!last_tile) {
             load(it + 1, nxt);
@@ -280,16 +298,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         unsigned char* st = smem + s * kTcTileBytes;
 #pragma unroll
         for (int q = 0; q < kTcQuads; ++q) {
-            const int i = tid + q * kTcThreads;
-            if (i >= nq) continue;
-            const int r = i >> 4, k = 4 * (i & 15);
+            if (tid + q * TH >= nq) continue;
             const float4 v = cur[q];
             const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
             const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
             const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
             const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-            *reinterpret_cast<uint2*>(st + tile_off(r, k)) = make_uint2(bf2_bits(h01), bf2_bits(h23));
-            *reinterpret_cast<uint2*>(st + tile_off(NO + r, k)) = make_uint2(bf2_bits(l01), bf2_bits(l23));
+            *reinterpret_cast<uint2*>(st + qhi[q]) = make_uint2(bf2_bits(h01), bf2_bits(h23));
+            *reinterpret_cast<uint2*>(st + qlo[q]) = make_uint2(bf2_bits(l01), bf2_bits(l23));
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (__syncthreads_or(late)) {
@@ -310,7 +326,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             in_chunk = 0;
             const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity, wait_limit));
             tc_fence_after();
-            if (ok && lane_base < R) {  // the two warp groups drain alternate 16-column blocks
+            if (ok && warp < 8 && lane_base < R) {  // two groups of four warps drain alternate 16-column blocks
                 const int row = lane_base + (tid & 31);
                 for (int cb = 16 * half; cb < NM; cb += 32) {
                     uint32_t v[16];
@@ -359,7 +375,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     double* partial = sys_partial(sc);
 #pragma unroll
     for (int q = 0; q < kTcMaxPairs; ++q) {
-        const int k = tid + q * kTcThreads;
+        const int k = tid + q * TH;
         if (k < NP) partial[(size_t)blockIdx.x * NP + k] = failed ? __longlong_as_double(0x7ff8000000000000ll) : acc[q];
     }
     double* tot = reinterpret_cast<double*>(fold);  // NP doubles fit in the fold buffer
@@ -368,10 +384,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                             LAM ? sigma + y * NO : nullptr);
 }
 
-template <bool LAM, bool BULK, int MAXO>
+template <bool LAM, bool BULK, int MAXO, int TH = kTcThreads>
 static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
                                   double* sigma, const Scratch& sc, int B, int drain_tiles, cudaStream_t st) {
-    auto kern = k_gram_tc<LAM, BULK, MAXO>;
+    auto kern = k_gram_tc<LAM, BULK, MAXO, TH>;
     const int R = 2 * NO, NM = (R + 15) & ~15;
     const int ncols = NM <= 32 ? 32 : NM <= 64 ? 64 : 128;
     size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (BULK ? (size_t)kInStages * NO * kTcSites * 4 : 0) +
@@ -382,7 +398,7 @@ static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* 
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TH, smem);
     if (e != cudaSuccess) return e;
     // The occupancy query has reported one block per SM where two fit (shared
     // memory and registers both allow two, and two run when launched): take
@@ -397,7 +413,7 @@ static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* 
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0) {
             const int regs = (fa.numRegs + 7) & ~7;
-            const int by_regs = 65536 / (regs * kTcThreads);
+            const int by_regs = 65536 / (regs * TH);
             const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
             occ = std::max(occ, std::min(by_regs, by_smem));
         }
@@ -408,14 +424,14 @@ static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* 
         smem += 4096;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kTcThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TH, smem);
         if (e != cudaSuccess) return e;
     }
     if (occ < 1 || occ > cap) return cudaErrorInvalidConfiguration;
     const size_t tiles = (g.N + kTcSites - 1) / kTcSites;
     const int per = std::max(1, std::min(sc.max_blocks, occ * num_sms() / std::max(B, 1)));
     const dim3 grid((unsigned)std::max<size_t>(1, std::min<size_t>(tiles, (size_t)per)), (unsigned)B);
-    kern<<<grid, kTcThreads, smem, st>>>(g, h, psi, NO, drain_tiles, S, lam, sigma, sc, g_wait_limit.load());
+    kern<<<grid, TH, smem, st>>>(g, h, psi, NO, drain_tiles, S, lam, sigma, sc, g_wait_limit.load());
     count_launches(1);
     return cudaGetLastError();
 }
@@ -433,6 +449,14 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
                        : gram_tc_launch<false, false, MAXO>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st));
     if (NO <= 16) LBKS_TC(16)
     if (NO <= 32) LBKS_TC(32)
+    if (NO <= 40) {  // 16 NO 4-site groups of a tile: two per thread of ten warps
+        return lam ? (bulk ? gram_tc_launch<true, true, 40, 320>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
+                           : gram_tc_launch<true, false, 40, 320>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st))
+                   : (bulk ? gram_tc_launch<false, true, 40, 320>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles,
+                                                                 st)
+                           : gram_tc_launch<false, false, 40, 320>(NO, g, h, psi, S, nullptr, nullptr, sc, B,
+                                                                  drain_tiles, st));
+    }
     if (NO <= 48) LBKS_TC(48)
     LBKS_TC(kMaxOrbWide)
 #undef LBKS_TC

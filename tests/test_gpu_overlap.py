@@ -42,7 +42,9 @@ def _scaled_err(S, ref):
     ((64, 48, 40), 64, True),
     ((23, 19, 17), 16, False),   # ragged N: scalar loads, partial last tile
     ((31, 7, 5), 33, False),
-    ((24, 20, 16), 20, False),   # each compile-time bound of the kernel: <= 16, 32, 48, 64 orbitals
+    ((24, 20, 16), 20, False),   # each compile-time bound of the kernel: <= 16, 32, 40 (ten warps), 48, 64 orbitals
+    ((21, 17, 15), 45, False),
+    ((32, 16, 12), 36, True),
     ((12, 10, 8), 3, True),
 ])
 def test_fp32_overlap_tensor_cores(n, n_orb, smooth):
