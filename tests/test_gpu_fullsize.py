@@ -1,14 +1,17 @@
 """The relaxation step at the 8-water cluster's full size (256^3 grid, 40
 orbitals, FP32) in the launch configuration the bench times, checked on sampled
-sites that the oracle's definition gives one by one: the orbital at r is the
-scaled sum of the populations arriving from r - v_p (Eq. KSLB, pull
-streaming, nothing from outside the box), plus the W source xi_p u(r - v_p).
-The overlap is checked through properties that hold at any size (symmetry,
-the diagonal against an FP64 sum of the returned orbitals)."""
+sites against the oracle: each sampled site's 3 x 3 x 3 neighbourhood (zeros
+outside the box) goes through the oracle's own step -- ``lb.pull_stream`` and
+``lb.collide`` for populations (Eq. KSLB), ``psi.step`` for orbital storage --
+and its centre must equal the GPU's orbitals and, for populations, all 19
+post-collision populations.  The overlap is checked through properties that
+hold at any size (symmetry, the diagonal against an FP64 sum of the returned
+orbitals)."""
 import numpy as np
 import pytest
 
-from oracle import lattice
+from oracle import lattice, lb
+from oracle import psi as opsi
 
 from gpu_util import require_gpu
 
@@ -25,18 +28,15 @@ def _sample_sites(rng, n, count):
     return pts
 
 
-def _pulled(torch, arr, n, pts, p):
-    """Values arr[..., z - vz, y - vy, x - vx] for each sampled site (0 outside)."""
-    nx, ny, nz = n
-    vx, vy, vz = lattice.VELOCITIES[p]
-    out = []
-    for (x, y, z) in pts:
-        sx, sy, sz = x - vx, y - vy, z - vz
-        if 0 <= sx < nx and 0 <= sy < ny and 0 <= sz < nz:
-            out.append(arr[..., sz, sy, sx])
-        else:
-            out.append(torch.zeros(arr.shape[:-3], dtype=arr.dtype, device=arr.device))
-    return torch.stack(out, dim=-1)  # [..., site]
+def _patch(arr, pt, n):
+    """arr[..., z-1:z+2, y-1:y+2, x-1:x+2] in FP64 on the host, zero outside the box."""
+    lo = [c - 1 for c in pt[::-1]]  # z, y, x
+    a = [max(l, 0) for l in lo]
+    b = [min(l + 3, m) for l, m in zip(lo, n[::-1])]
+    out = np.zeros(tuple(arr.shape[:-3]) + (3, 3, 3))
+    sub = arr[..., a[0]:b[0], a[1]:b[1], a[2]:b[2]].double().cpu().numpy()
+    out[..., a[0] - lo[0]:b[0] - lo[0], a[1] - lo[1]:b[1] - lo[1], a[2] - lo[2]:b[2] - lo[2]] = sub
+    return out
 
 
 @pytest.mark.parametrize("storage", ["populations", "psi"])
@@ -46,13 +46,14 @@ def test_cluster_step_on_sampled_sites(storage):
     rng = np.random.Generator(np.random.PCG64(17))
     gen = torch.Generator(device="cuda").manual_seed(17)
     xi = lattice.xi(THETA)
-    chi = lattice.chi()
     dt = lattice.time_step(THETA, 1.0, H)
     V = -3.0 * torch.rand((nz, ny, nx), generator=gen, dtype=torch.float64, device="cuda")
     sig = torch.from_numpy(rng.uniform(0.5, 2.0, NO)).cuda()
     S = torch.empty((NO, NO), dtype=torch.float64, device="cuda")
     lam, sig2 = torch.empty_like(S), torch.empty_like(sig)
     pts = _sample_sites(rng, N3, 48)
+    xi_b = xi[None, :, None, None, None]
+    sig_np = sig.cpu().numpy()
     if storage == "populations":
         f = torch.rand((NO, 19, nz, ny, nx), generator=gen, dtype=torch.float32, device="cuda")
         u = 0.1 * torch.rand((NO - 1, nz, ny, nx), generator=gen, dtype=torch.float32, device="cuda")
@@ -60,28 +61,35 @@ def test_cluster_step_on_sampled_sites(storage):
         psi = torch.empty((NO, nz, ny, nx), dtype=torch.float32, device="cuda")
         lbks.lbks_relax_step(lbks.FP32, nx, ny, nz, NO, H, 1.0, THETA, dt, f, u, V, sig, fo, psi, S, lam, sig2)
         torch.cuda.synchronize()
-        ref = torch.zeros((NO, len(pts)), dtype=torch.float64, device="cuda")
-        for p in range(19):
-            ref += _pulled(torch, f[:, p], N3, pts, p).double()
-            ref[1:] += xi[p] * _pulled(torch, u, N3, pts, p).double()
+        ref_psi, ref_f, got_f = [], [], []
+        for (x, y, z) in pts:
+            # the populations the (split) state stands for: f + xi_p u for orbitals 1..
+            fs = _patch(f, (x, y, z), N3)
+            fs[1:] += xi_b * _patch(u, (x, y, z), N3)[:, None]
+            arr = lb.pull_stream(fs)[:, :, 1:2, 1:2, 1:2] * sig_np[:, None, None, None, None]
+            ps = arr.sum(axis=1)
+            ref_psi.append(ps[:, 0, 0, 0])
+            ref_f.append(lb.collide(arr, ps, _patch(V, (x, y, z), N3)[1:2, 1:2, 1:2], 1.0, THETA, dt)[..., 0, 0, 0])
+            got_f.append(fo[:, :, z, y, x].double().cpu().numpy())
+        ref_f, got_f = np.stack(ref_f, axis=-1), np.stack(got_f, axis=-1)
+        assert np.abs(got_f - ref_f).max() / np.abs(ref_f).max() < 2e-5
         del f, fo, u
     else:
         pin = torch.rand((NO, nz, ny, nx), generator=gen, dtype=torch.float32, device="cuda")
-        lam_in = torch.from_numpy(np.tril(rng.uniform(-0.3, 0.3, (NO, NO)), -1)).cuda()
+        lam_np = np.tril(rng.uniform(-0.3, 0.3, (NO, NO)), -1)
+        lam_in = torch.from_numpy(lam_np).cuda()
         psi = torch.empty_like(pin)
         lbks.lbks_relax_step_psi(lbks.FP32, nx, ny, nz, NO, H, THETA, dt, pin, lam_in, V, sig, psi, S, lam, sig2)
         torch.cuda.synchronize()
-        # populations the state stands for: xi_p psi - dt chi_p V psi + xi_p u, u_j = -sum_k Lambda_jk psi_k
-        ref = torch.zeros((NO, len(pts)), dtype=torch.float64, device="cuda")
-        for p in range(19):
-            pp = _pulled(torch, pin, N3, pts, p).double()
-            vv = _pulled(torch, V, N3, pts, p)
-            uu = -(lam_in @ pp)
-            ref += (xi[p] - dt * chi[p] * vv)[None] * pp + xi[p] * uu
+        ref_psi = []
+        for (x, y, z) in pts:
+            st = opsi.PsiState(_patch(pin, (x, y, z), N3))
+            st.lam, st.vc = lam_np, _patch(V, (x, y, z), N3)
+            ref_psi.append(opsi.step(st, sig_np, st.vc, THETA, dt, H)["psi"][:, 1, 1, 1])
         del pin
-    ref *= sig[:, None]
-    got = torch.stack([psi[:, z, y, x] for (x, y, z) in pts], dim=-1).double()
-    err = (got - ref).abs().max().item() / ref.abs().max().item()
+    ref = np.stack(ref_psi, axis=-1)
+    got = torch.stack([psi[:, z, y, x] for (x, y, z) in pts], dim=-1).double().cpu().numpy()
+    err = np.abs(got - ref).max() / np.abs(ref).max()
     assert err < 2e-5, err
     # overlap: symmetric, diagonal = h^3 sum psi_j^2 (FP64 over the returned orbitals)
     Sd = S.cpu().numpy()
