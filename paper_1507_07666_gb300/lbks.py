@@ -477,16 +477,6 @@ PSI_TILES = ((32, 8, 4), (32, 8, 8), (64, 4, 4), (32, 8, 2), (64, 8, 4), (64, 8,
 PSI_TILE_SITES_PER_THREAD = (1, 1, 1, 1, 2, 2)
 
 
-def psi_tile_runs(elem, n_orb, shape):
-    """Whether a tile shape runs as itself for n_orb orbitals of elem bytes
-    (else the default shape runs): the box of psi and Vc with 16-byte row
-    padding fits 227 KB, and two sites per thread take FP32 or up to three
-    FP64 orbitals."""
-    tx, ty, tz = PSI_TILES[shape]
-    box = (n_orb + 1) * (tx + 2 * (16 // elem)) * (ty + 2) * (tz + 2) * elem
-    return box <= 227 * 1024 and (PSI_TILE_SITES_PER_THREAD[shape] == 1 or elem <= 4 or n_orb <= 3)
-
-
 def lbks_set_psi_tile(shape):
     """-1: tuned per grid shape; 0..5: forced (PSI_TILES).  Returns the previous setting."""
     code = _lib.lbks_set_psi_tile(shape)
