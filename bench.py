@@ -333,7 +333,7 @@ WIDE_SEGMENTS = (
     # the wide stream-collide kernel, up to the next kernel of its header
     (b"__global__ void __launch_bounds__(kThreads, 4) k_stream_collide_wide", b"// S = h^3 Psi Psi^T over the packed"),
     # the tensor-core overlap kernel and its device helpers, up to its launcher
-    (b"", b"template <bool LAM, bool BULK, int MAXO, int TH = kTcThreads>\nstatic cudaError_t gram_tc_launch"),
+    (b"", b"template <bool LAM, bool BULK, int MAXO, int TH = kTcThreads, int TPB = 1>\nstatic cudaError_t gram_tc_launch"),
 )
 
 

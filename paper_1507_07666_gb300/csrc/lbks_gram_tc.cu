@@ -38,7 +38,7 @@ namespace {
 constexpr int kTcThreads = 256;                              // 8 warps (the default block)
 constexpr int kTcSites = 64;                                 // sites per tile: 64 bf16 = one 128-byte row
 constexpr int kTcRows = 128;                                 // MMA M
-constexpr int kTcStages = 2;
+constexpr int kTcStages = 2;                                 // bf16 stages per tile of a barrier (below)
 constexpr int kTcTileBytes = kTcRows * kTcSites * 2;         // 16 KB
 // Per-thread work bounds for at most MAXO orbitals: 4-site groups of a tile,
 // and overlap pairs of the packed lower triangle.
@@ -49,6 +49,21 @@ struct TcBounds {
 };
 constexpr int kDrainTiles = 8;
 constexpr int kInStages = 4;                                 // staged FP32 tiles in flight (bulk-copy path)
+// Shared-memory layout for at most MAXO orbitals and TPB tiles split between
+// two block barriers (2 TPB bf16 stages).  TPB = 1: 128-row stages, the FP32
+// fold buffer after the cp.async ring.  TPB > 1: a stage holds only the
+// 2 MAXO rows in use (stride bytes apart, whole 1 KB swizzle groups) -- the
+// M = 128 MMA reads 128 rows from a stage's start, and the rows past 2 MAXO
+// (the next stage, or the slack after the last one) feed only accumulator
+// rows that are never read -- and the fold buffer shares the stages' bytes
+// where it fits (it is written only while no MMA is in flight).
+template <int MAXO, int TPB>
+struct TcLayout {
+    static constexpr int stages = kTcStages * TPB;
+    static constexpr int stride = TPB > 1 ? ((2 * MAXO * 128 + 1023) / 1024) * 1024 : kTcTileBytes;
+    static constexpr int tiles = stages * stride + (kTcTileBytes - stride);
+    static constexpr bool fold_in_tiles = TPB > 1 && 2 * MAXO * (2 * MAXO + 1) * 4 <= tiles;
+};
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr int kTmemColumnsPerSm = 512;
 
@@ -153,10 +168,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // loads its values for the next tile into registers while it converts the
 // current one.
 //
-// Dynamic shared memory: 1 KB alignment slack, kTcStages bf16 tiles, the
-// staging ring (BULK), the (2N_O) x (2N_O + 1) FP32 fold buffer (reused for
-// the block totals).
-template <bool LAM, bool BULK, int MAXO, int TH>
+// TPB tiles are split between two block barriers, and one thread issues their
+// MMAs together.
+//
+// Dynamic shared memory (TcLayout): 1 KB alignment slack, the bf16 stages,
+// the staging ring (BULK), the (2N_O) x (2N_O + 1) FP32 fold buffer unless it
+// shares the stages' bytes (reused for the block totals).
+template <bool LAM, bool BULK, int MAXO, int TH, int TPB>
 __global__ void __launch_bounds__(TH, 2)
     k_gram_tc(Grid g, double h, const float* __restrict__ psi, int NO, int drain_tiles, double* S, double* lam,
               double* sigma, Scratch sc, uint32_t wait_limit) {
@@ -164,10 +182,12 @@ __global__ void __launch_bounds__(TH, 2)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
+    using L = TcLayout<MAXO, TPB>;
+    constexpr int NS = L::stages;
     const uint32_t stage_bytes = (uint32_t)NO * kTcSites * 4;  // one staged FP32 tile
-    unsigned char* ring = smem + kTcStages * kTcTileBytes;
-    float* fold = reinterpret_cast<float*>(ring + (BULK ? kInStages * stage_bytes : 0));
-    __shared__ __align__(8) uint64_t mbar[kTcStages];
+    unsigned char* ring = smem + L::tiles;
+    float* fold = reinterpret_cast<float*>(L::fold_in_tiles ? smem : ring + (BULK ? kInStages * stage_bytes : 0));
+    __shared__ __align__(8) uint64_t mbar[NS];
     __shared__ uint32_t tmem_sh;
 
     constexpr int kTcQuads = TcBounds<MAXO, TH>::quads, kTcMaxPairs = TcBounds<MAXO, TH>::pairs;
@@ -184,10 +204,10 @@ __global__ void __launch_bounds__(TH, 2)
     const uint32_t ntiles = (N + kTcSites - 1) / kTcSites;
     const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);  // >= 1: gridDim.x <= ntiles
 
-    for (int i = tid; i < kTcStages * kTcTileBytes / 16; i += TH)
+    for (int i = tid; i < L::tiles / 16; i += TH)
         reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s)
+        for (int s = 0; s < NS; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -270,42 +290,52 @@ __global__ void __launch_bounds__(TH, 2)
     int in_chunk = 0;
     uint32_t last_bar = 0, last_parity = 0;
     if (!BULK) load(0, cur);
-    for (int it = 0; it < my_tiles; ++it) {
-        const bool last_tile = it + 1 == my_tiles;
+    for (int it0 = 0; it0 < my_tiles; it0 += TPB) {
+        const int nt = min(TPB, my_tiles - it0);  // tiles before this barrier
+        const bool last_group = it0 + nt == my_tiles;
         bool late = false;
-        if (BULK) {
-            // this thread's pieces of tile `it` have landed; every thread reads
-            // back only the pieces it copied itself, so no block barrier is
-            // needed, and slot (it - 1) % kInStages, which it refills now, was
-            // read into its registers in the previous iteration
-            cp_async_wait<kInStages - 2>();
-            issue(it + kInStages - 1);
-            const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
-            const unsigned char* stg = ring + (it % kInStages) * stage_bytes;
+#pragma unroll
+        for (int u = 0; u < TPB; ++u) {
+            if (u >= nt) break;
+            const int it = it0 + u;
+            if (BULK) {
+                // this thread's pieces of tile `it` have landed; every thread
+                // reads back only the pieces it copied itself, so no block
+                // barrier is needed, and slot (it - 1) % kInStages, which it
+                // refills now, was read into its registers for tile it - 1
+                cp_async_wait<kInStages - 2>();
+                issue(it + kInStages - 1);
+                const uint32_t base = (blockIdx.x + (uint32_t)it * gridDim.x) * kTcSites;
+                const unsigned char* stg = ring + (it % kInStages) * stage_bytes;
+#pragma unroll
+                for (int q = 0; q < kTcQuads; ++q) {
+                    if (tid + q * TH >= nq) continue;
+                    cur[q] = base + qk[q] < N ? *reinterpret_cast<const float4*>(stg + qring[q])
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else if (it + 1 < my_tiles) {
+                load(it + 1, nxt);
+            }
+            const int s = it % NS;
+            // the MMAs of tile it - NS read this stage
+            late = late ||
+                   (it >= NS && !mbar_wait(smem_u32(&mbar[s]), (uint32_t)((it / NS) + 1) & 1u, wait_limit));
+            unsigned char* st = smem + s * L::stride;
 #pragma unroll
             for (int q = 0; q < kTcQuads; ++q) {
                 if (tid + q * TH >= nq) continue;
-                cur[q] = base + qk[q] < N ? *reinterpret_cast<const float4*>(stg + qring[q])
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v = cur[q];
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+                const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+                const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+                *reinterpret_cast<uint2*>(st + qhi[q]) = make_uint2(bf2_bits(h01), bf2_bits(h23));
+                *reinterpret_cast<uint2*>(st + qlo[q]) = make_uint2(bf2_bits(l01), bf2_bits(l23));
             }
-        } else if (!last_tile) {
-            load(it + 1, nxt);
-        }
-        const int s = it % kTcStages;
-        const uint32_t bar = smem_u32(&mbar[s]);
-        // the MMAs of tile it - kTcStages read this stage
-        late = late || (it >= kTcStages && !mbar_wait(bar, (uint32_t)((it / kTcStages) + 1) & 1u, wait_limit));
-        unsigned char* st = smem + s * kTcTileBytes;
+            if (!BULK) {
 #pragma unroll
-        for (int q = 0; q < kTcQuads; ++q) {
-            if (tid + q * TH >= nq) continue;
-            const float4 v = cur[q];
-            const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
-            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-            const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
-            const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
-            *reinterpret_cast<uint2*>(st + qhi[q]) = make_uint2(bf2_bits(h01), bf2_bits(h23));
-            *reinterpret_cast<uint2*>(st + qlo[q]) = make_uint2(bf2_bits(l01), bf2_bits(l23));
+                for (int q = 0; q < kTcQuads; ++q) cur[q] = nxt[q];
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (__syncthreads_or(late)) {
@@ -314,17 +344,23 @@ __global__ void __launch_bounds__(TH, 2)
         }
         if (tid == 0) {
             tc_fence_after();
-            const uint64_t d0 = sw128_desc(tiles_u32 + s * kTcTileBytes);
+            for (int u = 0; u < nt; ++u) {
+                const int s = (it0 + u) % NS;
+                const uint64_t d0 = sw128_desc(tiles_u32 + s * L::stride);
 #pragma unroll
-            for (int k = 0; k < kTcSites / 16; ++k)  // K = 16 bf16 = 32 bytes = 2 descriptor units
-                mma_bf16(tmem, d0 + 2 * k, d0 + 2 * k, idesc, (in_chunk > 0 || k > 0) ? 1u : 0u);
-            mma_commit(bar);
+                for (int k = 0; k < kTcSites / 16; ++k)  // K = 16 bf16 = 32 bytes = 2 descriptor units
+                    mma_bf16(tmem, d0 + 2 * k, d0 + 2 * k, idesc, (in_chunk > 0 || u > 0 || k > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&mbar[s]));
+            }
         }
-        last_bar = bar;
-        last_parity = (uint32_t)(it / kTcStages) & 1u;
-        if (++in_chunk == drain_tiles || last_tile) {
+        const int it_last = it0 + nt - 1;
+        last_bar = smem_u32(&mbar[it_last % NS]);
+        last_parity = (uint32_t)(it_last / NS) & 1u;
+        in_chunk += nt;
+        if (in_chunk >= drain_tiles || last_group) {
             in_chunk = 0;
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar, last_parity, wait_limit));
+            // the last commit tracks every earlier MMA of the issuing thread
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(last_bar, last_parity, wait_limit));
             tc_fence_after();
             if (ok && warp < 8 && lane_base < R) {  // two groups of four warps drain alternate 16-column blocks
                 const int row = lane_base + (tid & 31);
@@ -351,10 +387,7 @@ __global__ void __launch_bounds__(TH, 2)
                 const float d10 = fold[(NO + a) * ld + b], d11 = fold[(NO + a) * ld + NO + b];
                 acc[q] += (double)d00 + (double)((d01 + d10) + d11);
             }
-        }
-        if (!BULK) {
-#pragma unroll
-            for (int q = 0; q < kTcQuads; ++q) cur[q] = nxt[q];
+            if (L::fold_in_tiles) __syncthreads();  // the fold is read before the next tiles overwrite it
         }
     }
 
@@ -384,14 +417,15 @@ __global__ void __launch_bounds__(TH, 2)
                             LAM ? sigma + y * NO : nullptr);
 }
 
-template <bool LAM, bool BULK, int MAXO, int TH = kTcThreads>
+template <bool LAM, bool BULK, int MAXO, int TH = kTcThreads, int TPB = 1>
 static cudaError_t gram_tc_launch(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
                                   double* sigma, const Scratch& sc, int B, int drain_tiles, cudaStream_t st) {
-    auto kern = k_gram_tc<LAM, BULK, MAXO, TH>;
+    auto kern = k_gram_tc<LAM, BULK, MAXO, TH, TPB>;
+    using L = TcLayout<MAXO, TPB>;
     const int R = 2 * NO, NM = (R + 15) & ~15;
     const int ncols = NM <= 32 ? 32 : NM <= 64 ? 64 : 128;
-    size_t smem = 1024 + (size_t)kTcStages * kTcTileBytes + (BULK ? (size_t)kInStages * NO * kTcSites * 4 : 0) +
-                  (size_t)R * (R + 1) * sizeof(float);
+    size_t smem = 1024 + (size_t)L::tiles + (BULK ? (size_t)kInStages * NO * kTcSites * 4 : 0) +
+                  (L::fold_in_tiles ? 0 : (size_t)R * (R + 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     // the largest shared-memory carveout, so that two blocks fit beside each other
     if (e == cudaSuccess)
@@ -449,13 +483,15 @@ cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, do
                        : gram_tc_launch<false, false, MAXO>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles, st));
     if (NO <= 16) LBKS_TC(16)
     if (NO <= 32) LBKS_TC(32)
-    if (NO <= 40) {  // 16 NO 4-site groups of a tile: two per thread of ten warps
-        return lam ? (bulk ? gram_tc_launch<true, true, 40, 320>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st)
-                           : gram_tc_launch<true, false, 40, 320>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles, st))
-                   : (bulk ? gram_tc_launch<false, true, 40, 320>(NO, g, h, psi, S, nullptr, nullptr, sc, B, drain_tiles,
-                                                                 st)
-                           : gram_tc_launch<false, false, 40, 320>(NO, g, h, psi, S, nullptr, nullptr, sc, B,
-                                                                  drain_tiles, st));
+    if (NO <= 40) {  // 16 NO 4-site groups of a tile: two per thread of ten warps; two tiles per barrier
+        return lam ? (bulk ? gram_tc_launch<true, true, 40, 320, 2>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles,
+                                                                    st)
+                           : gram_tc_launch<true, false, 40, 320, 2>(NO, g, h, psi, S, lam, sigma, sc, B, drain_tiles,
+                                                                     st))
+                   : (bulk ? gram_tc_launch<false, true, 40, 320, 2>(NO, g, h, psi, S, nullptr, nullptr, sc, B,
+                                                                     drain_tiles, st)
+                           : gram_tc_launch<false, false, 40, 320, 2>(NO, g, h, psi, S, nullptr, nullptr, sc, B,
+                                                                      drain_tiles, st));
     }
     if (NO <= 48) LBKS_TC(48)
     LBKS_TC(kMaxOrbWide)

@@ -85,7 +85,8 @@ struct Scratch {
 // Overlap S = h^3 Psi Psi^T of N_O FP32 orbitals per system (N_O <= kMaxOrbWide)
 // on the tensor cores (bf16 hi/lo split, FP64 block and grid sums); with lam
 // also Lambda and sigma as the relaxation step needs them.  drain_tiles: tiles
-// of 64 sites summed in TMEM before the FP64 fold (0: the default, 8).
+// of 64 sites summed in TMEM before the FP64 fold (0: the default, 8; the
+// 33..40-orbital kernel drains after whole pairs of tiles).
 cudaError_t launch_gram_tc(int NO, const Grid& g, double h, const float* psi, double* S, double* lam,
                            double* sigma, const Scratch& sc, int B, cudaStream_t st, int drain_tiles = 0);
 // Blocks of the tensor-core Gram kernel whose bounded mbarrier waits expired
