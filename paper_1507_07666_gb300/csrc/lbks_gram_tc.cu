@@ -6,9 +6,11 @@
 //
 // Precision.  Every FP32 orbital value x is split into bf16 parts
 // hi = rn(x), lo = rn(x - hi).  A shared-memory tile of 64 sites holds hi in
-// rows 0..N_O-1 and lo in rows N_O..2N_O-1 (rows up to 127 are zero), and one
-// M = 128 tcgen05.mma with A = B = that tile leaves the four blocks hi.hi,
-// hi.lo, lo.hi, lo.lo in TMEM.  Their sum is the product of the FP32 values up
+// rows 0..N_O-1 and lo in rows N_O..2N_O-1, and one M = 128 tcgen05.mma with
+// A = B = that tile (N = 2N_O rounded up to 16) leaves the four blocks hi.hi,
+// hi.lo, lo.hi, lo.lo in TMEM; A rows past 2N_O (zeros, or the next stage's
+// bytes in the compact layout of TcLayout) reach only accumulator rows that
+// are never read.  Their sum is the product of the FP32 values up
 // to the rounding of lo (2^-17 relative, unbiased).  TMEM accumulates in FP32
 // over kDrainTiles tiles; then the four blocks are folded and added to
 // per-thread FP64 sums, so no FP32 sum runs over more than 512 sites.  Blocks
@@ -16,10 +18,12 @@
 //
 // Pipeline.  256 threads (320 for 33..40 orbitals, so that every thread
 // splits two 4-site groups of a tile) stream the next tiles into a cp.async
-// ring (or registers) while they split the current one into a 128-byte-
-// swizzled K-major tile (two stages); one thread issues the four K = 16 MMAs
-// of a tile and commits them to the stage's mbarrier; warps 0..7 drain TMEM
-// (warp w reads lanes 32 (w % 4) .. 32 (w % 4) + 31).  Every wait on an
+// ring (or registers) while they split the current ones into 128-byte-
+// swizzled K-major tiles: one tile per block barrier into two stages, or, for
+// 33..40 orbitals, two tiles per barrier into four.  After each barrier one
+// thread issues the tiles' K = 16 MMAs (four per tile) and commits each tile
+// to its stage's mbarrier; warps 0..7 drain TMEM (warp w reads lanes
+// 32 (w % 4) .. 32 (w % 4) + 31).  Every wait on an
 // mbarrier is bounded (lbks_set_wait_limit polls, default 2^22): on expiry the
 // block records a timeout, writes NaN partial sums (so the solve fails with a
 // non-finite energy), waits (2^22 polls at most) for its own MMAs, frees its
