@@ -464,7 +464,8 @@ cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO&
     return cudaGetLastError();
 }
 
-// Vector staging where rows are whole 16-byte pieces and the arrays aligned.
+// Vector staging where rows are whole 16-byte pieces and the arrays (psi in
+// and out, Vc) 16-byte aligned.
 // Shapes other than the default run with vector staging only; where it does
 // not apply (rows not of whole 16-byte pieces, unaligned arrays) the default
 // shape's scalar staging runs, and so does the default shape where another's
@@ -483,7 +484,8 @@ template <typename T, int NO, bool BATCHED>
 cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                   int shape, cudaStream_t st) {
     auto al = [](const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; };
-    if (!(g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V)))
+    // the output too: the two-site shapes store pairs of values
+    if (!(g.nx % vpad<T>() == 0 && al(io.f_in) && al(io.V) && al(io.f_out)))
         return launch_relax_psi_tile_v<T, NO, BATCHED, false, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
     switch (shape) {
         case 1: return launch_relax_psi_tile_k<T, NO, BATCHED, 1>(g, c, io, sc, B, st);

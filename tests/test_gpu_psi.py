@@ -74,6 +74,22 @@ def test_psi_step_tile_shapes_match_population_oracle(prec, n, n_orb, seed, shap
         lbks.lbks_set_psi_tile(prev_shape)
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [1, 4, 5], ids=["32x8x8", "64x8x4w2", "64x8x2w2"])
+def test_psi_step_unaligned_output_runs_the_scalar_staging(prec, shape):
+    """An output that is not 16-byte aligned (one value into its buffer)
+    sends every forced shape to the default shape's scalar staging, whose
+    one-value stores need no alignment: the results still match."""
+    torch, lbks = require_gpu()
+    prev = lbks.lbks_set_relax_variant(1)
+    prev_shape = lbks.lbks_set_psi_tile(shape)
+    try:
+        _psi_step_case(torch, lbks, prec, (36, 11, 13), 3, 24, True, out_offset=1)
+    finally:
+        lbks.lbks_set_relax_variant(prev)
+        lbks.lbks_set_psi_tile(prev_shape)
+
+
 def test_psi_tile_shape_is_tuned():
     """The tuner times every tile shape of the staged stencil and keeps the
     fastest; a bad shape is refused."""
@@ -93,7 +109,7 @@ def test_psi_tile_shape_is_tuned():
         lbks.lbks_set_psi_tile(len(lbks.PSI_TILES))
 
 
-def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w):
+def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w, out_offset=0):
     theta, h = 0.5, 0.3
     dt = lattice.time_step(theta, 1.0, h)
     nx, ny, nz = n
@@ -108,7 +124,8 @@ def _psi_step_case(torch, lbks, prec, n, n_orb, seed, with_w):
     u = -np.tensordot(lam_in, A, axes=(1, 0))[1:]
     P = torch.float64 if prec == 0 else torch.float32
     psi_in = to_dev(torch, A, P)
-    psi_out = torch.empty_like(psi_in)
+    # out_offset > 0: the output starts that many values into its buffer (not 16-byte aligned)
+    psi_out = torch.empty(psi_in.numel() + out_offset, dtype=P, device="cuda")[out_offset:].view(psi_in.shape)
     S = torch.empty((n_orb, n_orb), dtype=torch.float64, device="cuda")
     lam, sig_out = torch.empty_like(S), torch.empty(n_orb, dtype=torch.float64, device="cuda")
     lam_dev = to_dev(torch, lam_in, torch.float64) if with_w else None
