@@ -284,16 +284,20 @@ int lbks_get_relax_variant(const lbks_system* sys, int* variant, double* ms);
  * (the box of every orbital's psi and of Vc that a block sums from shared
  * memory).  Shapes (x by y by z sites): 0 32 x 8 x 4 (the default),
  * 1 32 x 8 x 8, 2 64 x 4 x 4, 3 32 x 8 x 2, one site per thread; 4 64 x 8 x 4
- * and 5 64 x 8 x 2, two x-neighbouring sites per thread.  Shapes 1-5 need rows
- * of whole 16-byte pieces and a box that fits a block's shared memory; shapes
- * 4 and 5 take FP32, or FP64 up to three orbitals; elsewhere shape 0 runs.
+ * and 5 64 x 8 x 2, two x-neighbouring sites per thread; 6 32 x 8 x 8 and
+ * 7 32 x 8 x 4, one site per thread summing by velocity class from each
+ * plane's in-plane sums (plane sums).  Shapes 1-7 need rows of whole 16-byte
+ * pieces, 16-byte aligned psi in and out and Vc, and a box that fits a
+ * block's shared memory; shapes 4 and 5 take FP32, or FP64 up to three
+ * orbitals; shapes 6 and 7 FP32 up to six orbitals, or FP64 up to three;
+ * elsewhere shape 0 runs.
  * The tuner times every shape that runs as itself on the first handle of a
  * grid shape and keeps the fastest with the staged kernel (then compares the
- * staged kernel with the others).  lbks_set_psi_tile(-1) restores that; 0..5
+ * staged kernel with the others).  lbks_set_psi_tile(-1) restores that; 0..7
  * forces the shape for later handles and lbks_relax_step_psi calls.  Returns
  * the previous setting, or -2 for a bad shape (lbks_last_error says why).
  * lbks_get_psi_tile: the handle's shape and the tuner's ms per step of each
- * shape in ms[0..5] (may be NULL; negative: not timed). */
+ * shape in ms[0..7] (may be NULL; negative: not timed). */
 int lbks_set_psi_tile(int shape);
 int lbks_get_psi_tile(const lbks_system* sys, int* shape, double* ms);
 

@@ -302,7 +302,7 @@ struct lbks_system {
     cudaStream_t cap = nullptr;  // capture stream
     int variant = kRelaxSites;   // stream-collide variant (tuned per shape)
     double tune_ms[kRelaxVariants] = {-1.0, -1.0, -1.0, -1.0};
-    double tune_shape_ms[kPsiShapes] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0};  // orbital storage: the staged kernel per tile shape
+    double tune_shape_ms[kPsiShapes] = {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0, -1.0};  // orbital storage: the staged kernel per tile shape
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     uint64_t graph_nodes[2] = {0, 0};
     std::vector<std::vector<double>> xyz, Z;  // per system

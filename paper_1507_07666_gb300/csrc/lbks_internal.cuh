@@ -126,24 +126,28 @@ constexpr int kPsiKernelZ = kRelaxBulk;  // up to kMaxOrb orbitals: marching alo
 // The staged kernel (up to kMaxOrb orbitals) takes its tile shape from the
 // kernel id's bits from kPsiShapeShift on (0: the default 32 x 8 x 4).
 constexpr int kPsiShapeShift = 8;
-constexpr int kPsiShapes = 6;
+constexpr int kPsiShapes = 8;
 // The shapes: TX x (kThreads XW / TX) x TZ sites, XW x-neighbouring sites per
 // thread.  XW = 2 sums two sites from 8- or 16-byte shared-memory loads (half
-// the load instructions of the 19-point sums).
-constexpr int kPsiTileTX[kPsiShapes] = {32, 32, 64, 32, 64, 64};
-constexpr int kPsiTileTZ[kPsiShapes] = {4, 8, 4, 2, 4, 2};
-constexpr int kPsiTileXW[kPsiShapes] = {1, 1, 1, 1, 2, 2};
+// the load instructions of the 19-point sums).  PL: plane sums -- the pulled
+// sums by velocity class (rest, faces, edges) from each plane's in-plane face
+// and diagonal sums, carried along the thread's z-column.
+constexpr int kPsiTileTX[kPsiShapes] = {32, 32, 64, 32, 64, 64, 32, 32};
+constexpr int kPsiTileTZ[kPsiShapes] = {4, 8, 4, 2, 4, 2, 8, 4};
+constexpr int kPsiTileXW[kPsiShapes] = {1, 1, 1, 1, 2, 2, 1, 1};
+constexpr bool kPsiTilePL[kPsiShapes] = {false, false, false, false, false, false, true, true};
 // Whether shape k runs as itself for no orbitals of elem bytes (else the
 // default shape runs): its box of the no orbitals and Vc, rows padded by 16
 // bytes on each side, fits a block's 227 KB of shared memory, and at two
-// sites per thread the accumulators fit the registers (FP32, or FP64 up to
-// three orbitals).
+// sites per thread or with plane sums the accumulators fit the registers
+// (FP32 -- up to six orbitals with plane sums -- or FP64 up to three).
 constexpr bool psi_tile_runs(int elem, int no, int k) {
     return k >= 0 && k < kPsiShapes &&
            (size_t)(no + 1) * (size_t)(kPsiTileTX[k] + 2 * (16 / elem)) * (size_t)(kThreads * kPsiTileXW[k] / kPsiTileTX[k] + 2) *
                    (size_t)(kPsiTileTZ[k] + 2) * (size_t)elem <=
                227 * 1024 &&
-           (kPsiTileXW[k] == 1 || elem <= 4 || no <= 3);
+           (kPsiTileXW[k] == 1 || elem <= 4 || no <= 3) &&
+           (!kPsiTilePL[k] || (elem <= 4 && no <= 6) || no <= 3);
 }
 // The TMA kernel's tensor maps need rows of whole 16-byte units (nx a
 // multiple of 16 / elem, elem the bytes of an orbital value) and 16-byte

@@ -234,15 +234,16 @@ __device__ __forceinline__ void zero16(T* dst) { *reinterpret_cast<float4*>(dst)
 
 // Two sites per thread take twice the accumulators and their larger boxes
 // leave at most two CTAs per SM anyway: at least two resident CTAs there.
-template <typename T, int NO, int XW>
+template <typename T, int NO, int XW, bool PL = false>
 constexpr int psi_tile_min_blocks() {
-    return XW == 2 && psi_min_blocks<T, NO>() > 2 ? 2 : psi_min_blocks<T, NO>();
+    return (XW == 2 || PL) && psi_min_blocks<T, NO>() > 2 ? 2 : psi_min_blocks<T, NO>();
 }
 
-template <typename T, int NO, bool BATCHED, bool VEC, int TX = kTX, int TZ = kTZ, int XW = 1>
-__global__ void __launch_bounds__(kThreads, (psi_tile_min_blocks<T, NO, XW>())) k_relax_psi_tile(Grid g, Coef c, RelaxIO io,
-                                                                                         Scratch sc) {
+template <typename T, int NO, bool BATCHED, bool VEC, int TX = kTX, int TZ = kTZ, int XW = 1, bool PL = false>
+__global__ void __launch_bounds__(kThreads, (psi_tile_min_blocks<T, NO, XW, PL>()))
+    k_relax_psi_tile(Grid g, Coef c, RelaxIO io, Scratch sc) {
     static_assert(XW == 1 || VEC, "two sites per thread read aligned pairs: vector staging only");
+    static_assert(!PL || XW == 1, "plane sums: one site per thread");
     constexpr int NP = NO * (NO + 1) / 2;
     constexpr int NL = NO > 1 ? NO * (NO - 1) / 2 : 1;
     using TS_ = PsiTile<TX, TZ, XW>;
@@ -397,6 +398,70 @@ __global__ void __launch_bounds__(kThreads, (psi_tile_min_blocks<T, NO, XW>())) 
             }
             continue;
         }
+        if constexpr (PL) {
+            // plane sums: the pulled sum of a field over a velocity class is
+            // rest u(r), faces Pf(z) + u(z - 1) + u(z + 1) and edges
+            // Pe(z) + Pf(z - 1) + Pf(z + 1), with Pf / Pe the sums over the
+            // four in-plane face / diagonal neighbours of the column in plane
+            // z.  Fields: psi_j and g_j = Vc psi_j; the value and Pf of planes
+            // t - 2, t - 1, t ride in registers (slot t % 3) down the column.
+            const int gx = xs + tx, gy = y0 + 1 + ty;
+            const int c0 = (ty + 1) * PX + (tx + XO);  // the column in box plane 0
+            const T* vb = box + NO * BOX;
+            T u0[3][NO], uf[3][NO], g0[3][NO], gf[3][NO];
+#pragma unroll
+            for (int t = 0; t < TZ + 2; ++t) {
+                const int k = t % 3, cp = t * BY * PX + c0;
+                {
+                    const T v0 = vb[cp], vw = vb[cp - 1], ve = vb[cp + 1], vs = vb[cp - PX], vn = vb[cp + PX];
+#pragma unroll
+                    for (int j = 0; j < NO; ++j) {
+                        const T* f = box + j * BOX;
+                        const T a0 = f[cp], aw = f[cp - 1], ae = f[cp + 1], as = f[cp - PX], an = f[cp + PX];
+                        u0[k][j] = a0;
+                        uf[k][j] = (aw + ae) + (as + an);
+                        g0[k][j] = v0 * a0;
+                        gf[k][j] = (vw * aw + ve * ae) + (vs * as + vn * an);
+                    }
+                }
+                if (t < 2) continue;
+                // output: box plane t - 1, grid plane z0 + t - 1
+                const int km = (t - 2) % 3, kc = (t - 1) % 3, kp = k, cc = (t - 1) * BY * PX + c0;
+                const int gz = z0 + t - 1;
+                const bool live = gx < g.nx && gy < g.ny && gz < g.nz;
+                const T dsw = vb[cc - 1 - PX], dse = vb[cc + 1 - PX], dnw = vb[cc - 1 + PX], dne = vb[cc + 1 + PX];
+                T ps[NO], kx[NO];
+#pragma unroll
+                for (int j = 0; j < NO; ++j) {
+                    const T* f = box + j * BOX;
+                    const T bsw = f[cc - 1 - PX], bse = f[cc + 1 - PX], bnw = f[cc - 1 + PX], bne = f[cc + 1 + PX];
+                    const T ue = (bsw + bse) + (bnw + bne);
+                    const T ge = (dsw * bsw + dse * bse) + (dnw * bnw + dne * bne);
+                    const T uF = uf[kc][j] + (u0[km][j] + u0[kp][j]);
+                    const T uE = ue + (uf[km][j] + uf[kp][j]);
+                    const T gF = gf[kc][j] + (g0[km][j] + g0[kp][j]);
+                    const T gE = ge + (gf[km][j] + gf[kp][j]);
+                    kx[j] = xi[0] * u0[kc][j] + xi[1] * uF + xi[2] * uE;
+                    ps[j] = kx[j] - dt * (chi[0] * g0[kc][j] + chi[1] * gF + chi[2] * gE);
+                }
+#pragma unroll
+                for (int j = 0; j < NO; ++j) {
+#pragma unroll
+                    for (int i = 0; i < j; ++i) ps[j] += wl[tri(j - 1, i)] * kx[i];
+                    ps[j] = live ? ps[j] * sig[j] : T(0);
+                }
+                if (live) {
+                    const size_t s = ((size_t)gz * g.ny + gy) * g.nx + gx;
+#pragma unroll
+                    for (int j = 0; j < NO; ++j) pout[(size_t)j * N + s] = ps[j];
+                }
+#pragma unroll
+                for (int j = 0; j < NO; ++j)
+#pragma unroll
+                    for (int i = 0; i <= j; ++i) acc[tri(j, i)] += ps[j] * ps[i];
+            }
+            continue;
+        }
         const int gx = xs + tx, gy = y0 + 1 + ty;
 #pragma unroll 1
         for (int dz = 0; dz < TZ; ++dz) {
@@ -444,10 +509,10 @@ __global__ void __launch_bounds__(kThreads, (psi_tile_min_blocks<T, NO, XW>())) 
         store_overlap(tot, NO, c.h, io.S_out + y * NO * NO, io.lambda_out + y * NO * NO, io.sigma_out + y * NO);
 }
 
-template <typename T, int NO, bool BATCHED, bool VEC, int TX, int TZ, int XW = 1>
+template <typename T, int NO, bool BATCHED, bool VEC, int TX, int TZ, int XW = 1, bool PL = false>
 cudaError_t launch_relax_psi_tile_v(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                     cudaStream_t st) {
-    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC, TX, TZ, XW>;
+    auto kern = k_relax_psi_tile<T, NO, BATCHED, VEC, TX, TZ, XW, PL>;
     using TS_ = PsiTile<TX, TZ, XW>;
     const size_t smem = (size_t)(NO + 1) * TS_::template size<T, VEC>() * sizeof(T);
     // opted in whatever the size: static and dynamic shared memory together may exceed 48 KB
@@ -475,8 +540,8 @@ template <typename T, int NO, bool BATCHED, int K>
 cudaError_t launch_relax_psi_tile_k(const Grid& g, const Coef& c, const RelaxIO& io, const Scratch& sc, int B,
                                     cudaStream_t st) {
     if constexpr (K > 0 && psi_tile_runs((int)sizeof(T), NO, K))
-        return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[K], kPsiTileTZ[K], kPsiTileXW[K]>(g, c, io, sc,
-                                                                                                         B, st);
+        return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[K], kPsiTileTZ[K], kPsiTileXW[K],
+                                       kPsiTilePL[K]>(g, c, io, sc, B, st);
     else
         return launch_relax_psi_tile_v<T, NO, BATCHED, true, kPsiTileTX[0], kPsiTileTZ[0]>(g, c, io, sc, B, st);
 }
@@ -493,6 +558,8 @@ cudaError_t launch_relax_psi_tile(const Grid& g, const Coef& c, const RelaxIO& i
         case 3: return launch_relax_psi_tile_k<T, NO, BATCHED, 3>(g, c, io, sc, B, st);
         case 4: return launch_relax_psi_tile_k<T, NO, BATCHED, 4>(g, c, io, sc, B, st);
         case 5: return launch_relax_psi_tile_k<T, NO, BATCHED, 5>(g, c, io, sc, B, st);
+        case 6: return launch_relax_psi_tile_k<T, NO, BATCHED, 6>(g, c, io, sc, B, st);
+        case 7: return launch_relax_psi_tile_k<T, NO, BATCHED, 7>(g, c, io, sc, B, st);
         default: return launch_relax_psi_tile_k<T, NO, BATCHED, 0>(g, c, io, sc, B, st);
     }
 }

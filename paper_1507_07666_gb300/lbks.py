@@ -472,13 +472,15 @@ def lbks_get_relax_variant(handle) -> dict:
     return out
 
 
-# staged orbital-storage stencil tile shapes (x, y, z sites) and the sites per thread of each
-PSI_TILES = ((32, 8, 4), (32, 8, 8), (64, 4, 4), (32, 8, 2), (64, 8, 4), (64, 8, 2))
-PSI_TILE_SITES_PER_THREAD = (1, 1, 1, 1, 2, 2)
+# staged orbital-storage stencil tile shapes (x, y, z sites), the sites per thread of each and
+# whether it sums by velocity class from per-plane sums
+PSI_TILES = ((32, 8, 4), (32, 8, 8), (64, 4, 4), (32, 8, 2), (64, 8, 4), (64, 8, 2), (32, 8, 8), (32, 8, 4))
+PSI_TILE_SITES_PER_THREAD = (1, 1, 1, 1, 2, 2, 1, 1)
+PSI_TILE_PLANE_SUMS = (False, False, False, False, False, False, True, True)
 
 
 def lbks_set_psi_tile(shape):
-    """-1: tuned per grid shape; 0..5: forced (PSI_TILES).  Returns the previous setting."""
+    """-1: tuned per grid shape; 0..7: forced (PSI_TILES).  Returns the previous setting."""
     code = _lib.lbks_set_psi_tile(shape)
     if code < -1:
         raise LbksError(EINVAL, last_error())

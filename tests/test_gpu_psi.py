@@ -57,13 +57,14 @@ def test_psi_step_matches_population_oracle(prec, n, n_orb, seed, with_w, mode):
 @pytest.mark.parametrize("n,n_orb,seed", [((36, 11, 13), 5, 8), ((40, 8, 3), 8, 12), ((64, 17, 19), 3, 20),
                                           ((68, 9, 10), 1, 21), ((8, 2, 2), 1, 13), ((33, 20, 17), 5, 1),
                                           ((132, 10, 5), 6, 22), ((4, 9, 9), 2, 23)])
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5],
-                         ids=["32x8x4", "32x8x8", "64x4x4", "32x8x2", "64x8x4w2", "64x8x2w2"])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6, 7],
+                         ids=["32x8x4", "32x8x8", "64x4x4", "32x8x2", "64x8x4w2", "64x8x2w2", "32x8x8pl", "32x8x4pl"])
 def test_psi_step_tile_shapes_match_population_oracle(prec, n, n_orb, seed, shape):
     """The staged stencil at every tile shape the tuner tries (ragged tiles in
     x, y and z; an odd nx runs the default shape's scalar staging); shapes 4
     and 5 sum two x-neighbouring sites per thread (FP32, FP64 up to three
-    orbitals)."""
+    orbitals), shapes 6 and 7 by velocity class from plane sums (FP32 up to
+    six orbitals, FP64 up to three)."""
     torch, lbks = require_gpu()
     prev = lbks.lbks_set_relax_variant(1)
     prev_shape = lbks.lbks_set_psi_tile(shape)
@@ -75,7 +76,7 @@ def test_psi_step_tile_shapes_match_population_oracle(prec, n, n_orb, seed, shap
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("shape", [1, 4, 5], ids=["32x8x8", "64x8x4w2", "64x8x2w2"])
+@pytest.mark.parametrize("shape", [1, 4, 5, 6], ids=["32x8x8", "64x8x4w2", "64x8x2w2", "32x8x8pl"])
 def test_psi_step_unaligned_output_runs_the_scalar_staging(prec, shape):
     """An output that is not 16-byte aligned (one value into its buffer)
     sends every forced shape to the default shape's scalar staging, whose
