@@ -399,10 +399,17 @@ def psi_kernel_index(w, pe, mode):
     return 0 if (k == 3 and w.n_orb > 8) or (k == 2 and not tma_ok) else k
 
 
-def time_relax_psi(torch, lbks, w, prec, stream, launches=20, mode=None):
+def time_relax_psi(torch, lbks, w, prec, stream, launches=20, mode=None, shape=None):
     """Average duration of the orbital-storage step (omega = 1) in the
     solver's launch configuration, CUDA events on the launching stream;
-    mode: the lbks_set_relax_variant mode to time under (None: as set)."""
+    mode: the lbks_set_relax_variant mode to time under, shape: the staged
+    stencil's tile shape (lbks_set_psi_tile; None: as set)."""
+    if shape is not None:
+        prev_shape = lbks.lbks_set_psi_tile(shape)
+        try:
+            return time_relax_psi(torch, lbks, w, prec, stream, launches, mode)
+        finally:
+            lbks.lbks_set_psi_tile(prev_shape)
     if mode is not None:
         prev = lbks.lbks_set_relax_variant(mode)
         try:
@@ -979,9 +986,16 @@ def main_lbks(args):
 
     tuned = lbks.lbks_get_relax_variant(sysm.handle)
     tuned_index = tuned["index"]
+    psi_shape = None
     if psi_mode:  # orbital storage names its kernels differently
         tuned = {"variant": ("tiled", "direct", "tma", "zmarch")[tuned["index"]], "ms_tiled": tuned["ms_sites"],
                  "ms_direct": tuned["ms_pairs"], "ms_tma": tuned["ms_prefetch"], "ms_zmarch": tuned["ms_bulk"]}
+        if tuned_index == 0 and w.n_orb <= 8:  # the staged stencil: its tuned tile shape
+            psi_tile = lbks.lbks_get_psi_tile(sysm.handle)
+            psi_shape = psi_tile["shape"]
+            tuned["tile"] = {"shape": psi_shape, "sites": list(lbks.PSI_TILES[psi_shape]),
+                             "sites_per_thread": lbks.PSI_TILE_SITES_PER_THREAD[psi_shape],
+                             "plane_sums": lbks.PSI_TILE_PLANE_SUMS[psi_shape]}
     sysm.close()  # the kernel timing below allocates its own population pair
 
     # dominant kernel alone, same launch configuration
@@ -992,7 +1006,7 @@ def main_lbks(args):
     if psi_mode:
         # orbital storage: the step the solver runs (its tuned kernel), timed
         # through lbks_relax_step_psi with that kernel forced
-        ms, units = time_relax_psi(torch, lbks, w, prec, stream, mode=1 + tuned_index)
+        ms, units = time_relax_psi(torch, lbks, w, prec, stream, mode=1 + tuned_index, shape=psi_shape)
         N = units // w.n_orb
         kname, per_site = psi_step_kernels(w, psi_elem, tuned_index)
         bytes_per_launch = per_site * N
