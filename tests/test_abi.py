@@ -77,3 +77,29 @@ def test_fast_division_formula():
         m, l = fastdiv(d)
         q = ((((ns * np.uint64(m)) >> np.uint64(32)) + ns) & np.uint64(0xFFFFFFFF)) >> np.uint64(l)
         assert (q == ns // np.uint64(d)).all(), d
+
+
+def _c_array(text, name):
+    m = re.search(r"constexpr \w+ " + name + r"\[kPsiShapes\] = \{([^}]*)\};", text)
+    assert m, name
+    return [v.strip() for v in m.group(1).split(",")]
+
+
+def test_binding_tile_shapes_match_the_library_tables():
+    """The binding's tile-shape tables (index = lbks_set_psi_tile's shape)
+    restate the library's: x and z extents, sites per thread, plane sums, and
+    y = threads x sites per thread / x."""
+    from paper_1507_07666_gb300 import lbks
+    text = open(os.path.join(os.path.dirname(HEADER), os.pardir, "paper_1507_07666_gb300", "csrc",
+                             "lbks_internal.cuh")).read()
+    threads = int(re.search(r"constexpr int kThreads = (\d+);", text).group(1))
+    tx = [int(v) for v in _c_array(text, "kPsiTileTX")]
+    tz = [int(v) for v in _c_array(text, "kPsiTileTZ")]
+    xw = [int(v) for v in _c_array(text, "kPsiTileXW")]
+    pl = [v == "true" for v in _c_array(text, "kPsiTilePL")]
+    assert len(lbks.PSI_TILES) == len(tx)
+    assert [t[0] for t in lbks.PSI_TILES] == tx
+    assert [t[2] for t in lbks.PSI_TILES] == tz
+    assert [t[1] for t in lbks.PSI_TILES] == [threads * w // x for x, w in zip(tx, xw)]
+    assert list(lbks.PSI_TILE_SITES_PER_THREAD) == xw
+    assert list(lbks.PSI_TILE_PLANE_SUMS) == pl
